@@ -1,0 +1,240 @@
+/*
+ * osmodi -- matrix-based omnidirectional pressure integration on one GB300
+ * (Zigunov & Charonko, "A fast, matrix-based method to perform
+ * omnidirectional pressure integration", arXiv 2311.16935).
+ *
+ * C interface.  Every pointer named *_dev is device memory of the calling
+ * process's current CUDA device; *_host pointers are host memory.  The caller
+ * owns all buffers it passes in; the library never frees them.  Streams are
+ * passed as `void*` holding a cudaStream_t (NULL = the legacy default stream).
+ *
+ * Grids are uniform boxes of nx x ny (2D) or nx x ny x nz (3D) cells stored
+ * x fastest: cell (i, j, k) is element (k*ny + j)*nx + i.  Face neighbours are
+ * E = +x, W = -x, N = +y, S = -y, F = +z, B = -z.  A gradient field holds ndim
+ * such planes back to back (component x first).  Cells outside the box count
+ * as missing data (b = 1 in Section 2.2's notation).
+ *
+ * Error behaviour: every call returns an osmodi_status.  Negative values
+ * mean nothing usable was written to the outputs; OSMODI_NOT_CONVERGED means
+ * the best iterate was written and the result struct is filled.  No call
+ * traps, asserts or aborts on bad input; device-side faults of the inputs
+ * (NaN gradients at valid cells) come back as OSMODI_E_NAN_INPUT.
+ */
+#ifndef OSMODI_H
+#define OSMODI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define OSMODI_API __attribute__((visibility("default")))
+#else
+#define OSMODI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct osmodi_plan_s* osmodi_plan; /* opaque, host-owned */
+
+typedef enum {
+    OSMODI_OK = 0,
+    OSMODI_NOT_CONVERGED = 1, /* max_iter reached or stagnated; best iterate written */
+    OSMODI_E_INVALID = -1,    /* bad argument (NULL pointer, bad dims/spacing/dtype/tol) */
+    OSMODI_E_UNSUPPORTED = -2,
+    OSMODI_E_NOMEM = -3,      /* device allocation at plan creation failed */
+    OSMODI_E_CUDA = -4,       /* a CUDA call failed; see osmodi_last_cuda_error() */
+    OSMODI_E_DIVERGED = -5,   /* eps_R grew 1e3x above its minimum */
+    OSMODI_E_TIMEOUT = -6,    /* a bounded device-side wait ran out */
+    OSMODI_E_EMPTY = -7,      /* the mask leaves no valid cell */
+    OSMODI_E_NAN_INPUT = -8,  /* non-finite gradient (or initial pressure) at a valid cell */
+    OSMODI_E_WORKSPACE = -9   /* workspace pointer NULL, misaligned or too small */
+} osmodi_status;
+
+/* element types of caller buffers */
+enum { OSMODI_F32 = 0, OSMODI_F64 = 1 };
+
+/* arithmetic of the iterations (Section 2.1 leaves it open; the paper's GPU
+ * code used FP64 throughout) */
+enum {
+    OSMODI_FP64 = 0,        /* every vector and operation in FP64 */
+    OSMODI_FP32 = 1,        /* FP32 vectors and sweeps; FP64 only for the residual
+                               of the initial guess, norms, dot products and the
+                               constant removal */
+    OSMODI_FP32_REFINE = 2  /* FP32 sweeps inside an FP64 iterative-refinement loop:
+                               r = b - A p in FP64, FP32 correction solve, p += e */
+};
+
+/* iteration scheme.  Both reach the same fixed point: Algorithm 1's answer,
+ * which solves (I - W^{n+1}_off - W^n) P = S (Eq. MatrixEquation at P^{n+1} =
+ * P^n, i.e. a zero momentum residual of Eq. ResidualMomentum). */
+enum {
+    OSMODI_FPCG = 0,  /* conjugate gradients on (I - W^{n+1}_off - W^n) P = S directly
+                         (the boundary term is applied in every iteration) */
+    OSMODI_OUTER = 1  /* Algorithm 1 as written: each outer iteration refreshes the
+                         boundary term W^n P^n + S and solves Eq. MatrixEquation */
+};
+
+/* inner solver of Eq. MatrixEquation in the OUTER scheme */
+enum {
+    OSMODI_INNER_CG = 0,     /* conjugate gradients on M = I - W^{n+1}_off, warm-started
+                                from P^n, as the paper's GPU code (Section 2.1) */
+    OSMODI_INNER_JACOBI = 1  /* fixed number of Jacobi sweeps P <- W^{n+1}_off P + RHS
+                                (diag M = 1), several fused per pass */
+};
+
+typedef struct {
+    int precision;       /* OSMODI_FP64 | OSMODI_FP32 | OSMODI_FP32_REFINE (default) */
+    int scheme;          /* OSMODI_FPCG (default) | OSMODI_OUTER */
+    int inner;           /* OUTER only: OSMODI_INNER_CG (default) | OSMODI_INNER_JACOBI */
+    int inner_max;       /* FPCG: max CG iterations per refinement step (default 1<<20);
+                            OUTER: max inner iterations (or sweeps) per outer iteration */
+    double inner_tol;    /* FP32_REFINE: relative reduction of each correction solve
+                            (default 1e-5); OUTER+CG: relative tolerance of each
+                            inner solve (default 1e-6) */
+    int check_every;     /* iterations between host convergence checks (default 64) */
+    int sweeps_per_pass; /* OUTER+JACOBI: Jacobi sweeps fused per pass, 1..4 (default 2) */
+    int max_refine;      /* FP32_REFINE: max refinement steps (default 32) */
+    int record_history;  /* OUTER: keep eps_R of every outer iteration (osmodi_history) */
+    int threads;         /* threads per block of the sweep kernels (0 = tuned) */
+    int blocks_per_sm;   /* resident blocks per SM used to size persistent grids (0 = tuned) */
+    int profile;         /* 1 = launch the CG iterations one by one (no CUDA graph) with
+                            CUDA events around every sweep kernel on the caller's stream;
+                            durations readable with osmodi_kernel_stats */
+    int reserved[4];
+} osmodi_options;
+
+typedef struct {
+    int status;              /* osmodi_status of the solve */
+    int outer_iters;         /* OUTER: Algorithm 1 iterations; FPCG: refinement steps */
+    int64_t inner_iters;     /* CG iterations or Jacobi sweeps, all steps together */
+    int refine_steps;        /* FP64 residual evaluations r = b - A p */
+    double eps_R;            /* Eq. ResidualMomentum of the returned pressure, in FP64 */
+    double eps_P;            /* OUTER: Eq. ResidualPressure of the last outer iteration */
+    double ms;               /* wall-clock of the call (host timer around the stream) */
+    double point_updates;    /* valid cells x stencil applications (GLUPS numerator) */
+    double seed_rel_dist;    /* ||P0 - P|| / ||P|| over valid cells, both gauge-fixed
+                                (0 for a zero initial pressure) */
+} osmodi_result;
+
+/* Fill *opt with the defaults listed above. */
+OSMODI_API void osmodi_default_options(osmodi_options* opt);
+
+/*
+ * Build a plan for one grid (Section 2.2: the weights depend only on the
+ * grid and its mask, "precomputed for a given grid topology").
+ *   ndim       2 or 3
+ *   dims       {nx, ny, nz} (nz ignored in 2D); each >= 1, nx*ny*nz < 2^40
+ *   spacing    {dx, dy, dz} > 0 (dz ignored in 2D).  Unequal 3D spacing uses the
+ *              quadrature of Eqs. FarFaceEquation and IAc-ICc; equal spacing the
+ *              closed forms of Eqs. ConstantFarFace/ConstantNearFaces.
+ *   mask_dev   nx*ny*nz bytes, nonzero = data available; NULL = every cell valid.
+ *              Plays the role of the paper's NaN encoding of missing vectors
+ *              (Section 2.2, b_j).
+ *   opt        NULL = defaults
+ *   stream     used for the set-up kernels; the call returns after they finish
+ *   out        receives the plan
+ * The plan owns the device arrays it allocates here (per-cell neighbour codes
+ * and component labels, about 5-9 bytes per cell); osmodi_destroy frees them.
+ * Errors: E_INVALID, E_EMPTY (no valid cell), E_NOMEM, E_CUDA.
+ */
+OSMODI_API osmodi_status osmodi_create(int ndim, const int64_t dims[3], const double spacing[3], const uint8_t* mask_dev,
+                            const osmodi_options* opt, void* stream, osmodi_plan* out);
+
+/* Device workspace bytes that osmodi_solve needs for this plan (256-byte
+ * aligned start required). */
+OSMODI_API size_t osmodi_workspace_bytes(osmodi_plan plan);
+
+/*
+ * Solve for the pressure (Algorithm 1's converged answer).
+ *   grad_dev    ndim planes of nx*ny*nz values (f = grad P), grad_dtype
+ *               OSMODI_F32 or OSMODI_F64.  Values at missing cells are never
+ *               read; a non-finite value at a valid cell is E_NAN_INPUT.
+ *   p_dev       nx*ny*nz values of p_dtype.  In: initial pressure P^0 (zeros
+ *               = the paper's start, Algorithm 1; missing cells ignored).
+ *               Out: the pressure with zero mean on every connected component
+ *               of valid cells (pressure is defined up to a constant, Eq. 1)
+ *               and NaN on missing cells.
+ *   tol         threshold on eps_R (Eq. ResidualMomentum, denominator ||S||),
+ *               > 0
+ *   max_iter    FPCG: total CG iterations; OUTER: outer iterations
+ *   workspace   osmodi_workspace_bytes(plan) bytes of device memory
+ *   stream      all work is ordered on it; the call synchronises the stream
+ *               to read convergence flags and fill *res
+ *   res         may be NULL
+ * Returns OK (eps_R <= tol), NOT_CONVERGED, E_NAN_INPUT, E_DIVERGED,
+ * E_WORKSPACE, E_INVALID or E_CUDA.  A plan is not thread-safe: one solve at
+ * a time per plan.
+ */
+OSMODI_API osmodi_status osmodi_solve(osmodi_plan plan, const void* grad_dev, int grad_dtype, void* p_dev, int p_dtype,
+                           double tol, int max_iter, void* workspace_dev, void* stream, osmodi_result* res);
+
+/*
+ * Solve `count` independent problems (many PIV snapshots of uneven sizes and
+ * masks) in one persistent cooperative launch that keeps a convergence flag
+ * per instance; converged instances drop out while the others continue.
+ * All plans must share ndim; precision and scheme come from plans[0]
+ * (FP32_REFINE and FP32 supported, scheme FPCG).  grads[i], ps[i] are laid
+ * out as for osmodi_solve.  results may be NULL, else count entries.
+ * Returns OK when every instance converged, NOT_CONVERGED if any did not, or
+ * the first error.
+ */
+OSMODI_API osmodi_status osmodi_solve_batched(int count, const osmodi_plan* plans, const void* const* grads, int grad_dtype,
+                                   void* const* ps, int p_dtype, double tol, int max_iter, void* workspace_dev,
+                                   void* stream, osmodi_result* results);
+
+/* Workspace bytes for osmodi_solve_batched over these plans. */
+OSMODI_API size_t osmodi_batched_workspace_bytes(int count, const osmodi_plan* plans);
+
+/* eps_R of every outer iteration of the plan's last OUTER solve with
+ * record_history set; copies min(cap, n) values, returns n. */
+OSMODI_API int osmodi_history(osmodi_plan plan, double* out_host, int cap);
+
+/*
+ * Step-level entry points (the pieces of the solve, for checking each one
+ * against a CPU evaluation of the paper's formulas).  All synchronous on
+ * `stream`; dense nx*ny*nz FP64 arrays.
+ *
+ * osmodi_ray_counts: per valid cell the 2 + 4*ndim ray counts A_C^n,
+ *   A_C^{n+1}, then (A_f^n, A_f^{n+1}) for f = E, W, N, S[, F, B]
+ *   (Eqs. Acn, AEnp1, AEn, ANnp1, ANn and the 3D pattern), decoded from the
+ *   plan's per-cell neighbour codes; zeros on missing cells.  counts_dev
+ *   holds nx*ny*nz*(2+4*ndim) doubles, cell-major.
+ * osmodi_source: S of Eq. ExplicitEqn (last sum), 0 on missing cells.
+ * osmodi_apply: which = 0: W^{n+1}_off x; 1: W^n x (diagonal included);
+ *   2: (I - W^{n+1}_off - W^n) x.  Missing cells of y get 0.
+ * osmodi_residual: eps_R of Eq. ResidualMomentum for pressure p (p_dtype).
+ */
+OSMODI_API osmodi_status osmodi_ray_counts(osmodi_plan plan, double* counts_dev, void* stream);
+OSMODI_API osmodi_status osmodi_source(osmodi_plan plan, const void* grad_dev, int grad_dtype, double* S_dev, void* stream);
+OSMODI_API osmodi_status osmodi_apply(osmodi_plan plan, int which, const double* x_dev, double* y_dev, void* stream);
+OSMODI_API osmodi_status osmodi_residual(osmodi_plan plan, const void* grad_dev, int grad_dtype, const void* p_dev, int p_dtype,
+                              double* eps_R_host, void* stream);
+
+/* Device time of the sweep kernels in the plan's last solve with
+ * options.profile set, from CUDA events on the solve's stream:
+ * out[0] / out[1]: total ms / launches of the CG kernel that applies the
+ * stencil (p update, q = A p, x update, p.q); out[2] / out[3]: the CG
+ * residual-update kernel (r -= alpha q, r.r); out[4] / out[5]: the FP64
+ * residual kernel of the refinement loop; out[6] / out[7]: reserved (0). */
+OSMODI_API osmodi_status osmodi_kernel_stats(osmodi_plan plan, double out[8]);
+
+/* Plan facts: out[0] nx, [1] ny, [2] nz, [3] valid cells, [4] connected
+ * components, [5] padded row pitch, [6] padded cells, [7] launch blocks. */
+OSMODI_API osmodi_status osmodi_plan_info(osmodi_plan plan, int64_t out[8]);
+
+/* The constants the plan uses: c[9] = c_jk row-major (x, y, z), F[3] = face
+ * totals, a_tot (Eqs. cxx2D, Atot2D; Section 2.2.2). */
+OSMODI_API osmodi_status osmodi_plan_constants(osmodi_plan plan, double c[9], double F[3], double* a_tot);
+
+OSMODI_API void osmodi_destroy(osmodi_plan plan);
+OSMODI_API const char* osmodi_status_string(int status);
+/* Text of the last CUDA error seen by this thread (empty if none). */
+OSMODI_API const char* osmodi_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OSMODI_H */

@@ -1,0 +1,1063 @@
+// osmodi_solve: the iterative solve of Eq. MatrixEquation to its fixed point.
+//
+// Structure (FP64 iterative refinement around an inner solver):
+//   b = A_tot S (source, Eq. ExplicitEqn), p64 = P^0
+//   loop:  r = b - L p64                          FP64 stencil + FP64 norms
+//          eps_R = ||r|| / ||b||                   (Eq. ResidualMomentum)
+//          stop when eps_R <= tol
+//          r -= mean of r on each component        (null space of L)
+//          solve L e = r (inner precision T):
+//             FPCG : conjugate gradients on L
+//             OUTER: Algorithm 1 on the correction: e^{n+1} = M^{-1}(W^n e^n + r)
+//                    with inner CG on M (the paper's GPU solver) or Jacobi
+//                    sweeps on M
+//          p64 += e
+//   output p64 minus its mean on each component; NaN on missing cells.
+// With precision FP64 the inner solver runs in FP64 to the final tolerance
+// (normally one pass); FP32 runs one FP32 pass; FP32_REFINE repeats FP32
+// passes of relative tolerance inner_tol.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "internal.cuh"
+#include "stencil.cuh"
+
+namespace osm {
+
+enum { kRunning = 0, kConverged = 1, kFinished = 2 };
+enum { OP_L = 0, OP_M = 1 };
+// reduction partials: one range of kMaxBlocks doubles per slot
+enum { kSlotA = 0, kSlotB = 1, kSlotRes = 2 /* 3 slots */, kSlotMisc = 5 /* 3 slots */, kPartialSlots = 8 };
+
+struct CgState {
+    double rho, rho0, pq, alpha, beta, stop2;
+    long long it, max_it;
+    int status, first, breakdown, pad;
+    unsigned ticketA, ticketB, ticketI, pad2;
+};
+
+struct Scalars {
+    double bnorm2, p0sum, rnorm2, rsum, psum, dist2, pnorm2, outer_r2;
+    int nan_flag, pad;
+    unsigned t_src, t_res, t_out, t_init, t_outer, t_misc, pad2, pad3;
+};
+
+// ---------------------------------------------------------------------------
+// source: b = A_tot S = - sum_j b~_j F_j dj (f_j(j) + f_j(C)) / 2, FP64
+// (last sum of Eq. ExplicitEqn times A_tot).  Also P^0 into the padded FP64
+// iterate, and the checks for non-finite input at valid cells.
+// ---------------------------------------------------------------------------
+struct SrcGeo {
+    int64_t px, nx, ny, nz, n_dense, n_box;
+    double F[3], h[3];
+};
+
+template <int NDIM, class TG, class TP>
+__global__ void k_source(const TG* __restrict__ f, const TP* __restrict__ p_in, const uint8_t* __restrict__ code8,
+                         double* __restrict__ b64, double* __restrict__ p64, SrcGeo g, Scalars* sc, double* partials) {
+    double acc[2] = {0.0, 0.0};
+    int bad = 0;
+    const int64_t sd[3] = {1, g.nx, g.nx * g.ny};
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < g.n_box; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = idx / g.px;
+        const int64_t i = idx - row * g.px;
+        const unsigned cw = code8[idx];
+        if (i >= g.nx || !(cw & 0x80u)) {
+            b64[idx] = 0.0;
+            p64[idx] = 0.0;
+            continue;
+        }
+        const int64_t d = row * g.nx + i;
+        double s = 0.0;
+#pragma unroll
+        for (int fc = 0; fc < 2 * NDIM; ++fc) {
+            if (!(cw & (1u << fc))) continue;
+            const int a = fc >> 1;
+            const double sgn = (fc & 1) ? -1.0 : 1.0;
+            const int64_t dn = d + ((fc & 1) ? -sd[a] : sd[a]);
+            const double fc_ = (double)f[a * g.n_dense + d];
+            const double fn_ = (double)f[a * g.n_dense + dn];
+            s -= sgn * g.h[a] * g.F[a] * 0.5 * (fn_ + fc_);
+        }
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a)
+            if (!isfinite((double)f[a * g.n_dense + d])) bad |= 1;
+        const double p0 = (double)p_in[d];
+        if (!isfinite(p0)) bad |= 2;
+        b64[idx] = s;
+        p64[idx] = p0;
+        acc[0] += s * s;
+        acc[1] += p0;
+    }
+    if (bad) atomicOr(&sc->nan_flag, bad);
+    double tot[2];
+    if (grid_sum<2>(acc, partials, &sc->t_src, tot) && threadIdx.x == 0) {
+        sc->bnorm2 = tot[0];
+        sc->p0sum = tot[1];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 residual of the refinement loop: p_out = p_in + e (if e), r = b - L p,
+// reductions ||r||^2, sum r, sum p.
+// ---------------------------------------------------------------------------
+template <class TI, int NDIM, bool HAS_E>
+__global__ void __launch_bounds__(512) k_residual(const double* __restrict__ p_in, const TI* __restrict__ e,
+                                                  double* __restrict__ p_out, const double* __restrict__ b64,
+                                                  TI* __restrict__ r_out, const uint8_t* __restrict__ code8,
+                                                  Geo<double> g, Scalars* sc, double* partials) {
+    ChunkLoop L;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int64_t base = L.base; base < g.n_chunks; base += L.stride) {
+        const int64_t ch = base + L.lane;
+        const bool act = ch < g.n_chunks;
+        const int64_t i0 = ch * 4;
+        const uint32_t cw = act ? *reinterpret_cast<const uint32_t*>(code8 + i0) : 0u;
+        V4<double> c = act ? ld4(p_in + i0) : zero4<double>();
+        if (HAS_E && act) {
+            V4<TI> ev = ld4(e + i0);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) c.v[m] += (double)ev.v[m];
+        }
+        unsigned fm[4], any = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            fm[m] = face_bits8(cw, m);
+            any |= fm[m];
+        }
+        auto f4 = [&](int64_t off) {
+            V4<double> v = ld4(p_in + i0 + off);
+            if (HAS_E) {
+                V4<TI> w = ld4(e + i0 + off);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) v.v[m] += (double)w.v[m];
+            }
+            return v;
+        };
+        auto f1 = [&](int64_t off) {
+            double v = p_in[i0 + off];
+            if (HAS_E) v += (double)e[i0 + off];
+            return v;
+        };
+        Nbrs<double> nb = gather<double, NDIM>(c, any, fm[0] & 2u, fm[3] & 1u, L.lane, g.px, g.plane, f4, f1);
+        if (act) {
+            const V4<double> bv = ld4(b64 + i0);
+            V4<TI> rv;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const double r = bv.v[m] - apply_L<double, NDIM>(fm[m], c, nb, m, g.F);
+                rv.v[m] = (TI)r;
+                acc[0] += r * r;
+                acc[1] += r;
+                acc[2] += c.v[m];
+            }
+            if (HAS_E) st4(p_out + i0, c);
+            st4(r_out + i0, rv);
+        }
+    }
+    double tot[3];
+    if (grid_sum<3>(acc, partials, &sc->t_res, tot) && threadIdx.x == 0) {
+        sc->rnorm2 = tot[0];
+        sc->rsum = tot[1];
+        sc->psum = tot[2];
+    }
+}
+
+// per-component sums (only when the valid cells form several components)
+template <class T>
+__global__ void k_comp_sums(const T* __restrict__ v, const int32_t* __restrict__ label, int64_t n_box, double* sums) {
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n_box; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t l = label[idx];
+        if (l >= 0) {
+            const double x = (double)v[idx];
+            if (x != 0.0) atomicAdd(&sums[l], x);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CG start: r -= its mean on each component (consistency of the singular
+// system), x = 0, rho_0 = ||r||^2, stopping threshold.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(512) k_cg_init(T* __restrict__ r, T* __restrict__ x, const uint8_t* __restrict__ code8,
+                                                 const int32_t* __restrict__ label, const double* __restrict__ comp_sum,
+                                                 const double* __restrict__ comp_cnt, int multi, int64_t n_chunks,
+                                                 Scalars* sc, CgState* st, double stop_abs2, double rel2,
+                                                 long long max_it, double* partials) {
+    const double mean1 = multi ? 0.0 : sc->rsum / comp_cnt[0];
+    double acc[1] = {0.0};
+    for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < n_chunks; ch += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i0 = ch * 4;
+        const uint32_t cw = *reinterpret_cast<const uint32_t*>(code8 + i0);
+        V4<T> rv = ld4c(r + i0);
+        T part = T(0);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            if (valid8(cw, m)) {
+                double mean = mean1;
+                if (multi) {
+                    const int32_t l = label[i0 + m];
+                    mean = comp_sum[l] / comp_cnt[l];
+                }
+                rv.v[m] = (T)((double)rv.v[m] - mean);
+            } else {
+                rv.v[m] = T(0);
+            }
+            part += rv.v[m] * rv.v[m];
+        }
+        st4(r + i0, rv);
+        st4(x + i0, zero4<T>());
+        acc[0] += (double)part;
+    }
+    double tot[1];
+    if (grid_sum<1>(acc, partials, &st->ticketI, tot) && threadIdx.x == 0) {
+        const double rho0 = tot[0];
+        st->rho = rho0;
+        st->rho0 = rho0;
+        st->stop2 = fmax(rel2 * rho0, stop_abs2);
+        st->alpha = 0.0;
+        st->beta = 0.0;
+        st->pq = 0.0;
+        st->first = 1;
+        st->it = 0;
+        st->max_it = max_it;
+        st->breakdown = 0;
+        st->status = (rho0 > st->stop2 && max_it > 0) ? kRunning : kFinished;
+    }
+}
+
+// inner CG of the OUTER scheme: state from the outer residual (warm start: x
+// already holds e^n)
+__global__ void k_state_outer(Scalars* sc, CgState* st, double rel2, long long max_it) {
+    const double rho0 = sc->outer_r2;
+    st->rho = rho0;
+    st->rho0 = rho0;
+    st->stop2 = rel2 * rho0;
+    st->alpha = 0.0;
+    st->beta = 0.0;
+    st->pq = 0.0;
+    st->first = 1;
+    st->it = 0;
+    st->max_it = max_it;
+    st->breakdown = 0;
+    st->status = (rho0 > st->stop2 && max_it > 0) ? kRunning : kFinished;
+}
+
+// ---------------------------------------------------------------------------
+// CG iteration, two kernels.
+//   A_k: p_k = r_k + beta_{k-1} p_{k-1}   (neighbours' p_k formed on the fly)
+//        q_k = Op p_k ; x_k = x_{k-1} + alpha_{k-1} p_{k-1} ; reduce p_k.q_k
+//        -> alpha_k = rho_k / (p_k.q_k)
+//   B_k: r_{k+1} = r_k - alpha_k q_k ; reduce rho_{k+1} -> beta_k, stop test
+// The x update trails by one iteration, so after convergence one more A
+// launch applies the last alpha p and marks the solve finished.
+// ---------------------------------------------------------------------------
+template <class T, int NDIM, int OP>
+__global__ void __launch_bounds__(512) k_cg_a(const T* __restrict__ r, const T* __restrict__ p_old, T* __restrict__ p_new,
+                                              T* __restrict__ q, T* __restrict__ x, const uint8_t* __restrict__ code8,
+                                              const uint32_t* __restrict__ code32, Geo<T> g, TableT<T> tabv, CgState* st,
+                                              double* partials) {
+    const int status = st->status;
+    if (status == kFinished) return;
+    const bool first = st->first != 0;
+    const bool conv = status == kConverged;
+    const T alpha = (T)st->alpha;
+    const T beta = (T)st->beta;
+    __shared__ T tab[3][kClasses];
+    if (OP == OP_M) {
+        for (int t = threadIdx.x; t < 3 * kClasses; t += blockDim.x) tab[t / kClasses][t % kClasses] = tabv.anp1[t / kClasses][t % kClasses];
+        __syncthreads();
+    }
+    ChunkLoop L;
+    double acc[1] = {0.0};
+    for (int64_t base = L.base; base < g.n_chunks; base += L.stride) {
+        const int64_t ch = base + L.lane;
+        const bool act = ch < g.n_chunks;
+        const int64_t i0 = ch * 4;
+        V4<T> po = zero4<T>();
+        if (act && !first) {
+            po = ld4(p_old + i0);
+            V4<T> xv = ld4c(x + i0);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) xv.v[m] += alpha * po.v[m];
+            st4(x + i0, xv);
+        }
+        if (conv) continue;
+        unsigned fm[4], any = 0;
+        uint4 w32 = make_uint4(0, 0, 0, 0);
+        if (OP == OP_L) {
+            const uint32_t cw = act ? *reinterpret_cast<const uint32_t*>(code8 + i0) : 0u;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) fm[m] = face_bits8(cw, m);
+        } else {
+            if (act) w32 = __ldg(reinterpret_cast<const uint4*>(code32 + i0));
+#pragma unroll
+            for (int m = 0; m < 4; ++m) fm[m] = face_bits32<NDIM>(word_of(w32, m));
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) any |= fm[m];
+        V4<T> c = act ? ld4(r + i0) : zero4<T>();
+        if (!first) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) c.v[m] += beta * po.v[m];
+        }
+        auto f4 = [&](int64_t off) {
+            V4<T> v = ld4(r + i0 + off);
+            if (!first) {
+                V4<T> o = ld4(p_old + i0 + off);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) v.v[m] += beta * o.v[m];
+            }
+            return v;
+        };
+        auto f1 = [&](int64_t off) {
+            T v = r[i0 + off];
+            if (!first) v += beta * p_old[i0 + off];
+            return v;
+        };
+        Nbrs<T> nb = gather<T, NDIM>(c, any, fm[0] & 2u, fm[3] & 1u, L.lane, g.px, g.plane, f4, f1);
+        if (act) {
+            V4<T> qv;
+            T part = T(0);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                T qm;
+                if (OP == OP_L) {
+                    qm = apply_L<T, NDIM>(fm[m], c, nb, m, g.F);
+                } else {
+                    const uint32_t w = word_of(w32, m);
+                    qm = (w >> 31) ? tabv.a_tot * c.v[m] - sum_np1<T, NDIM>(w, nb, m, tab) : T(0);
+                }
+                qv.v[m] = qm;
+                part += c.v[m] * qm;
+            }
+            st4(p_new + i0, c);
+            st4(q + i0, qv);
+            acc[0] += (double)part;
+        }
+    }
+    double tot[1];
+    if (grid_sum<1>(acc, partials, &st->ticketA, tot) && threadIdx.x == 0) {
+        if (conv) {
+            st->status = kFinished;
+        } else {
+            st->pq = tot[0];
+            st->first = 0;
+            // L is positive semidefinite; M~ is not symmetric, so its CG can break down
+            if (tot[0] > 0.0 && isfinite(tot[0])) {
+                st->alpha = st->rho / tot[0];
+            } else {
+                st->alpha = 0.0;
+                st->breakdown = 1;
+                st->status = kConverged;
+            }
+        }
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(512) k_cg_b(T* __restrict__ r, const T* __restrict__ q, int64_t n_chunks, CgState* st,
+                                              double* partials) {
+    if (st->status != kRunning) return;
+    const T alpha = (T)st->alpha;
+    double acc[1] = {0.0};
+    for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < n_chunks; ch += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i0 = ch * 4;
+        V4<T> rv = ld4c(r + i0);
+        const V4<T> qv = ld4(q + i0);
+        T part = T(0);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            rv.v[m] -= alpha * qv.v[m];
+            part += rv.v[m] * rv.v[m];
+        }
+        st4(r + i0, rv);
+        acc[0] += (double)part;
+    }
+    double tot[1];
+    if (grid_sum<1>(acc, partials, &st->ticketB, tot) && threadIdx.x == 0) {
+        const double rho_new = tot[0];
+        st->beta = rho_new / st->rho;
+        st->rho = rho_new;
+        st->it += 1;
+        if (!(rho_new > st->stop2) || st->it >= st->max_it || !isfinite(rho_new)) st->status = kConverged;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// OUTER scheme pieces (Algorithm 1 applied to the correction equation).
+// ---------------------------------------------------------------------------
+// r_cg = rc - L e  (the residual of e^n; also the warm-started inner CG's
+// first residual, since M~ e^{n+1} = W~^n e^n + rc)
+template <class T, int NDIM>
+__global__ void __launch_bounds__(512) k_outer_res(const T* __restrict__ e, const T* __restrict__ rc, T* __restrict__ r_cg,
+                                                   const uint8_t* __restrict__ code8, Geo<T> g, Scalars* sc, double* partials) {
+    ChunkLoop L;
+    double acc[1] = {0.0};
+    for (int64_t base = L.base; base < g.n_chunks; base += L.stride) {
+        const int64_t ch = base + L.lane;
+        const bool act = ch < g.n_chunks;
+        const int64_t i0 = ch * 4;
+        const uint32_t cw = act ? *reinterpret_cast<const uint32_t*>(code8 + i0) : 0u;
+        const V4<T> c = act ? ld4(e + i0) : zero4<T>();
+        unsigned fm[4], any = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            fm[m] = face_bits8(cw, m);
+            any |= fm[m];
+        }
+        auto f4 = [&](int64_t off) { return ld4(e + i0 + off); };
+        auto f1 = [&](int64_t off) { return e[i0 + off]; };
+        Nbrs<T> nb = gather<T, NDIM>(c, any, fm[0] & 2u, fm[3] & 1u, L.lane, g.px, g.plane, f4, f1);
+        if (act) {
+            const V4<T> rv = ld4(rc + i0);
+            V4<T> o;
+            T part = T(0);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                o.v[m] = rv.v[m] - apply_L<T, NDIM>(fm[m], c, nb, m, g.F);
+                part += o.v[m] * o.v[m];
+            }
+            st4(r_cg + i0, o);
+            acc[0] += (double)part;
+        }
+    }
+    double tot[1];
+    if (grid_sum<1>(acc, partials, &sc->t_outer, tot) && threadIdx.x == 0) sc->outer_r2 = tot[0];
+}
+
+// Boundary refresh (Eq. MatrixEquation's right-hand side): rhs = W~^n e + rc,
+// and the residual of e for the stopping test, in one pass.
+template <class T, int NDIM>
+__global__ void __launch_bounds__(512) k_outer_rhs(const T* __restrict__ e, const T* __restrict__ rc, T* __restrict__ rhs,
+                                                   const uint32_t* __restrict__ code32, Geo<T> g, TableT<T> tabv,
+                                                   Scalars* sc, double* partials) {
+    __shared__ T tab[3][kClasses];
+    for (int t = threadIdx.x; t < 3 * kClasses; t += blockDim.x) tab[t / kClasses][t % kClasses] = tabv.anp1[t / kClasses][t % kClasses];
+    __syncthreads();
+    ChunkLoop L;
+    double acc[1] = {0.0};
+    for (int64_t base = L.base; base < g.n_chunks; base += L.stride) {
+        const int64_t ch = base + L.lane;
+        const bool act = ch < g.n_chunks;
+        const int64_t i0 = ch * 4;
+        const uint4 w32 = act ? __ldg(reinterpret_cast<const uint4*>(code32 + i0)) : make_uint4(0, 0, 0, 0);
+        const V4<T> c = act ? ld4(e + i0) : zero4<T>();
+        unsigned fm[4], any = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            fm[m] = face_bits32<NDIM>(word_of(w32, m));
+            any |= fm[m];
+        }
+        auto f4 = [&](int64_t off) { return ld4(e + i0 + off); };
+        auto f1 = [&](int64_t off) { return e[i0 + off]; };
+        Nbrs<T> nb = gather<T, NDIM>(c, any, fm[0] & 2u, fm[3] & 1u, L.lane, g.px, g.plane, f4, f1);
+        if (act) {
+            const V4<T> rv = ld4(rc + i0);
+            V4<T> o;
+            T part = T(0);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const uint32_t w = word_of(w32, m);
+                if (!(w >> 31)) {
+                    o.v[m] = T(0);
+                    continue;
+                }
+                // A_C^n = sum over faces with a missing neighbour of F_a (Eq. Acn)
+                T acn = T(0);
+#pragma unroll
+                for (int f = 0; f < 2 * NDIM; ++f)
+                    if (!(fm[m] & (1u << f))) acn += g.F[f >> 1];
+                const T lc = apply_L<T, NDIM>(fm[m], c, nb, m, g.F);
+                const T snp1 = sum_np1<T, NDIM>(w, nb, m, tab);
+                // sum_j A_j^n e_j = sum_j b~_j F_j e_j - sum_j A_j^{n+1} e_j
+                T sfull = T(0);
+                if (fm[m] & 1u) sfull += g.F[0] * nb.e.v[m];
+                if (fm[m] & 2u) sfull += g.F[0] * nb.w.v[m];
+                if (fm[m] & 4u) sfull += g.F[1] * nb.n.v[m];
+                if (fm[m] & 8u) sfull += g.F[1] * nb.s.v[m];
+                if (NDIM == 3) {
+                    if (fm[m] & 16u) sfull += g.F[2] * nb.f.v[m];
+                    if (fm[m] & 32u) sfull += g.F[2] * nb.b.v[m];
+                }
+                o.v[m] = acn * c.v[m] + (sfull - snp1) + rv.v[m];
+                const T res = rv.v[m] - lc;
+                part += res * res;
+            }
+            st4(rhs + i0, o);
+            acc[0] += (double)part;
+        }
+    }
+    double tot[1];
+    if (grid_sum<1>(acc, partials, &sc->t_outer, tot) && threadIdx.x == 0) sc->outer_r2 = tot[0];
+}
+
+// One Jacobi sweep on M~ e = rhs:  e_out = (sum_j A_j^{n+1} e_in_j + rhs) / A_tot
+// (diag M = 1).
+template <class T, int NDIM>
+__global__ void __launch_bounds__(512) k_jacobi(const T* __restrict__ e_in, T* __restrict__ e_out, const T* __restrict__ rhs,
+                                                const uint32_t* __restrict__ code32, Geo<T> g, TableT<T> tabv) {
+    __shared__ T tab[3][kClasses];
+    for (int t = threadIdx.x; t < 3 * kClasses; t += blockDim.x) tab[t / kClasses][t % kClasses] = tabv.anp1[t / kClasses][t % kClasses];
+    __syncthreads();
+    const T inv = T(1) / tabv.a_tot;
+    ChunkLoop L;
+    for (int64_t base = L.base; base < g.n_chunks; base += L.stride) {
+        const int64_t ch = base + L.lane;
+        const bool act = ch < g.n_chunks;
+        const int64_t i0 = ch * 4;
+        const uint4 w32 = act ? __ldg(reinterpret_cast<const uint4*>(code32 + i0)) : make_uint4(0, 0, 0, 0);
+        const V4<T> c = act ? ld4(e_in + i0) : zero4<T>();
+        unsigned fm[4], any = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            fm[m] = face_bits32<NDIM>(word_of(w32, m));
+            any |= fm[m];
+        }
+        auto f4 = [&](int64_t off) { return ld4(e_in + i0 + off); };
+        auto f1 = [&](int64_t off) { return e_in[i0 + off]; };
+        Nbrs<T> nb = gather<T, NDIM>(c, any, fm[0] & 2u, fm[3] & 1u, L.lane, g.px, g.plane, f4, f1);
+        if (act) {
+            const V4<T> rv = ld4(rhs + i0);
+            V4<T> o;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const uint32_t w = word_of(w32, m);
+                o.v[m] = (w >> 31) ? (sum_np1<T, NDIM>(w, nb, m, tab) + rv.v[m]) * inv : T(0);
+            }
+            st4(e_out + i0, o);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// output: subtract each component's mean, NaN on missing cells, dense layout;
+// also ||P0 - P|| and ||P|| (both gauge-fixed) for the seed distance.
+// ---------------------------------------------------------------------------
+template <class TP>
+__global__ void k_output(const double* __restrict__ p64, const uint8_t* __restrict__ code8, const int32_t* __restrict__ label,
+                         const double* __restrict__ comp_p, const double* __restrict__ comp_p0,
+                         const double* __restrict__ comp_cnt, int multi, TP* __restrict__ p_user, int64_t px, int64_t nx,
+                         int64_t n_box, Scalars* sc, double* partials) {
+    const double m1 = multi ? 0.0 : sc->psum / comp_cnt[0];
+    const double m01 = multi ? 0.0 : sc->p0sum / comp_cnt[0];
+    double acc[2] = {0.0, 0.0};
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n_box; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = idx / px;
+        const int64_t i = idx - row * px;
+        if (i >= nx) continue;
+        const int64_t d = row * nx + i;
+        if (!(code8[idx] & 0x80u)) {
+            p_user[d] = (TP)NAN;
+            continue;
+        }
+        double m = m1, m0 = m01;
+        if (multi) {
+            const int32_t l = label[idx];
+            m = comp_p[l] / comp_cnt[l];
+            m0 = comp_p0[l] / comp_cnt[l];
+        }
+        const double v = p64[idx] - m;
+        const double v0 = (double)p_user[d] - m0;
+        acc[0] += (v0 - v) * (v0 - v);
+        acc[1] += v * v;
+        p_user[d] = (TP)v;
+    }
+    double tot[2];
+    if (grid_sum<2>(acc, partials, &sc->t_out, tot) && threadIdx.x == 0) {
+        sc->dist2 = tot[0];
+        sc->pnorm2 = tot[1];
+    }
+}
+
+__global__ void k_fill_zero_f64(double* v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) v[i] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+#define OSM_TRY(x)                          \
+    do {                                    \
+        osmodi_status st_ = (x);            \
+        if (st_ != OSMODI_OK) return st_;   \
+    } while (0)
+
+int tuned_blocks_per_sm(int ndim, int threads) {
+    int bps = 0;
+    cudaError_t e;
+    if (ndim == 2)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_cg_a<float, 2, OP_L>, threads, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_cg_a<float, 3, OP_L>, threads, 0);
+    if (e != cudaSuccess || bps < 1) {
+        cudaGetLastError();
+        bps = 2048 / threads;
+    }
+    return std::max(1, std::min(bps, 2048 / threads));
+}
+
+template <class T>
+struct Buffers {
+    double *p64a, *p64b, *b64;
+    T *r, *x, *q, *pA, *pB;
+    T *rc, *rhs, *e2;  // OUTER extras
+    double* partials;
+    double* comp;       // 3 * n_comp: sums of r, p, p0
+    CgState* st;
+    Scalars* sc;
+    void* host;         // pinned mirror (not workspace)
+};
+
+template <class T>
+static size_t carve(osmodi_plan p, void* ws, Buffers<T>* b) {
+    Workspace w;
+    w.base = (char*)ws;
+    const size_t n = (size_t)p->n_box;
+    Buffers<T> t{};
+    t.p64a = w.take<double>(n);
+    t.p64b = w.take<double>(n);
+    t.b64 = w.take<double>(n);
+    t.r = w.take<T>(n);
+    t.x = w.take<T>(n);
+    t.q = w.take<T>(n);
+    t.pA = w.take<T>(n);
+    t.pB = w.take<T>(n);
+    if (p->opt.scheme == OSMODI_OUTER) {
+        t.rc = w.take<T>(n);
+        if (p->opt.inner == OSMODI_INNER_JACOBI) {
+            t.rhs = w.take<T>(n);
+            t.e2 = w.take<T>(n);
+        }
+    }
+    t.partials = w.take<double>((size_t)kPartialSlots * kMaxBlocks);
+    t.comp = w.take<double>((size_t)3 * (size_t)std::max<int64_t>(1, p->n_comp));
+    t.st = w.take<CgState>(1);
+    t.sc = w.take<Scalars>(1);
+    if (b) *b = t;
+    return w.off;
+}
+
+static size_t workspace_bytes_for(osmodi_plan p) {
+    return p->opt.precision == OSMODI_FP64 ? carve<double>(p, nullptr, nullptr) : carve<float>(p, nullptr, nullptr);
+}
+
+template <class T>
+static Geo<T> geo(osmodi_plan p) {
+    Geo<T> g;
+    g.px = p->px;
+    g.plane = p->px * p->ny;
+    g.n_chunks = p->n_chunks;
+    for (int a = 0; a < 3; ++a) g.F[a] = (T)p->k.F[a];
+    return g;
+}
+
+template <class T>
+static TableT<T> table(osmodi_plan p) {
+    TableT<T> t;
+    for (int a = 0; a < 3; ++a) {
+        for (int c = 0; c < kClasses; ++c) t.anp1[a][c] = (T)p->table.anp1[a][c];
+        t.F[a] = (T)p->k.F[a];
+    }
+    t.a_tot = (T)p->k.a_tot;
+    return t;
+}
+
+struct HostMirror {
+    CgState st;
+    Scalars sc;
+};
+
+template <class T>
+static osmodi_status launch_cg_iters(osmodi_plan p, const Buffers<T>& b, int op, int iters, cudaStream_t s) {
+    const int G = p->launch.blocks, TH = p->launch.threads;
+    const Geo<T> g = geo<T>(p);
+    const TableT<T> tab = table<T>(p);
+    for (int k = 0; k < iters; ++k) {
+        const T* po = (k & 1) ? b.pB : b.pA;
+        T* pn = (k & 1) ? b.pA : b.pB;
+        if (p->ndim == 2) {
+            if (op == OP_L)
+                k_cg_a<T, 2, OP_L><<<G, TH, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials);
+            else
+                k_cg_a<T, 2, OP_M><<<G, TH, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials);
+        } else {
+            if (op == OP_L)
+                k_cg_a<T, 3, OP_L><<<G, TH, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials);
+            else
+                k_cg_a<T, 3, OP_M><<<G, TH, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials);
+        }
+        k_cg_b<T><<<G, TH, 0, s>>>(b.r, b.q, p->n_chunks, b.st, b.partials + kSlotB * kMaxBlocks);
+    }
+    OSM_CUDA(cudaGetLastError());
+    return OSMODI_OK;
+}
+
+// Run CG (already initialised) until the device marks it finished, in
+// captured chunks of check_every iterations.
+static osmodi_status ensure_events(osmodi_plan p, size_t n) {
+    while (p->events.size() < n) {
+        cudaEvent_t ev;
+        OSM_CUDA(cudaEventCreate(&ev));
+        p->events.push_back(ev);
+    }
+    return OSMODI_OK;
+}
+
+// Profile mode: the same iterations launched one by one with an event before
+// and after every kernel, so that each kernel's device time is known.
+template <class T>
+static osmodi_status run_cg_profiled(osmodi_plan p, const Buffers<T>& b, int op, cudaStream_t s, HostMirror* hm,
+                                     long long* iters_out) {
+    const int len = p->opt.check_every;
+    OSM_TRY(ensure_events(p, (size_t)(2 * len + 1)));
+    const int G = p->launch.blocks, TH = p->launch.threads;
+    const Geo<T> g = geo<T>(p);
+    const TableT<T> tab = table<T>(p);
+    long long k_global = 0;
+    for (;;) {
+        OSM_CUDA(cudaEventRecord(p->events[0], s));
+        for (int k = 0; k < len; ++k, ++k_global) {
+            const T* po = (k & 1) ? b.pB : b.pA;
+            T* pn = (k & 1) ? b.pA : b.pB;
+            if (p->ndim == 2) {
+                if (op == OP_L) k_cg_a<T, 2, OP_L><<<G, TH, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials);
+                else k_cg_a<T, 2, OP_M><<<G, TH, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials);
+            } else {
+                if (op == OP_L) k_cg_a<T, 3, OP_L><<<G, TH, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials);
+                else k_cg_a<T, 3, OP_M><<<G, TH, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials);
+            }
+            OSM_CUDA(cudaEventRecord(p->events[2 * k + 1], s));
+            k_cg_b<T><<<G, TH, 0, s>>>(b.r, b.q, p->n_chunks, b.st, b.partials + kSlotB * kMaxBlocks);
+            OSM_CUDA(cudaEventRecord(p->events[2 * k + 2], s));
+        }
+        OSM_CUDA(cudaGetLastError());
+        OSM_CUDA(cudaMemcpyAsync(&hm->st, b.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+        OSM_CUDA(cudaStreamSynchronize(s));
+        // count only launches that did work (the device skips the rest)
+        const long long done_before = k_global - len;
+        for (int k = 0; k < len; ++k) {
+            float ms_a = 0.f, ms_b = 0.f;
+            OSM_CUDA(cudaEventElapsedTime(&ms_a, p->events[2 * k], p->events[2 * k + 1]));
+            OSM_CUDA(cudaEventElapsedTime(&ms_b, p->events[2 * k + 1], p->events[2 * k + 2]));
+            const long long it_here = done_before + k;  // iteration index of this pair
+            if (it_here <= hm->st.it) {
+                p->kstats[0] += ms_a;
+                p->kstats[1] += 1;
+            }
+            if (it_here < hm->st.it) {
+                p->kstats[2] += ms_b;
+                p->kstats[3] += 1;
+            }
+        }
+        if (hm->st.status == kFinished) break;
+    }
+    *iters_out = hm->st.it;
+    return OSMODI_OK;
+}
+
+template <class T>
+static osmodi_status run_cg(osmodi_plan p, const Buffers<T>& b, int op, void* ws, cudaStream_t s, HostMirror* hm,
+                            long long* iters_out) {
+    if (p->opt.profile) return run_cg_profiled<T>(p, b, op, s, hm, iters_out);
+    const int kind = (sizeof(T) == 8 ? 2 : 0) + op;
+    GraphCache& gc = p->graphs[kind];
+    const int len = p->opt.check_every;
+    if (!gc.exec || gc.key_ws != ws || gc.key_len != len) {
+        if (gc.exec) {
+            cudaGraphExecDestroy(gc.exec);
+            gc.exec = nullptr;
+        }
+        cudaStream_t cap;
+        OSM_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t graph;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            set_cuda_error(e, "cudaStreamBeginCapture");
+            return OSMODI_E_CUDA;
+        }
+        osmodi_status st = launch_cg_iters<T>(p, b, op, len, cap);
+        e = cudaStreamEndCapture(cap, &graph);
+        cudaStreamDestroy(cap);
+        if (st != OSMODI_OK) return st;
+        if (e != cudaSuccess) {
+            set_cuda_error(e, "cudaStreamEndCapture");
+            return OSMODI_E_CUDA;
+        }
+        e = cudaGraphInstantiate(&gc.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            gc.exec = nullptr;
+            set_cuda_error(e, "cudaGraphInstantiate");
+            return OSMODI_E_CUDA;
+        }
+        gc.key_ws = ws;
+        gc.key_len = len;
+    }
+    for (;;) {
+        OSM_CUDA(cudaGraphLaunch(gc.exec, s));
+        OSM_CUDA(cudaMemcpyAsync(&hm->st, b.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+        OSM_CUDA(cudaStreamSynchronize(s));
+        if (hm->st.status == kFinished) break;
+    }
+    *iters_out = hm->st.it;
+    return OSMODI_OK;
+}
+
+template <class T>
+static osmodi_status launch_residual(osmodi_plan p, const Buffers<T>& b, const double* p_in, const T* e, double* p_out,
+                                     T* r_out, cudaStream_t s) {
+    const int G = p->launch.blocks, TH = p->launch.threads;
+    if (p->opt.profile) {
+        OSM_TRY(ensure_events(p, 2));
+        OSM_CUDA(cudaEventRecord(p->events[0], s));
+    }
+    const Geo<double> g = geo<double>(p);
+    if (p->ndim == 2) {
+        if (e) k_residual<T, 2, true><<<G, TH, 0, s>>>(p_in, e, p_out, b.b64, r_out, p->code8, g, b.sc, b.partials + kSlotRes * kMaxBlocks);
+        else k_residual<T, 2, false><<<G, TH, 0, s>>>(p_in, e, p_out, b.b64, r_out, p->code8, g, b.sc, b.partials + kSlotRes * kMaxBlocks);
+    } else {
+        if (e) k_residual<T, 3, true><<<G, TH, 0, s>>>(p_in, e, p_out, b.b64, r_out, p->code8, g, b.sc, b.partials + kSlotRes * kMaxBlocks);
+        else k_residual<T, 3, false><<<G, TH, 0, s>>>(p_in, e, p_out, b.b64, r_out, p->code8, g, b.sc, b.partials + kSlotRes * kMaxBlocks);
+    }
+    OSM_CUDA(cudaGetLastError());
+    if (p->opt.profile) {
+        OSM_CUDA(cudaEventRecord(p->events[1], s));
+        OSM_CUDA(cudaEventSynchronize(p->events[1]));
+        float ms = 0.f;
+        OSM_CUDA(cudaEventElapsedTime(&ms, p->events[0], p->events[1]));
+        p->kstats[4] += ms;
+        p->kstats[5] += 1;
+    }
+    return OSMODI_OK;
+}
+
+template <class T>
+static osmodi_status comp_sums(osmodi_plan p, const T* v, double* sums, cudaStream_t s) {
+    OSM_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * (size_t)p->n_comp, s));
+    const int G = std::min<int64_t>((p->n_box + 255) / 256, (int64_t)p->num_sms * 8);
+    k_comp_sums<T><<<G, 256, 0, s>>>(v, p->label, p->n_box, sums);
+    OSM_CUDA(cudaGetLastError());
+    return OSMODI_OK;
+}
+
+static osmodi_status read_mirror(void* dst, const void* src, size_t n, cudaStream_t s) {
+    OSM_CUDA(cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s));
+    OSM_CUDA(cudaStreamSynchronize(s));
+    return OSMODI_OK;
+}
+
+template <class T>
+static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* pu, int pdt, double tol, int max_iter,
+                                void* ws, cudaStream_t s, osmodi_result* res) {
+    auto t0 = std::chrono::steady_clock::now();
+    Buffers<T> b;
+    carve<T>(p, ws, &b);
+    if (!p->pinned) OSM_CUDA(cudaMallocHost(&p->pinned, 4096));
+    static_assert(sizeof(HostMirror) <= 4096, "pinned mirror");
+    HostMirror* hm = reinterpret_cast<HostMirror*>(p->pinned);
+    const int G = p->launch.blocks, TH = p->launch.threads;
+    const bool multi = p->n_comp > 1;
+    double* comp_r = b.comp;
+    double* comp_p = b.comp + std::max<int64_t>(1, p->n_comp);
+    double* comp_p0 = b.comp + 2 * std::max<int64_t>(1, p->n_comp);
+    p->history.clear();
+    for (double& v : p->kstats) v = 0.0;
+
+    OSM_CUDA(cudaMemsetAsync(b.sc, 0, sizeof(Scalars), s));
+    OSM_CUDA(cudaMemsetAsync(b.st, 0, sizeof(CgState), s));
+    OSM_CUDA(cudaMemsetAsync(b.partials, 0, sizeof(double) * kPartialSlots * kMaxBlocks, s));
+
+    // 1. source and initial pressure
+    SrcGeo sg{p->px, p->nx, p->ny, p->nz, p->n_dense, p->n_box, {p->k.F[0], p->k.F[1], p->k.F[2]}, {p->h[0], p->h[1], p->h[2]}};
+    {
+        const int GS = (int)std::min<int64_t>((p->n_box + 255) / 256, (int64_t)p->num_sms * 8);
+#define OSM_SRC(ND, TG, TP) k_source<ND, TG, TP><<<GS, 256, 0, s>>>((const TG*)grad, (const TP*)pu, p->code8, b.b64, b.p64a, sg, b.sc, b.partials + kSlotMisc * kMaxBlocks)
+        if (p->ndim == 2) {
+            if (gdt == OSMODI_F32 && pdt == OSMODI_F32) OSM_SRC(2, float, float);
+            else if (gdt == OSMODI_F32) OSM_SRC(2, float, double);
+            else if (pdt == OSMODI_F32) OSM_SRC(2, double, float);
+            else OSM_SRC(2, double, double);
+        } else {
+            if (gdt == OSMODI_F32 && pdt == OSMODI_F32) OSM_SRC(3, float, float);
+            else if (gdt == OSMODI_F32) OSM_SRC(3, float, double);
+            else if (pdt == OSMODI_F32) OSM_SRC(3, double, float);
+            else OSM_SRC(3, double, double);
+        }
+#undef OSM_SRC
+        OSM_CUDA(cudaGetLastError());
+    }
+    OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
+    if (hm->sc.nan_flag) return OSMODI_E_NAN_INPUT;
+    const double bnorm = std::sqrt(hm->sc.bnorm2);
+    if (multi) OSM_TRY(comp_sums<double>(p, b.p64a, comp_p0, s));
+
+    osmodi_status status = OSMODI_OK;
+    double eps = 0.0, eps_p = 0.0;
+    long long total_inner = 0;
+    int steps = 0, outer_total = 0, residual_evals = 0;
+    double* cur = b.p64a;
+    double* nxt = b.p64b;
+    const int prec = p->opt.precision;
+    const bool outer = p->opt.scheme == OSMODI_OUTER;
+    T* rtarget = outer ? b.rc : b.r;
+
+    if (bnorm == 0.0) {
+        // S = 0: the answer is a constant on every component; P = 0 after the gauge
+        k_fill_zero_f64<<<G, TH, 0, s>>>(cur, p->n_box);
+        OSM_CUDA(cudaGetLastError());
+        OSM_TRY(launch_residual<T>(p, b, cur, nullptr, nullptr, rtarget, s));
+        residual_evals++;
+        OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
+        eps = 0.0;
+    } else {
+        OSM_TRY(launch_residual<T>(p, b, cur, nullptr, nullptr, rtarget, s));
+        residual_evals++;
+        OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
+        eps = std::sqrt(hm->sc.rnorm2) / bnorm;
+        double best = eps;
+        const int max_steps = prec == OSMODI_FP32_REFINE ? p->opt.max_refine : (prec == OSMODI_FP32 ? 1 : 4);
+        int stall = 0;
+        while (eps > tol && steps < max_steps) {
+            if ((!outer && total_inner >= max_iter) || (outer && outer_total >= max_iter)) break;
+            if (multi) OSM_TRY(comp_sums<T>(p, rtarget, comp_r, s));
+            // inner tolerance: FP32_REFINE reduces the correction residual by
+            // inner_tol per step; FP64 / FP32 aim straight at the final tol
+            const double rel = prec == OSMODI_FP32_REFINE ? p->opt.inner_tol : 0.0;
+            const double stop_abs = 0.5 * tol * bnorm;
+            if (!outer) {
+                const long long budget = std::min<long long>((long long)p->opt.inner_max, (long long)max_iter - total_inner);
+                k_cg_init<T><<<G, TH, 0, s>>>(b.r, b.x, p->code8, p->label, comp_r, p->comp_count, multi ? 1 : 0,
+                                              p->n_chunks, b.sc, b.st, stop_abs * stop_abs, rel * rel, budget,
+                                              b.partials + kSlotMisc * kMaxBlocks);
+                OSM_CUDA(cudaGetLastError());
+                long long it = 0;
+                OSM_TRY(run_cg<T>(p, b, OP_L, ws, s, hm, &it));
+                total_inner += it;
+            } else {
+                // project rc (k_cg_init also zeroes e = x)
+                k_cg_init<T><<<G, TH, 0, s>>>(b.rc, b.x, p->code8, p->label, comp_r, p->comp_count, multi ? 1 : 0,
+                                              p->n_chunks, b.sc, b.st, 0.0, 0.0, 0, b.partials + kSlotMisc * kMaxBlocks);
+                OSM_CUDA(cudaGetLastError());
+                const Geo<T> g = geo<T>(p);
+                const TableT<T> tab = table<T>(p);
+                double eps_step0 = -1.0;
+                T* e_cur = b.x;
+                for (;;) {
+                    // residual of the current outer iterate (and boundary refresh for Jacobi)
+                    if (p->opt.inner == OSMODI_INNER_CG) {
+                        if (p->ndim == 2) k_outer_res<T, 2><<<G, TH, 0, s>>>(e_cur, b.rc, b.r, p->code8, g, b.sc, b.partials + kSlotMisc * kMaxBlocks);
+                        else k_outer_res<T, 3><<<G, TH, 0, s>>>(e_cur, b.rc, b.r, p->code8, g, b.sc, b.partials + kSlotMisc * kMaxBlocks);
+                    } else {
+                        if (p->ndim == 2) k_outer_rhs<T, 2><<<G, TH, 0, s>>>(e_cur, b.rc, b.rhs, p->code32, g, tab, b.sc, b.partials + kSlotMisc * kMaxBlocks);
+                        else k_outer_rhs<T, 3><<<G, TH, 0, s>>>(e_cur, b.rc, b.rhs, p->code32, g, tab, b.sc, b.partials + kSlotMisc * kMaxBlocks);
+                    }
+                    OSM_CUDA(cudaGetLastError());
+                    OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
+                    const double eps_o = std::sqrt(hm->sc.outer_r2) / bnorm;
+                    if (eps_step0 < 0) eps_step0 = eps_o;
+                    if (p->opt.record_history) p->history.push_back(eps_o);
+                    const double target = std::max(0.5 * tol, rel * eps_step0);
+                    if (eps_o <= target || outer_total >= max_iter || !std::isfinite(eps_o)) break;
+                    if (p->opt.inner == OSMODI_INNER_CG) {
+                        k_state_outer<<<1, 1, 0, s>>>(b.sc, b.st, p->opt.inner_tol * p->opt.inner_tol, (long long)p->opt.inner_max);
+                        OSM_CUDA(cudaGetLastError());
+                        long long it = 0;
+                        OSM_TRY(run_cg<T>(p, b, OP_M, ws, s, hm, &it));
+                        total_inner += it;
+                    } else {
+                        for (int sw = 0; sw < p->opt.inner_max; ++sw) {
+                            T* e_next = (e_cur == b.x) ? b.e2 : b.x;
+                            if (p->ndim == 2) k_jacobi<T, 2><<<G, TH, 0, s>>>(e_cur, e_next, b.rhs, p->code32, g, tab);
+                            else k_jacobi<T, 3><<<G, TH, 0, s>>>(e_cur, e_next, b.rhs, p->code32, g, tab);
+                            e_cur = e_next;
+                        }
+                        OSM_CUDA(cudaGetLastError());
+                        total_inner += p->opt.inner_max;
+                    }
+                    outer_total++;
+                }
+                if (e_cur != b.x) OSM_CUDA(cudaMemcpyAsync(b.x, e_cur, sizeof(T) * (size_t)p->n_box, cudaMemcpyDeviceToDevice, s));
+            }
+            // p64 += e ; new FP64 residual
+            OSM_TRY(launch_residual<T>(p, b, cur, b.x, nxt, rtarget, s));
+            residual_evals++;
+            std::swap(cur, nxt);
+            OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
+            const double eps_new = std::sqrt(hm->sc.rnorm2) / bnorm;
+            steps++;
+            if (!std::isfinite(eps_new) || eps_new > 1e3 * best) {
+                status = OSMODI_E_DIVERGED;
+                eps = eps_new;
+                break;
+            }
+            stall = (eps_new > 0.5 * eps) ? stall + 1 : 0;
+            eps = eps_new;
+            best = std::min(best, eps);
+            if (stall >= 2) break;
+        }
+        if (status == OSMODI_OK && eps > tol) status = OSMODI_NOT_CONVERGED;
+    }
+    if (status == OSMODI_E_DIVERGED) return status;
+
+    // gauge and output
+    if (multi) OSM_TRY(comp_sums<double>(p, cur, comp_p, s));
+    {
+        const int GS = (int)std::min<int64_t>((p->n_box + 255) / 256, (int64_t)p->num_sms * 8);
+        if (pdt == OSMODI_F32)
+            k_output<float><<<GS, 256, 0, s>>>(cur, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0,
+                                               (float*)pu, p->px, p->nx, p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks);
+        else
+            k_output<double><<<GS, 256, 0, s>>>(cur, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0,
+                                                (double*)pu, p->px, p->nx, p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks);
+        OSM_CUDA(cudaGetLastError());
+    }
+    OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
+    auto t1 = std::chrono::steady_clock::now();
+    if (res) {
+        res->status = status;
+        res->outer_iters = outer ? outer_total : steps;
+        res->inner_iters = total_inner;
+        res->refine_steps = residual_evals;
+        res->eps_R = eps;
+        res->eps_P = eps_p;
+        res->ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        double apps = (double)total_inner + (double)residual_evals + (outer ? (double)outer_total : 0.0);
+        res->point_updates = apps * (double)p->n_valid;
+        res->seed_rel_dist = hm->sc.pnorm2 > 0 ? std::sqrt(hm->sc.dist2 / hm->sc.pnorm2) : 0.0;
+    }
+    return status;
+}
+
+}  // namespace osm
+
+using namespace osm;
+
+extern "C" size_t osmodi_workspace_bytes(osmodi_plan p) {
+    if (!p) return 0;
+    return workspace_bytes_for(p);
+}
+
+extern "C" osmodi_status osmodi_solve(osmodi_plan p, const void* grad, int gdt, void* pu, int pdt, double tol, int max_iter,
+                                      void* ws, void* stream, osmodi_result* res) {
+    if (res) std::memset(res, 0, sizeof(*res));
+    if (!p || !grad || !pu) return OSMODI_E_INVALID;
+    if ((gdt != OSMODI_F32 && gdt != OSMODI_F64) || (pdt != OSMODI_F32 && pdt != OSMODI_F64)) return OSMODI_E_INVALID;
+    if (!(tol > 0.0) || !std::isfinite(tol) || max_iter < 0) return OSMODI_E_INVALID;
+    if (!ws || ((uintptr_t)ws & 255u)) return OSMODI_E_WORKSPACE;
+    int dev = -1;
+    OSM_CUDA(cudaGetDevice(&dev));
+    if (dev != p->device) return OSMODI_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    osmodi_status st = p->opt.precision == OSMODI_FP64
+                           ? solve_impl<double>(p, grad, gdt, pu, pdt, tol, max_iter, ws, s, res)
+                           : solve_impl<float>(p, grad, gdt, pu, pdt, tol, max_iter, ws, s, res);
+    if (res) res->status = st;
+    return st;
+}

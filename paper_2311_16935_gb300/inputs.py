@@ -110,9 +110,11 @@ def lamb_oseen_2d(n=64, noise=0.02, seed=1, rc=0.1, gamma=1.0, rho=1.0, device="
     Y, X = torch.meshgrid(x, x, indexing="ij")
     dx, dy = X - 0.5, Y - 0.5
     r = torch.sqrt(dx * dx + dy * dy)
-    ut = gamma / (2 * math.pi * r) * (1 - torch.exp(-r * r / (rc * rc)))
-    dpdr = rho * ut * ut / r
-    g = torch.stack([dpdr * dx / r, dpdr * dy / r])
+    rs = torch.where(r > 0, r, torch.ones_like(r))  # a node on the centre (odd n): gradient 0 there
+    ut = gamma / (2 * math.pi * rs) * (1 - torch.exp(-rs * rs / (rc * rc)))
+    dpdr = rho * ut * ut / rs
+    g = torch.stack([dpdr * dx / rs, dpdr * dy / rs])
+    g = torch.where(r > 0, g, torch.zeros_like(g))
     mask = torch.ones((n, n), dtype=torch.uint8, device=device)
     sigma = noise * _max_valid_norm(g, mask)
     g = g + _noise_like(g, sigma, (1, seed))

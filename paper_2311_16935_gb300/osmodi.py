@@ -1,0 +1,276 @@
+"""Python binding of libosmodi.so (argument marshalling only).
+
+Every function here forwards to the C entry point of the same name in
+``include/osmodi.h``; all computation happens in the library's CUDA kernels.
+Tensors are passed as raw device pointers.  The library must have been built
+(``paper_2311_16935_gb300.build.build()``); importing this module without it
+raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libosmodi.so")
+
+OK, NOT_CONVERGED = 0, 1
+E_INVALID, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_DIVERGED, E_TIMEOUT, E_EMPTY, E_NAN_INPUT, E_WORKSPACE = (
+    -1, -2, -3, -4, -5, -6, -7, -8, -9)
+F32, F64 = 0, 1
+FP64, FP32, FP32_REFINE = 0, 1, 2
+FPCG, OUTER = 0, 1
+INNER_CG, INNER_JACOBI = 0, 1
+
+
+class osmodi_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("scheme", ctypes.c_int), ("inner", ctypes.c_int),
+                ("inner_max", ctypes.c_int), ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
+                ("sweeps_per_pass", ctypes.c_int), ("max_refine", ctypes.c_int), ("record_history", ctypes.c_int),
+                ("threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("profile", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
+
+
+class osmodi_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int64),
+                ("refine_steps", ctypes.c_int), ("eps_R", ctypes.c_double), ("eps_P", ctypes.c_double),
+                ("ms", ctypes.c_double), ("point_updates", ctypes.c_double), ("seed_rel_dist", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class OsmodiError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = f"{what}: {status_string(status)} ({status})"
+        if status == E_CUDA:
+            msg += f" [{last_cuda_error()}]"
+        super().__init__(msg)
+
+
+_lib = None
+
+_SIGS = {
+    "osmodi_default_options": (None, [ctypes.c_void_p]),
+    "osmodi_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "osmodi_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                    ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_solve_batched": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_batched_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_void_p]),
+    "osmodi_history": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "osmodi_ray_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_source": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_residual": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_kernel_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_plan_constants": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_destroy": (None, [ctypes.c_void_p]),
+    "osmodi_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "osmodi_last_cuda_error": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """Load libosmodi.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2311_16935_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def status_string(st: int) -> str:
+    return lib().osmodi_status_string(int(st)).decode()
+
+
+def last_cuda_error() -> str:
+    return lib().osmodi_last_cuda_error().decode()
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _check_cuda(t: torch.Tensor, name: str):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+
+
+def default_options(**overrides) -> osmodi_options:
+    o = osmodi_options()
+    lib().osmodi_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+class Plan:
+    """Owns an osmodi_plan and a workspace tensor (device memory from torch)."""
+
+    def __init__(self, ndim, dims, spacing, mask=None, options=None, stream=None, **opt):
+        if options is None:
+            options = default_options(**opt)
+        self.ndim = ndim
+        self.dims = tuple(int(d) for d in dims) + (1,) * (3 - len(dims))
+        d = (ctypes.c_int64 * 3)(*self.dims)
+        sp = (ctypes.c_double * 3)(*(list(spacing) + [1.0] * (3 - len(spacing))))
+        mptr = None
+        if mask is not None:
+            _check_cuda(mask, "mask")
+            if mask.dtype != torch.uint8:
+                raise TypeError("mask must be uint8")
+            mptr = mask.data_ptr()
+        h = ctypes.c_void_p()
+        st = lib().osmodi_create(ndim, d, sp, mptr, ctypes.byref(options), _stream_ptr(stream), ctypes.byref(h))
+        if st != OK:
+            raise OsmodiError(st, "osmodi_create")
+        self.handle = h
+        self.options = options
+        self._ws = None
+
+    def workspace_bytes(self) -> int:
+        return int(lib().osmodi_workspace_bytes(self.handle))
+
+    def workspace(self) -> torch.Tensor:
+        n = self.workspace_bytes()
+        if self._ws is None or self._ws.numel() < n:
+            self._ws = torch.empty(n + 256, dtype=torch.uint8, device="cuda")
+        return self._ws
+
+    def _ws_ptr(self):
+        ws = self.workspace()
+        p = ws.data_ptr()
+        return (p + 255) // 256 * 256
+
+    def info(self):
+        out = (ctypes.c_int64 * 8)()
+        st = lib().osmodi_plan_info(self.handle, out)
+        if st != OK:
+            raise OsmodiError(st, "osmodi_plan_info")
+        keys = ["nx", "ny", "nz", "n_valid", "n_comp", "px", "n_box", "blocks"]
+        return dict(zip(keys, list(out)))
+
+    def constants(self):
+        c = (ctypes.c_double * 9)()
+        F = (ctypes.c_double * 3)()
+        a = ctypes.c_double()
+        st = lib().osmodi_plan_constants(self.handle, c, F, ctypes.byref(a))
+        if st != OK:
+            raise OsmodiError(st, "osmodi_plan_constants")
+        return list(c), list(F), a.value
+
+    def solve(self, grad: torch.Tensor, p: torch.Tensor, tol: float, max_iter: int = 1 << 30, stream=None,
+              check=True) -> osmodi_result:
+        """osmodi_solve: p holds P^0 on entry and the pressure on return."""
+        _check_cuda(grad, "grad")
+        _check_cuda(p, "p")
+        res = osmodi_result()
+        st = lib().osmodi_solve(self.handle, grad.data_ptr(), _dtype_code(grad), p.data_ptr(), _dtype_code(p),
+                                float(tol), int(min(max_iter, 2**31 - 1)), self._ws_ptr(), _stream_ptr(stream),
+                                ctypes.byref(res))
+        if check and st < 0:
+            raise OsmodiError(st, "osmodi_solve")
+        return res
+
+    def kernel_stats(self):
+        out = (ctypes.c_double * 8)()
+        st = lib().osmodi_kernel_stats(self.handle, out)
+        if st != OK:
+            raise OsmodiError(st, "osmodi_kernel_stats")
+        v = list(out)
+        return {"cg_apply_ms": v[0], "cg_apply_launches": int(v[1]), "cg_update_ms": v[2],
+                "cg_update_launches": int(v[3]), "residual64_ms": v[4], "residual64_launches": int(v[5])}
+
+    def history(self):
+        n = lib().osmodi_history(self.handle, None, 0)
+        buf = (ctypes.c_double * max(n, 1))()
+        lib().osmodi_history(self.handle, buf, n)
+        return list(buf)[:n]
+
+    def ray_counts(self, stream=None) -> torch.Tensor:
+        nx, ny, nz = self.dims
+        out = torch.empty((nx * ny * nz, 2 + 4 * self.ndim), dtype=torch.float64, device="cuda")
+        st = lib().osmodi_ray_counts(self.handle, out.data_ptr(), _stream_ptr(stream))
+        if st != OK:
+            raise OsmodiError(st, "osmodi_ray_counts")
+        return out
+
+    def source(self, grad: torch.Tensor, stream=None) -> torch.Tensor:
+        _check_cuda(grad, "grad")
+        out = torch.empty(grad.shape[1:], dtype=torch.float64, device="cuda")
+        st = lib().osmodi_source(self.handle, grad.data_ptr(), _dtype_code(grad), out.data_ptr(), _stream_ptr(stream))
+        if st != OK:
+            raise OsmodiError(st, "osmodi_source")
+        return out
+
+    def apply(self, which: int, x: torch.Tensor, stream=None) -> torch.Tensor:
+        _check_cuda(x, "x")
+        if x.dtype != torch.float64:
+            raise TypeError("x must be float64")
+        y = torch.empty_like(x)
+        st = lib().osmodi_apply(self.handle, int(which), x.data_ptr(), y.data_ptr(), _stream_ptr(stream))
+        if st != OK:
+            raise OsmodiError(st, "osmodi_apply")
+        return y
+
+    def residual(self, grad: torch.Tensor, p: torch.Tensor, stream=None) -> float:
+        _check_cuda(grad, "grad")
+        _check_cuda(p, "p")
+        eps = ctypes.c_double()
+        st = lib().osmodi_residual(self.handle, grad.data_ptr(), _dtype_code(grad), p.data_ptr(), _dtype_code(p),
+                                   ctypes.byref(eps), _stream_ptr(stream))
+        if st != OK:
+            raise OsmodiError(st, "osmodi_residual")
+        return eps.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().osmodi_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def osmodi_create(ndim, dims, spacing, mask=None, **opt) -> Plan:
+    return Plan(ndim, dims, spacing, mask, **opt)
+
+
+def osmodi_solve(plan: Plan, grad, p, tol, max_iter=1 << 30, stream=None) -> osmodi_result:
+    return plan.solve(grad, p, tol, max_iter, stream)
+
+
+def osmodi_destroy(plan: Plan):
+    plan.close()

@@ -184,6 +184,39 @@ OSMODI_API osmodi_status osmodi_solve_batched(int count, const osmodi_plan* plan
                                    void* const* ps, int p_dtype, double tol, int max_iter, void* workspace_dev,
                                    void* stream, osmodi_result* results);
 
+/*
+ * osmodi_solve_noalloc: the same solve as osmodi_solve for callers that
+ * cannot allocate device memory at solve time -- for example code running
+ * under a host framework whose caching allocator owns the device memory, or
+ * a latency-bound acquisition loop where cudaMalloc / cudaFree (which may
+ * synchronise the whole device) are not acceptable.  Such callers create
+ * their plans during set-up; this call then allocates nothing: no cudaMalloc,
+ * no cudaFree, no page-locked host memory, no CUDA graph.  The paper has no
+ * counterpart; it is an interface convenience.
+ *
+ * Its device scratch is one file-scope device array of
+ * OSMODI_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU that loads the
+ * library keeps until the process exits.  A plan whose
+ * osmodi_workspace_bytes() exceeds that size is rejected with
+ * OSMODI_E_WORKSPACE (osmodi_last_cuda_error() then says why).  For the
+ * default FP32_REFINE / FPCG options that admits grids of up to about
+ * 350,000 cells (e.g. 512 x 512 in 2D, 64^3 in 3D).
+ *
+ * The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) and keeps it; make that first call before any
+ * stream capture on that device.  All calls share the one array, which keeps
+ * the previous call's contents (every value the solve needs zeroed is
+ * cleared at the start of each call).  Calls whose GPU work overlaps -- on
+ * two streams, from two threads or on plans that share a device -- race on
+ * the array and must be serialised by the caller.
+ * Arguments, results and error codes are those of osmodi_solve, without the
+ * workspace.
+ */
+#define OSMODI_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+OSMODI_API osmodi_status osmodi_solve_noalloc(osmodi_plan plan, const void* grad_dev, int grad_dtype, void* p_dev,
+                                              int p_dtype, double tol, int max_iter, void* stream,
+                                              osmodi_result* res);
+
 /* Workspace bytes for osmodi_solve_batched over these plans. */
 OSMODI_API size_t osmodi_batched_workspace_bytes(int count, const osmodi_plan* plans);
 

@@ -26,6 +26,8 @@ void set_cuda_error(cudaError_t e, const char* where) {
 
 const char* last_cuda_error() { return g_last_cuda_error.c_str(); }
 
+void set_error_text(const char* msg) { g_last_cuda_error = msg; }
+
 // ---------------------------------------------------------------------------
 // Constants
 // ---------------------------------------------------------------------------

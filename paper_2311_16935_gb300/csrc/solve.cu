@@ -761,9 +761,25 @@ static osmodi_status run_cg_profiled(osmodi_plan p, const Buffers<T>& b, int op,
     return OSMODI_OK;
 }
 
+// Direct launches in chunks of check_every iterations: no CUDA graph is
+// instantiated and nothing is allocated (used by the allocation-free entry).
+template <class T>
+static osmodi_status run_cg_direct(osmodi_plan p, const Buffers<T>& b, int op, cudaStream_t s, HostMirror* hm,
+                                   long long* iters_out) {
+    for (;;) {
+        OSM_TRY(launch_cg_iters<T>(p, b, op, p->opt.check_every, s));
+        OSM_CUDA(cudaMemcpyAsync(&hm->st, b.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+        OSM_CUDA(cudaStreamSynchronize(s));
+        if (hm->st.status == kFinished) break;
+    }
+    *iters_out = hm->st.it;
+    return OSMODI_OK;
+}
+
 template <class T>
 static osmodi_status run_cg(osmodi_plan p, const Buffers<T>& b, int op, void* ws, cudaStream_t s, HostMirror* hm,
-                            long long* iters_out) {
+                            long long* iters_out, bool noalloc) {
+    if (noalloc) return run_cg_direct<T>(p, b, op, s, hm, iters_out);
     if (p->opt.profile) return run_cg_profiled<T>(p, b, op, s, hm, iters_out);
     const int kind = (sizeof(T) == 8 ? 2 : 0) + op;
     GraphCache& gc = p->graphs[kind];
@@ -812,9 +828,9 @@ static osmodi_status run_cg(osmodi_plan p, const Buffers<T>& b, int op, void* ws
 
 template <class T>
 static osmodi_status launch_residual(osmodi_plan p, const Buffers<T>& b, const double* p_in, const T* e, double* p_out,
-                                     T* r_out, cudaStream_t s) {
+                                     T* r_out, cudaStream_t s, bool prof) {
     const int G = p->launch.blocks, TH = p->launch.threads;
-    if (p->opt.profile) {
+    if (prof) {
         OSM_TRY(ensure_events(p, 2));
         OSM_CUDA(cudaEventRecord(p->events[0], s));
     }
@@ -827,7 +843,7 @@ static osmodi_status launch_residual(osmodi_plan p, const Buffers<T>& b, const d
         else k_residual<T, 3, false><<<G, TH, 0, s>>>(p_in, e, p_out, b.b64, r_out, p->code8, g, b.sc, b.partials + kSlotRes * kMaxBlocks);
     }
     OSM_CUDA(cudaGetLastError());
-    if (p->opt.profile) {
+    if (prof) {
         OSM_CUDA(cudaEventRecord(p->events[1], s));
         OSM_CUDA(cudaEventSynchronize(p->events[1]));
         float ms = 0.f;
@@ -855,13 +871,15 @@ static osmodi_status read_mirror(void* dst, const void* src, size_t n, cudaStrea
 
 template <class T>
 static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* pu, int pdt, double tol, int max_iter,
-                                void* ws, cudaStream_t s, osmodi_result* res) {
+                                void* ws, cudaStream_t s, osmodi_result* res, HostMirror* hm_given = nullptr) {
+    const bool noalloc = hm_given != nullptr;
+    const bool prof = p->opt.profile && !noalloc;
     auto t0 = std::chrono::steady_clock::now();
     Buffers<T> b;
     carve<T>(p, ws, &b);
-    if (!p->pinned) OSM_CUDA(cudaMallocHost(&p->pinned, 4096));
     static_assert(sizeof(HostMirror) <= 4096, "pinned mirror");
-    HostMirror* hm = reinterpret_cast<HostMirror*>(p->pinned);
+    if (!noalloc && !p->pinned) OSM_CUDA(cudaMallocHost(&p->pinned, 4096));
+    HostMirror* hm = noalloc ? hm_given : reinterpret_cast<HostMirror*>(p->pinned);
     const int G = p->launch.blocks, TH = p->launch.threads;
     const bool multi = p->n_comp > 1;
     double* comp_r = b.comp;
@@ -912,12 +930,12 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
         // S = 0: the answer is a constant on every component; P = 0 after the gauge
         k_fill_zero_f64<<<G, TH, 0, s>>>(cur, p->n_box);
         OSM_CUDA(cudaGetLastError());
-        OSM_TRY(launch_residual<T>(p, b, cur, nullptr, nullptr, rtarget, s));
+        OSM_TRY(launch_residual<T>(p, b, cur, nullptr, nullptr, rtarget, s, prof));
         residual_evals++;
         OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
         eps = 0.0;
     } else {
-        OSM_TRY(launch_residual<T>(p, b, cur, nullptr, nullptr, rtarget, s));
+        OSM_TRY(launch_residual<T>(p, b, cur, nullptr, nullptr, rtarget, s, prof));
         residual_evals++;
         OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
         eps = std::sqrt(hm->sc.rnorm2) / bnorm;
@@ -938,7 +956,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                                               b.partials + kSlotMisc * kMaxBlocks);
                 OSM_CUDA(cudaGetLastError());
                 long long it = 0;
-                OSM_TRY(run_cg<T>(p, b, OP_L, ws, s, hm, &it));
+                OSM_TRY(run_cg<T>(p, b, OP_L, ws, s, hm, &it, noalloc));
                 total_inner += it;
             } else {
                 // project rc (k_cg_init also zeroes e = x)
@@ -969,7 +987,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                         k_state_outer<<<1, 1, 0, s>>>(b.sc, b.st, p->opt.inner_tol * p->opt.inner_tol, (long long)p->opt.inner_max);
                         OSM_CUDA(cudaGetLastError());
                         long long it = 0;
-                        OSM_TRY(run_cg<T>(p, b, OP_M, ws, s, hm, &it));
+                        OSM_TRY(run_cg<T>(p, b, OP_M, ws, s, hm, &it, noalloc));
                         total_inner += it;
                     } else {
                         for (int sw = 0; sw < p->opt.inner_max; ++sw) {
@@ -986,7 +1004,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                 if (e_cur != b.x) OSM_CUDA(cudaMemcpyAsync(b.x, e_cur, sizeof(T) * (size_t)p->n_box, cudaMemcpyDeviceToDevice, s));
             }
             // p64 += e ; new FP64 residual
-            OSM_TRY(launch_residual<T>(p, b, cur, b.x, nxt, rtarget, s));
+            OSM_TRY(launch_residual<T>(p, b, cur, b.x, nxt, rtarget, s, prof));
             residual_evals++;
             std::swap(cur, nxt);
             OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
@@ -1033,6 +1051,16 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
         res->seed_rel_dist = hm->sc.pnorm2 > 0 ? std::sqrt(hm->sc.dist2 / hm->sc.pnorm2) : 0.0;
     }
     return status;
+}
+
+// The solve with caller-chosen device scratch and host mirror: no CUDA graph,
+// no events, no allocation of any kind.
+osmodi_status solve_into_scratch(osmodi_plan p, const void* grad, int gdt, void* pu, int pdt, double tol, int max_iter,
+                                 void* scratch, cudaStream_t s, osmodi_result* res) {
+    static thread_local HostMirror mirror;
+    return p->opt.precision == OSMODI_FP64
+               ? solve_impl<double>(p, grad, gdt, pu, pdt, tol, max_iter, scratch, s, res, &mirror)
+               : solve_impl<float>(p, grad, gdt, pu, pdt, tol, max_iter, scratch, s, res, &mirror);
 }
 
 }  // namespace osm

@@ -64,6 +64,9 @@ _SIGS = {
                                             ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_batched_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_void_p]),
+    "osmodi_solve_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_void_p]),
     "osmodi_history": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "osmodi_ray_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_source": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
@@ -209,6 +212,20 @@ class Plan:
         v = list(out)
         return {"cg_apply_ms": v[0], "cg_apply_launches": int(v[1]), "cg_update_ms": v[2],
                 "cg_update_launches": int(v[3]), "residual64_ms": v[4], "residual64_launches": int(v[5])}
+
+    def solve_noalloc(self, grad: torch.Tensor, p: torch.Tensor, tol: float, max_iter: int = 1 << 30, stream=None,
+                      check=True) -> osmodi_result:
+        """osmodi_solve_noalloc: as solve(), with the library's fixed device
+        scratch instead of a workspace (nothing is allocated)."""
+        _check_cuda(grad, "grad")
+        _check_cuda(p, "p")
+        res = osmodi_result()
+        st = lib().osmodi_solve_noalloc(self.handle, grad.data_ptr(), _dtype_code(grad), p.data_ptr(), _dtype_code(p),
+                                        float(tol), int(min(max_iter, 2**31 - 1)), _stream_ptr(stream),
+                                        ctypes.byref(res))
+        if check and st < 0:
+            raise OsmodiError(st, "osmodi_solve_noalloc")
+        return res
 
     def history(self):
         n = lib().osmodi_history(self.handle, None, 0)

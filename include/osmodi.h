@@ -90,9 +90,11 @@ typedef struct {
     int inner;           /* OUTER only: OSMODI_INNER_CG (default) | OSMODI_INNER_JACOBI */
     int inner_max;       /* FPCG: max CG iterations per refinement step (default 1<<20);
                             OUTER: max inner iterations (or sweeps) per outer iteration */
-    double inner_tol;    /* FP32_REFINE: relative reduction of each correction solve
-                            (default 1e-5); OUTER+CG: relative tolerance of each
-                            inner solve (default 1e-6) */
+    double inner_tol;    /* FP32_REFINE: the FP32 CG runs until its residual has dropped
+                            by this factor since the last FP64 residual replacement
+                            (default 0.1); the search direction carries over
+                            ("reliable updates").  OUTER+CG: relative tolerance of
+                            each inner solve (default 1e-6) */
     int check_every;     /* iterations between host convergence checks (default 64) */
     int sweeps_per_pass; /* OUTER+JACOBI: Jacobi sweeps fused per pass, 1..4 (default 2) */
     int max_refine;      /* FP32_REFINE: max refinement steps (default 32) */
@@ -102,7 +104,9 @@ typedef struct {
     int profile;         /* 1 = launch the CG iterations one by one (no CUDA graph) with
                             CUDA events around every sweep kernel on the caller's stream;
                             durations readable with osmodi_kernel_stats */
-    int reserved[4];
+    int slab;            /* z-planes per work item of the tiled 3D sweep kernel (0 = tuned) */
+    int flat_sweeps;     /* 1 (default) = flat grid-stride sweep kernel; 0 = z-marching tiled one */
+    int reserved[2];
 } osmodi_options;
 
 typedef struct {

@@ -1,18 +1,774 @@
-// osmodi_solve_batched: many independent problems in one persistent launch.
+// osmodi_solve_batched: many independent problems (PIV snapshots of uneven
+// sizes and masks) solved in ONE persistent cooperative launch.
+//
+// The kernel runs the whole solve of osmodi_solve for every instance at once:
+// source, FP64 residual / refinement rounds, constant removal, FP32 (or FP64)
+// conjugate-gradient segments with reliable updates, gauge and output.  Work
+// is a list of tiles (a block of 256 threads takes one tile of up to 256
+// chunks = 1024 cells; every tile lies inside one instance).  Phases are
+// separated by a grid barrier; the per-instance scalars (alpha, beta, rho,
+// convergence flags) are finalised without extra barriers by the block that
+// completes an instance's last tile of a phase (a per-instance ticket), which
+// adds the instance's tile partials in tile order (deterministic).  Converged
+// instances drop out of every later phase; the others continue.  Every wait
+// is bounded: a grid barrier that does not complete within ~2 s sets an error
+// flag and every block leaves (OSMODI_E_TIMEOUT).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "internal.cuh"
+#include "stencil.cuh"
+
+namespace osm {
+
+namespace {
+
+enum { kRun = 0, kConv = 1, kSegDone = 2, kInit = 3, kDone = 4, kFail = 5, kNaN = 6 };
+enum { TK_S = 0, TK_R = 1, TK_I = 2, TK_A = 3, TK_B = 4, TK_O = 5, kTickets = 6 };
+constexpr int kPartK = 3;  // doubles per tile partial
+constexpr int kTileThreads = 256;
+
+struct BInst {
+    int64_t off;  // first cell of the instance's padded box in the arena
+    int64_t px, ny, nz, nx, plane, n_box, n_dense;
+    int tile0, ntiles;
+    int comp_off, n_comp;
+    double n_valid;
+    double F[3], h[3];
+    const uint8_t* code8;
+    const int32_t* label;       // nullptr when the valid cells form one component
+    const double* comp_count;   // valid cells per component (the plan's array)
+    const void* grad;
+    void* p_user;
+};
+
+struct BTile {
+    int inst;
+    int nchunks;
+    int64_t chunk0;  // first chunk of the tile inside the instance
+};
+
+struct BState {
+    double bnorm2, p0sum, rsum, psum, rnorm2, eps, best;
+    double rho, rho0, rho_k, beta, alpha, stop2;
+    double dist2, pnorm2;
+    long long it, seg_it;
+    int status, first, par, p64par, rounds, stall, cont, breakdown, nan_in, pad;
+    unsigned ticket[kTickets];
+};
+
+struct BGlobal {
+    unsigned bar_count, bar_gen;
+    int error, pad;
+    int n_live, n_need;  // instances inside a CG segment / needing another round
+    int snap[2][2];      // the loop counters as of each barrier (double-buffered)
+};
+
+struct BParams {
+    const BInst* inst;
+    const BTile* tiles;
+    BState* st;
+    BGlobal* gl;
+    double* partials;  // ntiles * kPartK
+    double* comp;      // per component: [sum r, sum p, sum p0]
+    double *b64, *p64a, *p64b;
+    void *r, *x, *q, *pA, *pB;  // inner type T
+    int count, ntiles, max_refine;
+    long long max_iter, inner_max;
+    double tol, inner_tol;
+};
+
+// ---- bounded grid barrier (the cooperative launch guarantees co-residency) ----
+__device__ bool grid_barrier(BGlobal* gl) {
+    __syncthreads();
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = &gl->bar_gen;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&gl->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            // last arriver: snapshot the loop counters for everyone, then release
+            gl->snap[(g + 1) & 1][0] = *(volatile int*)&gl->n_live;
+            gl->snap[(g + 1) & 1][1] = *(volatile int*)&gl->n_need;
+            gl->bar_count = 0;
+            __threadfence();
+            atomicAdd(&gl->bar_gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g) {
+                if (*(volatile int*)&gl->error) break;
+                if (++spins > (1LL << 25)) {  // about 2 s with the sleep below
+                    atomicExch(&gl->error, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok = *(volatile int*)&gl->error == 0;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__device__ __forceinline__ int snap_of(BGlobal* gl, int which) {
+    const unsigned g = *(volatile unsigned*)&gl->bar_gen;
+    return *(volatile int*)&gl->snap[g & 1][which];
+}
+
+// Block sum of K values -> the tile's partial.  Returns true (in all threads)
+// in the block that completed the instance's last tile of this phase, with
+// the instance totals (tile partials added in tile order) in tot.
+template <int K>
+__device__ bool tile_done(const BParams& P, int tile, const BInst& I, BState* S, int kind, double (&v)[K],
+                          double (&tot)[K]) {
+    __shared__ double smem[32 * K];
+    __shared__ bool last;
+    block_sum<K>(v, smem);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) P.partials[(size_t)tile * kPartK + q] = v[q];
+        __threadfence();
+        const unsigned t = atomicAdd(&S->ticket[kind], 1u);
+        last = (t == (unsigned)I.ntiles - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double s[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        s[q] = 0.0;
+        for (int t = threadIdx.x; t < I.ntiles; t += blockDim.x) s[q] += __ldcg(&P.partials[(size_t)(I.tile0 + t) * kPartK + q]);
+    }
+    block_sum<K>(s, smem);
+    __shared__ double out[K];
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) out[q] = s[q];
+        S->ticket[kind] = 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < K; ++q) tot[q] = out[q];
+    return true;
+}
+
+template <class T>
+__device__ __forceinline__ Geo<T> inst_geo(const BInst& I) {
+    Geo<T> g;
+    g.px = I.px;
+    g.plane = I.plane;
+    g.n_chunks = I.n_box / 4;
+    for (int a = 0; a < 3; ++a) g.F[a] = (T)I.F[a];
+    return g;
+}
+
+__device__ __forceinline__ double* comp_of(const BParams& P, const BInst& I, int32_t l) {
+    return P.comp + 3 * (size_t)(I.comp_off + l);
+}
+
+// ---- the persistent kernel ----
+template <class T, int NDIM, class TG, class TP>
+__global__ void __launch_bounds__(kTileThreads) k_batched(BParams P) {
+    const int lane = threadIdx.x & 31;
+    T* const r_all = (T*)P.r;
+    T* const x_all = (T*)P.x;
+    T* const q_all = (T*)P.q;
+    T* const pA_all = (T*)P.pA;
+    T* const pB_all = (T*)P.pB;
+
+    // ===== phase S: b = A_tot S from the dense gradient, p64 = P^0 =====
+    for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x) {
+        const BTile tl = P.tiles[t];
+        const BInst I = P.inst[tl.inst];
+        BState* S = &P.st[tl.inst];
+        double acc[2] = {0.0, 0.0};
+        int bad = 0;
+        const TG* f = (const TG*)I.grad;
+        const TP* pin = (const TP*)I.p_user;
+        const int64_t sd[3] = {1, I.nx, I.nx * I.ny};
+        for (int c = threadIdx.x; c < tl.nchunks * 4; c += blockDim.x) {
+            const int64_t cell = tl.chunk0 * 4 + c;
+            const int64_t row = cell / I.px;
+            const int64_t i = cell - row * I.px;
+            const unsigned cw = I.code8[cell];
+            double bval = 0.0, p0 = 0.0;
+            if (i < I.nx && (cw & 0x80u)) {
+                const int64_t d = row * I.nx + i;
+#pragma unroll
+                for (int fc = 0; fc < 2 * NDIM; ++fc) {
+                    if (!(cw & (1u << fc))) continue;
+                    const int a = fc >> 1;
+                    const double sgn = (fc & 1) ? -1.0 : 1.0;
+                    const int64_t dn = d + ((fc & 1) ? -sd[a] : sd[a]);
+                    bval -= sgn * I.h[a] * I.F[a] * 0.5 * ((double)f[a * I.n_dense + dn] + (double)f[a * I.n_dense + d]);
+                }
+#pragma unroll
+                for (int a = 0; a < NDIM; ++a)
+                    if (!isfinite((double)f[a * I.n_dense + d])) bad = 1;
+                p0 = (double)pin[d];
+                if (!isfinite(p0)) bad = 1;
+                if (I.label && p0 != 0.0) atomicAdd(comp_of(P, I, I.label[cell]) + 2, p0);
+            }
+            P.b64[I.off + cell] = bval;
+            P.p64a[I.off + cell] = p0;
+            acc[0] += bval * bval;
+            acc[1] += p0;
+        }
+        if (bad) atomicExch(&S->nan_in, 1);
+        double tot[2];
+        if (tile_done<2>(P, t, I, S, TK_S, acc, tot) && threadIdx.x == 0) {
+            S->bnorm2 = tot[0];
+            S->p0sum = tot[1];
+        }
+    }
+    if (!grid_barrier(P.gl)) return;
+
+    // ===== refinement rounds =====
+    for (int round = 0;; ++round) {
+        // --- phase R: p64' = p64 + e (rounds > 0); r = b - L p64' in FP64; norms
+        for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x) {
+            const BTile tl = P.tiles[t];
+            const BInst I = P.inst[tl.inst];
+            BState* S = &P.st[tl.inst];
+            const int status = __ldcg(&S->status);
+            if (status == kDone || status == kFail || status == kNaN) continue;
+            const bool has_e = round > 0;
+            const int p64par = __ldcg(&S->p64par);
+            const double* pin = (p64par ? P.p64b : P.p64a) + I.off;
+            double* pout = (p64par ? P.p64a : P.p64b) + I.off;
+            const T* e = x_all + I.off;
+            T* rr = r_all + I.off;
+            const double* b = P.b64 + I.off;
+            const Geo<double> g = inst_geo<double>(I);
+            double acc[3] = {0.0, 0.0, 0.0};
+            const bool act = threadIdx.x < tl.nchunks;
+            const int64_t i0 = (tl.chunk0 + threadIdx.x) * 4;
+            const uint32_t cw = act ? *reinterpret_cast<const uint32_t*>(I.code8 + i0) : 0u;
+            V4<double> c = act ? ld4cg(pin + i0) : zero4<double>();
+            if (has_e && act) {
+                const V4<T> ev = ld4cg(e + i0);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) c.v[m] += (double)ev.v[m];
+            }
+            auto f4 = [&](int64_t off) {
+                V4<double> v = ld4cg(pin + i0 + off);
+                if (has_e) {
+                    const V4<T> w = ld4cg(e + i0 + off);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) v.v[m] += (double)w.v[m];
+                }
+                return v;
+            };
+            auto f1 = [&](int64_t off) {
+                double v = __ldcg(pin + i0 + off);
+                if (has_e) v += (double)__ldcg(e + i0 + off);
+                return v;
+            };
+            const Nbrs<double> nb = gather_clamped<double, NDIM>(c, i0, I.n_box, lane, g.px, g.plane, act, f4, f1);
+            if (act) {
+                const V4<double> bv = ld4cg(b + i0);
+                V4<T> rv;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const double res = bv.v[m] - apply_L<double, NDIM>(face_bits8(cw, m), c, nb, m, g.F);
+                    rv.v[m] = (T)res;
+                    acc[0] += res * res;
+                    acc[1] += res;
+                    acc[2] += c.v[m];
+                    if (I.label && valid8(cw, m)) {
+                        double* cs = comp_of(P, I, I.label[i0 + m]);
+                        if (res != 0.0) atomicAdd(cs + 0, res);
+                        if (c.v[m] != 0.0) atomicAdd(cs + 1, c.v[m]);
+                    }
+                }
+                if (has_e) st4(pout + i0, c);
+                st4(rr + i0, rv);
+            }
+            double tot[3];
+            if (tile_done<3>(P, t, I, S, TK_R, acc, tot) && threadIdx.x == 0) {
+                if (has_e) S->p64par = __ldcg(&S->p64par) ^ 1;
+                S->rnorm2 = tot[0];
+                S->rsum = tot[1];
+                S->psum = tot[2];
+                const double bn = sqrt(__ldcg(&S->bnorm2));
+                const double eps = bn > 0.0 ? sqrt(tot[0]) / bn : 0.0;
+                if (round > 0) S->stall = (eps > 0.9 * __ldcg(&S->eps)) ? __ldcg(&S->stall) + 1 : 0;
+                S->eps = eps;
+                S->best = round == 0 ? eps : fmin(__ldcg(&S->best), eps);
+                S->rounds = round;
+                if (__ldcg(&S->nan_in)) {
+                    S->status = kNaN;
+                } else if (eps <= P.tol || bn == 0.0) {
+                    S->status = kDone;
+                } else if (round >= P.max_refine || __ldcg(&S->it) >= P.max_iter || __ldcg(&S->stall) >= 3 || !isfinite(eps)) {
+                    S->status = kFail;
+                } else {
+                    S->status = kInit;
+                    atomicAdd(&P.gl->n_need, 1);
+                }
+            }
+        }
+        if (!grid_barrier(P.gl)) return;
+        if (snap_of(P.gl, 1) == 0) break;
+
+        // --- phase I: remove the constant, x = 0, CG start or continuation
+        for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x) {
+            const BTile tl = P.tiles[t];
+            const BInst I = P.inst[tl.inst];
+            BState* S = &P.st[tl.inst];
+            if (__ldcg(&S->status) != kInit) continue;
+            T* rr = r_all + I.off;
+            T* xx = x_all + I.off;
+            const double mean1 = I.label ? 0.0 : __ldcg(&S->rsum) / I.n_valid;
+            double acc[1] = {0.0};
+            if (threadIdx.x < tl.nchunks) {
+                const int64_t i0 = (tl.chunk0 + threadIdx.x) * 4;
+                const uint32_t cw = *reinterpret_cast<const uint32_t*>(I.code8 + i0);
+                V4<T> rv = ld4cg(rr + i0);
+                T part = T(0);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    if (valid8(cw, m)) {
+                        double mean = mean1;
+                        if (I.label) {
+                            const int32_t l = I.label[i0 + m];
+                            mean = __ldcg(comp_of(P, I, l)) / I.comp_count[l];
+                        }
+                        rv.v[m] = (T)((double)rv.v[m] - mean);
+                    } else {
+                        rv.v[m] = T(0);
+                    }
+                    part += rv.v[m] * rv.v[m];
+                }
+                st4(rr + i0, rv);
+                st4(xx + i0, zero4<T>());
+                acc[0] = (double)part;
+            }
+            double tot[1];
+            if (tile_done<1>(P, t, I, S, TK_I, acc, tot)) {
+                // every tile of the instance has read its component sums: clear
+                // the per-round ones for the next residual
+                if (I.label)
+                    for (int c = threadIdx.x; c < I.n_comp; c += blockDim.x) {
+                        P.comp[3 * (size_t)(I.comp_off + c) + 0] = 0.0;
+                        P.comp[3 * (size_t)(I.comp_off + c) + 1] = 0.0;
+                    }
+                if (threadIdx.x == 0) {
+                    const double rho0 = tot[0];
+                    const bool keep = __ldcg(&S->cont) && __ldcg(&S->breakdown) == 0 && __ldcg(&S->rho_k) > 0.0;
+                    const double bn = sqrt(__ldcg(&S->bnorm2));
+                    const double stop_abs = 0.5 * P.tol * bn;
+                    S->beta = keep ? rho0 / __ldcg(&S->rho_k) : 0.0;
+                    S->first = keep ? 0 : 1;
+                    S->alpha = 0.0;
+                    S->rho = rho0;
+                    S->rho0 = rho0;
+                    S->stop2 = fmax(P.inner_tol * P.inner_tol * rho0, stop_abs * stop_abs);
+                    S->seg_it = 0;
+                    S->breakdown = 0;
+                    if (rho0 > __ldcg(&S->stop2)) {
+                        S->status = kRun;
+                        atomicAdd(&P.gl->n_live, 1);
+                    } else {
+                        S->status = kSegDone;
+                    }
+                    atomicAdd(&P.gl->n_need, -1);
+                }
+            }
+        }
+        if (!grid_barrier(P.gl)) return;
+
+        // --- a CG segment: phases A and B until no instance is live
+        while (snap_of(P.gl, 0) > 0) {
+            // phase A: p = r + beta p_old, q = L p, x += alpha_prev p_old, p.q
+            for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x) {
+                const BTile tl = P.tiles[t];
+                const BInst I = P.inst[tl.inst];
+                BState* S = &P.st[tl.inst];
+                const int status = __ldcg(&S->status);
+                if (status != kRun && status != kConv) continue;
+                const bool conv = status == kConv;
+                const bool first = __ldcg(&S->first) != 0;
+                const T alpha = (T)__ldcg(&S->alpha), beta = (T)__ldcg(&S->beta);
+                const int par = __ldcg(&S->par);
+                const T* r = r_all + I.off;
+                const T* po = (par ? pB_all : pA_all) + I.off;
+                T* pn = (par ? pA_all : pB_all) + I.off;
+                T* q = q_all + I.off;
+                T* x = x_all + I.off;
+                const Geo<T> g = inst_geo<T>(I);
+                double acc[1] = {0.0};
+                const bool act = threadIdx.x < tl.nchunks;
+                const int64_t i0 = (tl.chunk0 + threadIdx.x) * 4;
+                V4<T> pold = zero4<T>();
+                if (act && !first) {
+                    pold = ld4cg(po + i0);
+                    V4<T> xv = ld4cg(x + i0);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) xv.v[m] += alpha * pold.v[m];
+                    st4(x + i0, xv);
+                }
+                if (!conv) {
+                    const uint32_t cw = act ? *reinterpret_cast<const uint32_t*>(I.code8 + i0) : 0u;
+                    V4<T> c = act ? ld4cg(r + i0) : zero4<T>();
+                    if (!first) {
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) c.v[m] += beta * pold.v[m];
+                    }
+                    auto f4 = [&](int64_t off) {
+                        V4<T> v = ld4cg(r + i0 + off);
+                        if (!first) {
+                            const V4<T> o = ld4cg(po + i0 + off);
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) v.v[m] += beta * o.v[m];
+                        }
+                        return v;
+                    };
+                    auto f1 = [&](int64_t off) {
+                        T v = __ldcg(r + i0 + off);
+                        if (!first) v += beta * __ldcg(po + i0 + off);
+                        return v;
+                    };
+                    const Nbrs<T> nb = gather_clamped<T, NDIM>(c, i0, I.n_box, lane, g.px, g.plane, act, f4, f1);
+                    if (act) {
+                        V4<T> qv;
+                        T part = T(0);
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            qv.v[m] = apply_L<T, NDIM>(face_bits8(cw, m), c, nb, m, g.F);
+                            part += c.v[m] * qv.v[m];
+                        }
+                        st4(pn + i0, c);
+                        st4(q + i0, qv);
+                        acc[0] = (double)part;
+                    }
+                }
+                double tot[1];
+                if (tile_done<1>(P, t, I, S, TK_A, acc, tot) && threadIdx.x == 0) {
+                    if (conv) {
+                        S->status = kSegDone;
+                        S->cont = __ldcg(&S->seg_it) > 0 ? 1 : 0;
+                        atomicAdd(&P.gl->n_live, -1);
+                    } else {
+                        S->par = __ldcg(&S->par) ^ 1;
+                        S->first = 0;
+                        if (tot[0] > 0.0 && isfinite(tot[0])) {
+                            S->alpha = __ldcg(&S->rho) / tot[0];
+                        } else {
+                            S->alpha = 0.0;
+                            S->breakdown = 1;
+                            S->status = kConv;
+                        }
+                    }
+                }
+            }
+            if (!grid_barrier(P.gl)) return;
+            // phase B: r -= alpha q, r.r, stopping test
+            for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x) {
+                const BTile tl = P.tiles[t];
+                const BInst I = P.inst[tl.inst];
+                BState* S = &P.st[tl.inst];
+                if (__ldcg(&S->status) != kRun) continue;
+                const T alpha = (T)__ldcg(&S->alpha);
+                T* r = r_all + I.off;
+                const T* q = q_all + I.off;
+                double acc[1] = {0.0};
+                if (threadIdx.x < tl.nchunks) {
+                    const int64_t i0 = (tl.chunk0 + threadIdx.x) * 4;
+                    V4<T> rv = ld4cg(r + i0);
+                    const V4<T> qv = ld4cg(q + i0);
+                    T part = T(0);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        rv.v[m] -= alpha * qv.v[m];
+                        part += rv.v[m] * rv.v[m];
+                    }
+                    st4(r + i0, rv);
+                    acc[0] = (double)part;
+                }
+                double tot[1];
+                if (tile_done<1>(P, t, I, S, TK_B, acc, tot) && threadIdx.x == 0) {
+                    const double rho_new = tot[0];
+                    S->rho_k = __ldcg(&S->rho);
+                    S->beta = rho_new / __ldcg(&S->rho);
+                    S->rho = rho_new;
+                    S->it = __ldcg(&S->it) + 1;
+                    S->seg_it = __ldcg(&S->seg_it) + 1;
+                    if (!(rho_new > __ldcg(&S->stop2)) || __ldcg(&S->it) >= P.max_iter || __ldcg(&S->seg_it) >= P.inner_max || !isfinite(rho_new))
+                        S->status = kConv;
+                }
+            }
+            if (!grid_barrier(P.gl)) return;
+        }
+    }
+
+    // ===== phase O: gauge and dense output (instances with bad input untouched) =====
+    for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x) {
+        const BTile tl = P.tiles[t];
+        const BInst I = P.inst[tl.inst];
+        BState* S = &P.st[tl.inst];
+        const bool write = __ldcg(&S->status) != kNaN;
+        const double* p64 = (__ldcg(&S->p64par) ? P.p64b : P.p64a) + I.off;
+        TP* out = (TP*)I.p_user;
+        const double m1 = I.label ? 0.0 : __ldcg(&S->psum) / I.n_valid;
+        const double m01 = I.label ? 0.0 : __ldcg(&S->p0sum) / I.n_valid;
+        double acc[2] = {0.0, 0.0};
+        for (int c = threadIdx.x; write && c < tl.nchunks * 4; c += blockDim.x) {
+            const int64_t cell = tl.chunk0 * 4 + c;
+            const int64_t row = cell / I.px;
+            const int64_t i = cell - row * I.px;
+            if (i >= I.nx) continue;
+            const int64_t d = row * I.nx + i;
+            if (!(I.code8[cell] & 0x80u)) {
+                out[d] = (TP)NAN;
+                continue;
+            }
+            double m = m1, m0 = m01;
+            if (I.label) {
+                const int32_t l = I.label[cell];
+                const double* cs = comp_of(P, I, l);
+                m = __ldcg(cs + 1) / I.comp_count[l];
+                m0 = __ldcg(cs + 2) / I.comp_count[l];
+            }
+            const double v = __ldcg(p64 + cell) - m;
+            const double v0 = (double)out[d] - m0;
+            acc[0] += (v0 - v) * (v0 - v);
+            acc[1] += v * v;
+            out[d] = (TP)v;
+        }
+        double tot[2];
+        if (tile_done<2>(P, t, I, S, TK_O, acc, tot) && threadIdx.x == 0) {
+            S->dist2 = tot[0];
+            S->pnorm2 = tot[1];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct Layout {
+    std::vector<BInst> inst;
+    std::vector<BTile> tiles;
+    int64_t arena = 0;  // cells
+    int total_comp = 0;
+    size_t bytes = 0;
+    // offsets in the workspace
+    size_t o_inst, o_tiles, o_st, o_gl, o_part, o_comp, o_b64, o_pa, o_pb, o_r, o_x, o_q, o_pA, o_pB;
+};
+
+static bool build_layout(int count, const osmodi_plan* plans, size_t tsize, Layout* L) {
+    L->inst.resize(count);
+    L->tiles.clear();
+    int64_t off = 0;
+    int comp = 0;
+    for (int i = 0; i < count; ++i) {
+        const osmodi_plan p = plans[i];
+        BInst& I = L->inst[i];
+        std::memset(&I, 0, sizeof(I));
+        I.off = off;
+        I.px = p->px;
+        I.ny = p->ny;
+        I.nz = p->nz;
+        I.nx = p->nx;
+        I.plane = p->px * p->ny;
+        I.n_box = p->n_box;
+        I.n_dense = p->n_dense;
+        I.n_valid = (double)p->n_valid;
+        for (int a = 0; a < 3; ++a) {
+            I.F[a] = p->k.F[a];
+            I.h[a] = p->h[a];
+        }
+        I.code8 = p->code8;
+        I.label = p->n_comp > 1 ? p->label : nullptr;
+        I.comp_count = p->comp_count;
+        I.comp_off = comp;
+        I.n_comp = (int)p->n_comp;
+        comp += (int)p->n_comp;
+        I.tile0 = (int)L->tiles.size();
+        const int64_t nch = p->n_chunks;
+        for (int64_t c = 0; c < nch; c += kTileThreads) {
+            BTile t;
+            t.inst = i;
+            t.chunk0 = c;
+            t.nchunks = (int)std::min<int64_t>(kTileThreads, nch - c);
+            L->tiles.push_back(t);
+        }
+        I.ntiles = (int)L->tiles.size() - I.tile0;
+        off += (p->n_box + 31) / 32 * 32;  // 128-byte aligned boxes
+    }
+    L->arena = off;
+    L->total_comp = std::max(1, comp);
+    Workspace w;
+    w.base = nullptr;
+    L->o_inst = w.off; w.take<BInst>(count);
+    L->o_tiles = w.off; w.take<BTile>(L->tiles.size());
+    L->o_st = w.off; w.take<BState>(count);
+    L->o_gl = w.off; w.take<BGlobal>(1);
+    L->o_part = w.off; w.take<double>(L->tiles.size() * kPartK);
+    L->o_comp = w.off; w.take<double>((size_t)3 * L->total_comp);
+    L->o_b64 = w.off; w.take<double>((size_t)off);
+    L->o_pa = w.off; w.take<double>((size_t)off);
+    L->o_pb = w.off; w.take<double>((size_t)off);
+    const size_t vbytes = ((size_t)off * tsize + 255) & ~size_t(255);
+    L->o_r = w.off; w.off += vbytes;
+    L->o_x = w.off; w.off += vbytes;
+    L->o_q = w.off; w.off += vbytes;
+    L->o_pA = w.off; w.off += vbytes;
+    L->o_pB = w.off; w.off += vbytes;
+    L->bytes = w.off;
+    return true;
+}
+
+template <class T, int NDIM, class TG, class TP>
+static cudaError_t launch_batched(const BParams& P, int grid, cudaStream_t s) {
+    void* args[] = {(void*)&P};
+    return cudaLaunchCooperativeKernel((const void*)k_batched<T, NDIM, TG, TP>, dim3(grid), dim3(kTileThreads), args, 0, s);
+}
+
+template <class T, int NDIM, class TG, class TP>
+static int max_grid(int num_sms) {
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_batched<T, NDIM, TG, TP>, kTileThreads, 0) != cudaSuccess || bps < 1) {
+        cudaGetLastError();
+        bps = 1;
+    }
+    return bps * num_sms;
+}
+
+template <class T, int NDIM>
+static osmodi_status run_batched(int count, const osmodi_plan* plans, const void* const* grads, int gdt, void* const* ps,
+                                 int pdt, double tol, int max_iter, void* ws, cudaStream_t s, osmodi_result* results) {
+    auto t0 = std::chrono::steady_clock::now();
+    Layout L;
+    build_layout(count, plans, sizeof(T), &L);
+    for (int i = 0; i < count; ++i) {
+        L.inst[i].grad = grads[i];
+        L.inst[i].p_user = ps[i];
+    }
+    char* base = (char*)ws;
+    BParams P{};
+    P.inst = (const BInst*)(base + L.o_inst);
+    P.tiles = (const BTile*)(base + L.o_tiles);
+    P.st = (BState*)(base + L.o_st);
+    P.gl = (BGlobal*)(base + L.o_gl);
+    P.partials = (double*)(base + L.o_part);
+    P.comp = (double*)(base + L.o_comp);
+    P.b64 = (double*)(base + L.o_b64);
+    P.p64a = (double*)(base + L.o_pa);
+    P.p64b = (double*)(base + L.o_pb);
+    P.r = base + L.o_r;
+    P.x = base + L.o_x;
+    P.q = base + L.o_q;
+    P.pA = base + L.o_pA;
+    P.pB = base + L.o_pB;
+    P.count = count;
+    P.ntiles = (int)L.tiles.size();
+    const osmodi_options& o = plans[0]->opt;
+    P.max_refine = o.precision == OSMODI_FP32_REFINE ? o.max_refine : (o.precision == OSMODI_FP32 ? 1 : 4);
+    P.max_iter = max_iter;
+    P.inner_max = o.inner_max;
+    P.tol = tol;
+    P.inner_tol = o.precision == OSMODI_FP32_REFINE ? o.inner_tol : 0.0;
+
+    OSM_CUDA(cudaMemcpyAsync((void*)P.inst, L.inst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, s));
+    OSM_CUDA(cudaMemcpyAsync((void*)P.tiles, L.tiles.data(), sizeof(BTile) * L.tiles.size(), cudaMemcpyHostToDevice, s));
+    OSM_CUDA(cudaMemsetAsync(P.st, 0, sizeof(BState) * count, s));
+    OSM_CUDA(cudaMemsetAsync(P.gl, 0, sizeof(BGlobal), s));
+    OSM_CUDA(cudaMemsetAsync(P.comp, 0, sizeof(double) * 3 * L.total_comp, s));
+
+    const int num_sms = plans[0]->num_sms;
+    int grid = 0;
+    cudaError_t e;
+#define OSM_BL(TG, TP)                                                  \
+    do {                                                                \
+        grid = std::min(max_grid<T, NDIM, TG, TP>(num_sms), P.ntiles);  \
+        e = launch_batched<T, NDIM, TG, TP>(P, std::max(grid, 1), s);   \
+    } while (0)
+    if (gdt == OSMODI_F32 && pdt == OSMODI_F32) OSM_BL(float, float);
+    else if (gdt == OSMODI_F32) OSM_BL(float, double);
+    else if (pdt == OSMODI_F32) OSM_BL(double, float);
+    else OSM_BL(double, double);
+#undef OSM_BL
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "cudaLaunchCooperativeKernel(k_batched)");
+        return OSMODI_E_CUDA;
+    }
+    std::vector<BState> st(count);
+    BGlobal gl;
+    OSM_CUDA(cudaMemcpyAsync(st.data(), P.st, sizeof(BState) * count, cudaMemcpyDeviceToHost, s));
+    OSM_CUDA(cudaMemcpyAsync(&gl, P.gl, sizeof(BGlobal), cudaMemcpyDeviceToHost, s));
+    OSM_CUDA(cudaStreamSynchronize(s));
+    auto t1 = std::chrono::steady_clock::now();
+    const double ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    if (gl.error) return OSMODI_E_TIMEOUT;
+    osmodi_status overall = OSMODI_OK;
+    for (int i = 0; i < count; ++i) {
+        const BState& S = st[i];
+        osmodi_status si = S.status == kDone ? OSMODI_OK : (S.status == kNaN ? OSMODI_E_NAN_INPUT : OSMODI_NOT_CONVERGED);
+        if (si == OSMODI_E_NAN_INPUT && overall >= 0) overall = si;
+        else if (si == OSMODI_NOT_CONVERGED && overall == OSMODI_OK) overall = si;
+        if (results) {
+            osmodi_result& R = results[i];
+            std::memset(&R, 0, sizeof(R));
+            R.status = si;
+            R.outer_iters = S.rounds;
+            R.inner_iters = S.it;
+            R.refine_steps = S.rounds + 1;
+            R.eps_R = S.eps;
+            R.ms = ms;
+            R.point_updates = ((double)S.it + (double)S.rounds + 1.0) * L.inst[i].n_valid;
+            R.seed_rel_dist = S.pnorm2 > 0 ? std::sqrt(S.dist2 / S.pnorm2) : 0.0;
+        }
+    }
+    return overall;
+}
+
+}  // namespace
+}  // namespace osm
+
+using namespace osm;
 
 extern "C" size_t osmodi_batched_workspace_bytes(int count, const osmodi_plan* plans) {
-    (void)count;
-    (void)plans;
-    return 0;
+    if (count <= 0 || !plans) return 0;
+    for (int i = 0; i < count; ++i)
+        if (!plans[i]) return 0;
+    Layout L;
+    build_layout(count, plans, plans[0]->opt.precision == OSMODI_FP64 ? 8 : 4, &L);
+    return L.bytes;
 }
 
 extern "C" osmodi_status osmodi_solve_batched(int count, const osmodi_plan* plans, const void* const* grads, int grad_dtype,
                                               void* const* ps, int p_dtype, double tol, int max_iter, void* workspace,
                                               void* stream, osmodi_result* results) {
-    (void)count; (void)plans; (void)grads; (void)grad_dtype; (void)ps; (void)p_dtype; (void)tol; (void)max_iter;
-    (void)workspace; (void)stream; (void)results;
-    return OSMODI_E_UNSUPPORTED;
+    if (results && count > 0) std::memset(results, 0, sizeof(osmodi_result) * (size_t)count);
+    if (count <= 0 || !plans || !grads || !ps) return OSMODI_E_INVALID;
+    if ((grad_dtype != OSMODI_F32 && grad_dtype != OSMODI_F64) || (p_dtype != OSMODI_F32 && p_dtype != OSMODI_F64))
+        return OSMODI_E_INVALID;
+    if (!(tol > 0.0) || !std::isfinite(tol) || max_iter < 0) return OSMODI_E_INVALID;
+    if (!workspace || ((uintptr_t)workspace & 255u)) return OSMODI_E_WORKSPACE;
+    const int ndim = plans[0] ? plans[0]->ndim : 0;
+    int dev = -1;
+    OSM_CUDA(cudaGetDevice(&dev));
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i] || !grads[i] || !ps[i]) return OSMODI_E_INVALID;
+        if (plans[i]->ndim != ndim || plans[i]->device != dev) return OSMODI_E_INVALID;
+        if (plans[i]->n_chunks > (int64_t)kTileThreads * (int64_t)(1 << 30)) return OSMODI_E_INVALID;
+    }
+    if (plans[0]->opt.scheme != OSMODI_FPCG) return OSMODI_E_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool fp64 = plans[0]->opt.precision == OSMODI_FP64;
+    if (ndim == 2)
+        return fp64 ? run_batched<double, 2>(count, plans, grads, grad_dtype, ps, p_dtype, tol, max_iter, workspace, s, results)
+                    : run_batched<float, 2>(count, plans, grads, grad_dtype, ps, p_dtype, tol, max_iter, workspace, s, results);
+    return fp64 ? run_batched<double, 3>(count, plans, grads, grad_dtype, ps, p_dtype, tol, max_iter, workspace, s, results)
+                : run_batched<float, 3>(count, plans, grads, grad_dtype, ps, p_dtype, tol, max_iter, workspace, s, results);
 }

@@ -56,7 +56,11 @@ struct GraphCache {
 
 struct Launch {
     int threads = 256;
-    int blocks = 0;  // persistent grid (multiple of the SM count)
+    int blocks = 0;        // persistent grid (multiple of the SM count)
+    int blocks_tiled = 0;  // grid of the tiled sweep kernel (256 threads)
+    int blocks_a = 0;      // grid of the CG stencil kernel (256 threads)
+    int blocks_b = 0;      // grid of the CG update kernel (256 threads)
+    int slab = 16;         // z-planes per tiled work item
 };
 
 }  // namespace osm
@@ -137,6 +141,35 @@ __device__ __forceinline__ void st4(float* p, const V4<float>& a) {
 __device__ __forceinline__ void st4(double* p, const V4<double>& a) {
     reinterpret_cast<double2*>(p)[0] = make_double2(a.v[0], a.v[1]);
     reinterpret_cast<double2*>(p)[1] = make_double2(a.v[2], a.v[3]);
+}
+// L2-only loads (bypass L1): for data that other SMs rewrite while a
+// persistent kernel is running (L1 is not coherent across SMs)
+__device__ __forceinline__ V4<float> ld4cg(const float* p) {
+    float4 a = __ldcg(reinterpret_cast<const float4*>(p));
+    return {{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ V4<double> ld4cg(const double* p) {
+    double2 a = __ldcg(reinterpret_cast<const double2*>(p));
+    double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+    return {{a.x, a.y, b.x, b.y}};
+}
+
+// streaming (evict-first) variants for vectors touched once per kernel
+__device__ __forceinline__ V4<float> ld4s(const float* p) {
+    float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+    return {{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ V4<double> ld4s(const double* p) {
+    double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+    double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+    return {{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4s(float* p, const V4<float>& a) {
+    __stcs(reinterpret_cast<float4*>(p), make_float4(a.v[0], a.v[1], a.v[2], a.v[3]));
+}
+__device__ __forceinline__ void st4s(double* p, const V4<double>& a) {
+    __stcs(reinterpret_cast<double2*>(p), make_double2(a.v[0], a.v[1]));
+    __stcs(reinterpret_cast<double2*>(p) + 1, make_double2(a.v[2], a.v[3]));
 }
 template <class T>
 __device__ __forceinline__ V4<T> zero4() {

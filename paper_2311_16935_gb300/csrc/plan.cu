@@ -254,6 +254,7 @@ extern "C" void osmodi_default_options(osmodi_options* o) {
     o->inner_tol = -1.0;  // scheme-dependent default, resolved at create
     o->check_every = 64;
     o->sweeps_per_pass = 2;
+    o->flat_sweeps = 1;
     o->max_refine = 32;
     o->record_history = 0;
     o->threads = 0;
@@ -299,6 +300,8 @@ static void free_plan_device(osmodi_plan p) {
 
 namespace osm {
 int tuned_blocks_per_sm(int ndim, int threads);  // solve.cu
+int tiled_blocks_per_sm(int ndim, int requested); // solve.cu
+void sweep_blocks_per_sm(int ndim, bool fp64, int* bps_a, int* bps_b);  // solve.cu
 }
 
 extern "C" osmodi_status osmodi_create(int ndim, const int64_t dims[3], const double spacing[3], const uint8_t* mask_dev,
@@ -318,7 +321,7 @@ extern "C" osmodi_status osmodi_create(int ndim, const int64_t dims[3], const do
     if (o.scheme != OSMODI_FPCG && o.scheme != OSMODI_OUTER) return OSMODI_E_INVALID;
     if (o.inner != OSMODI_INNER_CG && o.inner != OSMODI_INNER_JACOBI) return OSMODI_E_INVALID;
     if (o.inner_max < 1) o.inner_max = 1 << 20;
-    if (!(o.inner_tol > 0.0)) o.inner_tol = (o.scheme == OSMODI_OUTER) ? 1e-6 : 1e-5;
+    if (!(o.inner_tol > 0.0)) o.inner_tol = (o.scheme == OSMODI_OUTER) ? 1e-6 : 0.1;
     if (o.check_every < 2) o.check_every = 64;
     o.check_every += o.check_every & 1;  // even: the direction buffers alternate
     if (o.sweeps_per_pass < 1) o.sweeps_per_pass = 1;
@@ -447,6 +450,23 @@ extern "C" osmodi_status osmodi_create(int ndim, const int64_t dims[3], const do
     int64_t g = std::min<int64_t>((int64_t)p->num_sms * bps, need);
     g = std::max<int64_t>(1, std::min<int64_t>(g, kMaxBlocks));
     p->launch.blocks = (int)g;
+    {
+        int ba = 0, bb = 0;
+        sweep_blocks_per_sm(ndim, o.precision == OSMODI_FP64, &ba, &bb);
+        if (o.blocks_per_sm) ba = std::min(ba, o.blocks_per_sm);
+        const int64_t need256 = (p->n_chunks + 255) / 256;
+        p->launch.blocks_a = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)p->num_sms * ba, need256, (int64_t)kMaxBlocks}));
+        p->launch.blocks_b = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)p->num_sms * bb, need256, (int64_t)kMaxBlocks}));
+    }
+    p->launch.slab = o.slab > 0 ? o.slab : 16;
+    {
+        const int64_t cpr = p->px / 4;
+        const int64_t n_tx = (cpr + 31) / 32, n_ty = (ny + 7) / 8;
+        const int64_t n_slab = ndim == 3 ? (nz + p->launch.slab - 1) / p->launch.slab : 1;
+        const int64_t items = n_tx * n_ty * n_slab;
+        const int64_t gt = std::min<int64_t>((int64_t)p->num_sms * tiled_blocks_per_sm(ndim, o.blocks_per_sm), items);
+        p->launch.blocks_tiled = (int)std::max<int64_t>(1, std::min<int64_t>(gt, kMaxBlocks));
+    }
     *out = p;
     return OSMODI_OK;
 }
@@ -466,7 +486,7 @@ extern "C" osmodi_status osmodi_plan_info(osmodi_plan p, int64_t out[8]) {
     out[4] = p->n_comp;
     out[5] = p->px;
     out[6] = p->n_box;
-    out[7] = p->launch.blocks;
+    out[7] = p->launch.blocks_a;
     return OSMODI_OK;
 }
 

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(512) k_cg_init(T* __restrict__ r, T* __restric
                                                  const int32_t* __restrict__ label, const double* __restrict__ comp_sum,
                                                  const double* __restrict__ comp_cnt, int multi, int64_t n_chunks,
                                                  Scalars* sc, CgState* st, double stop_abs2, double rel2,
-                                                 long long max_it, double* partials) {
+                                                 long long max_it, double* partials, int cont = 0) {
     const double mean1 = multi ? 0.0 : sc->rsum / comp_cnt[0];
     double acc[1] = {0.0};
     for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < n_chunks; ch += (int64_t)gridDim.x * blockDim.x) {
@@ -217,13 +217,18 @@ __global__ void __launch_bounds__(512) k_cg_init(T* __restrict__ r, T* __restric
     double tot[1];
     if (grid_sum<1>(acc, partials, &st->ticketI, tot) && threadIdx.x == 0) {
         const double rho0 = tot[0];
+        // continuation (reliable update): the residual has been replaced by the
+        // true one and x folded into the FP64 iterate; keep the previous search
+        // direction, with beta = |r_true|^2 / rho_k (rho_k = rho_{k+1} / beta_k)
+        const bool keep = cont && st->breakdown == 0 && st->rho > 0.0 && st->beta > 0.0 && isfinite(st->beta);
+        const double beta = keep ? rho0 * st->beta / st->rho : 0.0;
         st->rho = rho0;
         st->rho0 = rho0;
         st->stop2 = fmax(rel2 * rho0, stop_abs2);
         st->alpha = 0.0;
-        st->beta = 0.0;
+        st->beta = beta;
         st->pq = 0.0;
-        st->first = 1;
+        st->first = keep ? 0 : 1;
         st->it = 0;
         st->max_it = max_it;
         st->breakdown = 0;
@@ -257,8 +262,8 @@ __global__ void k_state_outer(Scalars* sc, CgState* st, double rel2, long long m
 // The x update trails by one iteration, so after convergence one more A
 // launch applies the last alpha p and marks the solve finished.
 // ---------------------------------------------------------------------------
-template <class T, int NDIM, int OP>
-__global__ void __launch_bounds__(512) k_cg_a(const T* __restrict__ r, const T* __restrict__ p_old, T* __restrict__ p_new,
+template <class T, int NDIM, int OP, int HINT = 0, int MINB = 1>
+__global__ void __launch_bounds__(256, MINB) k_cg_a(const T* __restrict__ r, const T* __restrict__ p_old, T* __restrict__ p_new,
                                               T* __restrict__ q, T* __restrict__ x, const uint8_t* __restrict__ code8,
                                               const uint32_t* __restrict__ code32, Geo<T> g, TableT<T> tabv, CgState* st,
                                               double* partials) {
@@ -282,10 +287,11 @@ __global__ void __launch_bounds__(512) k_cg_a(const T* __restrict__ r, const T* 
         V4<T> po = zero4<T>();
         if (act && !first) {
             po = ld4(p_old + i0);
-            V4<T> xv = ld4c(x + i0);
+            V4<T> xv = HINT ? ld4s(x + i0) : ld4c(x + i0);
 #pragma unroll
             for (int m = 0; m < 4; ++m) xv.v[m] += alpha * po.v[m];
-            st4(x + i0, xv);
+            if (HINT) st4s(x + i0, xv);
+            else st4(x + i0, xv);
         }
         if (conv) continue;
         unsigned fm[4], any = 0;
@@ -320,7 +326,8 @@ __global__ void __launch_bounds__(512) k_cg_a(const T* __restrict__ r, const T* 
             if (!first) v += beta * p_old[i0 + off];
             return v;
         };
-        Nbrs<T> nb = gather<T, NDIM>(c, any, fm[0] & 2u, fm[3] & 1u, L.lane, g.px, g.plane, f4, f1);
+        Nbrs<T> nb = (OP == OP_L) ? gather_clamped<T, NDIM>(c, i0, g.n_chunks * 4, L.lane, g.px, g.plane, act, f4, f1)
+                                  : gather<T, NDIM>(c, any, fm[0] & 2u, fm[3] & 1u, L.lane, g.px, g.plane, f4, f1);
         if (act) {
             V4<T> qv;
             T part = T(0);
@@ -336,8 +343,13 @@ __global__ void __launch_bounds__(512) k_cg_a(const T* __restrict__ r, const T* 
                 qv.v[m] = qm;
                 part += c.v[m] * qm;
             }
-            st4(p_new + i0, c);
-            st4(q + i0, qv);
+            if (HINT) {
+                st4s(p_new + i0, c);
+                st4s(q + i0, qv);
+            } else {
+                st4(p_new + i0, c);
+                st4(q + i0, qv);
+            }
             acc[0] += (double)part;
         }
     }
@@ -349,6 +361,159 @@ __global__ void __launch_bounds__(512) k_cg_a(const T* __restrict__ r, const T* 
             st->pq = tot[0];
             st->first = 0;
             // L is positive semidefinite; M~ is not symmetric, so its CG can break down
+            if (tot[0] > 0.0 && isfinite(tot[0])) {
+                st->alpha = st->rho / tot[0];
+            } else {
+                st->alpha = 0.0;
+                st->breakdown = 1;
+                st->status = kConverged;
+            }
+        }
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// The same CG "A" step, z-marching tiled form (operator L).  A block owns a
+// tile of 8 consecutive rows (one per warp) x 32 chunks (128 cells) and
+// marches a slab of z-planes.  The direction values of planes z-1, z, z+1 of
+// a warp's own row stay in registers, so the z-neighbours cost no load; the
+// N/S rows were loaded by the sibling warps of the same block at the same z
+// and hit in L1; W/E come from the neighbouring lanes.  DRAM traffic is the
+// compulsory 25 B per cell.
+// ---------------------------------------------------------------------------
+struct TileGeo {
+    int64_t px, plane, n_items;
+    int cpr, ny, nz, n_tx, n_ty, slab;
+};
+
+template <class T, int NDIM, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_cg_a_tiled(const T* __restrict__ r, const T* __restrict__ p_old,
+                                                    T* __restrict__ p_new, T* __restrict__ q, T* __restrict__ x,
+                                                    const uint8_t* __restrict__ code8, Geo<T> g, TileGeo tg,
+                                                    CgState* st, double* partials) {
+    const int status = st->status;
+    if (status == kFinished) return;
+    const bool first = st->first != 0;
+    const bool conv = status == kConverged;
+    const T alpha = (T)st->alpha;
+    const T beta = (T)st->beta;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    double acc[1] = {0.0};
+    if (conv) {
+        // the trailing x update only
+        for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < g.n_chunks; ch += (int64_t)gridDim.x * blockDim.x) {
+            const V4<T> po = ld4(p_old + ch * 4);
+            V4<T> xv = ld4c(x + ch * 4);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) xv.v[m] += alpha * po.v[m];
+            st4(x + ch * 4, xv);
+        }
+    } else {
+        auto pval4 = [&](int64_t idx) {
+            V4<T> v = ld4(r + idx);
+            if (!first) {
+                const V4<T> o = ld4(p_old + idx);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) v.v[m] += beta * o.v[m];
+            }
+            return v;
+        };
+        auto pval1 = [&](int64_t idx) {
+            T v = r[idx];
+            if (!first) v += beta * p_old[idx];
+            return v;
+        };
+        for (int64_t item = blockIdx.x; item < tg.n_items; item += gridDim.x) {
+            const int tx = (int)(item % tg.n_tx);
+            const int64_t rest = item / tg.n_tx;
+            const int ty = (int)(rest % tg.n_ty);
+            const int sl = (int)(rest / tg.n_ty);
+            const int y = ty * nwarps + warp;
+            const int cx = tx * 32 + lane;
+            const bool act = (y < tg.ny) && (cx < tg.cpr);
+            const int z0 = sl * tg.slab;
+            const int z1 = min(tg.nz, z0 + tg.slab);
+            const int64_t rowoff = (int64_t)y * tg.px + (int64_t)cx * 4;
+            V4<T> pB = zero4<T>(), pC = zero4<T>(), pF = zero4<T>(), poC = zero4<T>(), poF = zero4<T>();
+            if (act) {
+                const int64_t i0 = (int64_t)z0 * tg.plane + rowoff;
+                if (NDIM == 3 && z0 > 0) pB = pval4(i0 - tg.plane);
+                pC = ld4(r + i0);
+                if (!first) {
+                    poC = ld4(p_old + i0);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) pC.v[m] += beta * poC.v[m];
+                }
+            }
+            // neighbour rows / scalars exist by geometry (warp-uniform y, lane
+            // position), so every load of a step is issued before any is used
+            const int64_t off_n = (y + 1 < tg.ny) ? tg.px : 0;
+            const int64_t off_s = (y > 0) ? -tg.px : 0;
+            const int64_t off_w = (cx > 0) ? -1 : 0;
+            const int64_t off_e = (cx + 1 < tg.cpr) ? 4 : 3;
+            for (int z = z0; z < z1; ++z) {
+                const int64_t i0 = (int64_t)z * tg.plane + rowoff;
+                V4<T> vn = zero4<T>(), vs = zero4<T>(), xv = zero4<T>();
+                T wv1 = T(0), ev1 = T(0);
+                uint32_t cw = 0u;
+                if (act) {
+                    cw = *reinterpret_cast<const uint32_t*>(code8 + i0);
+                    if (NDIM == 3) {
+                        const int64_t off_f = (z + 1 < tg.nz) ? tg.plane : 0;
+                        pF = pval4(i0 + off_f);
+                        if (!first) poF = ld4(p_old + i0 + off_f);
+                    }
+                    if (!first) xv = ld4c(x + i0);
+                    vn = pval4(i0 + off_n);
+                    vs = pval4(i0 + off_s);
+                    if (lane == 0) wv1 = pval1(i0 + off_w);
+                    if (lane == 31) ev1 = pval1(i0 + off_e);
+                }
+                unsigned fm[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) fm[m] = face_bits8(cw, m);
+                if (act && !first) {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) xv.v[m] += alpha * poC.v[m];
+                    st4(x + i0, xv);
+                }
+                Nbrs<T> nb;
+                T wv = __shfl_up_sync(0xffffffffu, pC.v[3], 1);
+                T ev = __shfl_down_sync(0xffffffffu, pC.v[0], 1);
+                if (lane == 0) wv = wv1;
+                if (lane == 31) ev = ev1;
+                nb.w = {{wv, pC.v[0], pC.v[1], pC.v[2]}};
+                nb.e = {{pC.v[1], pC.v[2], pC.v[3], ev}};
+                nb.n = vn;
+                nb.s = vs;
+                nb.f = pF;
+                nb.b = pB;
+                if (act) {
+                    V4<T> qv;
+                    T part = T(0);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        qv.v[m] = apply_L<T, NDIM>(fm[m], pC, nb, m, g.F);
+                        part += pC.v[m] * qv.v[m];
+                    }
+                    st4(p_new + i0, pC);
+                    st4(q + i0, qv);
+                    acc[0] += (double)part;
+                }
+                pB = pC;
+                pC = pF;
+                poC = poF;
+            }
+        }
+    }
+    double tot[1];
+    if (grid_sum<1>(acc, partials, &st->ticketA, tot) && threadIdx.x == 0) {
+        if (conv) {
+            st->status = kFinished;
+        } else {
+            st->pq = tot[0];
+            st->first = 0;
             if (tot[0] > 0.0 && isfinite(tot[0])) {
                 st->alpha = st->rho / tot[0];
             } else {
@@ -588,18 +753,74 @@ __global__ void k_fill_zero_f64(double* v, int64_t n) {
         if (st_ != OSMODI_OK) return st_;   \
     } while (0)
 
+// resident blocks the tiled kernel is compiled for: 0 = no bound, else 4/6/8
+static int tiled_minb(int requested) { return requested >= 4 ? 4 : 1; }
+
+int tiled_blocks_per_sm(int ndim, int requested) {
+    int bps = 0;
+    const int mb = tiled_minb(requested);
+    cudaError_t e;
+#define OSM_OCC(ND, MB) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_cg_a_tiled<float, ND, MB>, 256, 0)
+    if (ndim == 2) {
+        if (mb == 4) OSM_OCC(2, 4); else OSM_OCC(2, 1);
+    } else {
+        if (mb == 4) OSM_OCC(3, 4); else OSM_OCC(3, 1);
+    }
+#undef OSM_OCC
+    if (e != cudaSuccess || bps < 1) {
+        cudaGetLastError();
+        bps = 4;
+    }
+    return std::max(1, std::min(bps, 8));
+}
+
+static TileGeo tile_geo(osmodi_plan p) {
+    TileGeo t;
+    t.px = p->px;
+    t.plane = p->px * p->ny;
+    t.cpr = (int)(p->px / 4);
+    t.ny = (int)p->ny;
+    t.nz = (int)p->nz;
+    t.n_tx = (t.cpr + 31) / 32;
+    t.n_ty = (t.ny + 7) / 8;
+    t.slab = p->ndim == 3 ? p->launch.slab : 1;
+    const int n_slab = p->ndim == 3 ? (t.nz + t.slab - 1) / t.slab : 1;
+    t.n_items = (int64_t)t.n_tx * t.n_ty * n_slab;
+    return t;
+}
+
 int tuned_blocks_per_sm(int ndim, int threads) {
     int bps = 0;
     cudaError_t e;
     if (ndim == 2)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_cg_a<float, 2, OP_L>, threads, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_residual<float, 2, true>, threads, 0);
     else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_cg_a<float, 3, OP_L>, threads, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_residual<float, 3, true>, threads, 0);
     if (e != cudaSuccess || bps < 1) {
         cudaGetLastError();
         bps = 2048 / threads;
     }
     return std::max(1, std::min(bps, 2048 / threads));
+}
+
+// resident blocks of the two CG kernels (256 threads) for the plan's precision
+void sweep_blocks_per_sm(int ndim, bool fp64, int* bps_a, int* bps_b) {
+    int a = 0, b = 0;
+    cudaError_t e1, e2;
+    if (fp64) {
+        e1 = ndim == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cg_a<double, 2, OP_L, 0, 4>, 256, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cg_a<double, 3, OP_L, 0, 5>, 256, 0);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cg_b<double>, 256, 0);
+    } else {
+        e1 = ndim == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cg_a<float, 2, OP_L, 0, 4>, 256, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cg_a<float, 3, OP_L, 0, 5>, 256, 0);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cg_b<float>, 256, 0);
+    }
+    if (e1 != cudaSuccess || a < 1) a = 4;
+    if (e2 != cudaSuccess || b < 1) b = 6;
+    cudaGetLastError();
+    *bps_a = std::max(1, std::min(a, 8));
+    *bps_b = std::max(1, std::min(b, 8));
 }
 
 template <class T>
@@ -673,26 +894,50 @@ struct HostMirror {
     Scalars sc;
 };
 
+// one CG "A" launch
 template <class T>
-static osmodi_status launch_cg_iters(osmodi_plan p, const Buffers<T>& b, int op, int iters, cudaStream_t s) {
+static void launch_cg_a(osmodi_plan p, const Buffers<T>& b, int op, const T* po, T* pn, cudaStream_t s) {
     const int G = p->launch.blocks, TH = p->launch.threads;
     const Geo<T> g = geo<T>(p);
+    if (op == OP_L && !p->opt.flat_sweeps) {
+        const TileGeo tg = tile_geo(p);
+        const int GT = p->launch.blocks_tiled;
+        const int mb = tiled_minb(p->opt.blocks_per_sm);
+#define OSM_TL(ND, MB) k_cg_a_tiled<T, ND, MB><<<GT, 256, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, g, tg, b.st, b.partials)
+        if (p->ndim == 2) {
+            if (mb == 4) OSM_TL(2, 4); else OSM_TL(2, 1);
+        } else {
+            if (mb == 4) OSM_TL(3, 4); else OSM_TL(3, 1);
+        }
+#undef OSM_TL
+        return;
+    }
     const TableT<T> tab = table<T>(p);
+    const int variant = p->opt.reserved[0];  // 1 = streaming hints on the read-once / write-once vectors
+    const int GA = p->launch.blocks_a;
+#define OSM_FL(ND, OPV, H, MB) k_cg_a<T, ND, OPV, H, MB><<<GA, 256, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials)
+    if (p->ndim == 2) {
+        if (op == OP_L) OSM_FL(2, OP_L, 0, 4);
+        else OSM_FL(2, OP_M, 0, 4);
+    } else {
+        if (op == OP_L) {
+            if (variant == 1) OSM_FL(3, OP_L, 1, 5);
+            else OSM_FL(3, OP_L, 0, 5);
+        } else {
+            OSM_FL(3, OP_M, 0, 4);
+        }
+    }
+#undef OSM_FL
+}
+
+template <class T>
+static osmodi_status launch_cg_iters(osmodi_plan p, const Buffers<T>& b, int op, int iters, cudaStream_t s) {
+    const int GB = p->launch.blocks_b;
     for (int k = 0; k < iters; ++k) {
         const T* po = (k & 1) ? b.pB : b.pA;
         T* pn = (k & 1) ? b.pA : b.pB;
-        if (p->ndim == 2) {
-            if (op == OP_L)
-                k_cg_a<T, 2, OP_L><<<G, TH, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials);
-            else
-                k_cg_a<T, 2, OP_M><<<G, TH, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials);
-        } else {
-            if (op == OP_L)
-                k_cg_a<T, 3, OP_L><<<G, TH, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials);
-            else
-                k_cg_a<T, 3, OP_M><<<G, TH, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials);
-        }
-        k_cg_b<T><<<G, TH, 0, s>>>(b.r, b.q, p->n_chunks, b.st, b.partials + kSlotB * kMaxBlocks);
+        launch_cg_a<T>(p, b, op, po, pn, s);
+        k_cg_b<T><<<GB, 256, 0, s>>>(b.r, b.q, p->n_chunks, b.st, b.partials + kSlotB * kMaxBlocks);
     }
     OSM_CUDA(cudaGetLastError());
     return OSMODI_OK;
@@ -716,24 +961,15 @@ static osmodi_status run_cg_profiled(osmodi_plan p, const Buffers<T>& b, int op,
                                      long long* iters_out) {
     const int len = p->opt.check_every;
     OSM_TRY(ensure_events(p, (size_t)(2 * len + 1)));
-    const int G = p->launch.blocks, TH = p->launch.threads;
-    const Geo<T> g = geo<T>(p);
-    const TableT<T> tab = table<T>(p);
     long long k_global = 0;
     for (;;) {
         OSM_CUDA(cudaEventRecord(p->events[0], s));
         for (int k = 0; k < len; ++k, ++k_global) {
             const T* po = (k & 1) ? b.pB : b.pA;
             T* pn = (k & 1) ? b.pA : b.pB;
-            if (p->ndim == 2) {
-                if (op == OP_L) k_cg_a<T, 2, OP_L><<<G, TH, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials);
-                else k_cg_a<T, 2, OP_M><<<G, TH, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials);
-            } else {
-                if (op == OP_L) k_cg_a<T, 3, OP_L><<<G, TH, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials);
-                else k_cg_a<T, 3, OP_M><<<G, TH, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials);
-            }
+            launch_cg_a<T>(p, b, op, po, pn, s);
             OSM_CUDA(cudaEventRecord(p->events[2 * k + 1], s));
-            k_cg_b<T><<<G, TH, 0, s>>>(b.r, b.q, p->n_chunks, b.st, b.partials + kSlotB * kMaxBlocks);
+            k_cg_b<T><<<p->launch.blocks_b, 256, 0, s>>>(b.r, b.q, p->n_chunks, b.st, b.partials + kSlotB * kMaxBlocks);
             OSM_CUDA(cudaEventRecord(p->events[2 * k + 2], s));
         }
         OSM_CUDA(cudaGetLastError());
@@ -941,6 +1177,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
         eps = std::sqrt(hm->sc.rnorm2) / bnorm;
         double best = eps;
         const int max_steps = prec == OSMODI_FP32_REFINE ? p->opt.max_refine : (prec == OSMODI_FP32 ? 1 : 4);
+        bool cont = false, last_dir_in_a = true;
         int stall = 0;
         while (eps > tol && steps < max_steps) {
             if ((!outer && total_inner >= max_iter) || (outer && outer_total >= max_iter)) break;
@@ -951,13 +1188,22 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
             const double stop_abs = 0.5 * tol * bnorm;
             if (!outer) {
                 const long long budget = std::min<long long>((long long)p->opt.inner_max, (long long)max_iter - total_inner);
+                // the search direction of the previous segment must sit where the
+                // next iteration reads it (the direction buffers alternate)
+                if (cont && !(last_dir_in_a)) {
+                    OSM_CUDA(cudaMemcpyAsync(b.pA, b.pB, sizeof(T) * (size_t)p->n_box, cudaMemcpyDeviceToDevice, s));
+                }
                 k_cg_init<T><<<G, TH, 0, s>>>(b.r, b.x, p->code8, p->label, comp_r, p->comp_count, multi ? 1 : 0,
                                               p->n_chunks, b.sc, b.st, stop_abs * stop_abs, rel * rel, budget,
-                                              b.partials + kSlotMisc * kMaxBlocks);
+                                              b.partials + kSlotMisc * kMaxBlocks, cont ? 1 : 0);
                 OSM_CUDA(cudaGetLastError());
                 long long it = 0;
                 OSM_TRY(run_cg<T>(p, b, OP_L, ws, s, hm, &it, noalloc));
                 total_inner += it;
+                // iteration k (from 0 in each segment) writes its direction to pB
+                // when k is even, to pA when odd; the last one was k = it - 1
+                cont = it > 0;
+                last_dir_in_a = it > 0 && ((it - 1) & 1);
             } else {
                 // project rc (k_cg_init also zeroes e = x)
                 k_cg_init<T><<<G, TH, 0, s>>>(b.rc, b.x, p->code8, p->label, comp_r, p->comp_count, multi ? 1 : 0,

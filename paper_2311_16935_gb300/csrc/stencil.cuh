@@ -77,6 +77,39 @@ __device__ __forceinline__ Nbrs<T> gather(const V4<T>& c, unsigned any, bool nee
     return nb;
 }
 
+// The same neighbours with every load issued unconditionally: offsets that
+// would leave the array are clamped to the chunk itself (the value is then
+// never used, because the corresponding face bit is 0).  This keeps the loads
+// independent of the code word, so they are all in flight at once.
+template <class T, int NDIM, class F4, class F1>
+__device__ __forceinline__ Nbrs<T> gather_clamped(const V4<T>& c, int64_t i0, int64_t n_box, int lane, int64_t px,
+                                                  int64_t plane, bool act, F4 fetch4, F1 fetch1) {
+    Nbrs<T> nb;
+    V4<T> vn = zero4<T>(), vs = zero4<T>(), vf = zero4<T>(), vb = zero4<T>();
+    T w1 = T(0), e1 = T(0);
+    if (act) {
+        vn = fetch4(i0 + px < n_box ? px : 0);
+        vs = fetch4(i0 >= px ? -px : 0);
+        if (NDIM == 3) {
+            vf = fetch4(i0 + plane < n_box ? plane : 0);
+            vb = fetch4(i0 >= plane ? -plane : 0);
+        }
+        if (lane == 0) w1 = fetch1(i0 > 0 ? -1 : 0);
+        if (lane == 31) e1 = fetch1(i0 + 4 < n_box ? 4 : 3);
+    }
+    T wv = __shfl_up_sync(0xffffffffu, c.v[3], 1);
+    T ev = __shfl_down_sync(0xffffffffu, c.v[0], 1);
+    if (lane == 0) wv = w1;
+    if (lane == 31) ev = e1;
+    nb.w = {{wv, c.v[0], c.v[1], c.v[2]}};
+    nb.e = {{c.v[1], c.v[2], c.v[3], ev}};
+    nb.n = vn;
+    nb.s = vs;
+    nb.f = vf;
+    nb.b = vb;
+    return nb;
+}
+
 // (L p)_C for cell m of the chunk.
 template <class T, int NDIM>
 __device__ __forceinline__ T apply_L(unsigned fm, const V4<T>& c, const Nbrs<T>& nb, int m, const T* F) {

@@ -30,7 +30,7 @@ class osmodi_options(ctypes.Structure):
                 ("inner_max", ctypes.c_int), ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
                 ("sweeps_per_pass", ctypes.c_int), ("max_refine", ctypes.c_int), ("record_history", ctypes.c_int),
                 ("threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("profile", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("slab", ctypes.c_int), ("flat_sweeps", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class osmodi_result(ctypes.Structure):
@@ -279,6 +279,44 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Workspace holder for osmodi_solve_batched over a fixed list of plans."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        self._arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        n = int(lib().osmodi_batched_workspace_bytes(len(self.plans), self._arr))
+        if n == 0:
+            raise OsmodiError(E_INVALID, "osmodi_batched_workspace_bytes")
+        self.ws = torch.empty(n + 256, dtype=torch.uint8, device="cuda")
+
+    def solve(self, grads, ps, tol, max_iter=1 << 30, stream=None, check=True):
+        """osmodi_solve_batched; returns (status, [osmodi_result])"""
+        count = len(self.plans)
+        if len(grads) != count or len(ps) != count:
+            raise ValueError("one gradient and one pressure tensor per plan")
+        for g, p in zip(grads, ps):
+            _check_cuda(g, "grad")
+            _check_cuda(p, "p")
+        gdt = {_dtype_code(g) for g in grads}
+        pdt = {_dtype_code(p) for p in ps}
+        if len(gdt) != 1 or len(pdt) != 1:
+            raise TypeError("all gradients (and all pressures) must share one dtype")
+        ga = (ctypes.c_void_p * count)(*[g.data_ptr() for g in grads])
+        pa = (ctypes.c_void_p * count)(*[p.data_ptr() for p in ps])
+        res = (osmodi_result * count)()
+        ws = (self.ws.data_ptr() + 255) // 256 * 256
+        st = lib().osmodi_solve_batched(count, self._arr, ga, gdt.pop(), pa, pdt.pop(), float(tol),
+                                        int(min(max_iter, 2**31 - 1)), ws, _stream_ptr(stream), res)
+        if check and st < 0 and st != E_NAN_INPUT:
+            raise OsmodiError(st, "osmodi_solve_batched")
+        return st, list(res)
+
+
+def osmodi_solve_batched(plans, grads, ps, tol, max_iter=1 << 30, stream=None):
+    return Batch(plans).solve(grads, ps, tol, max_iter, stream)
 
 
 def osmodi_create(ndim, dims, spacing, mask=None, **opt) -> Plan:

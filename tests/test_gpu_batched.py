@@ -1,0 +1,144 @@
+"""The batched persistent solve against the oracle and against single
+solves.  Needs a GPU."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2311_16935_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def osm():
+    from paper_2311_16935_gb300 import build
+
+    build.build()
+    from paper_2311_16935_gb300 import osmodi
+
+    return osmodi
+
+
+def _rel(a, b, valid):
+    return float(np.linalg.norm(a[valid] - b[valid]) / max(np.linalg.norm(b[valid]), 1e-300))
+
+
+def _random_instances(n, seed, ndim=2):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        if ndim == 2:
+            shape = (int(rng.integers(3, 70)), int(rng.integers(5, 90)))
+            spacing = (float(rng.uniform(0.05, 0.2)), float(rng.uniform(0.05, 0.2)))
+        else:
+            shape = tuple(int(v) for v in rng.integers(3, 14, size=3))
+            spacing = (1.0, 1.0, 1.0) if i % 2 else (1.0, 1.3, 0.7)
+        valid = rng.random(shape) > rng.uniform(0.0, 0.3)
+        if not valid.any():
+            valid.flat[0] = True
+        f = rng.normal(size=(ndim,) + shape)
+        out.append((valid, spacing, f))
+    return out
+
+
+@pytest.mark.parametrize("precision", [2, 0])
+def test_batched_matches_oracle_2d(osm, precision):
+    inst = _random_instances(14, 1)
+    plans, grads, ps = [], [], []
+    for valid, spacing, f in inst:
+        plans.append(osm.Plan(2, valid.shape[::-1], spacing, torch.from_numpy(valid.astype(np.uint8)).cuda(),
+                              precision=precision))
+        grads.append(torch.from_numpy(f).cuda())
+        ps.append(torch.zeros(valid.shape, dtype=torch.float64, device="cuda"))
+    st, res = osm.Batch(plans).solve(grads, ps, 1e-12)
+    assert st == osm.OK, [r.as_dict() for r in res]
+    for (valid, spacing, f), p, r in zip(inst, ps, res):
+        want = oracle.solve_direct(oracle.Grid(valid, spacing), f)
+        got = p.cpu().numpy()
+        assert r.status == osm.OK and r.eps_R <= 1e-12
+        assert _rel(got, want, valid) < 1e-10
+        assert np.isnan(got[~valid]).all()
+
+
+def test_batched_equals_single_solves_and_isolates_bad_input(osm):
+    inst = _random_instances(9, 2)
+    plans, grads, ps, singles = [], [], [], []
+    for k, (valid, spacing, f) in enumerate(inst):
+        m = torch.from_numpy(valid.astype(np.uint8)).cuda()
+        plan = osm.Plan(2, valid.shape[::-1], spacing, m)
+        g = torch.from_numpy(f).float().cuda()
+        p1 = torch.zeros(valid.shape, dtype=torch.float64, device="cuda")
+        plan.solve(g, p1, 1e-11)
+        singles.append(p1.cpu().numpy())
+        plans.append(plan)
+        grads.append(g)
+        ps.append(torch.zeros(valid.shape, dtype=torch.float64, device="cuda"))
+    # instance 4 gets a NaN at a valid cell: it alone fails, untouched
+    bad = 4
+    vb = inst[bad][0]
+    j, i = np.argwhere(vb)[0]
+    grads[bad][0, j, i] = float("nan")
+    ps[bad].fill_(3.0)
+    st, res = osm.Batch(plans).solve(grads, ps, 1e-11)
+    assert st == osm.E_NAN_INPUT
+    for k, ((valid, spacing, f), p, r) in enumerate(zip(inst, ps, res)):
+        got = p.cpu().numpy()
+        if k == bad:
+            assert r.status == osm.E_NAN_INPUT and (got == 3.0).all()
+        else:
+            assert r.status == osm.OK
+            assert _rel(got, singles[k], valid) < 1e-9
+
+
+def test_batched_piv_snapshots(osm):
+    """Snapshots of the PIV-like workload (elliptical solid masks, FP32
+    gradients), reduced sizes so the oracle finishes quickly."""
+    probs = [inputs.piv_snapshot_2d(i, size_range=((64, 160), (64, 120))) for i in range(10)]
+    plans, grads, ps = [], [], []
+    for pr in probs:
+        plans.append(osm.Plan(2, pr.dims, pr.spacing, pr.mask.cuda()))
+        grads.append(pr.grad.cuda())
+        ps.append(torch.zeros(pr.mask.shape, dtype=torch.float64, device="cuda"))
+    st, res = osm.Batch(plans).solve(grads, ps, 1e-11)
+    assert st == osm.OK
+    for pr, p, r in zip(probs, ps, res):
+        valid = pr.mask.numpy().astype(bool)
+        grid = oracle.Grid(valid, pr.spacing)
+        want, it, e = oracle.solve_cg(grid, pr.grad.double().numpy(), tol=1e-14)
+        assert _rel(p.cpu().numpy(), want, valid) < 1e-9
+
+
+def test_batched_3d(osm):
+    inst = _random_instances(6, 3, ndim=3)
+    plans, grads, ps = [], [], []
+    for valid, spacing, f in inst:
+        plans.append(osm.Plan(3, valid.shape[::-1], spacing, torch.from_numpy(valid.astype(np.uint8)).cuda()))
+        grads.append(torch.from_numpy(f).cuda())
+        ps.append(torch.zeros(valid.shape, dtype=torch.float32, device="cuda"))
+    st, res = osm.Batch(plans).solve(grads, ps, 1e-10)
+    assert st == osm.OK
+    for (valid, spacing, f), p in zip(inst, ps):
+        want = oracle.solve_direct(oracle.Grid(valid, spacing), f)
+        assert _rel(p.cpu().numpy().astype(np.float64), want, valid) < 1e-6
+
+
+def test_batched_zero_gradient_and_repeat(osm):
+    """An instance with S = 0 finishes at once while the others continue;
+    repeating the call on the same workspace gives the same answer (to
+    rounding: instances with several connected components add their
+    per-component means with atomics, whose order varies)."""
+    inst = _random_instances(5, 4)
+    inst[2] = (inst[2][0], inst[2][1], np.zeros_like(inst[2][2]))
+    plans = [osm.Plan(2, v.shape[::-1], s, torch.from_numpy(v.astype(np.uint8)).cuda()) for v, s, f in inst]
+    batch = osm.Batch(plans)
+    outs = []
+    for rep in range(2):
+        grads = [torch.from_numpy(f).cuda() for v, s, f in inst]
+        ps = [torch.zeros(v.shape, dtype=torch.float64, device="cuda") for v, s, f in inst]
+        st, res = batch.solve(grads, ps, 1e-11)
+        assert st == osm.OK
+        assert res[2].inner_iters == 0 and res[2].eps_R == 0.0
+        outs.append([p.cpu().numpy() for p in ps])
+    for a, b, (v, s, f) in zip(outs[0], outs[1], inst):
+        np.testing.assert_allclose(a[v], b[v], rtol=1e-12, atol=1e-14)

@@ -266,6 +266,48 @@ OSMODI_API osmodi_status osmodi_plan_info(osmodi_plan plan, int64_t out[8]);
 OSMODI_API osmodi_status osmodi_plan_constants(osmodi_plan plan, double c[9], double F[3], double* a_tot);
 
 OSMODI_API void osmodi_destroy(osmodi_plan plan);
+
+/*
+ * The seed network (learned initial pressure).  A small 3D convolutional
+ * encoder-decoder (4 resolution levels, 16-64 channels, skip additions)
+ * maps the gradient field and the mask to a pressure guess P^0 that
+ * osmodi_solve then iterates to the usual tolerance (Algorithm 1 starts from
+ * any P^0; the answer does not depend on it).  BF16 weights and activations,
+ * FP32 accumulation on the tensor cores.  The network is not part of the
+ * paper's method; the solve that follows always runs to tolerance, and
+ * osmodi_result.seed_rel_dist reports how far the guess started.
+ *
+ * Inputs: 3D grids whose three sizes are multiples of 8; gradient and target
+ * as for osmodi_solve (3 planes, x fastest); mask_dev as for osmodi_create
+ * (NULL = all valid); spacing = the (isotropic) grid spacing.
+ * Parameters are one FP32 array of osmodi_net_param_count() values: per
+ * layer (e0, e1, e1b, e2, e2b, e3, m, m2, u2, u2b, u1, u1b, u0, out) the
+ * weights (taps, cin, cout) followed by the biases (cout).
+ */
+typedef struct osmodi_net_s* osmodi_net;
+OSMODI_API size_t osmodi_net_param_count(void);
+/* dims = {nx, ny, nz}; train = 1 also allocates gradients, Adam moments and
+ * activation gradients.  Parameters start undefined: call set_params. */
+OSMODI_API osmodi_status osmodi_net_create(const int64_t dims[3], int train, osmodi_net* out);
+OSMODI_API osmodi_status osmodi_net_set_params(osmodi_net net, const float* params_host);
+OSMODI_API osmodi_status osmodi_net_get_params(osmodi_net net, float* params_host);
+/* accumulated parameter gradients (training nets) */
+OSMODI_API osmodi_status osmodi_net_get_grads(osmodi_net net, float* grads_host);
+/* the normalised network output of the last forward (nx*ny*nz floats) */
+OSMODI_API osmodi_status osmodi_net_get_output(osmodi_net net, float* out_host);
+/* P^0 = network output * s into p_dev (0 on missing cells); asynchronous */
+OSMODI_API osmodi_status osmodi_net_forward(osmodi_net net, const void* grad_dev, int grad_dtype, const uint8_t* mask_dev,
+                                            double spacing, void* p_dev, int p_dtype, void* stream);
+/* forward + loss (mean over valid cells of the squared difference of the
+ * mean-removed normalised output and target/s) + backward; gradients are
+ * added to the accumulated ones.  loss_host may be NULL (else the call
+ * synchronises). */
+OSMODI_API osmodi_status osmodi_net_backward(osmodi_net net, const void* grad_dev, int grad_dtype, const uint8_t* mask_dev,
+                                             double spacing, const double* target_dev, double* loss_host, void* stream);
+/* one Adam step with the accumulated gradients divided by `batch`; clears them */
+OSMODI_API osmodi_status osmodi_net_adam(osmodi_net net, double lr, double beta1, double beta2, double eps, int batch,
+                                         void* stream);
+OSMODI_API void osmodi_net_destroy(osmodi_net net);
 OSMODI_API const char* osmodi_status_string(int status);
 /* Text of the last CUDA error seen by this thread (empty if none). */
 OSMODI_API const char* osmodi_last_cuda_error(void);

@@ -32,6 +32,7 @@ enum { kRun = 0, kConv = 1, kSegDone = 2, kInit = 3, kDone = 4, kFail = 5, kNaN 
 enum { TK_S = 0, TK_R = 1, TK_I = 2, TK_A = 3, TK_B = 4, TK_O = 5, kTickets = 6 };
 constexpr int kPartK = 3;  // doubles per tile partial
 constexpr int kTileThreads = 256;
+constexpr int kMaxCpt = 8;  // chunks per thread per tile (tile = 256 * cpt chunks)
 
 struct BInst {
     int64_t off;  // first cell of the instance's padded box in the arena
@@ -78,7 +79,7 @@ struct BParams {
     double* comp;      // per component: [sum r, sum p, sum p0]
     double *b64, *p64a, *p64b;
     void *r, *x, *q, *pA, *pB;  // inner type T
-    int count, ntiles, max_refine;
+    int count, ntiles, max_refine, cpt;
     long long max_iter, inner_max;
     double tol, inner_tol;
 };
@@ -176,7 +177,7 @@ __device__ __forceinline__ double* comp_of(const BParams& P, const BInst& I, int
 
 // ---- the persistent kernel ----
 template <class T, int NDIM, class TG, class TP>
-__global__ void __launch_bounds__(kTileThreads) k_batched(BParams P) {
+__global__ void __launch_bounds__(kTileThreads, 3) k_batched(BParams P) {
     const int lane = threadIdx.x & 31;
     T* const r_all = (T*)P.r;
     T* const x_all = (T*)P.x;
@@ -249,8 +250,10 @@ __global__ void __launch_bounds__(kTileThreads) k_batched(BParams P) {
             const double* b = P.b64 + I.off;
             const Geo<double> g = inst_geo<double>(I);
             double acc[3] = {0.0, 0.0, 0.0};
-            const bool act = threadIdx.x < tl.nchunks;
-            const int64_t i0 = (tl.chunk0 + threadIdx.x) * 4;
+            for (int j = 0; j < P.cpt; ++j) {
+            const int cc = j * kTileThreads + threadIdx.x;
+            const bool act = cc < tl.nchunks;
+            const int64_t i0 = (tl.chunk0 + cc) * 4;
             const uint32_t cw = act ? *reinterpret_cast<const uint32_t*>(I.code8 + i0) : 0u;
             V4<double> c = act ? ld4cg(pin + i0) : zero4<double>();
             if (has_e && act) {
@@ -292,6 +295,7 @@ __global__ void __launch_bounds__(kTileThreads) k_batched(BParams P) {
                 if (has_e) st4(pout + i0, c);
                 st4(rr + i0, rv);
             }
+            }
             double tot[3];
             if (tile_done<3>(P, t, I, S, TK_R, acc, tot) && threadIdx.x == 0) {
                 if (has_e) S->p64par = __ldcg(&S->p64par) ^ 1;
@@ -329,8 +333,10 @@ __global__ void __launch_bounds__(kTileThreads) k_batched(BParams P) {
             T* xx = x_all + I.off;
             const double mean1 = I.label ? 0.0 : __ldcg(&S->rsum) / I.n_valid;
             double acc[1] = {0.0};
-            if (threadIdx.x < tl.nchunks) {
-                const int64_t i0 = (tl.chunk0 + threadIdx.x) * 4;
+            for (int j = 0; j < P.cpt; ++j) {
+                const int cc = j * kTileThreads + threadIdx.x;
+                if (cc >= tl.nchunks) break;
+                const int64_t i0 = (tl.chunk0 + cc) * 4;
                 const uint32_t cw = *reinterpret_cast<const uint32_t*>(I.code8 + i0);
                 V4<T> rv = ld4cg(rr + i0);
                 T part = T(0);
@@ -350,7 +356,7 @@ __global__ void __launch_bounds__(kTileThreads) k_batched(BParams P) {
                 }
                 st4(rr + i0, rv);
                 st4(xx + i0, zero4<T>());
-                acc[0] = (double)part;
+                acc[0] += (double)part;
             }
             double tot[1];
             if (tile_done<1>(P, t, I, S, TK_I, acc, tot)) {
@@ -406,8 +412,10 @@ __global__ void __launch_bounds__(kTileThreads) k_batched(BParams P) {
                 T* x = x_all + I.off;
                 const Geo<T> g = inst_geo<T>(I);
                 double acc[1] = {0.0};
-                const bool act = threadIdx.x < tl.nchunks;
-                const int64_t i0 = (tl.chunk0 + threadIdx.x) * 4;
+                for (int j = 0; j < P.cpt; ++j) {
+                const int cc = j * kTileThreads + threadIdx.x;
+                const bool act = cc < tl.nchunks;
+                const int64_t i0 = (tl.chunk0 + cc) * 4;
                 V4<T> pold = zero4<T>();
                 if (act && !first) {
                     pold = ld4cg(po + i0);
@@ -448,8 +456,9 @@ __global__ void __launch_bounds__(kTileThreads) k_batched(BParams P) {
                         }
                         st4(pn + i0, c);
                         st4(q + i0, qv);
-                        acc[0] = (double)part;
+                        acc[0] += (double)part;
                     }
+                }
                 }
                 double tot[1];
                 if (tile_done<1>(P, t, I, S, TK_A, acc, tot) && threadIdx.x == 0) {
@@ -481,8 +490,10 @@ __global__ void __launch_bounds__(kTileThreads) k_batched(BParams P) {
                 T* r = r_all + I.off;
                 const T* q = q_all + I.off;
                 double acc[1] = {0.0};
-                if (threadIdx.x < tl.nchunks) {
-                    const int64_t i0 = (tl.chunk0 + threadIdx.x) * 4;
+                for (int j = 0; j < P.cpt; ++j) {
+                    const int cc = j * kTileThreads + threadIdx.x;
+                    if (cc >= tl.nchunks) break;
+                    const int64_t i0 = (tl.chunk0 + cc) * 4;
                     V4<T> rv = ld4cg(r + i0);
                     const V4<T> qv = ld4cg(q + i0);
                     T part = T(0);
@@ -492,7 +503,7 @@ __global__ void __launch_bounds__(kTileThreads) k_batched(BParams P) {
                         part += rv.v[m] * rv.v[m];
                     }
                     st4(r + i0, rv);
-                    acc[0] = (double)part;
+                    acc[0] += (double)part;
                 }
                 double tot[1];
                 if (tile_done<1>(P, t, I, S, TK_B, acc, tot) && threadIdx.x == 0) {
@@ -555,6 +566,13 @@ __global__ void __launch_bounds__(kTileThreads) k_batched(BParams P) {
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// chunks per thread per tile: the plan's `slab` option doubles as the batched
+// tile depth (1..8); default 4 (4096-cell tiles)
+static int batched_cpt(osmodi_plan p) {
+    const int v = p->opt.slab;
+    return v >= 1 && v <= kMaxCpt ? v : 4;
+}
+
 struct Layout {
     std::vector<BInst> inst;
     std::vector<BTile> tiles;
@@ -565,7 +583,7 @@ struct Layout {
     size_t o_inst, o_tiles, o_st, o_gl, o_part, o_comp, o_b64, o_pa, o_pb, o_r, o_x, o_q, o_pA, o_pB;
 };
 
-static bool build_layout(int count, const osmodi_plan* plans, size_t tsize, Layout* L) {
+static bool build_layout(int count, const osmodi_plan* plans, size_t tsize, int cpt, Layout* L) {
     L->inst.resize(count);
     L->tiles.clear();
     int64_t off = 0;
@@ -595,11 +613,12 @@ static bool build_layout(int count, const osmodi_plan* plans, size_t tsize, Layo
         comp += (int)p->n_comp;
         I.tile0 = (int)L->tiles.size();
         const int64_t nch = p->n_chunks;
-        for (int64_t c = 0; c < nch; c += kTileThreads) {
+        const int64_t tile = (int64_t)kTileThreads * cpt;
+        for (int64_t c = 0; c < nch; c += tile) {
             BTile t;
             t.inst = i;
             t.chunk0 = c;
-            t.nchunks = (int)std::min<int64_t>(kTileThreads, nch - c);
+            t.nchunks = (int)std::min<int64_t>(tile, nch - c);
             L->tiles.push_back(t);
         }
         I.ntiles = (int)L->tiles.size() - I.tile0;
@@ -649,7 +668,8 @@ static osmodi_status run_batched(int count, const osmodi_plan* plans, const void
                                  int pdt, double tol, int max_iter, void* ws, cudaStream_t s, osmodi_result* results) {
     auto t0 = std::chrono::steady_clock::now();
     Layout L;
-    build_layout(count, plans, sizeof(T), &L);
+    const int cpt = batched_cpt(plans[0]);
+    build_layout(count, plans, sizeof(T), cpt, &L);
     for (int i = 0; i < count; ++i) {
         L.inst[i].grad = grads[i];
         L.inst[i].p_user = ps[i];
@@ -671,6 +691,7 @@ static osmodi_status run_batched(int count, const osmodi_plan* plans, const void
     P.pA = base + L.o_pA;
     P.pB = base + L.o_pB;
     P.count = count;
+    P.cpt = cpt;
     P.ntiles = (int)L.tiles.size();
     const osmodi_options& o = plans[0]->opt;
     P.max_refine = o.precision == OSMODI_FP32_REFINE ? o.max_refine : (o.precision == OSMODI_FP32 ? 1 : 4);
@@ -742,7 +763,7 @@ extern "C" size_t osmodi_batched_workspace_bytes(int count, const osmodi_plan* p
     for (int i = 0; i < count; ++i)
         if (!plans[i]) return 0;
     Layout L;
-    build_layout(count, plans, plans[0]->opt.precision == OSMODI_FP64 ? 8 : 4, &L);
+    build_layout(count, plans, plans[0]->opt.precision == OSMODI_FP64 ? 8 : 4, batched_cpt(plans[0]), &L);
     return L.bytes;
 }
 

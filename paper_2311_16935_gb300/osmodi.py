@@ -77,6 +77,19 @@ _SIGS = {
     "osmodi_kernel_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_plan_constants": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_destroy": (None, [ctypes.c_void_p]),
+    "osmodi_net_param_count": (ctypes.c_size_t, []),
+    "osmodi_net_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "osmodi_net_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_net_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_net_get_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_net_get_output": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_net_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_double, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "osmodi_net_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_net_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
+    "osmodi_net_destroy": (None, [ctypes.c_void_p]),
     "osmodi_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "osmodi_last_cuda_error": (ctypes.c_char_p, []),
 }
@@ -317,6 +330,102 @@ class Batch:
 
 def osmodi_solve_batched(plans, grads, ps, tol, max_iter=1 << 30, stream=None):
     return Batch(plans).solve(grads, ps, tol, max_iter, stream)
+
+
+class Net:
+    """The seed network (osmodi_net_*): parameters live on the device."""
+
+    def __init__(self, dims, train=False):
+        d = (ctypes.c_int64 * 3)(*[int(v) for v in dims])
+        h = ctypes.c_void_p()
+        st = lib().osmodi_net_create(d, 1 if train else 0, ctypes.byref(h))
+        if st != OK:
+            raise OsmodiError(st, "osmodi_net_create")
+        self.handle = h
+        self.dims = tuple(int(v) for v in dims)
+        self.train = train
+
+    @staticmethod
+    def param_count() -> int:
+        return int(lib().osmodi_net_param_count())
+
+    def set_params(self, params):
+        import numpy as np
+
+        a = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        if a.size != self.param_count():
+            raise ValueError("wrong parameter count")
+        st = lib().osmodi_net_set_params(self.handle, a.ctypes.data)
+        if st != OK:
+            raise OsmodiError(st, "osmodi_net_set_params")
+
+    def get_params(self):
+        import numpy as np
+
+        a = np.empty(self.param_count(), dtype=np.float32)
+        st = lib().osmodi_net_get_params(self.handle, a.ctypes.data)
+        if st != OK:
+            raise OsmodiError(st, "osmodi_net_get_params")
+        return a
+
+    def get_grads(self):
+        import numpy as np
+
+        a = np.empty(self.param_count(), dtype=np.float32)
+        st = lib().osmodi_net_get_grads(self.handle, a.ctypes.data)
+        if st != OK:
+            raise OsmodiError(st, "osmodi_net_get_grads")
+        return a
+
+    def get_output(self):
+        import numpy as np
+
+        nx, ny, nz = self.dims
+        a = np.empty(nx * ny * nz, dtype=np.float32)
+        st = lib().osmodi_net_get_output(self.handle, a.ctypes.data)
+        if st != OK:
+            raise OsmodiError(st, "osmodi_net_get_output")
+        return a.reshape(nz, ny, nx)
+
+    def forward(self, grad, mask, spacing, p, stream=None):
+        _check_cuda(grad, "grad")
+        _check_cuda(p, "p")
+        mptr = None if mask is None else mask.data_ptr()
+        st = lib().osmodi_net_forward(self.handle, grad.data_ptr(), _dtype_code(grad), mptr, float(spacing),
+                                      p.data_ptr(), _dtype_code(p), _stream_ptr(stream))
+        if st != OK:
+            raise OsmodiError(st, "osmodi_net_forward")
+
+    def backward(self, grad, mask, spacing, target, want_loss=True, stream=None):
+        _check_cuda(grad, "grad")
+        _check_cuda(target, "target")
+        if target.dtype != torch.float64:
+            raise TypeError("target must be float64")
+        mptr = None if mask is None else mask.data_ptr()
+        loss = ctypes.c_double(0.0)
+        st = lib().osmodi_net_backward(self.handle, grad.data_ptr(), _dtype_code(grad), mptr, float(spacing),
+                                       target.data_ptr(), ctypes.byref(loss) if want_loss else None,
+                                       _stream_ptr(stream))
+        if st != OK:
+            raise OsmodiError(st, "osmodi_net_backward")
+        return loss.value
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, batch=1, stream=None):
+        st = lib().osmodi_net_adam(self.handle, float(lr), float(beta1), float(beta2), float(eps), int(batch),
+                                   _stream_ptr(stream))
+        if st != OK:
+            raise OsmodiError(st, "osmodi_net_adam")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().osmodi_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def osmodi_create(ndim, dims, spacing, mask=None, **opt) -> Plan:

@@ -1,0 +1,123 @@
+"""Training and use of the seed network (learned initial pressure).
+
+The network (built in the C library, ``osmodi_net_*``) maps the gradient
+field and the mask to a pressure guess; training pairs are made by the
+method itself: synthetic Gaussian-blob gradient fields solved by
+``osmodi_solve`` to a tight tolerance.  A seeded solve runs the usual
+iteration to the same tolerance from the network's guess and reports how far
+the guess started (``seed_rel_dist``).
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import inputs
+from . import osmodi as osm
+
+# name, kind, cin, cout (the order of the library's parameter array)
+LAYERS = [("e0", "conv3", 4, 16), ("e1", "down", 16, 32), ("e1b", "conv3", 32, 32), ("e2", "down", 32, 48),
+          ("e2b", "conv3", 48, 48), ("e3", "down", 48, 64), ("m", "conv3", 64, 64), ("m2", "conv3", 64, 64),
+          ("u2", "up", 64, 48), ("u2b", "conv3", 48, 48), ("u1", "up", 48, 32), ("u1b", "conv3", 32, 32),
+          ("u0", "up", 32, 16), ("out", "conv1", 16, 1)]
+TAPS = {"conv3": 27, "down": 8, "up": 8, "conv1": 1}
+
+
+def init_params(seed=0) -> np.ndarray:
+    """He-normal weights (taps, cin, cout) and zero biases, packed per layer."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, kind, cin, cout in LAYERS:
+        taps = TAPS[kind]
+        fan_in = cin * (taps if kind != "up" else 1)
+        std = math.sqrt(2.0 / fan_in) if kind != "conv1" else math.sqrt(1.0 / fan_in)
+        parts.append((rng.normal(size=(taps, cin, cout)) * std).ravel())
+        parts.append(np.zeros(cout))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def unpack(params: np.ndarray) -> dict:
+    out = {}
+    off = 0
+    for name, kind, cin, cout in LAYERS:
+        n = TAPS[kind] * cin * cout
+        out[name + ".w"] = params[off:off + n].reshape(TAPS[kind], cin, cout)
+        off += n
+        out[name + ".b"] = params[off:off + cout]
+        off += cout
+    return out
+
+
+def blob_problem(n, seed, device="cuda", noise=0.03):
+    """The Gaussian-blob generator scaled to an n^3 box (widths 5-40 cells of
+    a 500^3 box scaled by n/500, at least 1.5 cells)."""
+    scale = n / 500.0
+    lo, hi = max(1.5, 5.0 * scale), max(3.0, 40.0 * scale)
+    return inputs.gaussian_blobs_3d(n=(n, n, n), noise=noise, seed=seed, width_range=(lo, hi), device=device,
+                                    dtype=torch.float32)
+
+
+def make_pairs(count, n, seed0=1000, tol=1e-8, device="cuda"):
+    """Gradient fields and their converged pressures (targets)."""
+    plan = osm.Plan(3, (n, n, n), (1.0, 1.0, 1.0), None, precision=osm.FP32_REFINE)
+    pairs = []
+    for i in range(count):
+        prob = blob_problem(n, seed0 + i, device)
+        p = torch.zeros((n, n, n), dtype=torch.float64, device=device)
+        r = plan.solve(prob.grad, p, tol)
+        if r.status != osm.OK:
+            raise RuntimeError(f"target solve failed: {r.as_dict()}")
+        pairs.append((prob.grad, p))
+    plan.close()
+    return pairs
+
+
+def train(pairs, n, epochs=4, lr=1e-3, batch=4, seed=0, log=None, params=None):
+    """Adam on the mean-removed MSE of the normalised pressure; returns the
+    trained parameters and the loss history (per epoch)."""
+    net = osm.Net((n, n, n), train=True)
+    net.set_params(init_params(seed) if params is None else params)
+    rng = np.random.default_rng(seed)
+    hist = []
+    k = 0
+    for ep in range(epochs):
+        order = rng.permutation(len(pairs))
+        tot = 0.0
+        for j, idx in enumerate(order):
+            g, p = pairs[idx]
+            tot += net.backward(g, None, 1.0, p, want_loss=True)
+            k += 1
+            if k % batch == 0:
+                net.adam(lr, batch=batch)
+        hist.append(tot / len(pairs))
+        if log:
+            log(f"epoch {ep} loss {hist[-1]:.5f}")
+    out = net.get_params()
+    net.close()
+    return out, hist
+
+
+def seeded_solve(params, grad, n, tol, plan=None, net=None):
+    """P^0 from the network, then osmodi_solve to tol.  Returns (p, result,
+    zero-start result) -- the zero-start solve of the same problem for
+    comparison."""
+    own_plan = plan is None
+    own_net = net is None
+    if own_plan:
+        plan = osm.Plan(3, (n, n, n), (1.0, 1.0, 1.0), None, precision=osm.FP32_REFINE)
+    if own_net:
+        net = osm.Net((n, n, n), train=False)
+        net.set_params(params)
+    p = torch.empty((n, n, n), dtype=torch.float64, device=grad.device)
+    net.forward(grad, None, 1.0, p)
+    r_seed = plan.solve(grad, p, tol)
+    p0 = torch.zeros_like(p)
+    r_zero = plan.solve(grad, p0, tol)
+    if own_plan:
+        plan.close()
+    if own_net:
+        net.close()
+    return p, r_seed, r_zero

@@ -1,0 +1,133 @@
+"""The seed network's GPU kernels against the CPU reference (forward and
+parameter gradients, BF16 tolerance), and what the trained network gains the
+solve.  Needs a GPU."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import net as onet
+from paper_2311_16935_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def osm():
+    from paper_2311_16935_gb300 import build
+
+    build.build()
+    from paper_2311_16935_gb300 import osmodi
+
+    return osmodi
+
+
+def bf16_round(a):
+    """Round to the nearest bfloat16 (ties to even), returned as float64."""
+    u = np.ascontiguousarray(np.asarray(a, dtype=np.float32)).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _problem(n, seed):
+    rng = np.random.default_rng(seed)
+    z, y, x = np.meshgrid(*[np.arange(n)] * 3, indexing="ij")
+    valid = ((x - n / 2) ** 2 + (y - n / 3) ** 2 + (z - n / 2) ** 2 > (n / 5) ** 2) & (rng.random((n, n, n)) > 0.05)
+    f = rng.normal(size=(3, n, n, n)).astype(np.float32)
+    target = np.sin(x / 3.0) * np.cos(y / 4.0) + 0.1 * rng.normal(size=(n, n, n))
+    return valid, f, target
+
+
+def _params(seed):
+    from paper_2311_16935_gb300 import seednet
+
+    p = seednet.init_params(seed)
+    rng = np.random.default_rng(seed + 1)
+    d = seednet.unpack(p)
+    for k in d:
+        if k.endswith(".b"):
+            d[k][:] = rng.normal(size=d[k].shape) * 0.05
+    return p, d
+
+
+def _oracle_params(d):
+    out = {}
+    for k, v in d.items():
+        out[k] = bf16_round(v) if k.endswith(".w") else np.asarray(v, dtype=np.float32).astype(np.float64)
+    return out
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-30))
+
+
+def test_forward_matches_reference(osm):
+    n = 16
+    valid, f, target = _problem(n, 1)
+    params, d = _params(2)
+    net = osm.Net((n, n, n), train=False)
+    net.set_params(params)
+    g = torch.from_numpy(f).cuda()
+    m = torch.from_numpy(valid.astype(np.uint8)).cuda()
+    p = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+    net.forward(g, m, 1.0, p)
+    got = net.get_output()
+    x, s = onet.features(f.astype(np.float64), valid, 1.0)
+    want, _ = onet.forward(_oracle_params(d), bf16_round(x))
+    assert _rel(got, want) < 3e-2
+    np.testing.assert_allclose(p.cpu().numpy()[valid], got[valid] * s, rtol=1e-5, atol=1e-6 * s)
+    net.close()
+
+
+def test_parameter_gradients_match_reference(osm):
+    n = 16
+    valid, f, target = _problem(n, 3)
+    params, d = _params(4)
+    net = osm.Net((n, n, n), train=True)
+    net.set_params(params)
+    g = torch.from_numpy(f).cuda()
+    m = torch.from_numpy(valid.astype(np.uint8)).cuda()
+    tgt = torch.from_numpy(target).cuda()
+    loss = net.backward(g, m, 1.0, tgt)
+    grads = net.get_grads()
+    x, s = onet.features(f.astype(np.float64), valid, 1.0)
+    op = _oracle_params(d)
+    # the GPU stores activations and MMA operands in BF16: the reference
+    # quantises the same stored values (so both take the same ReLU decisions)
+    out, act = onet.forward(op, bf16_round(x), store=bf16_round)
+    L, gl = onet.loss(out, target / s, valid)
+    ref = onet.backward(op, act, gl, operand=bf16_round)
+    assert loss == pytest.approx(L, rel=1e-2)
+    from paper_2311_16935_gb300 import seednet
+
+    gd = seednet.unpack(grads)
+    scale = max(np.abs(v).max() for v in ref.values())
+    worst = {}
+    for k in ref:
+        if k == "out.b":  # exactly 0 (the loss ignores constants): compare absolutely
+            assert abs(float(gd[k][0])) <= 1e-5 * scale, (gd[k], ref[k])
+            continue
+        worst[k] = _rel(gd[k], ref[k])
+    bad = {k: v for k, v in worst.items() if v > 2e-2}
+    assert not bad, worst
+    net.close()
+
+
+def test_training_reduces_loss_and_seed_helps(osm):
+    """Train on a few method-solved pairs at 32^3, then seed held-out solves:
+    the guess starts closer than zero and the seeded solve needs fewer CG
+    iterations to the same tolerance."""
+    from paper_2311_16935_gb300 import seednet
+
+    n = 32
+    pairs = seednet.make_pairs(24, n, seed0=2000, tol=1e-9)
+    params, hist = seednet.train(pairs, n, epochs=25, lr=2e-3, batch=4, seed=0)
+    assert hist[-1] < 0.5 * hist[0], hist
+    dists, saved = [], []
+    for i in range(4):
+        prob = seednet.blob_problem(n, 9000 + i)
+        p, r_seed, r_zero = seednet.seeded_solve(params, prob.grad, n, 1e-9)
+        assert r_seed.status == osm.OK and r_zero.status == osm.OK
+        dists.append(r_seed.seed_rel_dist)
+        saved.append(r_zero.inner_iters - r_seed.inner_iters)
+    assert np.mean(dists) < 0.9, dists
+    assert np.mean(saved) > 0, saved

@@ -278,7 +278,8 @@ static void orc_project(int64_t n, const int32_t* label, int64_t ncomp, const do
  * every connected component (the operator's null space), starting from P
  * (P = 0 reproduces the paper's P^0 = 0).  The true residual replaces the
  * recursive one every 50 iterations.  Stops when
- * ||S - (I - T) P|| / ||S|| <= tol or after maxit iterations.
+ * ||S - (I - T) P|| / ||S|| <= tol, after maxit iterations, or when the true
+ * residual has not halved for 1000 iterations (rounding floor reached).
  * On return P has zero mean on every component and NaN on missing cells;
  * info[0] = iterations, info[1] = final relative residual.
  */
@@ -310,11 +311,14 @@ int orc_solve_cg(int ndim, const int64_t dims[3], const uint8_t* valid, const do
         memcpy(p, r, sizeof(double) * (size_t)n);
         double rr = orc_dot(valid, n, r, r);
         rel = sqrt(rr) / snorm;
+        double best_true = rel;
+        int64_t last_gain = 0;
         while (rel > tol && it < maxit) {
             orc_apply(ndim, dims, valid, A, a_tot, 2, p, q);
             double pq = orc_dot(valid, n, p, q);
             if (!(pq > 0.0)) break;
             double alpha = rr / pq;
+#pragma omp parallel for schedule(static)
             for (int64_t c2 = 0; c2 < n; ++c2) {
                 P[c2] += alpha * p[c2];
                 r[c2] -= alpha * q[c2];
@@ -324,11 +328,21 @@ int orc_solve_cg(int ndim, const int64_t dims[3], const uint8_t* valid, const do
                 orc_apply(ndim, dims, valid, A, a_tot, 2, P, q);
                 for (int64_t c2 = 0; c2 < n; ++c2) r[c2] = valid[c2] ? S[c2] - q[c2] : 0.0;
                 orc_project(n, label, ncomp, cnt, r, sum);
+                /* stop once rounding has stalled the true residual: no 2x
+                   improvement over the last 20 checks (1000 iterations) */
+                double tr = sqrt(orc_dot(valid, n, r, r)) / snorm;
+                if (tr < best_true * 0.5) {
+                    best_true = tr;
+                    last_gain = it;
+                } else if (it - last_gain >= 1000) {
+                    break;
+                }
             }
             double rr_new = orc_dot(valid, n, r, r);
             double beta = rr_new / rr;
             rr = rr_new;
             rel = sqrt(rr) / snorm;
+#pragma omp parallel for schedule(static)
             for (int64_t c2 = 0; c2 < n; ++c2) p[c2] = r[c2] + beta * p[c2];
         }
         /* report the true residual, not the recursive one */

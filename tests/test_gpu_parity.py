@@ -200,7 +200,7 @@ def test_sincos_sphere_small(osm):
     prob = inputs.sincos_3d(n=40, mask_radius=0.5 * 40 / 128 * 4)
     valid = prob.mask.numpy().astype(bool)
     grid = oracle.Grid(valid, prob.spacing)
-    want, it, r = oracle.solve_cg(grid, prob.grad.double().numpy(), tol=1e-14)
+    want, it, r = oracle.solve_cg(grid, prob.grad.double().numpy(), tol=1e-14, maxit=20000)
     plan, res, got = _solve(osm, prob.grad, prob.mask.numpy(), prob.spacing, 1e-12, precision=2)
     assert res.status == osm.OK, res.as_dict()
     assert _rel(got, want, valid) < 1e-10

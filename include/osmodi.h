@@ -106,7 +106,9 @@ typedef struct {
                             durations readable with osmodi_kernel_stats */
     int slab;            /* z-planes per work item of the tiled 3D sweep kernel (0 = tuned) */
     int flat_sweeps;     /* 1 (default) = flat grid-stride sweep kernel; 0 = z-marching tiled one */
-    int reserved[2];
+    int autotune;        /* 1 = look the launch geometry up in the autotune cache at plan
+                            creation (see osmodi_autotune) */
+    int reserved[1];
 } osmodi_options;
 
 typedef struct {
@@ -256,6 +258,29 @@ OSMODI_API osmodi_status osmodi_residual(osmodi_plan plan, const void* grad_dev,
  * residual-update kernel (r -= alpha q, r.r); out[4] / out[5]: the FP64
  * residual kernel of the refinement loop; out[6] / out[7]: reserved (0). */
 OSMODI_API osmodi_status osmodi_kernel_stats(osmodi_plan plan, double out[8]);
+
+/*
+ * Autotuner.  osmodi_autotune times short bursts of CG iterations on this
+ * plan (synthetic right-hand side, the caller's workspace) for every
+ * candidate launch geometry -- grid of the stencil kernel (2..5 blocks per
+ * SM), grid of the update kernel (4..8 per SM), flat or z-marching stencil
+ * kernel -- keeps the fastest in the plan, and records it in the cache file
+ * (cache_path, or $OSMODI_AUTOTUNE_CACHE, or ~/.cache/osmodi_autotune.txt;
+ * NULL-safe) keyed by GPU name, ndim, log2 of the cell count and precision.
+ * Plans created with options.autotune = 1 read that cache.  ms_out (may be
+ * NULL) receives the best time per CG iteration.  Synchronous.
+ *
+ * osmodi_autotune_batched picks the tile depth of osmodi_solve_batched (1, 2,
+ * 4 or 8 chunks of 4 cells per thread) by timing the batched solve capped at
+ * a few iterations on the caller's problems; the choice is stored in
+ * plans[0] (the batched solve reads it from there).  The caller's pressure
+ * buffers are overwritten.
+ */
+OSMODI_API osmodi_status osmodi_autotune(osmodi_plan plan, void* workspace_dev, void* stream, const char* cache_path,
+                                         double* ms_out);
+OSMODI_API osmodi_status osmodi_autotune_batched(int count, const osmodi_plan* plans, const void* const* grads,
+                                                 int grad_dtype, void* const* ps, int p_dtype, void* workspace_dev,
+                                                 void* stream, int* tile_depth_out);
 
 /* Plan facts: out[0] nx, [1] ny, [2] nz, [3] valid cells, [4] connected
  * components, [5] padded row pitch, [6] padded cells, [7] launch blocks. */

@@ -763,8 +763,38 @@ extern "C" size_t osmodi_batched_workspace_bytes(int count, const osmodi_plan* p
     for (int i = 0; i < count; ++i)
         if (!plans[i]) return 0;
     Layout L;
-    build_layout(count, plans, plans[0]->opt.precision == OSMODI_FP64 ? 8 : 4, batched_cpt(plans[0]), &L);
+    // sized for the finest tiling the autotuner may pick
+    build_layout(count, plans, plans[0]->opt.precision == OSMODI_FP64 ? 8 : 4, 1, &L);
     return L.bytes;
+}
+
+extern "C" osmodi_status osmodi_autotune_batched(int count, const osmodi_plan* plans, const void* const* grads, int grad_dtype,
+                                                 void* const* ps, int p_dtype, void* workspace, void* stream, int* depth_out) {
+    if (count <= 0 || !plans || !plans[0]) return OSMODI_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    double best = 1e300;
+    int pick = 4;
+    const int saved = plans[0]->opt.slab;
+    for (int cpt : {1, 2, 4, 8}) {
+        plans[0]->opt.slab = cpt;
+        OSM_CUDA(cudaStreamSynchronize(s));
+        auto t0 = std::chrono::steady_clock::now();
+        osmodi_status st = osmodi_solve_batched(count, plans, grads, grad_dtype, ps, p_dtype, 1e-300, 48, workspace, stream,
+                                                nullptr);
+        auto t1 = std::chrono::steady_clock::now();
+        if (st < 0 && st != OSMODI_E_NAN_INPUT) {
+            plans[0]->opt.slab = saved;
+            return st;
+        }
+        const double ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        if (ms < best) {
+            best = ms;
+            pick = cpt;
+        }
+    }
+    plans[0]->opt.slab = pick;
+    if (depth_out) *depth_out = pick;
+    return OSMODI_OK;
 }
 
 extern "C" osmodi_status osmodi_solve_batched(int count, const osmodi_plan* plans, const void* const* grads, int grad_dtype,

@@ -302,6 +302,7 @@ namespace osm {
 int tuned_blocks_per_sm(int ndim, int threads);  // solve.cu
 int tiled_blocks_per_sm(int ndim, int requested); // solve.cu
 void sweep_blocks_per_sm(int ndim, bool fp64, int* bps_a, int* bps_b);  // solve.cu
+void apply_tuned(osmodi_plan p);                                        // solve.cu
 }
 
 extern "C" osmodi_status osmodi_create(int ndim, const int64_t dims[3], const double spacing[3], const uint8_t* mask_dev,
@@ -467,6 +468,7 @@ extern "C" osmodi_status osmodi_create(int ndim, const int64_t dims[3], const do
         const int64_t gt = std::min<int64_t>((int64_t)p->num_sms * tiled_blocks_per_sm(ndim, o.blocks_per_sm), items);
         p->launch.blocks_tiled = (int)std::max<int64_t>(1, std::min<int64_t>(gt, kMaxBlocks));
     }
+    if (o.autotune) apply_tuned(p);
     *out = p;
     return OSMODI_OK;
 }

@@ -21,7 +21,12 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <string>
+#include <sys/stat.h>
+#include <vector>
 
 #include "internal.cuh"
 #include "stencil.cuh"
@@ -700,6 +705,80 @@ __global__ void __launch_bounds__(512) k_jacobi(const T* __restrict__ e_in, T* _
     }
 }
 
+
+// k Jacobi sweeps on M~ e = rhs fused in one pass (ghost-zone temporal
+// blocking): a block stages its tile plus a k-cell halo of e (and a
+// (k-1)-cell halo of rhs and the codes) in shared memory, sweeps k times on a
+// region that shrinks by one cell per sweep, and writes the interior.  Each
+// sweep computes exactly what k_jacobi computes, in the same order.
+constexpr int JTX = 32, JTY = 8;
+
+template <class T, int NDIM>
+__global__ void __launch_bounds__(256) k_jacobi_fused(const T* __restrict__ e_in, T* __restrict__ e_out,
+                                                      const T* __restrict__ rhs, const uint32_t* __restrict__ code32,
+                                                      int64_t px, int64_t ny, int64_t nz, int k, TableT<T> tabv) {
+    extern __shared__ __align__(16) unsigned char jsm[];
+    __shared__ T tab[3][kClasses];
+    for (int t = threadIdx.x; t < 3 * kClasses; t += blockDim.x) tab[t / kClasses][t % kClasses] = tabv.anp1[t / kClasses][t % kClasses];
+    const int TZ = NDIM == 3 ? 4 : 1;
+    const int hz = NDIM == 3 ? k : 0;
+    const int SX = JTX + 2 * k, SY = JTY + 2 * k, SZ = TZ + 2 * hz;
+    const int ncell = SX * SY * SZ;
+    T* bufA = reinterpret_cast<T*>(jsm);
+    T* bufB = bufA + ncell;
+    T* rs = bufB + ncell;
+    uint32_t* cs = reinterpret_cast<uint32_t*>(rs + ncell);
+    const int64_t x0 = (int64_t)blockIdx.x * JTX - k, y0 = (int64_t)blockIdx.y * JTY - k;
+    const int64_t z0 = (int64_t)blockIdx.z * TZ - hz;
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        const int lx = c % SX, ly = (c / SX) % SY, lz = c / (SX * SY);
+        const int64_t gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+        const bool in = gx >= 0 && gy >= 0 && gz >= 0 && gx < px && gy < ny && gz < nz;
+        const int64_t gi = in ? (gz * ny + gy) * px + gx : 0;
+        bufA[c] = in ? e_in[gi] : T(0);
+        rs[c] = in ? rhs[gi] : T(0);
+        cs[c] = in ? code32[gi] : 0u;
+    }
+    __syncthreads();
+    const T inv = T(1) / tabv.a_tot;
+    T* cur = bufA;
+    T* nxt = bufB;
+    for (int sw = 1; sw <= k; ++sw) {
+        const int m = sw;  // cells within m of the tile edge are not updated in this sweep
+        const int mz = NDIM == 3 ? sw : 0;
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+            const int lx = c % SX, ly = (c / SX) % SY, lz = c / (SX * SY);
+            if (lx < m || ly < m || lx >= SX - m || ly >= SY - m || lz < mz || lz >= SZ - mz) {
+                nxt[c] = cur[c];
+                continue;
+            }
+            const uint32_t w = cs[c];
+            T v = T(0);
+            if (w >> 31) {
+                T acc = tab[0][w & 31u] * cur[c + 1];
+                acc += tab[0][(w >> 5) & 31u] * cur[c - 1];
+                acc += tab[1][(w >> 10) & 31u] * cur[c + SX];
+                acc += tab[1][(w >> 15) & 31u] * cur[c - SX];
+                if (NDIM == 3) {
+                    acc += tab[2][(w >> 20) & 31u] * cur[c + SX * SY];
+                    acc += tab[2][(w >> 25) & 31u] * cur[c - SX * SY];
+                }
+                v = (acc + rs[c]) * inv;
+            }
+            nxt[c] = v;
+        }
+        __syncthreads();
+        T* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    for (int c = threadIdx.x; c < JTX * JTY * TZ; c += blockDim.x) {
+        const int lx = c % JTX, ly = (c / JTX) % JTY, lz = c / (JTX * JTY);
+        const int64_t gx = x0 + k + lx, gy = y0 + k + ly, gz = z0 + hz + lz;
+        if (gx < px && gy < ny && gz < nz) e_out[(gz * ny + gy) * px + gx] = cur[((lz + hz) * SY + (ly + k)) * SX + (lx + k)];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // output: subtract each component's mean, NaN on missing cells, dense layout;
 // also ||P0 - P|| and ||P|| (both gauge-fixed) for the seed distance.
@@ -913,7 +992,7 @@ static void launch_cg_a(osmodi_plan p, const Buffers<T>& b, int op, const T* po,
         return;
     }
     const TableT<T> tab = table<T>(p);
-    const int variant = p->opt.reserved[0];  // 1 = streaming hints on the read-once / write-once vectors
+    const int variant = 0;  // 1 = streaming hints on the read-once / write-once vectors (measured: no gain)
     const int GA = p->launch.blocks_a;
 #define OSM_FL(ND, OPV, H, MB) k_cg_a<T, ND, OPV, H, MB><<<GA, 256, 0, s>>>(b.r, po, pn, b.q, b.x, p->code8, p->code32, g, tab, b.st, b.partials)
     if (p->ndim == 2) {
@@ -1236,11 +1315,29 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                         OSM_TRY(run_cg<T>(p, b, OP_M, ws, s, hm, &it, noalloc));
                         total_inner += it;
                     } else {
-                        for (int sw = 0; sw < p->opt.inner_max; ++sw) {
+                        const int kf = p->opt.sweeps_per_pass;
+                        for (int sw = 0; sw < p->opt.inner_max;) {
                             T* e_next = (e_cur == b.x) ? b.e2 : b.x;
-                            if (p->ndim == 2) k_jacobi<T, 2><<<G, TH, 0, s>>>(e_cur, e_next, b.rhs, p->code32, g, tab);
-                            else k_jacobi<T, 3><<<G, TH, 0, s>>>(e_cur, e_next, b.rhs, p->code32, g, tab);
+                            const int k = std::min(kf, p->opt.inner_max - sw);
+                            if (k == 1) {
+                                if (p->ndim == 2) k_jacobi<T, 2><<<G, TH, 0, s>>>(e_cur, e_next, b.rhs, p->code32, g, tab);
+                                else k_jacobi<T, 3><<<G, TH, 0, s>>>(e_cur, e_next, b.rhs, p->code32, g, tab);
+                            } else {
+                                const int tz = p->ndim == 3 ? 4 : 1, hz = p->ndim == 3 ? k : 0;
+                                const size_t cells = (size_t)(JTX + 2 * k) * (JTY + 2 * k) * (tz + 2 * hz);
+                                const size_t smem = cells * (3 * sizeof(T) + sizeof(uint32_t));
+                                dim3 grid((unsigned)((p->px + JTX - 1) / JTX), (unsigned)((p->ny + JTY - 1) / JTY),
+                                          (unsigned)((p->nz + tz - 1) / tz));
+                                if (p->ndim == 2) {
+                                    OSM_CUDA(cudaFuncSetAttribute(k_jacobi_fused<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                                    k_jacobi_fused<T, 2><<<grid, 256, smem, s>>>(e_cur, e_next, b.rhs, p->code32, p->px, p->ny, p->nz, k, tab);
+                                } else {
+                                    OSM_CUDA(cudaFuncSetAttribute(k_jacobi_fused<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                                    k_jacobi_fused<T, 3><<<grid, 256, smem, s>>>(e_cur, e_next, b.rhs, p->code32, p->px, p->ny, p->nz, k, tab);
+                                }
+                            }
                             e_cur = e_next;
+                            sw += k;
                         }
                         OSM_CUDA(cudaGetLastError());
                         total_inner += p->opt.inner_max;
@@ -1309,9 +1406,140 @@ osmodi_status solve_into_scratch(osmodi_plan p, const void* grad, int gdt, void*
                : solve_impl<float>(p, grad, gdt, pu, pdt, tol, max_iter, scratch, s, res, &mirror);
 }
 
+// ---------------------------------------------------------------------------
+// autotuner: time bursts of CG iterations per candidate launch geometry
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_fill_pattern(T* r, const uint8_t* code8, int64_t n_box) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_box; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t h = (uint32_t)(i * 2654435761ull) ^ 0x9e3779b9u;
+        h ^= h >> 15;
+        h *= 0x85ebca6bu;
+        h ^= h >> 13;
+        r[i] = (code8[i] & 0x80u) ? (T)((double)(h & 0xffffu) / 65536.0 - 0.5) : T(0);
+    }
+}
+
+static std::string cache_file(const char* given) {
+    if (given && *given) return given;
+    const char* env = std::getenv("OSMODI_AUTOTUNE_CACHE");
+    if (env && *env) return env;
+    const char* home = std::getenv("HOME");
+    return std::string(home ? home : "/tmp") + "/.cache/osmodi_autotune.txt";
+}
+
+static std::string cache_key(osmodi_plan p) {
+    cudaDeviceProp prop;
+    std::string name = "gpu";
+    if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) name = prop.name;
+    for (char& c : name)
+        if (c == ' ') c = '_';
+    int lg = 0;
+    for (int64_t v = p->n_box; v > 1; v >>= 1) ++lg;
+    return name + "|" + std::to_string(p->ndim) + "|" + std::to_string(lg) + "|" + std::to_string(p->opt.precision);
+}
+
+static void set_geometry(osmodi_plan p, int ga_per_sm, int gb_per_sm, int flat) {
+    const int64_t need = (p->n_chunks + 255) / 256;
+    p->launch.blocks_a = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)p->num_sms * ga_per_sm, need, (int64_t)kMaxBlocks}));
+    p->launch.blocks_b = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)p->num_sms * gb_per_sm, need, (int64_t)kMaxBlocks}));
+    p->opt.flat_sweeps = flat;
+    for (auto& g : p->graphs)
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+}
+
+// read the cache entry for this plan (if any) into its launch geometry
+void apply_tuned(osmodi_plan p) {
+    std::FILE* f = std::fopen(cache_file(nullptr).c_str(), "r");
+    if (!f) return;
+    const std::string key = cache_key(p);
+    char k[512];
+    int ga, gb, fl;
+    double ms;
+    while (std::fscanf(f, "%511s %d %d %d %lf", k, &ga, &gb, &fl, &ms) == 5)
+        if (key == k) set_geometry(p, ga, gb, fl);
+    std::fclose(f);
+}
+
+template <class T>
+static osmodi_status tune_impl(osmodi_plan p, void* ws, cudaStream_t s, const char* path, double* ms_out) {
+    Buffers<T> b;
+    carve<T>(p, ws, &b);
+    int bps_a = 0, bps_b = 0;
+    sweep_blocks_per_sm(p->ndim, sizeof(T) == 8, &bps_a, &bps_b);
+    struct Cand {
+        int ga, gb, flat;
+    };
+    std::vector<Cand> cands;
+    for (int ga = 2; ga <= bps_a; ++ga)
+        for (int gb : {4, 6, 8})
+            if (gb <= bps_b) cands.push_back({ga, gb, 1});
+    if (p->ndim == 3)
+        for (int gb : {4, 6, 8})
+            if (gb <= bps_b) cands.push_back({bps_a, gb, 0});
+    cudaEvent_t e0, e1;
+    OSM_CUDA(cudaEventCreate(&e0));
+    OSM_CUDA(cudaEventCreate(&e1));
+    const int G = p->launch.blocks, TH = p->launch.threads;
+    const Launch saved = p->launch;
+    const int saved_flat = p->opt.flat_sweeps;
+    double best = 1e300;
+    Cand pick = {0, 0, saved_flat};
+    const int iters = 16;
+    osmodi_status st = OSMODI_OK;
+    for (const Cand& c : cands) {
+        set_geometry(p, c.ga, c.gb, c.flat);
+        k_fill_pattern<T><<<G, TH, 0, s>>>(b.r, p->code8, p->n_box);
+        OSM_CUDA(cudaMemsetAsync(b.sc, 0, sizeof(Scalars), s));
+        OSM_CUDA(cudaMemsetAsync(b.st, 0, sizeof(CgState), s));
+        k_cg_init<T><<<G, TH, 0, s>>>(b.r, b.x, p->code8, p->label, b.comp, p->comp_count, 0, p->n_chunks, b.sc, b.st,
+                                      0.0, 0.0, (long long)1 << 40, b.partials + kSlotMisc * kMaxBlocks);
+        if ((st = launch_cg_iters<T>(p, b, OP_L, 4, s)) != OSMODI_OK) break;
+        OSM_CUDA(cudaEventRecord(e0, s));
+        if ((st = launch_cg_iters<T>(p, b, OP_L, iters, s)) != OSMODI_OK) break;
+        OSM_CUDA(cudaEventRecord(e1, s));
+        OSM_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        OSM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms / iters < best) {
+            best = ms / iters;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != OSMODI_OK || pick.ga == 0) {
+        p->launch = saved;
+        p->opt.flat_sweeps = saved_flat;
+        return st != OSMODI_OK ? st : OSMODI_E_CUDA;
+    }
+    set_geometry(p, pick.ga, pick.gb, pick.flat);
+    if (ms_out) *ms_out = best;
+    // record (append; the last entry for a key wins when read back)
+    const std::string file = cache_file(path);
+    const size_t slash = file.find_last_of('/');
+    if (slash != std::string::npos) ::mkdir(file.substr(0, slash).c_str(), 0755);  // may already exist
+    if (std::FILE* f = std::fopen(file.c_str(), "a")) {
+        std::fprintf(f, "%s %d %d %d %.6f\n", cache_key(p).c_str(), pick.ga, pick.gb, pick.flat, best);
+        std::fclose(f);
+    }
+    return OSMODI_OK;
+}
+
 }  // namespace osm
 
 using namespace osm;
+
+extern "C" osmodi_status osmodi_autotune(osmodi_plan p, void* ws, void* stream, const char* cache_path, double* ms_out) {
+    if (!p) return OSMODI_E_INVALID;
+    if (!ws || ((uintptr_t)ws & 255u)) return OSMODI_E_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    return p->opt.precision == OSMODI_FP64 ? tune_impl<double>(p, ws, s, cache_path, ms_out)
+                                           : tune_impl<float>(p, ws, s, cache_path, ms_out);
+}
 
 extern "C" size_t osmodi_workspace_bytes(osmodi_plan p) {
     if (!p) return 0;

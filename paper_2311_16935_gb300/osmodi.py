@@ -30,7 +30,8 @@ class osmodi_options(ctypes.Structure):
                 ("inner_max", ctypes.c_int), ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
                 ("sweeps_per_pass", ctypes.c_int), ("max_refine", ctypes.c_int), ("record_history", ctypes.c_int),
                 ("threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("profile", ctypes.c_int),
-                ("slab", ctypes.c_int), ("flat_sweeps", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("slab", ctypes.c_int), ("flat_sweeps", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
 class osmodi_result(ctypes.Structure):
@@ -77,6 +78,11 @@ _SIGS = {
     "osmodi_kernel_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_plan_constants": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_destroy": (None, [ctypes.c_void_p]),
+    "osmodi_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p,
+                                       ctypes.c_void_p]),
+    "osmodi_autotune_batched": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                               ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p]),
     "osmodi_net_param_count": (ctypes.c_size_t, []),
     "osmodi_net_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "osmodi_net_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -240,6 +246,15 @@ class Plan:
             raise OsmodiError(st, "osmodi_solve_noalloc")
         return res
 
+    def autotune(self, cache_path=None, stream=None):
+        """osmodi_autotune; returns the best time per CG iteration (ms)."""
+        ms = ctypes.c_double(0.0)
+        st = lib().osmodi_autotune(self.handle, self._ws_ptr(), _stream_ptr(stream),
+                                   None if cache_path is None else str(cache_path).encode(), ctypes.byref(ms))
+        if st != OK:
+            raise OsmodiError(st, "osmodi_autotune")
+        return ms.value
+
     def history(self):
         n = lib().osmodi_history(self.handle, None, 0)
         buf = (ctypes.c_double * max(n, 1))()
@@ -326,6 +341,20 @@ class Batch:
         if check and st < 0 and st != E_NAN_INPUT:
             raise OsmodiError(st, "osmodi_solve_batched")
         return st, list(res)
+
+
+    def autotune(self, grads, ps, stream=None):
+        """osmodi_autotune_batched; returns the chosen tile depth."""
+        count = len(self.plans)
+        ga = (ctypes.c_void_p * count)(*[g.data_ptr() for g in grads])
+        pa = (ctypes.c_void_p * count)(*[p.data_ptr() for p in ps])
+        depth = ctypes.c_int(0)
+        ws = (self.ws.data_ptr() + 255) // 256 * 256
+        st = lib().osmodi_autotune_batched(count, self._arr, ga, _dtype_code(grads[0]), pa, _dtype_code(ps[0]), ws,
+                                           _stream_ptr(stream), ctypes.byref(depth))
+        if st != OK:
+            raise OsmodiError(st, "osmodi_autotune_batched")
+        return depth.value
 
 
 def osmodi_solve_batched(plans, grads, ps, tol, max_iter=1 << 30, stream=None):

@@ -142,3 +142,20 @@ def test_batched_zero_gradient_and_repeat(osm):
         outs.append([p.cpu().numpy() for p in ps])
     for a, b, (v, s, f) in zip(outs[0], outs[1], inst):
         np.testing.assert_allclose(a[v], b[v], rtol=1e-12, atol=1e-14)
+
+
+def test_batched_autotune_tile_depth(osm):
+    inst = _random_instances(7, 6)
+    plans = [osm.Plan(2, v.shape[::-1], s, torch.from_numpy(v.astype(np.uint8)).cuda()) for v, s, f in inst]
+    batch = osm.Batch(plans)
+    grads = [torch.from_numpy(f).cuda() for v, s, f in inst]
+    ps = [torch.zeros(v.shape, dtype=torch.float64, device="cuda") for v, s, f in inst]
+    depth = batch.autotune(grads, ps)
+    assert depth in (1, 2, 4, 8)
+    for p in ps:
+        p.zero_()
+    st, res = batch.solve(grads, ps, 1e-11)
+    assert st == osm.OK
+    for (valid, spacing, f), p in zip(inst, ps):
+        want = oracle.solve_direct(oracle.Grid(valid, spacing), f)
+        assert _rel(p.cpu().numpy(), want, valid) < 1e-9

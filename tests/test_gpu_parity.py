@@ -316,3 +316,49 @@ def test_fp32_output_buffer(osm):
     # the FP32-rounded gradient is the input both sides see
     want32 = oracle.solve_direct(grid, prob.grad.float().double().numpy())
     assert _rel(got, want32, grid.valid) < 1e-6
+
+
+def test_autotune_keeps_results_and_caches(osm, tmp_path):
+    """The autotuner only changes the launch geometry: the solve after tuning
+    gives the same answer; a new plan with autotune=1 reads the cache."""
+    prob = inputs.sincos_3d(n=48, mask_radius=1.0)
+    cache = tmp_path / "tune.txt"
+    plan = osm.Plan(3, prob.dims, prob.spacing, prob.mask.cuda())
+    g = prob.grad.cuda()
+    p0 = torch.zeros((48, 48, 48), dtype=torch.float64, device="cuda")
+    plan.solve(g, p0, 1e-11)
+    ms = plan.autotune(cache_path=str(cache))
+    assert ms > 0 and cache.exists() and cache.read_text().strip()
+    p1 = torch.zeros_like(p0)
+    r = plan.solve(g, p1, 1e-11)
+    assert r.status == osm.OK
+    valid = prob.mask.numpy().astype(bool)
+    assert _rel(p1.cpu().numpy(), p0.cpu().numpy(), valid) < 1e-10
+    import os
+
+    os.environ["OSMODI_AUTOTUNE_CACHE"] = str(cache)
+    try:
+        plan2 = osm.Plan(3, prob.dims, prob.spacing, prob.mask.cuda(), autotune=1)
+        p2 = torch.zeros_like(p0)
+        assert plan2.solve(g, p2, 1e-11).status == osm.OK
+        assert _rel(p2.cpu().numpy(), p0.cpu().numpy(), valid) < 1e-10
+    finally:
+        del os.environ["OSMODI_AUTOTUNE_CACHE"]
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+@pytest.mark.parametrize("precision", [0, 2])
+def test_fused_jacobi_sweeps_equal_single_sweeps(osm, ndim, precision):
+    """OUTER scheme with Jacobi inner sweeps: k sweeps fused per pass (shared
+    memory, ghost zones) give the same iterates as k single-sweep passes."""
+    rng = np.random.default_rng(12 + ndim)
+    shape = (37, 45) if ndim == 2 else (11, 13, 42)
+    spacing = (0.1, 0.13) if ndim == 2 else (1.0, 1.0, 1.0)
+    valid = rng.random(shape) > 0.15
+    f = rng.normal(size=(ndim,) + shape)
+    outs = []
+    for spp in (1, 3):
+        plan, res, got = _solve(osm, f, valid.astype(np.uint8), spacing, 1e-30, precision=precision, scheme=1, inner=1,
+                                inner_max=3, sweeps_per_pass=spp, max_iter=40)
+        outs.append(got)
+    assert _rel(outs[1], outs[0], valid) < 1e-12

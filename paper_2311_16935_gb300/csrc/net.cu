@@ -174,17 +174,49 @@ __global__ void __launch_bounds__(128) k_conv(ConvArgs a) {
     const int arow = threadIdx.x >> 1, akh = (threadIdx.x & 1) * 8;
     const long long am = m0 + arow;
     const int brow = threadIdx.x >> 3, bcol = (threadIdx.x & 7) * 8;
+    const bool vec_a = (a.Ka & 7) == 0;  // a thread's 8 reduction elements share one tap and voxel
     for (int k0 = 0; k0 < a.K; k0 += BK) {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int k = k0 + akh + e;
-            float v = 0.f;
+        if (vec_a) {
+            const int k = k0 + akh;
+            uint4 packed = make_uint4(0, 0, 0, 0);
             if (am < a.M && k < a.K) {
                 const int t = k / a.Ka, ci = k - t * a.Ka;
                 const long long vox = src_voxel(a, am, t);
-                if (vox >= 0) v = load_a(a, vox, ci);
+                if (vox >= 0) {
+                    const long long idx = vox * a.Ka + ci;
+                    bf16 vals[8];
+                    if (a.a_float) {
+                        const float4 lo = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(a.A) + idx);
+                        const float4 hi = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(a.A) + idx + 4);
+                        const float f8[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) vals[e] = __float2bfloat16(f8[e]);
+                    } else {
+                        *reinterpret_cast<uint4*>(vals) = *reinterpret_cast<const uint4*>(reinterpret_cast<const bf16*>(a.A) + idx);
+                    }
+                    if (a.amask) {
+                        bf16 mk[8];
+                        *reinterpret_cast<uint4*>(mk) = *reinterpret_cast<const uint4*>(a.amask + idx);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            if (!(__bfloat162float(mk[e]) > 0.f)) vals[e] = __float2bfloat16(0.f);
+                    }
+                    packed = *reinterpret_cast<uint4*>(vals);
+                }
             }
-            As[arow * BK + akh + e] = __float2bfloat16(v);
+            *reinterpret_cast<uint4*>(As + arow * BK + akh) = packed;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int k = k0 + akh + e;
+                float v = 0.f;
+                if (am < a.M && k < a.K) {
+                    const int t = k / a.Ka, ci = k - t * a.Ka;
+                    const long long vox = src_voxel(a, am, t);
+                    if (vox >= 0) v = load_a(a, vox, ci);
+                }
+                As[arow * BK + akh + e] = __float2bfloat16(v);
+            }
         }
 #pragma unroll
         for (int e = 0; e < 8; ++e) {

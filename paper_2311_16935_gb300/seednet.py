@@ -121,3 +121,79 @@ def seeded_solve(params, grad, n, tol, plan=None, net=None):
     if own_net:
         net.close()
     return p, r_seed, r_zero
+
+
+def run_experiment(pairs=2000, train_n=128, epochs=4, lr=1e-3, batch=8, eval_n=256, eval_count=16, tol=1e-10,
+                   log=print):
+    """The network-seeded workload: train on `pairs` method-solved fields at
+    train_n^3, then solve `eval_count` held-out fields at eval_n^3 to `tol`
+    from the network's guess and from zero.  Returns a result dict."""
+    t0 = time.perf_counter()
+    data = make_pairs(pairs, train_n, tol=1e-8)
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    log(f"{pairs} training pairs at {train_n}^3 solved in {t_pairs:.1f} s")
+    t1 = time.perf_counter()
+    params, hist = train(data, train_n, epochs=epochs, lr=lr, batch=batch, log=log)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    del data
+    torch.cuda.empty_cache()
+    plan = osm.Plan(3, (eval_n,) * 3, (1.0, 1.0, 1.0), None, precision=osm.FP32_REFINE)
+    net = osm.Net((eval_n,) * 3, train=False)
+    net.set_params(params)
+    rows = []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for i in range(eval_count):
+        prob = blob_problem(eval_n, 50000 + i)
+        p = torch.empty((eval_n,) * 3, dtype=torch.float64, device="cuda")
+        plan.solve(prob.grad, torch.zeros_like(p), tol)  # warm (graph capture)
+        ev[0].record()
+        net.forward(prob.grad, None, 1.0, p)
+        ev[1].record()
+        r_seed = plan.solve(prob.grad, p, tol)
+        ev[2].record()
+        p0 = torch.zeros_like(p)
+        r_zero = plan.solve(prob.grad, p0, tol)
+        ev[3].record()
+        torch.cuda.synchronize()
+        rows.append(dict(field=i, seed_rel_dist=r_seed.seed_rel_dist, cg_seeded=r_seed.inner_iters,
+                         cg_zero=r_zero.inner_iters, ms_net=ev[0].elapsed_time(ev[1]),
+                         ms_seeded_solve=ev[1].elapsed_time(ev[2]), ms_zero_solve=ev[2].elapsed_time(ev[3]),
+                         eps_seeded=r_seed.eps_R, eps_zero=r_zero.eps_R,
+                         ok=r_seed.status == osm.OK and r_zero.status == osm.OK))
+        log(str(rows[-1]))
+    plan.close()
+    net.close()
+    mean = lambda k: float(np.mean([r[k] for r in rows]))
+    return dict(pairs=pairs, train_n=train_n, epochs=epochs, lr=lr, batch=batch, eval_n=eval_n, eval_count=eval_count,
+                tol=tol, seconds_pairs=t_pairs, seconds_train=t_train, loss_history=hist,
+                mean_seed_rel_dist=mean("seed_rel_dist"), mean_cg_seeded=mean("cg_seeded"),
+                mean_cg_zero=mean("cg_zero"), mean_ms_seeded_total=mean("ms_net") + mean("ms_seeded_solve"),
+                mean_ms_zero=mean("ms_zero_solve"), all_converged=all(r["ok"] for r in rows), fields=rows)
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description=run_experiment.__doc__)
+    ap.add_argument("--pairs", type=int, default=2000)
+    ap.add_argument("--train-n", type=int, default=128)
+    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--eval-n", type=int, default=256)
+    ap.add_argument("--eval-count", type=int, default=16)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    from . import build
+
+    build.build()
+    res = run_experiment(a.pairs, a.train_n, a.epochs, a.lr, a.batch, a.eval_n, a.eval_count, a.tol)
+    txt = json.dumps(res)
+    print(txt)
+    if a.out:
+        with open(a.out, "w") as fh:
+            fh.write(txt + "\n")

@@ -23,6 +23,10 @@ What it computes, each piece written from the paper:
 * ``solve_literal``         Algorithm 1 as written: each outer iteration solves
                             Eq. MatrixEquation exactly (sparse LU, the analogue of
                             the paper's Matlab backslash)
+* ``solve_outer_anderson``  Algorithm 1's outer map P -> M^-1 (W^n P + S), boundary
+                            term refreshed every iteration, accelerated by Anderson
+                            mixing of depth m (Anderson 1965, in the difference form
+                            of Walker & Ni 2011); m = 0 is Algorithm 1 itself
 * ``brute_force_counts_2d`` the ray counts of every cell by direct quadrature of
                             the ray integral (Eq. AE_Interior's (s, theta) integral,
                             classifying each ray by tracing it back one cell)
@@ -426,6 +430,70 @@ def solve_literal(grid: Grid, f, tol: float = 1e-10, max_outer: int = 100000, P0
     out = np.full(grid.n, np.nan)
     out[vidx] = P
     return gauge(grid, out.reshape(grid.valid.shape)), n, eps_r, eps_p
+
+
+def _outer_parts(grid: Grid, f):
+    """The pieces of Algorithm 1 on the valid cells: LU of M = I - W^{n+1}_off,
+    W^n, the fixed-point operator I - W^{n+1}_off - W^n and S."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+
+    S = source(grid, f).reshape(-1)
+    W1, Wn = operators(grid)
+    vidx = np.flatnonzero(grid.valid.reshape(-1))
+    I = sp.identity(grid.n, format="csr")
+    M = (I - W1)[vidx][:, vidx].tocsc()
+    return spla.splu(M), Wn[vidx][:, vidx], (I - W1 - Wn)[vidx][:, vidx], S[vidx], vidx
+
+
+def solve_outer_anderson(grid: Grid, f, depth: int, tol: float = 1e-10, max_outer: int = 100000, P0=None,
+                         callback=None):
+    """Anderson acceleration of Algorithm 1.
+
+    The outer map is Algorithm 1's step, G(P) = M^-1 (W^n P + S) with M =
+    I - W^{n+1}_off (Eq. MatrixEquation, solved exactly by sparse LU): the
+    boundary term W^n P is refreshed from the current iterate every time.
+    With f_k = G(x_k) - x_k and the last min(k, depth) differences
+    dF_i = f_{i+1} - f_i, dG_i = G(x_{i+1}) - G(x_i), each step takes
+    gamma = argmin || f_k - dF gamma ||_2 (a least-squares solve) and
+    x_{k+1} = G(x_k) - dG gamma.  depth = 0 gives x_{k+1} = G(x_k), i.e.
+    Algorithm 1 unchanged.  Every fixed point of G is Algorithm 1's fixed
+    point.  eps_R (Eq. ResidualMomentum) of each new iterate is recorded;
+    callback(n, x) (optional) sees every new iterate on the valid cells.
+    Returns (P gauged, n_outer, eps_R history)."""
+    lu, Wnv, K, Sv, vidx = _outer_parts(grid, f)
+    snorm = np.linalg.norm(Sv)
+    x = np.zeros(vidx.size) if P0 is None else np.array(P0, dtype=np.float64).reshape(-1)[vidx].copy()
+    dF, dG = [], []
+    f_prev = g_prev = None
+    eps_r = []
+    n = 0
+    while n < max_outer:
+        g = lu.solve(Wnv @ x + Sv)
+        fk = g - x
+        if f_prev is not None and depth > 0:
+            dF.append(fk - f_prev)
+            dG.append(g - g_prev)
+            if len(dF) > depth:
+                dF.pop(0)
+                dG.pop(0)
+        f_prev, g_prev = fk, g
+        if dF:
+            DF = np.stack(dF, axis=1)
+            gamma = np.linalg.lstsq(DF, fk, rcond=None)[0]
+            x = g - np.stack(dG, axis=1) @ gamma
+        else:
+            x = g
+        n += 1
+        if callback is not None:
+            callback(n, x.copy())
+        er = 0.0 if snorm == 0 else float(np.linalg.norm(K @ x - Sv) / snorm)
+        eps_r.append(er)
+        if er <= tol:
+            break
+    out = np.full(grid.n, np.nan)
+    out[vidx] = x
+    return gauge(grid, out.reshape(grid.valid.shape)), n, eps_r
 
 
 # --------------------------------------------------------------------------

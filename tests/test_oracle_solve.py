@@ -175,3 +175,68 @@ def test_noise_lowers_attainable_accuracy_but_converges():
     P_def = oracle.solve_direct(grid, f)
     P_cg, it, res = oracle.solve_cg(grid, f, tol=1e-14)
     assert _rel(P_cg, P_def, grid.valid) < 1e-11
+
+
+def _masked_problem(shape, spacing, seed, drop=0.15):
+    rng = np.random.default_rng(seed)
+    valid = rng.random(shape) > drop
+    f = rng.normal(size=(len(shape),) + shape)
+    return oracle.Grid(valid, spacing), f
+
+
+def test_anderson_depth_zero_is_algorithm_1():
+    """Depth 0 is Algorithm 1 step for step: the same eps_R history and the
+    same answer as the literal oracle."""
+    grid, f = _masked_problem((11, 13), (0.1, 0.13), 21)
+    P_lit, n_lit, er_lit, _ = oracle.solve_literal(grid, f, tol=1e-9)
+    P_aa, n_aa, er_aa = oracle.solve_outer_anderson(grid, f, 0, tol=1e-9)
+    assert n_aa == n_lit
+    np.testing.assert_allclose(er_aa, er_lit, rtol=1e-12, atol=0)
+    assert _rel(P_aa, P_lit, grid.valid) < 1e-13
+
+
+@pytest.mark.parametrize("depth", [1, 3, 8])
+def test_anderson_reaches_the_fixed_point_faster(depth):
+    grid, f = _masked_problem((14, 19), (0.1, 0.13), 3)
+    want = oracle.solve_direct(grid, f)
+    _, n_lit, _, _ = oracle.solve_literal(grid, f, tol=1e-11)
+    P, n, er = oracle.solve_outer_anderson(grid, f, depth, tol=1e-11)
+    assert er[-1] <= 1e-11
+    assert _rel(P, want, grid.valid) < 1e-9
+    assert n < n_lit / 2
+
+
+def _gmres_brute_force(A, b, k):
+    """The k-th GMRES iterate from x0 = 0 by definition: the minimiser of
+    ||b - A x|| over the Krylov space span{b, A b, ..., A^(k-1) b}, from an
+    explicit (twice orthogonalised) basis and a dense least-squares solve."""
+    Q = np.zeros((b.size, k))
+    v = b / np.linalg.norm(b)
+    for j in range(k):
+        for _ in range(2):
+            v = v - Q[:, :j] @ (Q[:, :j].T @ v)
+        Q[:, j] = v / np.linalg.norm(v)
+        v = A @ Q[:, j]
+    y = np.linalg.lstsq(A @ Q, b, rcond=None)[0]
+    return Q @ y
+
+
+def test_anderson_is_gmres_on_the_outer_map():
+    """For the affine outer map G(x) = M^-1 W^n x + M^-1 S, Anderson mixing
+    without truncation satisfies x_{k+1} = G(x_k^GMRES), with x_k^GMRES the
+    k-th GMRES iterate of (I - M^-1 W^n) x = M^-1 S (Walker & Ni 2011,
+    Theorem 2.2).  GMRES is computed here by its definition, independently of
+    the mixing formula, so a wrong sign, index or difference in the mixing
+    fails this."""
+    grid, f = _masked_problem((5, 6), (0.1, 0.13), 8, drop=0.1)
+    lu, Wnv, K, Sv, vidx = oracle._outer_parts(grid, f)
+    n = vidx.size
+    Glin = lu.solve(Wnv.toarray())
+    b = lu.solve(Sv)
+    A = np.eye(n) - Glin
+    its = {}
+    oracle.solve_outer_anderson(grid, f, depth=50, tol=0.0, max_outer=8, callback=lambda k, x: its.__setitem__(k, x))
+    for k in range(1, 7):
+        xg = _gmres_brute_force(A, b, k)
+        want = Glin @ xg + b
+        assert np.linalg.norm(its[k + 1] - want) <= 1e-8 * np.linalg.norm(want), k

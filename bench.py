@@ -204,6 +204,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-front", action="store_true")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--ref-crop", type=int, default=100)
     ap.add_argument("--ref-iters", type=int, default=150)
@@ -214,30 +215,15 @@ def main():
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2311_16935_gb300 import replicas
+
+    info_r = replicas.RankInfo.from_env()
+    world, rank, local = info_r.world, info_r.rank, info_r.local
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    group = replicas.RankGroup(info_r, device="cuda")
+    barrier, max_over_ranks, sum_over_ranks = group.barrier, group.max, group.sum
 
     from paper_2311_16935_gb300 import build, inputs
 
@@ -280,15 +266,16 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    ms_max = max_over_ranks(ms)
     updates = sum(r["point_updates"] for r in results)
-    updates_all = sum_over_ranks(updates)
-    value = updates_all / (ms_max / 1e3) / 1e9
+    ups, ms_max = replicas.aggregate_throughput(updates, ev0.elapsed_time(ev1), group)
+    value = ups / 1e9
     clocks = clk.summary()
     if any(r["status"] != osm.OK for r in results):
         raise SystemExit(f"solve did not converge: {results}")
 
+    # kernels per solve: the two CG kernels, one FP64 residual per refinement
+    # step plus the initial one, one CG initialisation per step, source and
+    # output (refine_steps counts the residual evaluations)
     # roofline of the dominant kernel (the CG kernel applying the stencil):
     # algorithmic bytes per cell = read r, p_old, x (3 x 4 B) + code (1 B) + write p_new, q, x (3 x 4 B)
     cells = info["n_box"]
@@ -316,7 +303,7 @@ def main():
                          "avg_launch_ms": ka_avg,
                          "second_kernel": {"name": "k_cg_b (r update + r.r)", "avg_launch_ms": kb_avg,
                                            "achieved": 12.0 * cells / (kb_avg / 1e3) / 1e9 if kb_avg > 0 else None}},
-            "clocks": clocks, "gpu_launches": int(ka_n + kb_n + sum(r["refine_steps"] for r in results) + 3 * args.steps)}
+            "clocks": clocks, "gpu_launches": int(ka_n + kb_n + sum(2 * r["refine_steps"] + 1 for r in results))}
 
     # plain FP64 solve of the same problem (time-to-tolerance comparison)
     if not args.no_fp64:
@@ -364,6 +351,30 @@ def main():
     else:
         line["e2e"] = None
 
+    # the source-term front end (Eq. RANS_f) on the same grid: mean velocity
+    # and Reynolds stresses in, the gradient field out (inputs > L2)
+    if not args.no_front:
+        gen = torch.Generator(device="cuda").manual_seed(5)
+        U = torch.randn((3, n, n, n), device="cuda", dtype=torch.float32, generator=gen)
+        R = 0.1 * torch.randn((6, n, n, n), device="cuda", dtype=torch.float32, generator=gen)
+        plan.source_rans(U, R)  # warm-up
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        f0.record(stream)
+        for _ in range(reps):
+            out_f = plan.source_rans(U, R)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        f_ms = f0.elapsed_time(f1) / reps
+        f_bytes = 52.0 * n ** 3  # read U (12) + stresses (24) + class word (4), write f (12)
+        line["front_end"] = {"kernel": "k_front_rans<3> (Eq. RANS_f source from U and stresses)",
+                             "ms": f_ms, "bytes_per_launch": f_bytes,
+                             "achieved_GBps": f_bytes / (f_ms / 1e3) / 1e9,
+                             "frac": f_bytes / (f_ms / 1e3) / 1e9 / peak, "peak_source": peak_kind}
+        del U, R, out_f
+        torch.cuda.empty_cache()
+
     # the batched workload: PIV-like snapshots of uneven sizes and masks, one
     # persistent launch per batch (reported beside the headline)
     if not args.no_batch:
@@ -375,16 +386,23 @@ def main():
         batch = osm.Batch(plans_b)
         grads_b = [pr.grad for pr in probs]
         outs = [torch.zeros(pr.mask.shape, dtype=torch.float64, device="cuda") for pr in probs]
-        batch.solve(grads_b, outs, 1e-10)  # warm-up
+        depth = batch.autotune(grads_b, outs)  # tile depth of the persistent kernel
+        graph = batch.capture(grads_b, outs, 1e-10)  # one graph: tables, resets, persistent launch, states
+        for o in outs:
+            o.zero_()
+        graph.launch(stream)  # warm-up replay
+        graph.results()
         for o in outs:
             o.zero_()
         torch.cuda.synchronize()
         b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         b0.record(stream)
-        st_b, res_b = batch.solve(grads_b, outs, 1e-10)
+        graph.launch(stream)
         b1.record(stream)
         torch.cuda.synchronize()
+        st_b, res_b = graph.results()
         bms = b0.elapsed_time(b1)
+        graph.close()
         its = [r.inner_iters for r in res_b]
         line["batched_piv"] = {"workload": f"piv_batch_2d_{args.batch_count}", "tol_eps_R": 1e-10,
                                "cells": int(sum(pr.mask.numel() for pr in probs)),
@@ -393,7 +411,7 @@ def main():
                                "seconds": bms / 1e3, "solves_per_s": args.batch_count / (bms / 1e3),
                                "GLUPS": sum(r.point_updates for r in res_b) / (bms / 1e3) / 1e9,
                                "cg_iterations_min_mean_max": [min(its), float(sum(its)) / len(its), max(its)],
-                               "launches": 1}
+                               "launches": 1, "graph_captured": True, "tile_depth_chunks_per_thread": depth}
         del batch, plans_b, probs, grads_b, outs
     if rank == 0 and world == 1 and not args.no_cpu:
         try:

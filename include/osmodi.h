@@ -105,10 +105,28 @@ typedef struct {
                             CUDA events around every sweep kernel on the caller's stream;
                             durations readable with osmodi_kernel_stats */
     int slab;            /* z-planes per work item of the tiled 3D sweep kernel (0 = tuned) */
-    int flat_sweeps;     /* 1 (default) = flat grid-stride sweep kernel; 0 = z-marching tiled one */
+    int flat_sweeps;     /* sweep kernel of the CG on L: 1 (default) flat grid-stride;
+                            0 = z-marching tiled; 2 = z-marching with the r / p planes
+                            staged in shared memory by bulk tensor (TMA) copies
+                            (3D, FP32 inner precision; otherwise falls back to 1) */
     int autotune;        /* 1 = look the launch geometry up in the autotune cache at plan
                             creation (see osmodi_autotune) */
-    int reserved[1];
+    int accel;           /* OUTER: depth m (0..8) of Anderson mixing of the outer
+                            iterates (default 0 = Algorithm 1 unchanged).  Each outer
+                            iteration still refreshes the boundary term W^n P^n and
+                            solves Eq. MatrixEquation; the new iterate is then
+                            x = G(x_k) - sum_i gamma_i dG_i with gamma minimising
+                            || f_k - sum_i gamma_i dF_i ||, f = G(x) - x, over the
+                            last m differences (Anderson 1965; Walker & Ni 2011).
+                            Same fixed point; far fewer outer iterations.  Adds
+                            2m + 3 work vectors to the workspace. */
+    int precond;         /* FPCG: 1 = multigrid-preconditioned CG (aggregation of 2x2(x2)
+                            cells per level, Galerkin coarse weights, damped Jacobi
+                            smoothing; a fixed symmetric operator, so CG still converges
+                            to the same fixed point in far fewer iterations); 0 = plain
+                            CG.  Built at plan creation (about 2 B of device memory per
+                            cell); grids of at most 8 cells per axis use plain CG.
+                            Not part of the paper's method. */
 } osmodi_options;
 
 typedef struct {
@@ -226,6 +244,42 @@ OSMODI_API osmodi_status osmodi_solve_noalloc(osmodi_plan plan, const void* grad
 /* Workspace bytes for osmodi_solve_batched over these plans. */
 OSMODI_API size_t osmodi_batched_workspace_bytes(int count, const osmodi_plan* plans);
 
+/*
+ * The batched solve as a CUDA graph, for a stream of batches over the same
+ * geometry (PIV acquisition: fixed masks, new gradients every snapshot).
+ *
+ * osmodi_batch_graph_create checks its arguments as osmodi_solve_batched
+ * does, then captures one solve of the batch -- the upload of the instance
+ * and tile tables from page-locked host copies the graph owns, the state
+ * resets, the single persistent cooperative launch (a kernel node with the
+ * cooperative attribute) and the copy of the per-instance states to
+ * page-locked host memory -- and instantiates it.  Because every replay
+ * rewrites its tables, the workspace may serve other solves between
+ * replays (never while one is in flight).  The graph keeps the addresses it was created with: the
+ * plans' codes and labels, grads[i], ps[i] and the workspace must stay alive
+ * and unmoved until osmodi_batch_graph_destroy, and the plans must not be
+ * destroyed before it.  Between launches the caller writes new gradients
+ * into the same buffers and resets (or seeds) ps[i]: as in
+ * osmodi_solve_batched, ps[i] holds the initial guess on entry and the
+ * solution on exit.
+ *
+ * osmodi_batch_graph_launch enqueues one replay on `stream` (asynchronous;
+ * one replay in flight per graph and per workspace).
+ * osmodi_batch_graph_results waits for the last replay and fills `results`
+ * (count entries, may be NULL); ms is the replay's device time.  Its return
+ * value is that of osmodi_solve_batched for the same solve.
+ * OSMODI_E_INVALID: NULL handle, no replay yet, or a launch on another
+ * device.  OSMODI_E_CUDA: capture or instantiation refused (the message is in
+ * osmodi_last_cuda_error()).
+ */
+typedef struct osmodi_batch_graph_s* osmodi_batch_graph;
+OSMODI_API osmodi_status osmodi_batch_graph_create(int count, const osmodi_plan* plans, const void* const* grads,
+                                                   int grad_dtype, void* const* ps, int p_dtype, double tol, int max_iter,
+                                                   void* workspace_dev, void* stream, osmodi_batch_graph* out);
+OSMODI_API osmodi_status osmodi_batch_graph_launch(osmodi_batch_graph graph, void* stream);
+OSMODI_API osmodi_status osmodi_batch_graph_results(osmodi_batch_graph graph, osmodi_result* results);
+OSMODI_API void osmodi_batch_graph_destroy(osmodi_batch_graph graph);
+
 /* eps_R of every outer iteration of the plan's last OUTER solve with
  * record_history set; copies min(cap, n) values, returns n. */
 OSMODI_API int osmodi_history(osmodi_plan plan, double* out_host, int cap);
@@ -251,12 +305,59 @@ OSMODI_API osmodi_status osmodi_apply(osmodi_plan plan, int which, const double*
 OSMODI_API osmodi_status osmodi_residual(osmodi_plan plan, const void* grad_dev, int grad_dtype, const void* p_dev, int p_dtype,
                               double* eps_R_host, void* stream);
 
+/*
+ * Source-term front ends: the pressure gradient f that osmodi_solve
+ * integrates, computed from velocity data on the plan's grid and mask.  All
+ * arrays are FP32 device buffers, dense nx*ny*nz per plane (x fastest),
+ * components as consecutive planes; grad_dev receives ndim planes laid out
+ * as osmodi_solve's gradient input.  Missing cells of the output get 0.
+ * Asynchronous on `stream` (except osmodi_source_compressible, which
+ * synchronises to report singular cells).
+ *
+ * Derivatives (the paper does not fix a scheme): centred where both
+ * neighbours along the axis are valid, else the second-order one-sided
+ * three-point difference towards the valid side when the cell two steps away
+ * is valid too, else the two-point difference, else 0.  Second derivatives:
+ * centred, else three-point one-sided, else 0.  Derivatives of products (the
+ * conservative terms) difference the product field.
+ *
+ * osmodi_source_incompressible: Eq. 1 (Section 1),
+ *   f = -rho (du/dt + (u . grad) u) + mu lap u.
+ *   u_dev: ndim planes at time t.  u_prev_dev / u_next_dev: the snapshots at
+ *   t - dt / t + dt, either may be NULL: both given -> centred time
+ *   difference, one -> one-sided, none -> steady (du/dt = 0).  dt > 0 when a
+ *   neighbour snapshot is given.
+ * osmodi_source_rans: Eq. RANS_f (Section 3.3), viscous terms dropped,
+ *   f_i = -rho (U_j dU_i/dx_j + d<u_i' u_j'>/dx_j).  u_mean_dev: ndim planes;
+ *   stress_dev: the symmetric Reynolds stresses, 3 planes in 2D (xx, yy, xy),
+ *   6 in 3D (xx, yy, zz, xy, xz, yz).
+ * osmodi_source_compressible: Eq. compressible-pressure (Section 3.4):
+ *   per cell the ndim x ndim system (delta_ij + <u_i u_j>/(R T)) g_j =
+ *   -(1/(R T)) (d<u_i u_j>/dx_j - <u_i u_j>/T dT/dx_j), <u_i u_j> = U_i U_j +
+ *   <u_i' u_j'>, T = T_inf (1 + (gamma - 1)/2 M_inf^2 (1 - |U|^2/V_inf^2)),
+ *   solved for g = grad ln(P/P_inf) (written to grad_dev; osmodi_solve then
+ *   gives ln(P/P_inf) up to a constant).  temperature_dev (NULL allowed)
+ *   receives T.  gamma > 1, mach_inf >= 0, v_inf, t_inf, r_gas > 0.
+ *   Returns OSMODI_E_NAN_INPUT when the system was singular at some cell
+ *   (only possible for non-physical stresses); those cells hold 0.
+ */
+OSMODI_API osmodi_status osmodi_source_incompressible(osmodi_plan plan, const float* u_dev, const float* u_prev_dev,
+                                                      const float* u_next_dev, double dt, double rho, double mu,
+                                                      float* grad_dev, void* stream);
+OSMODI_API osmodi_status osmodi_source_rans(osmodi_plan plan, const float* u_mean_dev, const float* stress_dev,
+                                            double rho, float* grad_dev, void* stream);
+OSMODI_API osmodi_status osmodi_source_compressible(osmodi_plan plan, const float* u_mean_dev, const float* stress_dev,
+                                                    double gamma, double mach_inf, double v_inf, double t_inf,
+                                                    double r_gas, float* grad_dev, float* temperature_dev,
+                                                    void* stream);
+
 /* Device time of the sweep kernels in the plan's last solve with
  * options.profile set, from CUDA events on the solve's stream:
  * out[0] / out[1]: total ms / launches of the CG kernel that applies the
  * stencil (p update, q = A p, x update, p.q); out[2] / out[3]: the CG
  * residual-update kernel (r -= alpha q, r.r); out[4] / out[5]: the FP64
- * residual kernel of the refinement loop; out[6] / out[7]: reserved (0). */
+ * residual kernel of the refinement loop; out[6] / out[7]: the multigrid
+ * preconditioner (one application z = B r per CG iteration; 0 without it). */
 OSMODI_API osmodi_status osmodi_kernel_stats(osmodi_plan plan, double out[8]);
 
 /*

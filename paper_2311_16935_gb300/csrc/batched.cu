@@ -19,6 +19,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <vector>
 
 #include "internal.cuh"
@@ -648,9 +649,25 @@ static bool build_layout(int count, const osmodi_plan* plans, size_t tsize, int 
 }
 
 template <class T, int NDIM, class TG, class TP>
-static cudaError_t launch_batched(const BParams& P, int grid, cudaStream_t s) {
-    void* args[] = {(void*)&P};
-    return cudaLaunchCooperativeKernel((const void*)k_batched<T, NDIM, TG, TP>, dim3(grid), dim3(kTileThreads), args, 0, s);
+static cudaError_t launch_batched(const BParams& P, int grid, cudaStream_t s, bool for_graph) {
+    if (!for_graph) {
+        void* args[] = {(void*)&P};
+        return cudaLaunchCooperativeKernel((const void*)k_batched<T, NDIM, TG, TP>, dim3(grid), dim3(kTileThreads), args, 0,
+                                           s);
+    }
+    // inside stream capture: the cooperative launch attribute becomes a
+    // property of the graph's kernel node (co-residency kept on replay)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kTileThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batched<T, NDIM, TG, TP>, P);
 }
 
 template <class T, int NDIM, class TG, class TP>
@@ -663,56 +680,61 @@ static int max_grid(int num_sms) {
     return bps * num_sms;
 }
 
-template <class T, int NDIM>
-static osmodi_status run_batched(int count, const osmodi_plan* plans, const void* const* grads, int gdt, void* const* ps,
-                                 int pdt, double tol, int max_iter, void* ws, cudaStream_t s, osmodi_result* results) {
-    auto t0 = std::chrono::steady_clock::now();
-    Layout L;
+// Layout, parameters and the upload of the instance / tile tables (these
+// stay in the workspace; a captured graph reads them on every replay).
+template <class T>
+static osmodi_status prepare_batched(int count, const osmodi_plan* plans, const void* const* grads, void* const* ps,
+                                     double tol, int max_iter, void* ws, cudaStream_t s, Layout* L, BParams* P) {
     const int cpt = batched_cpt(plans[0]);
-    build_layout(count, plans, sizeof(T), cpt, &L);
+    build_layout(count, plans, sizeof(T), cpt, L);
     for (int i = 0; i < count; ++i) {
-        L.inst[i].grad = grads[i];
-        L.inst[i].p_user = ps[i];
+        L->inst[i].grad = grads[i];
+        L->inst[i].p_user = ps[i];
     }
     char* base = (char*)ws;
-    BParams P{};
-    P.inst = (const BInst*)(base + L.o_inst);
-    P.tiles = (const BTile*)(base + L.o_tiles);
-    P.st = (BState*)(base + L.o_st);
-    P.gl = (BGlobal*)(base + L.o_gl);
-    P.partials = (double*)(base + L.o_part);
-    P.comp = (double*)(base + L.o_comp);
-    P.b64 = (double*)(base + L.o_b64);
-    P.p64a = (double*)(base + L.o_pa);
-    P.p64b = (double*)(base + L.o_pb);
-    P.r = base + L.o_r;
-    P.x = base + L.o_x;
-    P.q = base + L.o_q;
-    P.pA = base + L.o_pA;
-    P.pB = base + L.o_pB;
-    P.count = count;
-    P.cpt = cpt;
-    P.ntiles = (int)L.tiles.size();
+    *P = BParams{};
+    P->inst = (const BInst*)(base + L->o_inst);
+    P->tiles = (const BTile*)(base + L->o_tiles);
+    P->st = (BState*)(base + L->o_st);
+    P->gl = (BGlobal*)(base + L->o_gl);
+    P->partials = (double*)(base + L->o_part);
+    P->comp = (double*)(base + L->o_comp);
+    P->b64 = (double*)(base + L->o_b64);
+    P->p64a = (double*)(base + L->o_pa);
+    P->p64b = (double*)(base + L->o_pb);
+    P->r = base + L->o_r;
+    P->x = base + L->o_x;
+    P->q = base + L->o_q;
+    P->pA = base + L->o_pA;
+    P->pB = base + L->o_pB;
+    P->count = count;
+    P->cpt = cpt;
+    P->ntiles = (int)L->tiles.size();
     const osmodi_options& o = plans[0]->opt;
-    P.max_refine = o.precision == OSMODI_FP32_REFINE ? o.max_refine : (o.precision == OSMODI_FP32 ? 1 : 4);
-    P.max_iter = max_iter;
-    P.inner_max = o.inner_max;
-    P.tol = tol;
-    P.inner_tol = o.precision == OSMODI_FP32_REFINE ? o.inner_tol : 0.0;
+    P->max_refine = o.precision == OSMODI_FP32_REFINE ? o.max_refine : (o.precision == OSMODI_FP32 ? 1 : 4);
+    P->max_iter = max_iter;
+    P->inner_max = o.inner_max;
+    P->tol = tol;
+    P->inner_tol = o.precision == OSMODI_FP32_REFINE ? o.inner_tol : 0.0;
+    OSM_CUDA(cudaMemcpyAsync((void*)P->inst, L->inst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, s));
+    OSM_CUDA(cudaMemcpyAsync((void*)P->tiles, L->tiles.data(), sizeof(BTile) * L->tiles.size(), cudaMemcpyHostToDevice, s));
+    return OSMODI_OK;
+}
 
-    OSM_CUDA(cudaMemcpyAsync((void*)P.inst, L.inst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, s));
-    OSM_CUDA(cudaMemcpyAsync((void*)P.tiles, L.tiles.data(), sizeof(BTile) * L.tiles.size(), cudaMemcpyHostToDevice, s));
-    OSM_CUDA(cudaMemsetAsync(P.st, 0, sizeof(BState) * count, s));
+// What one solve of the batch puts on the stream: the state resets and the
+// persistent launch.  The same sequence is issued directly or under capture.
+template <class T, int NDIM>
+static osmodi_status enqueue_batched(const BParams& P, int total_comp, int gdt, int pdt, int num_sms, cudaStream_t s,
+                                     bool for_graph) {
+    OSM_CUDA(cudaMemsetAsync(P.st, 0, sizeof(BState) * P.count, s));
     OSM_CUDA(cudaMemsetAsync(P.gl, 0, sizeof(BGlobal), s));
-    OSM_CUDA(cudaMemsetAsync(P.comp, 0, sizeof(double) * 3 * L.total_comp, s));
-
-    const int num_sms = plans[0]->num_sms;
+    OSM_CUDA(cudaMemsetAsync(P.comp, 0, sizeof(double) * 3 * total_comp, s));
     int grid = 0;
     cudaError_t e;
-#define OSM_BL(TG, TP)                                                  \
-    do {                                                                \
-        grid = std::min(max_grid<T, NDIM, TG, TP>(num_sms), P.ntiles);  \
-        e = launch_batched<T, NDIM, TG, TP>(P, std::max(grid, 1), s);   \
+#define OSM_BL(TG, TP)                                                          \
+    do {                                                                        \
+        grid = std::min(max_grid<T, NDIM, TG, TP>(num_sms), P.ntiles);          \
+        e = launch_batched<T, NDIM, TG, TP>(P, std::max(grid, 1), s, for_graph); \
     } while (0)
     if (gdt == OSMODI_F32 && pdt == OSMODI_F32) OSM_BL(float, float);
     else if (gdt == OSMODI_F32) OSM_BL(float, double);
@@ -720,16 +742,16 @@ static osmodi_status run_batched(int count, const osmodi_plan* plans, const void
     else OSM_BL(double, double);
 #undef OSM_BL
     if (e != cudaSuccess) {
-        set_cuda_error(e, "cudaLaunchCooperativeKernel(k_batched)");
+        set_cuda_error(e, for_graph ? "cudaLaunchKernelEx(k_batched, cooperative, captured)"
+                                    : "cudaLaunchCooperativeKernel(k_batched)");
         return OSMODI_E_CUDA;
     }
-    std::vector<BState> st(count);
-    BGlobal gl;
-    OSM_CUDA(cudaMemcpyAsync(st.data(), P.st, sizeof(BState) * count, cudaMemcpyDeviceToHost, s));
-    OSM_CUDA(cudaMemcpyAsync(&gl, P.gl, sizeof(BGlobal), cudaMemcpyDeviceToHost, s));
-    OSM_CUDA(cudaStreamSynchronize(s));
-    auto t1 = std::chrono::steady_clock::now();
-    const double ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    return OSMODI_OK;
+}
+
+// Per-instance results from the states the kernel left behind.
+static osmodi_status finish_batched(int count, const BState* st, const BGlobal& gl, const double* n_valid, double ms,
+                                    osmodi_result* results) {
     if (gl.error) return OSMODI_E_TIMEOUT;
     osmodi_status overall = OSMODI_OK;
     for (int i = 0; i < count; ++i) {
@@ -746,11 +768,150 @@ static osmodi_status run_batched(int count, const osmodi_plan* plans, const void
             R.refine_steps = S.rounds + 1;
             R.eps_R = S.eps;
             R.ms = ms;
-            R.point_updates = ((double)S.it + (double)S.rounds + 1.0) * L.inst[i].n_valid;
+            R.point_updates = ((double)S.it + (double)S.rounds + 1.0) * n_valid[i];
             R.seed_rel_dist = S.pnorm2 > 0 ? std::sqrt(S.dist2 / S.pnorm2) : 0.0;
         }
     }
     return overall;
+}
+
+template <class T, int NDIM>
+static osmodi_status run_batched(int count, const osmodi_plan* plans, const void* const* grads, int gdt, void* const* ps,
+                                 int pdt, double tol, int max_iter, void* ws, cudaStream_t s, osmodi_result* results) {
+    auto t0 = std::chrono::steady_clock::now();
+    Layout L;
+    BParams P;
+    osmodi_status rc = prepare_batched<T>(count, plans, grads, ps, tol, max_iter, ws, s, &L, &P);
+    if (rc != OSMODI_OK) return rc;
+    rc = enqueue_batched<T, NDIM>(P, L.total_comp, gdt, pdt, plans[0]->num_sms, s, false);
+    if (rc != OSMODI_OK) return rc;
+    std::vector<BState> st(count);
+    BGlobal gl;
+    OSM_CUDA(cudaMemcpyAsync(st.data(), P.st, sizeof(BState) * count, cudaMemcpyDeviceToHost, s));
+    OSM_CUDA(cudaMemcpyAsync(&gl, P.gl, sizeof(BGlobal), cudaMemcpyDeviceToHost, s));
+    OSM_CUDA(cudaStreamSynchronize(s));
+    auto t1 = std::chrono::steady_clock::now();
+    const double ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    std::vector<double> nv(count);
+    for (int i = 0; i < count; ++i) nv[i] = L.inst[i].n_valid;
+    return finish_batched(count, st.data(), gl, nv.data(), ms, results);
+}
+
+// ---- graph-captured batch ----
+struct GraphBatch {
+    int count = 0, device = -1;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    BState* h_st = nullptr;   // page-locked: the graph's copy nodes write here
+    BGlobal* h_gl = nullptr;
+    BInst* h_inst = nullptr;  // page-locked tables the graph uploads on every replay
+    BTile* h_tiles = nullptr;
+    std::vector<double> n_valid;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool launched = false;
+};
+
+static void free_graph(GraphBatch* g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->h_st) cudaFreeHost(g->h_st);
+    if (g->h_gl) cudaFreeHost(g->h_gl);
+    if (g->h_inst) cudaFreeHost(g->h_inst);
+    if (g->h_tiles) cudaFreeHost(g->h_tiles);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    delete g;
+}
+
+template <class T, int NDIM>
+static osmodi_status capture_batched(int count, const osmodi_plan* plans, const void* const* grads, int gdt,
+                                     void* const* ps, int pdt, double tol, int max_iter, void* ws, cudaStream_t s,
+                                     GraphBatch* g) {
+    Layout L;
+    BParams P;
+    osmodi_status rc = prepare_batched<T>(count, plans, grads, ps, tol, max_iter, ws, s, &L, &P);
+    if (rc != OSMODI_OK) return rc;
+    OSM_CUDA(cudaStreamSynchronize(s));
+    g->n_valid.resize(count);
+    for (int i = 0; i < count; ++i) g->n_valid[i] = L.inst[i].n_valid;
+    OSM_CUDA(cudaMallocHost((void**)&g->h_st, sizeof(BState) * count));
+    OSM_CUDA(cudaMallocHost((void**)&g->h_gl, sizeof(BGlobal)));
+    OSM_CUDA(cudaMallocHost((void**)&g->h_inst, sizeof(BInst) * count));
+    OSM_CUDA(cudaMallocHost((void**)&g->h_tiles, sizeof(BTile) * L.tiles.size()));
+    std::memset(g->h_gl, 0, sizeof(BGlobal));
+    std::memcpy(g->h_inst, L.inst.data(), sizeof(BInst) * count);
+    std::memcpy(g->h_tiles, L.tiles.data(), sizeof(BTile) * L.tiles.size());
+    const size_t n_tiles = L.tiles.size();
+    // the legacy default stream cannot be captured: capture on a private one
+    cudaStream_t cs = nullptr;
+    OSM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        set_cuda_error(e, "cudaStreamBeginCapture(batched)");
+        return OSMODI_E_CUDA;
+    }
+    // the tables first, so that a replay does not depend on what other
+    // solves left in the workspace
+    e = cudaMemcpyAsync((void*)P.inst, g->h_inst, sizeof(BInst) * count, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((void*)P.tiles, g->h_tiles, sizeof(BTile) * n_tiles, cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "cudaMemcpyAsync(batched tables, captured)");
+        rc = OSMODI_E_CUDA;
+    } else {
+        rc = enqueue_batched<T, NDIM>(P, L.total_comp, gdt, pdt, plans[0]->num_sms, cs, true);
+    }
+    if (rc == OSMODI_OK) {
+        e = cudaMemcpyAsync(g->h_st, P.st, sizeof(BState) * count, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->h_gl, P.gl, sizeof(BGlobal), cudaMemcpyDeviceToHost, cs);
+        if (e != cudaSuccess) {
+            set_cuda_error(e, "cudaMemcpyAsync(batched states, captured)");
+            rc = OSMODI_E_CUDA;
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (rc != OSMODI_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc;
+    }
+    if (e != cudaSuccess || !graph) {
+        set_cuda_error(e, "cudaStreamEndCapture(batched)");
+        return OSMODI_E_CUDA;
+    }
+    g->graph = graph;
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "cudaGraphInstantiate(batched)");
+        return OSMODI_E_CUDA;
+    }
+    OSM_CUDA(cudaEventCreate(&g->ev0));
+    OSM_CUDA(cudaEventCreate(&g->ev1));
+    return OSMODI_OK;
+}
+
+// the checks osmodi_solve_batched and osmodi_batch_graph_create share
+static osmodi_status check_batch(int count, const osmodi_plan* plans, const void* const* grads, int grad_dtype,
+                                 void* const* ps, int p_dtype, double tol, int max_iter, void* workspace) {
+    if (count <= 0 || !plans || !grads || !ps) return OSMODI_E_INVALID;
+    if ((grad_dtype != OSMODI_F32 && grad_dtype != OSMODI_F64) || (p_dtype != OSMODI_F32 && p_dtype != OSMODI_F64))
+        return OSMODI_E_INVALID;
+    if (!(tol > 0.0) || !std::isfinite(tol) || max_iter < 0) return OSMODI_E_INVALID;
+    if (!workspace || ((uintptr_t)workspace & 255u)) return OSMODI_E_WORKSPACE;
+    const int ndim = plans[0] ? plans[0]->ndim : 0;
+    int dev = -1;
+    OSM_CUDA(cudaGetDevice(&dev));
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i] || !grads[i] || !ps[i]) return OSMODI_E_INVALID;
+        if (plans[i]->ndim != ndim || plans[i]->device != dev) return OSMODI_E_INVALID;
+        if (plans[i]->n_chunks > (int64_t)kTileThreads * (int64_t)(1 << 30)) return OSMODI_E_INVALID;
+    }
+    if (plans[0]->opt.scheme != OSMODI_FPCG) return OSMODI_E_UNSUPPORTED;
+    return OSMODI_OK;
 }
 
 }  // namespace
@@ -801,25 +962,74 @@ extern "C" osmodi_status osmodi_solve_batched(int count, const osmodi_plan* plan
                                               void* const* ps, int p_dtype, double tol, int max_iter, void* workspace,
                                               void* stream, osmodi_result* results) {
     if (results && count > 0) std::memset(results, 0, sizeof(osmodi_result) * (size_t)count);
-    if (count <= 0 || !plans || !grads || !ps) return OSMODI_E_INVALID;
-    if ((grad_dtype != OSMODI_F32 && grad_dtype != OSMODI_F64) || (p_dtype != OSMODI_F32 && p_dtype != OSMODI_F64))
-        return OSMODI_E_INVALID;
-    if (!(tol > 0.0) || !std::isfinite(tol) || max_iter < 0) return OSMODI_E_INVALID;
-    if (!workspace || ((uintptr_t)workspace & 255u)) return OSMODI_E_WORKSPACE;
-    const int ndim = plans[0] ? plans[0]->ndim : 0;
-    int dev = -1;
-    OSM_CUDA(cudaGetDevice(&dev));
-    for (int i = 0; i < count; ++i) {
-        if (!plans[i] || !grads[i] || !ps[i]) return OSMODI_E_INVALID;
-        if (plans[i]->ndim != ndim || plans[i]->device != dev) return OSMODI_E_INVALID;
-        if (plans[i]->n_chunks > (int64_t)kTileThreads * (int64_t)(1 << 30)) return OSMODI_E_INVALID;
-    }
-    if (plans[0]->opt.scheme != OSMODI_FPCG) return OSMODI_E_UNSUPPORTED;
+    const osmodi_status chk = check_batch(count, plans, grads, grad_dtype, ps, p_dtype, tol, max_iter, workspace);
+    if (chk != OSMODI_OK) return chk;
     cudaStream_t s = (cudaStream_t)stream;
+    const int ndim = plans[0]->ndim;
     const bool fp64 = plans[0]->opt.precision == OSMODI_FP64;
     if (ndim == 2)
         return fp64 ? run_batched<double, 2>(count, plans, grads, grad_dtype, ps, p_dtype, tol, max_iter, workspace, s, results)
                     : run_batched<float, 2>(count, plans, grads, grad_dtype, ps, p_dtype, tol, max_iter, workspace, s, results);
     return fp64 ? run_batched<double, 3>(count, plans, grads, grad_dtype, ps, p_dtype, tol, max_iter, workspace, s, results)
                 : run_batched<float, 3>(count, plans, grads, grad_dtype, ps, p_dtype, tol, max_iter, workspace, s, results);
+}
+
+extern "C" osmodi_status osmodi_batch_graph_create(int count, const osmodi_plan* plans, const void* const* grads,
+                                                   int grad_dtype, void* const* ps, int p_dtype, double tol, int max_iter,
+                                                   void* workspace, void* stream, osmodi_batch_graph* out) {
+    if (!out) return OSMODI_E_INVALID;
+    *out = nullptr;
+    const osmodi_status chk = check_batch(count, plans, grads, grad_dtype, ps, p_dtype, tol, max_iter, workspace);
+    if (chk != OSMODI_OK) return chk;
+    GraphBatch* g = new (std::nothrow) GraphBatch;
+    if (!g) return OSMODI_E_NOMEM;
+    g->count = count;
+    cudaGetDevice(&g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ndim = plans[0]->ndim;
+    const bool fp64 = plans[0]->opt.precision == OSMODI_FP64;
+    osmodi_status rc;
+    if (ndim == 2)
+        rc = fp64 ? capture_batched<double, 2>(count, plans, grads, grad_dtype, ps, p_dtype, tol, max_iter, workspace, s, g)
+                  : capture_batched<float, 2>(count, plans, grads, grad_dtype, ps, p_dtype, tol, max_iter, workspace, s, g);
+    else
+        rc = fp64 ? capture_batched<double, 3>(count, plans, grads, grad_dtype, ps, p_dtype, tol, max_iter, workspace, s, g)
+                  : capture_batched<float, 3>(count, plans, grads, grad_dtype, ps, p_dtype, tol, max_iter, workspace, s, g);
+    if (rc != OSMODI_OK) {
+        free_graph(g);
+        return rc;
+    }
+    *out = reinterpret_cast<osmodi_batch_graph>(g);
+    return OSMODI_OK;
+}
+
+extern "C" osmodi_status osmodi_batch_graph_launch(osmodi_batch_graph h, void* stream) {
+    GraphBatch* g = reinterpret_cast<GraphBatch*>(h);
+    if (!g || !g->exec) return OSMODI_E_INVALID;
+    int dev = -1;
+    OSM_CUDA(cudaGetDevice(&dev));
+    if (dev != g->device) return OSMODI_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    OSM_CUDA(cudaEventRecord(g->ev0, s));
+    OSM_CUDA(cudaGraphLaunch(g->exec, s));
+    OSM_CUDA(cudaEventRecord(g->ev1, s));
+    g->launched = true;
+    return OSMODI_OK;
+}
+
+extern "C" osmodi_status osmodi_batch_graph_results(osmodi_batch_graph h, osmodi_result* results) {
+    GraphBatch* g = reinterpret_cast<GraphBatch*>(h);
+    if (!g || !g->exec || !g->launched) return OSMODI_E_INVALID;
+    if (results) std::memset(results, 0, sizeof(osmodi_result) * (size_t)g->count);
+    OSM_CUDA(cudaEventSynchronize(g->ev1));
+    float ms = 0.f;
+    OSM_CUDA(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+    return finish_batched(g->count, g->h_st, *g->h_gl, g->n_valid.data(), (double)ms, results);
+}
+
+extern "C" void osmodi_batch_graph_destroy(osmodi_batch_graph h) {
+    GraphBatch* g = reinterpret_cast<GraphBatch*>(h);
+    if (!g) return;
+    if (g->ev1 && g->launched) cudaEventSynchronize(g->ev1);
+    free_graph(g);
 }

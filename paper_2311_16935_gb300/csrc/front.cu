@@ -1,0 +1,343 @@
+// Source-term front ends: the pressure gradient f that the integration
+// consumes, computed on the GPU from velocity data.
+//
+//   incompressible  Eq. 1 (Section 1): f = -rho (du/dt + (u . grad) u) + mu lap u
+//   rans            Eq. RANS_f (Section 3.3): f_i = -rho (U_j dU_i/dx_j + d<u_i'u_j'>/dx_j)
+//   compressible    Eq. compressible-pressure (Section 3.4), per cell the
+//                   system (delta_ij + <u_i u_j>/(R T)) g_j = -(1/(R T)) (d<u_i u_j>/dx_j
+//                   - <u_i u_j>/T dT/dx_j) for g = grad ln(P/P_inf), with
+//                   T = T_inf (1 + (gamma-1)/2 M_inf^2 (1 - |U|^2/V_inf^2)).
+//
+// Differences (the paper does not fix a scheme): centred where both
+// neighbours along the axis are valid, else the three-point one-sided
+// difference towards the valid side when the cell two steps away is valid
+// too, else the two-point difference, else 0; second derivatives centred,
+// else three-point one-sided, else 0.  Derivatives of products difference
+// the product.  Which neighbours are valid comes from the plan's per-cell
+// class word: a face class is 0 when the neighbour is missing and >= 10 when
+// the cell beyond it is valid as well.  One thread per cell, FP32 arithmetic
+// (PIV data is FP32); missing cells get f = 0.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace osm {
+namespace {
+
+struct FrontGeo {
+    int64_t nx, ny, nz, px, n_dense;
+    int64_t st[3];   // dense strides per axis
+    float inv_h[3];
+    int ndim, xblocks;
+};
+
+// the cell of this thread: 128 threads along x, blocks over (x block, row)
+__device__ __forceinline__ bool cell_of(const FrontGeo& g, int64_t* d, int64_t* pad) {
+    const int64_t row = blockIdx.x / g.xblocks;
+    const int64_t i = (int64_t)(blockIdx.x % g.xblocks) * blockDim.x + threadIdx.x;
+    if (i >= g.nx || row >= g.ny * g.nz) return false;
+    *d = row * g.nx + i;
+    *pad = row * g.px + i;
+    return true;
+}
+
+__device__ __forceinline__ unsigned cls_of(uint32_t w, int f) { return (w >> (5 * f)) & 31u; }
+
+// first derivative along one axis; q(idx) loads (or forms) the field at a
+// dense index, qc is its value at the cell; cp / cm the face classes
+template <class Q>
+__device__ __forceinline__ float d1(Q q, int64_t c, int64_t st, float inv_h, unsigned cp, unsigned cm, float qc) {
+    if (cp && cm) return (q(c + st) - q(c - st)) * 0.5f * inv_h;
+    if (cp) {
+        if (cp >= 10u) return (-3.f * qc + 4.f * q(c + st) - q(c + 2 * st)) * 0.5f * inv_h;
+        return (q(c + st) - qc) * inv_h;
+    }
+    if (cm) {
+        if (cm >= 10u) return (3.f * qc - 4.f * q(c - st) + q(c - 2 * st)) * 0.5f * inv_h;
+        return (qc - q(c - st)) * inv_h;
+    }
+    return 0.f;
+}
+
+template <class Q>
+__device__ __forceinline__ float d2(Q q, int64_t c, int64_t st, float inv_h, unsigned cp, unsigned cm, float qc) {
+    const float i2 = inv_h * inv_h;
+    if (cp && cm) return (q(c + st) - 2.f * qc + q(c - st)) * i2;
+    if (cp >= 10u) return (qc - 2.f * q(c + st) + q(c + 2 * st)) * i2;
+    if (cm >= 10u) return (qc - 2.f * q(c - st) + q(c - 2 * st)) * i2;
+    return 0.f;
+}
+
+// symmetric stress plane of (i, j): xx, yy, [zz,] xy[, xz, yz]
+template <int NDIM>
+__device__ __forceinline__ int splane(int i, int j) {
+    if (i == j) return i;
+    const int a = i < j ? i : j, b = i < j ? j : i;
+    if (NDIM == 2) return 2;
+    return a == 0 ? (b == 1 ? 3 : 4) : 5;
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(128) k_front_incompressible(FrontGeo g, const uint32_t* __restrict__ code32,
+                                                              const float* __restrict__ u, const float* __restrict__ up,
+                                                              const float* __restrict__ un, float inv_dt, int tmode,
+                                                              float rho, float mu, float* __restrict__ f) {
+    int64_t c, pc;
+    if (!cell_of(g, &c, &pc)) return;
+    const uint32_t w = __ldg(code32 + pc);
+    if (!(w >> 31)) {
+#pragma unroll
+        for (int i = 0; i < NDIM; ++i) f[i * g.n_dense + c] = 0.f;
+        return;
+    }
+    float uc[NDIM];
+#pragma unroll
+    for (int i = 0; i < NDIM; ++i) uc[i] = __ldg(u + i * g.n_dense + c);
+#pragma unroll
+    for (int i = 0; i < NDIM; ++i) {
+        const float* ui = u + i * g.n_dense;
+        auto q = [&](int64_t k) { return __ldg(ui + k); };
+        float dudt = 0.f;
+        if (tmode == 3) dudt = (__ldg(un + i * g.n_dense + c) - __ldg(up + i * g.n_dense + c)) * 0.5f * inv_dt;
+        else if (tmode == 2) dudt = (__ldg(un + i * g.n_dense + c) - uc[i]) * inv_dt;
+        else if (tmode == 1) dudt = (uc[i] - __ldg(up + i * g.n_dense + c)) * inv_dt;
+        float conv = 0.f, lap = 0.f;
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const unsigned cp = cls_of(w, 2 * a), cm = cls_of(w, 2 * a + 1);
+            conv += uc[a] * d1(q, c, g.st[a], g.inv_h[a], cp, cm, uc[i]);
+            if (mu != 0.f) lap += d2(q, c, g.st[a], g.inv_h[a], cp, cm, uc[i]);
+        }
+        f[i * g.n_dense + c] = -rho * (dudt + conv) + mu * lap;
+    }
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(128) k_front_rans(FrontGeo g, const uint32_t* __restrict__ code32,
+                                                   const float* __restrict__ U, const float* __restrict__ R, float rho,
+                                                   float* __restrict__ f) {
+    int64_t c, pc;
+    if (!cell_of(g, &c, &pc)) return;
+    const uint32_t w = __ldg(code32 + pc);
+    if (!(w >> 31)) {
+#pragma unroll
+        for (int i = 0; i < NDIM; ++i) f[i * g.n_dense + c] = 0.f;
+        return;
+    }
+    float uc[NDIM];
+#pragma unroll
+    for (int i = 0; i < NDIM; ++i) uc[i] = __ldg(U + i * g.n_dense + c);
+#pragma unroll
+    for (int i = 0; i < NDIM; ++i) {
+        const float* ui = U + i * g.n_dense;
+        auto q = [&](int64_t k) { return __ldg(ui + k); };
+        float acc = 0.f;
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const unsigned cp = cls_of(w, 2 * a), cm = cls_of(w, 2 * a + 1);
+            acc += uc[a] * d1(q, c, g.st[a], g.inv_h[a], cp, cm, uc[i]);
+            const float* rij = R + splane<NDIM>(i, a) * g.n_dense;
+            auto qr = [&](int64_t k) { return __ldg(rij + k); };
+            acc += d1(qr, c, g.st[a], g.inv_h[a], cp, cm, __ldg(rij + c));
+        }
+        f[i * g.n_dense + c] = -rho * acc;
+    }
+}
+
+struct CompConsts {
+    float t_inf, c_adiab, inv_v2, inv_r;  // c_adiab = (gamma-1)/2 M_inf^2
+};
+
+template <int NDIM>
+__global__ void __launch_bounds__(128) k_front_compressible(FrontGeo g, const uint32_t* __restrict__ code32,
+                                                            const float* __restrict__ U, const float* __restrict__ R,
+                                                            CompConsts k, float* __restrict__ f, float* __restrict__ tout,
+                                                            int* __restrict__ singular) {
+    int64_t c, pc;
+    if (!cell_of(g, &c, &pc)) return;
+    const uint32_t w = __ldg(code32 + pc);
+    auto temp = [&](int64_t idx) {
+        float v2 = 0.f;
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const float ua = __ldg(U + a * g.n_dense + idx);
+            v2 += ua * ua;
+        }
+        return k.t_inf * (1.f + k.c_adiab * (1.f - v2 * k.inv_v2));
+    };
+    if (!(w >> 31)) {
+#pragma unroll
+        for (int i = 0; i < NDIM; ++i) f[i * g.n_dense + c] = 0.f;
+        if (tout) tout[c] = 0.f;
+        return;
+    }
+    float uc[NDIM];
+#pragma unroll
+    for (int i = 0; i < NDIM; ++i) uc[i] = __ldg(U + i * g.n_dense + c);
+    const float Tc = temp(c);
+    if (tout) tout[c] = Tc;
+    float dT[NDIM];
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a)
+        dT[a] = d1(temp, c, g.st[a], g.inv_h[a], cls_of(w, 2 * a), cls_of(w, 2 * a + 1), Tc);
+    const float rt_inv = k.inv_r / Tc;
+    float A[NDIM][NDIM + 1];
+#pragma unroll
+    for (int i = 0; i < NDIM; ++i) {
+        float div = 0.f, corr = 0.f;
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const float* ui = U + i * g.n_dense;
+            const float* ua = U + a * g.n_dense;
+            const float* rij = R + splane<NDIM>(i, a) * g.n_dense;
+            auto uu = [&](int64_t idx) { return __ldg(ui + idx) * __ldg(ua + idx) + __ldg(rij + idx); };
+            const float uuc = uc[i] * uc[a] + __ldg(rij + c);
+            div += d1(uu, c, g.st[a], g.inv_h[a], cls_of(w, 2 * a), cls_of(w, 2 * a + 1), uuc);
+            corr += uuc * dT[a];
+            A[i][a] = (i == a ? 1.f : 0.f) + uuc * rt_inv;
+        }
+        A[i][NDIM] = -(div - corr / Tc) * rt_inv;
+    }
+    // Gaussian elimination with partial pivoting on the NDIM x NDIM system
+    bool ok = true;
+#pragma unroll
+    for (int col = 0; col < NDIM; ++col) {
+        int piv = col;
+        float best = fabsf(A[col][col]);
+#pragma unroll
+        for (int r = col + 1; r < NDIM; ++r)
+            if (fabsf(A[r][col]) > best) {
+                best = fabsf(A[r][col]);
+                piv = r;
+            }
+        if (!(best > 1e-20f)) ok = false;
+#pragma unroll
+        for (int r = 0; r < NDIM; ++r) {
+            if (r != piv || piv == col) continue;
+#pragma unroll
+            for (int q = 0; q <= NDIM; ++q) {
+                const float t = A[col][q];
+                A[col][q] = A[r][q];
+                A[r][q] = t;
+            }
+        }
+        const float inv = ok ? 1.f / A[col][col] : 0.f;
+#pragma unroll
+        for (int r = col + 1; r < NDIM; ++r) {
+            const float m = A[r][col] * inv;
+#pragma unroll
+            for (int q = col; q <= NDIM; ++q) A[r][q] -= m * A[col][q];
+        }
+    }
+    float x[NDIM];
+#pragma unroll
+    for (int i = NDIM - 1; i >= 0; --i) {
+        float v = A[i][NDIM];
+#pragma unroll
+        for (int q = i + 1; q < NDIM; ++q) v -= A[i][q] * x[q];
+        x[i] = ok ? v / A[i][i] : 0.f;
+    }
+    if (!ok) atomicExch(singular, 1);
+#pragma unroll
+    for (int i = 0; i < NDIM; ++i) f[i * g.n_dense + c] = x[i];
+}
+
+FrontGeo front_geo(osmodi_plan p) {
+    FrontGeo g;
+    g.nx = p->nx;
+    g.ny = p->ny;
+    g.nz = p->nz;
+    g.px = p->px;
+    g.n_dense = p->n_dense;
+    g.st[0] = 1;
+    g.st[1] = p->nx;
+    g.st[2] = p->nx * p->ny;
+    for (int a = 0; a < 3; ++a) g.inv_h[a] = (float)(1.0 / p->h[a]);
+    g.ndim = p->ndim;
+    g.xblocks = (int)((p->nx + 127) / 128);
+    return g;
+}
+
+bool grid_of(const FrontGeo& g, unsigned* blocks) {
+    const long long b = (long long)g.xblocks * g.ny * g.nz;
+    if (b >= (1LL << 31)) return false;
+    *blocks = (unsigned)b;
+    return true;
+}
+
+}  // namespace
+}  // namespace osm
+
+using namespace osm;
+
+extern "C" osmodi_status osmodi_source_incompressible(osmodi_plan p, const float* u, const float* u_prev,
+                                                      const float* u_next, double dt, double rho, double mu, float* grad,
+                                                      void* stream) {
+    if (!p || !u || !grad) return OSMODI_E_INVALID;
+    if ((u_prev || u_next) && !(dt > 0.0 && std::isfinite(dt))) return OSMODI_E_INVALID;
+    if (!std::isfinite(rho) || !std::isfinite(mu)) return OSMODI_E_INVALID;
+    const FrontGeo g = front_geo(p);
+    unsigned blocks;
+    if (!grid_of(g, &blocks)) return OSMODI_E_INVALID;
+    const int tmode = (u_prev ? 1 : 0) | (u_next ? 2 : 0);
+    const float inv_dt = tmode ? (float)(1.0 / dt) : 0.f;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->ndim == 2)
+        k_front_incompressible<2><<<blocks, 128, 0, s>>>(g, p->code32, u, u_prev, u_next, inv_dt, tmode, (float)rho,
+                                                          (float)mu, grad);
+    else
+        k_front_incompressible<3><<<blocks, 128, 0, s>>>(g, p->code32, u, u_prev, u_next, inv_dt, tmode, (float)rho,
+                                                          (float)mu, grad);
+    OSM_CUDA(cudaGetLastError());
+    return OSMODI_OK;
+}
+
+extern "C" osmodi_status osmodi_source_rans(osmodi_plan p, const float* u_mean, const float* stress, double rho,
+                                            float* grad, void* stream) {
+    if (!p || !u_mean || !stress || !grad) return OSMODI_E_INVALID;
+    if (!std::isfinite(rho)) return OSMODI_E_INVALID;
+    const FrontGeo g = front_geo(p);
+    unsigned blocks;
+    if (!grid_of(g, &blocks)) return OSMODI_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->ndim == 2) k_front_rans<2><<<blocks, 128, 0, s>>>(g, p->code32, u_mean, stress, (float)rho, grad);
+    else k_front_rans<3><<<blocks, 128, 0, s>>>(g, p->code32, u_mean, stress, (float)rho, grad);
+    OSM_CUDA(cudaGetLastError());
+    return OSMODI_OK;
+}
+
+extern "C" osmodi_status osmodi_source_compressible(osmodi_plan p, const float* u_mean, const float* stress, double gamma,
+                                                    double mach_inf, double v_inf, double t_inf, double r_gas,
+                                                    float* grad, float* temperature, void* stream) {
+    if (!p || !u_mean || !stress || !grad) return OSMODI_E_INVALID;
+    if (!(gamma > 1.0) || !(mach_inf >= 0.0) || !(v_inf > 0.0) || !(t_inf > 0.0) || !(r_gas > 0.0)) return OSMODI_E_INVALID;
+    if (!std::isfinite(gamma) || !std::isfinite(mach_inf) || !std::isfinite(v_inf) || !std::isfinite(t_inf) ||
+        !std::isfinite(r_gas))
+        return OSMODI_E_INVALID;
+    const FrontGeo g = front_geo(p);
+    unsigned blocks;
+    if (!grid_of(g, &blocks)) return OSMODI_E_INVALID;
+    CompConsts k;
+    k.t_inf = (float)t_inf;
+    k.c_adiab = (float)(0.5 * (gamma - 1.0) * mach_inf * mach_inf);
+    k.inv_v2 = (float)(1.0 / (v_inf * v_inf));
+    k.inv_r = (float)(1.0 / r_gas);
+    cudaStream_t s = (cudaStream_t)stream;
+    int* flag = nullptr;
+    OSM_CUDA(cudaMallocAsync((void**)&flag, sizeof(int), s));
+    OSM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    if (p->ndim == 2) k_front_compressible<2><<<blocks, 128, 0, s>>>(g, p->code32, u_mean, stress, k, grad, temperature, flag);
+    else k_front_compressible<3><<<blocks, 128, 0, s>>>(g, p->code32, u_mean, stress, k, grad, temperature, flag);
+    cudaError_t e = cudaGetLastError();
+    int h_flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(flag, s);
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "osmodi_source_compressible");
+        return OSMODI_E_CUDA;
+    }
+    return h_flag ? OSMODI_E_NAN_INPUT : OSMODI_OK;
+}

@@ -33,6 +33,7 @@ namespace osm {
 
 constexpr int kClasses = 19;  // ray-count classes per face axis (0 = missing neighbour)
 constexpr int kMaxBlocks = 8192;
+constexpr int kAaMaxDepth = 8;  // Anderson mixing depth limit of the OUTER scheme
 
 struct Constants {
     double c[9];  // c_jk, row-major
@@ -90,6 +91,8 @@ struct osmodi_plan_s {
     void* pinned = nullptr;  // 4 KB page-locked host mirror of the device scalars
     double kstats[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // profile mode: ms / launches per kernel kind
     std::vector<cudaEvent_t> events;             // profile mode event pool
+    void* tma_maps = nullptr;                    // tensor maps of the TMA-staged sweep (solve.cu)
+    void* mg = nullptr;                          // multigrid hierarchy (mg.cu), when the preconditioner is on
 };
 
 namespace osm {

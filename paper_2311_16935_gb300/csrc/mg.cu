@@ -1,0 +1,555 @@
+// Multigrid preconditioner (see mg.cuh for what it computes and why it keeps
+// CG's requirements).  Level 0 is the plan's own grid: padded box, 4-cell
+// chunks, face weights b~_j F_j read from the 1-byte codes, the same
+// neighbour gather as the CG kernels.  Levels >= 1 are dense boxes with
+// explicit FP32 weights to the +x / +y / +z neighbour (0 when the aggregates
+// share no valid face) and omega / diagonal; one thread per cell.  The
+// coarsest level (at most 8 cells per axis) is swept by one block.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "cg_state.cuh"
+#include "internal.cuh"
+#include "mg.cuh"
+#include "stencil.cuh"
+
+namespace osm {
+
+namespace {
+
+constexpr float kOmega = 0.8f;   // Jacobi damping
+constexpr float kScale = 1.6f;   // coarse-correction scale (aggregation under-estimates the coarse operator)
+constexpr int kNu = 2;           // sweeps before and after the coarse correction
+constexpr int kCoarseSweeps = 40;
+constexpr int kCoarsestMax = 8;  // cells per axis on the coarsest level
+constexpr int kCoarsestThreads = 512;
+
+struct Level {
+    int64_t nx, ny, nz, n;
+    float *wx, *wy, *wz, *dinv;
+    double active;  // cells with a nonzero diagonal
+};
+
+struct Hier {
+    std::vector<Level> lv;  // lv[0] = level 1 (the first coarse level)
+    void* mem = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// setup
+// ---------------------------------------------------------------------------
+struct FineDims {
+    int64_t nx, ny, nz, px;
+    float F[3];
+};
+
+// level-1 weights from the fine codes: the +x weight of aggregate (I, J, K)
+// sums F_x over the fine cells (2I+1, 2J+dj, 2K+dk) whose +x face is valid
+__global__ void k_mg_setup_fine(const uint8_t* __restrict__ code8, FineDims f, Level c) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < c.n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t I = q % c.nx, J = (q / c.nx) % c.ny, K = q / (c.nx * c.ny);
+        float wx = 0.f, wy = 0.f, wz = 0.f;
+        auto bit = [&](int64_t i, int64_t j, int64_t k, int b) -> float {
+            if (i >= f.nx || j >= f.ny || k >= f.nz) return 0.f;
+            return (code8[(k * f.ny + j) * f.px + i] >> b) & 1u ? 1.f : 0.f;
+        };
+        const int dz = f.nz > 1 ? 2 : 1;
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < dz; ++b) {
+                wx += bit(2 * I + 1, 2 * J + a, 2 * K + b, 0);
+                wy += bit(2 * I + a, 2 * J + 1, 2 * K + b, 2);
+                if (f.nz > 1) wz += bit(2 * I + a, 2 * J + b, 2 * K + 1, 4);
+            }
+        c.wx[q] = wx * f.F[0];
+        c.wy[q] = wy * f.F[1];
+        c.wz[q] = wz * f.F[2];
+    }
+}
+
+// level l+1 weights from level l
+__global__ void k_mg_setup_coarse(Level f, Level c) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < c.n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t I = q % c.nx, J = (q / c.nx) % c.ny, K = q / (c.nx * c.ny);
+        float wx = 0.f, wy = 0.f, wz = 0.f;
+        auto at = [&](const float* w, int64_t i, int64_t j, int64_t k) -> float {
+            if (i >= f.nx || j >= f.ny || k >= f.nz) return 0.f;
+            return w[(k * f.ny + j) * f.nx + i];
+        };
+        const int dz = f.nz > 1 ? 2 : 1;
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < dz; ++b) {
+                wx += at(f.wx, 2 * I + 1, 2 * J + a, 2 * K + b);
+                wy += at(f.wy, 2 * I + a, 2 * J + 1, 2 * K + b);
+                if (f.nz > 1) wz += at(f.wz, 2 * I + a, 2 * J + b, 2 * K + 1);
+            }
+        c.wx[q] = wx;
+        c.wy[q] = wy;
+        c.wz[q] = wz;
+    }
+}
+
+__global__ void k_mg_setup_dinv(Level c, unsigned long long* active) {
+    unsigned long long cnt = 0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < c.n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q % c.nx, j = (q / c.nx) % c.ny, k = q / (c.nx * c.ny);
+        float d = c.wx[q] + c.wy[q] + c.wz[q];
+        if (i > 0) d += c.wx[q - 1];
+        if (j > 0) d += c.wy[q - c.nx];
+        if (k > 0) d += c.wz[q - c.nx * c.ny];
+        c.dinv[q] = d > 0.f ? kOmega / d : 0.f;
+        cnt += d > 0.f;
+    }
+    atomicAdd(active, cnt);
+}
+
+// ---------------------------------------------------------------------------
+// level 0 (the plan's grid)
+// ---------------------------------------------------------------------------
+enum { M_SWEEP = 0, M_FIRST = 1, M_RESID = 2, M_PROLONG = 3 };
+
+template <class T>
+struct FineArgs {
+    int64_t px, plane, n_chunks, n_box, cpr;  // cpr: chunks per padded row
+    int64_t nx, ny, nz;
+    int64_t cnx, cny;                         // level-1 dims (parents)
+    T F[3];
+    T omega, scale;
+};
+
+template <class T, int NDIM>
+__device__ __forceinline__ T diag0(uint32_t cw, int m, const T* F) {
+    const unsigned fm = face_bits8(cw, m);
+    T d = F[0] * (T)((fm & 1u) + ((fm >> 1) & 1u)) + F[1] * (T)(((fm >> 2) & 1u) + ((fm >> 3) & 1u));
+    if (NDIM == 3) d += F[2] * (T)(((fm >> 4) & 1u) + ((fm >> 5) & 1u));
+    return d;
+}
+
+// (r, z) of the preconditioned CG -> the state (beta, rho; the first direction
+// of a segment, keeping the previous one on a reliable-update continuation)
+__device__ __forceinline__ void finish_rz(CgState* st, double rz) {
+    if (st->pending) {
+        const bool keep = st->keep != 0;
+        st->beta = keep ? rz * st->beta / st->rho : 0.0;
+        st->first = keep ? 0 : 1;
+        st->pending = 0;
+    } else {
+        st->beta = rz / st->rho;
+    }
+    st->rho = rz;
+    if (!(rz > 0.0) || !isfinite(rz)) {  // B r = 0 with r != 0 cannot happen for SPD B: stop
+        st->breakdown = 1;
+        st->status = kConverged;
+    }
+}
+
+// MODE M_FIRST:   out = omega D^-1 r                 (first sweep from zero)
+// MODE M_SWEEP:   out = z + omega D^-1 (r - L z)
+// MODE M_RESID:   out = r - L z                      (for the restriction)
+// MODE M_PROLONG: z' = z + scale * P zc, out = z' + omega D^-1 (r - L z')
+// DOT: reduce (r, out) and finish the CG state
+template <class T, int NDIM, int MODE, bool DOT>
+__global__ void __launch_bounds__(256) k_mg_fine(const T* __restrict__ z, const T* __restrict__ r,
+                                                 const T* __restrict__ zc, T* __restrict__ out,
+                                                 const uint8_t* __restrict__ code8, FineArgs<T> g, CgState* st,
+                                                 double* partials) {
+    if (st->status != kRunning) return;
+    ChunkLoop L;
+    double acc[1] = {0.0};
+    for (int64_t base = L.base; base < g.n_chunks; base += L.stride) {
+        const int64_t ch = base + L.lane;
+        const bool act = ch < g.n_chunks;
+        const int64_t i0 = ch * 4;
+        const uint32_t cw = act ? __ldg(reinterpret_cast<const uint32_t*>(code8 + i0)) : 0u;
+        const V4<T> rv = act ? ld4(r + i0) : zero4<T>();
+        V4<T> o;
+        if (MODE == M_FIRST) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const T d = diag0<T, NDIM>(cw, m, g.F);
+                o.v[m] = (valid8(cw, m) && d > T(0)) ? g.omega * rv.v[m] / d : T(0);
+            }
+        } else {
+            // the chunk's row and plane (for the parents of MODE M_PROLONG)
+            const int64_t row = act ? ch / g.cpr : 0;
+            const int64_t ix = (ch - row * g.cpr) * 4;
+            const int64_t jy = NDIM == 3 ? row % g.ny : row;
+            const int64_t kz = NDIM == 3 ? row / g.ny : 0;
+            auto parent_row = [&](int64_t j, int64_t k) {
+                j = j < 0 ? 0 : (j >= g.ny ? g.ny - 1 : j);
+                k = k < 0 ? 0 : (k >= g.nz ? g.nz - 1 : k);
+                return zc + ((k >> 1) * g.cny + (j >> 1)) * g.cnx;
+            };
+            auto px_of = [&](int64_t i) {
+                i = i < 0 ? 0 : i;
+                const int64_t c = i >> 1;
+                return c >= g.cnx ? g.cnx - 1 : c;
+            };
+            auto f4 = [&](int64_t off) {
+                V4<T> v = ld4(z + i0 + off);
+                if (MODE == M_PROLONG) {
+                    // plane offsets first: with ny = 1 they equal the row
+                    // offsets, whose neighbours do not exist then
+                    int64_t j = jy, k = kz;
+                    if (NDIM == 3 && off == g.plane) ++k;
+                    else if (NDIM == 3 && off == -g.plane) --k;
+                    else if (off == g.px) ++j;
+                    else if (off == -g.px) --j;
+                    const T* cr = parent_row(j, k);
+                    const T a = g.scale * cr[px_of(ix)], b = g.scale * cr[px_of(ix + 2)];
+                    v.v[0] += a;
+                    v.v[1] += a;
+                    v.v[2] += b;
+                    v.v[3] += b;
+                }
+                return v;
+            };
+            auto f1 = [&](int64_t off) {
+                T v = z[i0 + off];
+                if (MODE == M_PROLONG) v += g.scale * parent_row(jy, kz)[px_of(ix + off)];
+                return v;
+            };
+            const V4<T> c = act ? f4(0) : zero4<T>();
+            const Nbrs<T> nb = gather_clamped<T, NDIM>(c, i0, g.n_box, L.lane, g.px, g.plane, act, f4, f1);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const unsigned fm = face_bits8(cw, m);
+                const T res = rv.v[m] - apply_L<T, NDIM>(fm, c, nb, m, g.F);
+                if (MODE == M_RESID) {
+                    o.v[m] = valid8(cw, m) ? res : T(0);
+                } else {
+                    const T d = diag0<T, NDIM>(cw, m, g.F);
+                    o.v[m] = (valid8(cw, m) && d > T(0)) ? c.v[m] + g.omega * res / d : T(0);
+                }
+            }
+        }
+        if (act) {
+            st4(out + i0, o);
+            if (DOT) {
+                T part = T(0);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) part += rv.v[m] * o.v[m];
+                acc[0] += (double)part;
+            }
+        }
+    }
+    if (DOT) {
+        double tot[1];
+        if (grid_sum<1>(acc, partials, &st->ticketM, tot) && threadIdx.x == 0) finish_rz(st, tot[0]);
+    }
+}
+
+// restriction: rc[I] = sum of the (up to 8) children of t (row pitch `pitch`)
+template <class T>
+__global__ void k_mg_restrict(const T* __restrict__ t, int64_t fnx, int64_t fny, int64_t fnz, int64_t pitch,
+                              T* __restrict__ rc, Level c, const CgState* st) {
+    if (st->status != kRunning) return;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < c.n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t I = q % c.nx, J = (q / c.nx) % c.ny, K = q / (c.nx * c.ny);
+        T s = T(0);
+        const int dz = fnz > 1 ? 2 : 1;
+        for (int b = 0; b < dz; ++b)
+            for (int a = 0; a < 2; ++a) {
+                const int64_t j = 2 * J + a, k = 2 * K + b;
+                if (j >= fny || k >= fnz) continue;
+                const T* row = t + (k * fny + j) * pitch;
+                const int64_t i = 2 * I;
+                s += row[i];
+                if (i + 1 < fnx) s += row[i + 1];
+            }
+        rc[q] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// levels >= 1 (dense, explicit weights)
+// ---------------------------------------------------------------------------
+template <class T>
+struct CoarseArgs {
+    Level lv;
+    int64_t cnx, cny;  // the next coarser level (parents)
+    T scale;
+};
+
+template <class T, int MODE>
+__global__ void k_mg_coarse(const T* __restrict__ z, const T* __restrict__ r, const T* __restrict__ zc,
+                            T* __restrict__ out, CoarseArgs<T> a, const CgState* st) {
+    if (st->status != kRunning) return;
+    const Level& g = a.lv;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < g.n; q += (int64_t)gridDim.x * blockDim.x) {
+        const T dv = (T)g.dinv[q];
+        if (MODE == M_FIRST) {
+            out[q] = dv * r[q];
+            continue;
+        }
+        const int64_t i = q % g.nx, j = (q / g.nx) % g.ny, k = q / (g.nx * g.ny);
+        auto zv = [&](int64_t ii, int64_t jj, int64_t kk) {
+            T v = z[(kk * g.ny + jj) * g.nx + ii];
+            if (MODE == M_PROLONG) v += a.scale * zc[((kk >> 1) * a.cny + (jj >> 1)) * a.cnx + (ii >> 1)];
+            return v;
+        };
+        const T zc0 = zv(i, j, k);
+        T az = T(0);
+        if (i + 1 < g.nx) az += (T)g.wx[q] * (zc0 - zv(i + 1, j, k));
+        if (i > 0) az += (T)g.wx[q - 1] * (zc0 - zv(i - 1, j, k));
+        if (j + 1 < g.ny) az += (T)g.wy[q] * (zc0 - zv(i, j + 1, k));
+        if (j > 0) az += (T)g.wy[q - g.nx] * (zc0 - zv(i, j - 1, k));
+        if (k + 1 < g.nz) az += (T)g.wz[q] * (zc0 - zv(i, j, k + 1));
+        if (k > 0) az += (T)g.wz[q - g.nx * g.ny] * (zc0 - zv(i, j, k - 1));
+        const T res = r[q] - az;
+        out[q] = MODE == M_RESID ? res : zc0 + dv * res;
+    }
+}
+
+// coarsest level: kCoarseSweeps damped Jacobi sweeps from zero in one block
+template <class T>
+__global__ void __launch_bounds__(kCoarsestThreads) k_mg_coarsest(const T* __restrict__ r, T* __restrict__ out, Level g,
+                                                                  const CgState* st) {
+    if (st->status != kRunning) return;
+    __shared__ T za[kCoarsestThreads], zb[kCoarsestThreads];
+    const int q = threadIdx.x;
+    const bool act = q < g.n;
+    int64_t i = 0, j = 0, k = 0;
+    T rq = T(0), dv = T(0), wxp = 0, wxm = 0, wyp = 0, wym = 0, wzp = 0, wzm = 0;
+    if (act) {
+        i = q % g.nx;
+        j = (q / g.nx) % g.ny;
+        k = q / (g.nx * g.ny);
+        rq = r[q];
+        dv = (T)g.dinv[q];
+        wxp = i + 1 < g.nx ? (T)g.wx[q] : T(0);
+        wxm = i > 0 ? (T)g.wx[q - 1] : T(0);
+        wyp = j + 1 < g.ny ? (T)g.wy[q] : T(0);
+        wym = j > 0 ? (T)g.wy[q - g.nx] : T(0);
+        wzp = k + 1 < g.nz ? (T)g.wz[q] : T(0);
+        wzm = k > 0 ? (T)g.wz[q - g.nx * g.ny] : T(0);
+    }
+    const int sx = 1, sy = (int)g.nx, sz = (int)(g.nx * g.ny);
+    za[q] = dv * rq;
+    __syncthreads();
+    T* cur = za;
+    T* nxt = zb;
+    for (int it = 1; it < kCoarseSweeps; ++it) {
+        if (act) {
+            const T c = cur[q];
+            T az = T(0);
+            if (wxp != T(0)) az += wxp * (c - cur[q + sx]);
+            if (wxm != T(0)) az += wxm * (c - cur[q - sx]);
+            if (wyp != T(0)) az += wyp * (c - cur[q + sy]);
+            if (wym != T(0)) az += wym * (c - cur[q - sy]);
+            if (wzp != T(0)) az += wzp * (c - cur[q + sz]);
+            if (wzm != T(0)) az += wzm * (c - cur[q - sz]);
+            nxt[q] = c + dv * (rq - az);
+        }
+        __syncthreads();
+        T* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    if (act) out[q] = cur[q];
+}
+
+Hier* hier_of(osmodi_plan p) { return reinterpret_cast<Hier*>(p->mg); }
+
+int grid_for(osmodi_plan p, int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)p->num_sms * 8));
+}
+
+// the coarse-level vectors of level l (1-based) inside the level workspace
+template <class T>
+struct LevelVecs {
+    T *r, *a, *b;
+};
+
+template <class T>
+LevelVecs<T> level_vecs(const Hier* h, char* base, int l) {
+    size_t off = 0;
+    LevelVecs<T> v{};
+    for (int q = 0; q < (int)h->lv.size(); ++q) {
+        const size_t bytes = (h->lv[q].n * sizeof(T) + 255) & ~size_t(255);
+        if (q == l - 1) {
+            v.r = reinterpret_cast<T*>(base + off);
+            v.a = reinterpret_cast<T*>(base + off + bytes);
+            v.b = reinterpret_cast<T*>(base + off + 2 * bytes);
+            return v;
+        }
+        off += 3 * bytes;
+    }
+    return v;
+}
+
+// V-cycle on level l >= 1; returns the buffer holding z_l
+template <class T>
+T* vcycle_coarse(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, cudaStream_t s) {
+    const Level& g = h->lv[l - 1];
+    LevelVecs<T> v = level_vecs<T>(h, base, l);
+    if (l == (int)h->lv.size()) {
+        k_mg_coarsest<T><<<1, kCoarsestThreads, 0, s>>>(v.r, v.a, g, st);
+        return v.a;
+    }
+    const Level& gc = h->lv[l];
+    CoarseArgs<T> a{g, gc.nx, gc.ny, (T)kScale};
+    const int G = grid_for(p, g.n);
+    T* cur = v.a;
+    T* oth = v.b;
+    k_mg_coarse<T, M_FIRST><<<G, 256, 0, s>>>(nullptr, v.r, nullptr, cur, a, st);
+    for (int i = 1; i < kNu; ++i) {
+        k_mg_coarse<T, M_SWEEP><<<G, 256, 0, s>>>(cur, v.r, nullptr, oth, a, st);
+        std::swap(cur, oth);
+    }
+    k_mg_coarse<T, M_RESID><<<G, 256, 0, s>>>(cur, v.r, nullptr, oth, a, st);
+    LevelVecs<T> vc = level_vecs<T>(h, base, l + 1);
+    k_mg_restrict<T><<<grid_for(p, gc.n), 256, 0, s>>>(oth, g.nx, g.ny, g.nz, g.nx, vc.r, gc, st);
+    T* zc = vcycle_coarse<T>(p, h, base, l + 1, st, s);
+    k_mg_coarse<T, M_PROLONG><<<G, 256, 0, s>>>(cur, v.r, zc, oth, a, st);
+    std::swap(cur, oth);
+    for (int i = 1; i < kNu; ++i) {
+        k_mg_coarse<T, M_SWEEP><<<G, 256, 0, s>>>(cur, v.r, nullptr, oth, a, st);
+        std::swap(cur, oth);
+    }
+    return cur;
+}
+
+template <class T, int NDIM>
+T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, double* partials, cudaStream_t s) {
+    const Hier* h = hier_of(p);
+    const Level& g1 = h->lv[0];
+    FineArgs<T> f;
+    f.px = p->px;
+    f.plane = p->px * p->ny;
+    f.n_chunks = p->n_chunks;
+    f.n_box = p->n_box;
+    f.cpr = p->px / 4;
+    f.nx = p->nx;
+    f.ny = p->ny;
+    f.nz = p->nz;
+    f.cnx = g1.nx;
+    f.cny = g1.ny;
+    for (int a = 0; a < 3; ++a) f.F[a] = (T)p->k.F[a];
+    f.omega = (T)kOmega;
+    f.scale = (T)kScale;
+    const int G = std::min(p->launch.blocks_b > 0 ? p->launch.blocks_b : p->num_sms * 4, kMaxBlocks);
+    T* cur = w.zA;
+    T* oth = w.zB;
+    k_mg_fine<T, NDIM, M_FIRST, false><<<G, 256, 0, s>>>(nullptr, r, nullptr, cur, p->code8, f, st, partials);
+    for (int i = 1; i < kNu; ++i) {
+        k_mg_fine<T, NDIM, M_SWEEP, false><<<G, 256, 0, s>>>(cur, r, nullptr, oth, p->code8, f, st, partials);
+        std::swap(cur, oth);
+    }
+    k_mg_fine<T, NDIM, M_RESID, false><<<G, 256, 0, s>>>(cur, r, nullptr, oth, p->code8, f, st, partials);
+    LevelVecs<T> v1 = level_vecs<T>(h, w.lv, 1);
+    k_mg_restrict<T><<<grid_for(p, g1.n), 256, 0, s>>>(oth, p->nx, p->ny, p->nz, p->px, v1.r, g1, st);
+    T* zc = vcycle_coarse<T>(p, h, w.lv, 1, st, s);
+    if (kNu == 1) {
+        k_mg_fine<T, NDIM, M_PROLONG, true><<<G, 256, 0, s>>>(cur, r, zc, oth, p->code8, f, st, partials);
+        return oth;
+    }
+    k_mg_fine<T, NDIM, M_PROLONG, false><<<G, 256, 0, s>>>(cur, r, zc, oth, p->code8, f, st, partials);
+    std::swap(cur, oth);
+    for (int i = 1; i < kNu; ++i) {
+        if (i == kNu - 1)
+            k_mg_fine<T, NDIM, M_SWEEP, true><<<G, 256, 0, s>>>(cur, r, nullptr, oth, p->code8, f, st, partials);
+        else
+            k_mg_fine<T, NDIM, M_SWEEP, false><<<G, 256, 0, s>>>(cur, r, nullptr, oth, p->code8, f, st, partials);
+        std::swap(cur, oth);
+    }
+    return cur;
+}
+
+}  // namespace
+
+osmodi_status mg_build(osmodi_plan p, cudaStream_t s) {
+    mg_free(p);
+    std::vector<Level> lv;
+    int64_t nx = p->nx, ny = p->ny, nz = p->nz;
+    while (std::max(nx, std::max(ny, nz)) > kCoarsestMax && lv.size() < 24) {
+        Level c{};
+        c.nx = (nx + 1) / 2;
+        c.ny = (ny + 1) / 2;
+        c.nz = p->ndim == 3 ? (nz + 1) / 2 : 1;
+        c.n = c.nx * c.ny * c.nz;
+        lv.push_back(c);
+        nx = c.nx;
+        ny = c.ny;
+        nz = c.nz;
+    }
+    if (lv.empty()) return OSMODI_OK;  // grid already coarse: plain CG
+    size_t bytes = 0;
+    for (const Level& c : lv) bytes += 4 * ((c.n * sizeof(float) + 255) & ~size_t(255));
+    Hier* h = new (std::nothrow) Hier;
+    if (!h) return OSMODI_E_NOMEM;
+    unsigned long long* cnt = nullptr;
+    if (cudaMalloc(&h->mem, bytes + 256) != cudaSuccess || cudaMalloc((void**)&cnt, sizeof(unsigned long long) * lv.size()) != cudaSuccess) {
+        cudaGetLastError();
+        if (h->mem) cudaFree(h->mem);
+        delete h;
+        return OSMODI_E_NOMEM;
+    }
+    char* b = reinterpret_cast<char*>(h->mem);
+    for (Level& c : lv) {
+        const size_t one = (c.n * sizeof(float) + 255) & ~size_t(255);
+        c.wx = reinterpret_cast<float*>(b);
+        c.wy = reinterpret_cast<float*>(b + one);
+        c.wz = reinterpret_cast<float*>(b + 2 * one);
+        c.dinv = reinterpret_cast<float*>(b + 3 * one);
+        b += 4 * one;
+    }
+    h->lv = lv;
+    p->mg = h;
+    OSM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * lv.size(), s));
+    FineDims fd{p->nx, p->ny, p->nz, p->px, {(float)p->k.F[0], (float)p->k.F[1], (float)p->k.F[2]}};
+    k_mg_setup_fine<<<grid_for(p, lv[0].n), 256, 0, s>>>(p->code8, fd, lv[0]);
+    for (size_t q = 1; q < lv.size(); ++q) k_mg_setup_coarse<<<grid_for(p, lv[q].n), 256, 0, s>>>(lv[q - 1], lv[q]);
+    for (size_t q = 0; q < lv.size(); ++q) k_mg_setup_dinv<<<grid_for(p, lv[q].n), 256, 0, s>>>(lv[q], cnt + q);
+    OSM_CUDA(cudaGetLastError());
+    std::vector<unsigned long long> hc(lv.size());
+    OSM_CUDA(cudaMemcpyAsync(hc.data(), cnt, sizeof(unsigned long long) * lv.size(), cudaMemcpyDeviceToHost, s));
+    OSM_CUDA(cudaStreamSynchronize(s));
+    cudaFree(cnt);
+    for (size_t q = 0; q < lv.size(); ++q) h->lv[q].active = (double)hc[q];
+    return OSMODI_OK;
+}
+
+void mg_free(osmodi_plan p) {
+    Hier* h = hier_of(p);
+    if (!h) return;
+    if (h->mem) cudaFree(h->mem);
+    delete h;
+    p->mg = nullptr;
+}
+
+bool mg_enabled(osmodi_plan p) { return p->mg != nullptr; }
+
+int mg_levels(osmodi_plan p) { return p->mg ? (int)hier_of(p)->lv.size() : 0; }
+
+size_t mg_level_bytes(osmodi_plan p, size_t tsize) {
+    const Hier* h = hier_of(p);
+    if (!h) return 0;
+    size_t bytes = 0;
+    for (const Level& c : h->lv) bytes += 3 * ((c.n * tsize + 255) & ~size_t(255));
+    return bytes;
+}
+
+double mg_updates_per_apply(osmodi_plan p) {
+    const Hier* h = hier_of(p);
+    if (!h) return 0.0;
+    // fine and intermediate levels: (nu - 1) + 1 (residual) + nu sweeps with a
+    // stencil application each; the coarsest: kCoarseSweeps - 1
+    double u = 2.0 * kNu * (double)p->n_valid;
+    for (size_t q = 0; q < h->lv.size(); ++q)
+        u += (q + 1 == h->lv.size() ? (double)(kCoarseSweeps - 1) : 2.0 * kNu) * h->lv[q].active;
+    return u;
+}
+
+template <class T>
+T* mg_apply(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, double* partials, cudaStream_t s) {
+    return p->ndim == 2 ? apply_nd<T, 2>(p, r, w, st, partials, s) : apply_nd<T, 3>(p, r, w, st, partials, s);
+}
+
+template float* mg_apply<float>(osmodi_plan, const float*, const MgBuffers<float>&, CgState*, double*, cudaStream_t);
+template double* mg_apply<double>(osmodi_plan, const double*, const MgBuffers<double>&, CgState*, double*, cudaStream_t);
+
+}  // namespace osm

@@ -1,0 +1,44 @@
+// Multigrid preconditioner for the conjugate-gradient solve of the
+// fixed-point system L P = A_tot S (L = A_tot (I - W^{n+1}_off - W^n), the
+// weighted graph Laplacian of the valid cells with face weights b~_j F_j).
+//
+// Not part of the paper: it changes how fast CG reaches the fixed point, not
+// the fixed point.  Aggregation of 2 x 2 (x 2) cells per level with the
+// Galerkin coarse operator of piecewise-constant interpolation -- the coarse
+// face weight is the sum of the fine face weights between two aggregates, so
+// every level is again a weighted graph Laplacian on a regular grid -- damped
+// Jacobi smoothing, the coarse correction scaled by a constant, and damped
+// Jacobi sweeps on the coarsest grid.  Pre- and post-smoothing are the same
+// number of sweeps and the coarsest solve is a fixed polynomial in D^-1 A, so
+// z = B r is a fixed symmetric positive (semi)definite operator, as CG needs.
+#pragma once
+
+#include "cg_state.cuh"
+#include "internal.cuh"
+
+namespace osm {
+
+// hierarchy of the plan: built at plan creation when the preconditioner is on
+osmodi_status mg_build(osmodi_plan p, cudaStream_t s);
+void mg_free(osmodi_plan p);
+bool mg_enabled(osmodi_plan p);
+int mg_levels(osmodi_plan p);                           // coarse levels (0 when off)
+size_t mg_level_bytes(osmodi_plan p, size_t tsize);     // workspace for the coarse-level vectors
+double mg_updates_per_apply(osmodi_plan p);             // valid cells x stencil applications of one B r
+
+// two fine work vectors (padded box) and the coarse-level vectors
+template <class T>
+struct MgBuffers {
+    T* zA;
+    T* zB;
+    char* lv;
+};
+
+// z = B r on `s`; every kernel returns at once unless the CG state is
+// running.  The last fine-level kernel forms (r, z) and updates the state
+// (beta, rho; the first direction of a segment).  Returns the buffer (zA or
+// zB) that holds z.
+template <class T>
+T* mg_apply(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, double* partials, cudaStream_t s);
+
+}  // namespace osm

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "mg.cuh"
 
 namespace osm {
 
@@ -292,6 +293,9 @@ static void free_plan_device(osmodi_plan p) {
     p->pinned = nullptr;
     for (auto ev : p->events) cudaEventDestroy(ev);
     p->events.clear();
+    if (p->tma_maps) std::free(p->tma_maps);  // plain struct of tensor maps
+    p->tma_maps = nullptr;
+    osm::mg_free(p);
     p->code8 = nullptr;
     p->code32 = nullptr;
     p->label = nullptr;
@@ -329,6 +333,8 @@ extern "C" osmodi_status osmodi_create(int ndim, const int64_t dims[3], const do
     if (o.sweeps_per_pass > 4) o.sweeps_per_pass = 4;
     if (o.max_refine < 1) o.max_refine = 32;
     if (o.threads != 0 && o.threads != 128 && o.threads != 256 && o.threads != 512) return OSMODI_E_INVALID;
+    if (o.accel < 0 || o.accel > kAaMaxDepth) return OSMODI_E_INVALID;
+    if (o.precond != 0 && o.precond != 1) return OSMODI_E_INVALID;
 
     osmodi_plan p = new (std::nothrow) osmodi_plan_s();
     if (!p) return OSMODI_E_NOMEM;
@@ -469,6 +475,14 @@ extern "C" osmodi_status osmodi_create(int ndim, const int64_t dims[3], const do
         p->launch.blocks_tiled = (int)std::max<int64_t>(1, std::min<int64_t>(gt, kMaxBlocks));
     }
     if (o.autotune) apply_tuned(p);
+    if (o.precond == 1 && o.scheme == OSMODI_FPCG) {
+        const osmodi_status st = osm::mg_build(p, (cudaStream_t)stream);
+        if (st != OSMODI_OK) {
+            free_plan_device(p);
+            delete p;
+            return st;
+        }
+    }
     *out = p;
     return OSMODI_OK;
 }

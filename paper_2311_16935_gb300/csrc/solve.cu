@@ -24,26 +24,23 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <new>
 #include <string>
 #include <sys/stat.h>
 #include <vector>
 
+#include <cuda.h>
+
+#include "cg_state.cuh"
 #include "internal.cuh"
+#include "mg.cuh"
 #include "stencil.cuh"
 
 namespace osm {
 
-enum { kRunning = 0, kConverged = 1, kFinished = 2 };
 enum { OP_L = 0, OP_M = 1 };
 // reduction partials: one range of kMaxBlocks doubles per slot
 enum { kSlotA = 0, kSlotB = 1, kSlotRes = 2 /* 3 slots */, kSlotMisc = 5 /* 3 slots */, kPartialSlots = 8 };
-
-struct CgState {
-    double rho, rho0, pq, alpha, beta, stop2;
-    long long it, max_it;
-    int status, first, breakdown, pad;
-    unsigned ticketA, ticketB, ticketI, pad2;
-};
 
 struct Scalars {
     double bnorm2, p0sum, rnorm2, rsum, psum, dist2, pnorm2, outer_r2;
@@ -193,7 +190,7 @@ __global__ void __launch_bounds__(512) k_cg_init(T* __restrict__ r, T* __restric
                                                  const int32_t* __restrict__ label, const double* __restrict__ comp_sum,
                                                  const double* __restrict__ comp_cnt, int multi, int64_t n_chunks,
                                                  Scalars* sc, CgState* st, double stop_abs2, double rel2,
-                                                 long long max_it, double* partials, int cont = 0) {
+                                                 long long max_it, double* partials, int cont = 0, int precond = 0) {
     const double mean1 = multi ? 0.0 : sc->rsum / comp_cnt[0];
     double acc[1] = {0.0};
     for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < n_chunks; ch += (int64_t)gridDim.x * blockDim.x) {
@@ -226,14 +223,21 @@ __global__ void __launch_bounds__(512) k_cg_init(T* __restrict__ r, T* __restric
         // true one and x folded into the FP64 iterate; keep the previous search
         // direction, with beta = |r_true|^2 / rho_k (rho_k = rho_{k+1} / beta_k)
         const bool keep = cont && st->breakdown == 0 && st->rho > 0.0 && st->beta > 0.0 && isfinite(st->beta);
-        const double beta = keep ? rho0 * st->beta / st->rho : 0.0;
-        st->rho = rho0;
+        st->precond = precond;
+        if (precond) {
+            // (r, z) and beta follow once the preconditioner has run (mg_apply)
+            st->keep = keep ? 1 : 0;
+            st->pending = 1;
+            st->rr = rho0;
+        } else {
+            st->beta = keep ? rho0 * st->beta / st->rho : 0.0;
+            st->rho = rho0;
+            st->first = keep ? 0 : 1;
+        }
         st->rho0 = rho0;
         st->stop2 = fmax(rel2 * rho0, stop_abs2);
         st->alpha = 0.0;
-        st->beta = beta;
         st->pq = 0.0;
-        st->first = keep ? 0 : 1;
         st->it = 0;
         st->max_it = max_it;
         st->breakdown = 0;
@@ -530,6 +534,231 @@ __global__ void __launch_bounds__(256, MINB) k_cg_a_tiled(const T* __restrict__ 
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// The CG "A" step with TMA-staged planes (operator L, 3D).  A block owns a
+// tile of 128 x 16 cells in (x, y) and marches a slab of z-planes.  A ring of
+// TS shared-memory stages holds, per plane, the r and p_old boxes with a
+// 4-cell / 1-row halo (136 x 18) and the code tile (128 x 16), each filled by
+// one cp.async.bulk.tensor.3d load that completes on the stage's mbarrier;
+// planes z-1, z, z+1 are resident while z+2 .. z+TS-2 are in flight, so the
+// bytes in flight per SM do not depend on registers.  Out-of-range boxes are
+// zero-filled by the copy engine (their values are never used: the face bits
+// of the neighbouring cells are 0).  Every mbarrier wait is bounded.
+// ---------------------------------------------------------------------------
+constexpr int TTX = 128, TTY = 16, THX = 4, TS = 5;
+constexpr int TBX = TTX + 2 * THX, TBY = TTY + 2;
+constexpr int kBoxBytes = TBX * TBY * 4;                       // 9792
+constexpr int kBoxPad = (kBoxBytes + 127) / 128 * 128;         // 9856
+constexpr int kStageBytes = 2 * kBoxPad;                       // 19712
+constexpr int kTmaSmem = TS * kStageBytes + 128;
+
+struct TmaGeo {
+    int64_t px, plane, n_chunks;
+    int nx4, ny, nz, n_tx, n_ty, slab;
+    long long n_items;
+    float F[3];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__global__ void __launch_bounds__(256, 2) k_cg_a_tma(const __grid_constant__ CUtensorMap tm_r,
+                                                     const __grid_constant__ CUtensorMap tm_po,
+                                                     const uint8_t* __restrict__ code8,
+                                                     const float* __restrict__ p_old, float* __restrict__ p_new,
+                                                     float* __restrict__ q, float* __restrict__ x, TmaGeo g, CgState* st,
+                                                     double* partials) {
+    const int status = st->status;
+    if (status == kFinished) return;
+    const bool first = st->first != 0;
+    const bool conv = status == kConverged;
+    const float alpha = (float)st->alpha;
+    const float beta = (float)st->beta;
+    extern __shared__ __align__(128) unsigned char tsm[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tsm) + 127) & ~uintptr_t(127));
+    __shared__ __align__(8) uint64_t bars[TS];
+    __shared__ int abort_flag;
+    double acc[1] = {0.0};
+    if (conv) {
+        for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < g.n_chunks; ch += (int64_t)gridDim.x * blockDim.x) {
+            const V4<float> po = ld4(p_old + ch * 4);
+            V4<float> xv = ld4c(x + ch * 4);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) xv.v[m] += alpha * po.v[m];
+            st4(x + ch * 4, xv);
+        }
+    } else {
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < TS; ++i) mbar_init(&bars[i], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            abort_flag = 0;
+        }
+        __syncthreads();
+        unsigned uses[TS];    // completed phases per stage (uniform in the block)
+        unsigned issued[TS];  // loads issued per stage (every thread keeps the count)
+#pragma unroll
+        for (int i = 0; i < TS; ++i) uses[i] = issued[i] = 0;
+        const unsigned tx_bytes = (first ? 1u : 2u) * (unsigned)kBoxBytes;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (long long item = blockIdx.x; item < g.n_items; item += gridDim.x) {
+            const int tx = (int)(item % g.n_tx);
+            const long long rest = item / g.n_tx;
+            const int ty = (int)(rest % g.n_ty);
+            const int sl = (int)(rest / g.n_ty);
+            const int x0 = tx * TTX, y0 = ty * TTY;
+            const int z0 = sl * g.slab, z1 = min(g.nz, z0 + g.slab);
+            // plane P sits in stage (P - (z0 - 1)) % TS
+            auto stage_of = [&](int P) { return (P - z0 + 1) % TS; };
+            auto issue = [&](int P) {
+                if (P < 0 || P >= g.nz) return;
+                const int sidx = stage_of(P);
+                issued[sidx] += 1;
+                if (threadIdx.x != 0) return;
+                unsigned char* sb = base + sidx * kStageBytes;
+                mbar_expect_tx(&bars[sidx], tx_bytes);
+                tma_load_3d(sb, &tm_r, x0 - THX, y0 - 1, P, &bars[sidx]);
+                if (!first) tma_load_3d(sb + kBoxPad, &tm_po, x0 - THX, y0 - 1, P, &bars[sidx]);
+            };
+            auto wait = [&](int P) {
+                if (P < 0 || P >= g.nz) return;
+                const int sidx = stage_of(P);
+                const unsigned parity = uses[sidx] & 1u;
+                long long spins = 0;
+                while (!mbar_try_wait(&bars[sidx], parity)) {
+                    if (++spins > (1LL << 22)) {
+                        atomicExch(&abort_flag, 1);
+                        return;  // the phase stays pending for the drain below
+                    }
+                    __nanosleep(32);
+                }
+                uses[sidx] += 1;
+            };
+            // prologue: planes z0-1 .. z0+TS-2
+            for (int P = z0 - 1; P <= min(z1, z0 + TS - 2); ++P) issue(P);
+            wait(z0 - 1);
+            wait(z0);
+            for (int z = z0; z < z1; ++z) {
+                wait(z + 1);  // z+1 <= z1 always issued
+                __syncthreads();  // makes the abort decision uniform in the block
+                if (abort_flag) break;
+                const unsigned char* sC = base + stage_of(z) * kStageBytes;
+                const unsigned char* sF = base + stage_of(z + 1) * kStageBytes;
+                const unsigned char* sB = base + stage_of(z - 1) * kStageBytes;
+                const float* rC = reinterpret_cast<const float*>(sC);
+                const float* oC = reinterpret_cast<const float*>(sC + kBoxPad);
+                const float* rF = reinterpret_cast<const float*>(sF);
+                const float* oF = reinterpret_cast<const float*>(sF + kBoxPad);
+                const float* rB = reinterpret_cast<const float*>(sB);
+                const float* oB = reinterpret_cast<const float*>(sB + kBoxPad);
+                auto pv = [&](const float* rr, const float* oo, int idx) { return first ? rr[idx] : rr[idx] + beta * oo[idx]; };
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    const int row = warp + 8 * half;  // 0..15
+                    const int cx = lane;              // chunk within the row
+                    const int gy = y0 + row, gx4 = tx * 32 + cx;
+                    const bool act = gy < g.ny && gx4 < g.nx4;
+                    const int b0 = (row + 1) * TBX + THX + 4 * cx;  // box index of the chunk's first cell
+                    const int64_t i0 = (int64_t)z * g.plane + (int64_t)gy * g.px + (int64_t)gx4 * 4;
+                    const uint32_t cw = act ? __ldg(reinterpret_cast<const uint32_t*>(code8 + i0)) : 0u;
+                    V4<float> c, n, s, f, bk, po;
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        c.v[m] = pv(rC, oC, b0 + m);
+                        n.v[m] = pv(rC, oC, b0 + TBX + m);
+                        s.v[m] = pv(rC, oC, b0 - TBX + m);
+                        f.v[m] = pv(rF, oF, b0 + m);
+                        bk.v[m] = pv(rB, oB, b0 + m);
+                        po.v[m] = first ? 0.f : oC[b0 + m];
+                    }
+                    Nbrs<float> nb;
+                    const float wv = pv(rC, oC, b0 - 1), ev = pv(rC, oC, b0 + 4);
+                    nb.w = {{wv, c.v[0], c.v[1], c.v[2]}};
+                    nb.e = {{c.v[1], c.v[2], c.v[3], ev}};
+                    nb.n = n;
+                    nb.s = s;
+                    nb.f = f;
+                    nb.b = bk;
+                    if (act) {
+                        if (!first) {
+                            V4<float> xv = ld4c(x + i0);
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) xv.v[m] += alpha * po.v[m];
+                            st4(x + i0, xv);
+                        }
+                        V4<float> qv;
+                        float part = 0.f;
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            qv.v[m] = apply_L<float, 3>(face_bits8(cw, m), c, nb, m, g.F);
+                            part += c.v[m] * qv.v[m];
+                        }
+                        st4(p_new + i0, c);
+                        st4(q + i0, qv);
+                        acc[0] += (double)part;
+                    }
+                }
+                __syncthreads();  // everyone is done with plane z-1's stage
+                if (z + TS - 1 <= z1) issue(z + TS - 1);
+            }
+            if (abort_flag) break;
+            __syncthreads();
+        }
+        if (abort_flag) {
+            // a wait gave up: let the copies still in flight land (again
+            // bounded) before the block's shared memory is released
+#pragma unroll
+            for (int i = 0; i < TS; ++i) {
+                long long spins = 0;
+                while (uses[i] < issued[i] && spins < (1LL << 22)) {
+                    if (mbar_try_wait(&bars[i], uses[i] & 1u)) uses[i] += 1;
+                    else { ++spins; __nanosleep(32); }
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) st->err = 1;
+        }
+    }
+    double tot[1];
+    if (grid_sum<1>(acc, partials, &st->ticketA, tot) && threadIdx.x == 0) {
+        if (conv) {
+            st->status = kFinished;
+        } else {
+            st->pq = tot[0];
+            st->first = 0;
+            if (tot[0] > 0.0 && isfinite(tot[0]) && st->err == 0) {
+                st->alpha = st->rho / tot[0];
+            } else {
+                st->alpha = 0.0;
+                st->breakdown = 1;
+                st->status = kConverged;
+            }
+        }
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(512) k_cg_b(T* __restrict__ r, const T* __restrict__ q, int64_t n_chunks, CgState* st,
                                               double* partials) {
@@ -551,11 +780,16 @@ __global__ void __launch_bounds__(512) k_cg_b(T* __restrict__ r, const T* __rest
     }
     double tot[1];
     if (grid_sum<1>(acc, partials, &st->ticketB, tot) && threadIdx.x == 0) {
-        const double rho_new = tot[0];
-        st->beta = rho_new / st->rho;
-        st->rho = rho_new;
+        const double rr = tot[0];
         st->it += 1;
-        if (!(rho_new > st->stop2) || st->it >= st->max_it || !isfinite(rho_new)) st->status = kConverged;
+        if (st->precond) {
+            // beta comes from (r, z) after the preconditioner (mg_apply)
+            st->rr = rr;
+        } else {
+            st->beta = rr / st->rho;
+            st->rho = rr;
+        }
+        if (!(rr > st->stop2) || st->it >= st->max_it || !isfinite(rr)) st->status = kConverged;
     }
 }
 
@@ -780,6 +1014,108 @@ __global__ void __launch_bounds__(256) k_jacobi_fused(const T* __restrict__ e_in
 }
 
 // ---------------------------------------------------------------------------
+// Anderson mixing of the OUTER iterates (depth m <= kAaMaxDepth).
+//
+// x_k is the outer iterate, g = G(x_k) the result of the boundary refresh and
+// inner solve of Eq. MatrixEquation started from x_k, f_k = g - x_k.  The
+// differences dF = f_k - f_{k-1}, dG = g_k - g_{k-1} live in two rings of m
+// columns.  k_aa_diff forms f_k, writes the newest difference pair into ring
+// slot `jnew` (none at k = 0), keeps f_k and g_k for the next step, and
+// returns the FP64 dot products the least-squares problem needs: for every
+// active column c_t (cols[0..n-1], the new one among them) dF_{c_t} . dF_new
+// and dF_{c_t} . f_k.  The host solves the m x m normal equations; k_aa_mix
+// then writes x_{k+1} = g - sum_t gamma_t dG_{c_t} in place of g and into the
+// saved-iterate buffer.  Missing cells hold 0 in every vector.
+// ---------------------------------------------------------------------------
+struct AaState {
+    double dots[2 * kAaMaxDepth];
+    unsigned ticket, pad[3];
+};
+
+template <class T>
+struct AaArgs {
+    const T* xs;       // x_k (saved iterate)
+    const T* g;        // G(x_k)
+    T *f_prev, *g_prev;
+    T *dF, *dG;        // rings: column c at + c * n_box
+    int64_t n_box, n_chunks;
+    int jnew;          // ring slot of the new difference (-1: none)
+    int n;             // active columns, the new one included
+    int cols[kAaMaxDepth];
+    double gamma[kAaMaxDepth];
+};
+
+template <class T>
+__global__ void __launch_bounds__(256) k_aa_diff(AaArgs<T> a, const uint8_t* __restrict__ code8, AaState* st,
+                                                 double* partials) {
+    double acc[2 * kAaMaxDepth];
+#pragma unroll
+    for (int q = 0; q < 2 * kAaMaxDepth; ++q) acc[q] = 0.0;
+    for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < a.n_chunks;
+         ch += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i0 = ch * 4;
+        const uint32_t cw = __ldg(reinterpret_cast<const uint32_t*>(code8 + i0));
+        const V4<T> x = ld4(a.xs + i0), g = ld4(a.g + i0);
+        V4<T> fk;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) fk.v[m] = valid8(cw, m) ? g.v[m] - x.v[m] : T(0);
+        if (a.jnew >= 0) {
+            const V4<T> fp = ld4c(a.f_prev + i0), gp = ld4c(a.g_prev + i0);
+            V4<T> df, dg;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                df.v[m] = fk.v[m] - fp.v[m];
+                dg.v[m] = valid8(cw, m) ? g.v[m] - gp.v[m] : T(0);
+            }
+            st4(a.dF + (int64_t)a.jnew * a.n_box + i0, df);
+            st4(a.dG + (int64_t)a.jnew * a.n_box + i0, dg);
+#pragma unroll
+            for (int t = 0; t < kAaMaxDepth; ++t) {
+                if (t < a.n) {
+                    const int c = a.cols[t];
+                    const V4<T> col = c == a.jnew ? df : ld4(a.dF + (int64_t)c * a.n_box + i0);
+                    T s0 = 0, s1 = 0;
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        s0 += col.v[m] * df.v[m];
+                        s1 += col.v[m] * fk.v[m];
+                    }
+                    acc[t] += (double)s0;
+                    acc[kAaMaxDepth + t] += (double)s1;
+                }
+            }
+        }
+        st4(a.f_prev + i0, fk);
+        st4(a.g_prev + i0, g);
+    }
+    double tot[2 * kAaMaxDepth];
+    if (grid_sum<2 * kAaMaxDepth>(acc, partials, &st->ticket, tot) && threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < 2 * kAaMaxDepth; ++q) st->dots[q] = tot[q];
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_aa_mix(AaArgs<T> a, T* x_out, T* xs_out) {
+    for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < a.n_chunks;
+         ch += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i0 = ch * 4;
+        V4<T> v = ld4c(a.g + i0);
+#pragma unroll
+        for (int t = 0; t < kAaMaxDepth; ++t) {
+            if (t < a.n) {
+                const V4<T> dg = ld4(a.dG + (int64_t)a.cols[t] * a.n_box + i0);
+                const T gm = (T)a.gamma[t];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) v.v[m] -= gm * dg.v[m];
+            }
+        }
+        st4(x_out + i0, v);
+        st4(xs_out + i0, v);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // output: subtract each component's mean, NaN on missing cells, dense layout;
 // also ||P0 - P|| and ||P|| (both gauge-fixed) for the seed distance.
 // ---------------------------------------------------------------------------
@@ -907,6 +1243,11 @@ struct Buffers {
     double *p64a, *p64b, *b64;
     T *r, *x, *q, *pA, *pB;
     T *rc, *rhs, *e2;  // OUTER extras
+    T *mgA, *mgB;       // FPCG with the multigrid preconditioner: z = B r ends in mgB
+    char* mg_lv;        // coarse-level vectors
+    T *aa_xs, *aa_fp, *aa_gp, *aa_dF, *aa_dG;  // OUTER with Anderson mixing
+    double* aa_partials;
+    AaState* aa_st;
     double* partials;
     double* comp;       // 3 * n_comp: sums of r, p, p0
     CgState* st;
@@ -928,11 +1269,26 @@ static size_t carve(osmodi_plan p, void* ws, Buffers<T>* b) {
     t.q = w.take<T>(n);
     t.pA = w.take<T>(n);
     t.pB = w.take<T>(n);
+    if (p->opt.scheme == OSMODI_FPCG && mg_enabled(p)) {
+        t.mgA = w.take<T>(n);
+        t.mgB = w.take<T>(n);
+        t.mg_lv = w.take<char>(mg_level_bytes(p, sizeof(T)));
+    }
     if (p->opt.scheme == OSMODI_OUTER) {
         t.rc = w.take<T>(n);
         if (p->opt.inner == OSMODI_INNER_JACOBI) {
             t.rhs = w.take<T>(n);
             t.e2 = w.take<T>(n);
+        }
+        if (p->opt.accel > 0) {
+            const size_t m = (size_t)p->opt.accel;
+            t.aa_xs = w.take<T>(n);
+            t.aa_fp = w.take<T>(n);
+            t.aa_gp = w.take<T>(n);
+            t.aa_dF = w.take<T>(n * m);
+            t.aa_dG = w.take<T>(n * m);
+            t.aa_partials = w.take<double>((size_t)2 * kAaMaxDepth * kMaxBlocks);
+            t.aa_st = w.take<AaState>(1);
         }
     }
     t.partials = w.take<double>((size_t)kPartialSlots * kMaxBlocks);
@@ -971,13 +1327,105 @@ static TableT<T> table(osmodi_plan p) {
 struct HostMirror {
     CgState st;
     Scalars sc;
+    AaState aa;
 };
+
+
+// ---- tensor maps for the TMA-staged kernel ----
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                                  const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &ptr, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+static bool make_map(CUtensorMap* m, void* ptr, CUtensorMapDataType dt, int esize, osmodi_plan p, uint32_t bx, uint32_t by) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)p->px, (cuuint64_t)p->ny, (cuuint64_t)p->nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)p->px * esize, (cuuint64_t)p->px * p->ny * esize};
+    const cuuint32_t box[3] = {bx, by, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, dt, 3, ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct TmaMaps {
+    CUtensorMap r, pA, pB;
+    const void* key = nullptr;
+    bool ok = false;
+};
+
+static TmaMaps* tma_maps(osmodi_plan p, const Buffers<float>& b) {
+    if (!p->tma_maps) {
+        void* mem = std::calloc(1, sizeof(TmaMaps));  // released with free() by osmodi_destroy
+        if (mem) p->tma_maps = new (mem) TmaMaps();
+    }
+    TmaMaps* t = reinterpret_cast<TmaMaps*>(p->tma_maps);
+    if (!t) return nullptr;
+    if (t->key != (const void*)b.r) {
+        t->ok = make_map(&t->r, b.r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p, TBX, TBY) &&
+                make_map(&t->pA, b.pA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p, TBX, TBY) &&
+                make_map(&t->pB, b.pB, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p, TBX, TBY);
+        t->key = b.r;
+    }
+    return t->ok ? t : nullptr;
+}
+
+// true when the TMA-staged kernel handled the launch
+static bool launch_cg_a_tma(osmodi_plan p, const Buffers<float>& b, const float* po, float* pn, cudaStream_t s) {
+    TmaMaps* t = tma_maps(p, b);
+    if (!t) return false;
+    TmaGeo g;
+    g.px = p->px;
+    g.plane = p->px * p->ny;
+    g.n_chunks = p->n_chunks;
+    g.nx4 = (int)(p->px / 4);
+    g.ny = (int)p->ny;
+    g.nz = (int)p->nz;
+    g.n_tx = (int)((p->px + TTX - 1) / TTX);
+    g.n_ty = (int)((p->ny + TTY - 1) / TTY);
+    g.slab = p->launch.slab > 0 ? p->launch.slab : 16;
+    g.n_items = (long long)g.n_tx * g.n_ty * ((g.nz + g.slab - 1) / g.slab);
+    for (int a = 0; a < 3; ++a) g.F[a] = (float)p->k.F[a];
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_cg_a_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmem);
+        attr = true;
+    }
+    const int grid = (int)std::min<long long>(g.n_items, (long long)p->num_sms * 2);
+    const CUtensorMap& mpo = (po == b.pA) ? t->pA : t->pB;
+    k_cg_a_tma<<<grid, 256, kTmaSmem, s>>>(t->r, mpo, p->code8, po, pn, b.q, b.x, g, b.st, b.partials);
+    return true;
+}
+
+template <class T>
+static bool try_tma(osmodi_plan, const Buffers<T>&, const T*, T*, cudaStream_t) {
+    return false;
+}
+template <>
+bool try_tma<float>(osmodi_plan p, const Buffers<float>& b, const float* po, float* pn, cudaStream_t s) {
+    return launch_cg_a_tma(p, b, po, pn, s);
+}
 
 // one CG "A" launch
 template <class T>
 static void launch_cg_a(osmodi_plan p, const Buffers<T>& b, int op, const T* po, T* pn, cudaStream_t s) {
     const int G = p->launch.blocks, TH = p->launch.threads;
     const Geo<T> g = geo<T>(p);
+    if (op == OP_L && p->ndim == 3 && p->opt.flat_sweeps == 2 && try_tma<T>(p, b, po, pn, s)) return;
     if (op == OP_L && !p->opt.flat_sweeps) {
         const TileGeo tg = tile_geo(p);
         const int GT = p->launch.blocks_tiled;
@@ -1009,14 +1457,37 @@ static void launch_cg_a(osmodi_plan p, const Buffers<T>& b, int op, const T* po,
 #undef OSM_FL
 }
 
+// with the preconditioner the direction update p = z + beta p_old reads z
+// (the A kernel's residual operand), and z = B r follows every r update
+template <class T>
+static bool precond_on(osmodi_plan p, const Buffers<T>& b, int op) {
+    return op == OP_L && b.mgB != nullptr;
+}
+
+template <class T>
+static Buffers<T> a_operands(const Buffers<T>& b, bool pre) {
+    Buffers<T> ba = b;
+    if (pre) ba.r = b.mgB;
+    return ba;
+}
+
+template <class T>
+static void launch_mg(osmodi_plan p, const Buffers<T>& b, cudaStream_t s) {
+    MgBuffers<T> w{b.mgA, b.mgB, b.mg_lv};
+    mg_apply<T>(p, b.r, w, b.st, b.partials + kSlotMisc * kMaxBlocks, s);
+}
+
 template <class T>
 static osmodi_status launch_cg_iters(osmodi_plan p, const Buffers<T>& b, int op, int iters, cudaStream_t s) {
     const int GB = p->launch.blocks_b;
+    const bool pre = precond_on(p, b, op);
+    const Buffers<T> ba = a_operands(b, pre);
     for (int k = 0; k < iters; ++k) {
         const T* po = (k & 1) ? b.pB : b.pA;
         T* pn = (k & 1) ? b.pA : b.pB;
-        launch_cg_a<T>(p, b, op, po, pn, s);
+        launch_cg_a<T>(p, ba, op, po, pn, s);
         k_cg_b<T><<<GB, 256, 0, s>>>(b.r, b.q, p->n_chunks, b.st, b.partials + kSlotB * kMaxBlocks);
+        if (pre) launch_mg<T>(p, b, s);
     }
     OSM_CUDA(cudaGetLastError());
     return OSMODI_OK;
@@ -1039,17 +1510,24 @@ template <class T>
 static osmodi_status run_cg_profiled(osmodi_plan p, const Buffers<T>& b, int op, cudaStream_t s, HostMirror* hm,
                                      long long* iters_out) {
     const int len = p->opt.check_every;
-    OSM_TRY(ensure_events(p, (size_t)(2 * len + 1)));
+    const bool pre = precond_on(p, b, op);
+    const Buffers<T> ba = a_operands(b, pre);
+    const int per = pre ? 3 : 2;  // events per iteration
+    OSM_TRY(ensure_events(p, (size_t)(per * len + 1)));
     long long k_global = 0;
     for (;;) {
         OSM_CUDA(cudaEventRecord(p->events[0], s));
         for (int k = 0; k < len; ++k, ++k_global) {
             const T* po = (k & 1) ? b.pB : b.pA;
             T* pn = (k & 1) ? b.pA : b.pB;
-            launch_cg_a<T>(p, b, op, po, pn, s);
-            OSM_CUDA(cudaEventRecord(p->events[2 * k + 1], s));
+            launch_cg_a<T>(p, ba, op, po, pn, s);
+            OSM_CUDA(cudaEventRecord(p->events[per * k + 1], s));
             k_cg_b<T><<<p->launch.blocks_b, 256, 0, s>>>(b.r, b.q, p->n_chunks, b.st, b.partials + kSlotB * kMaxBlocks);
-            OSM_CUDA(cudaEventRecord(p->events[2 * k + 2], s));
+            OSM_CUDA(cudaEventRecord(p->events[per * k + 2], s));
+            if (pre) {
+                launch_mg<T>(p, b, s);
+                OSM_CUDA(cudaEventRecord(p->events[per * k + 3], s));
+            }
         }
         OSM_CUDA(cudaGetLastError());
         OSM_CUDA(cudaMemcpyAsync(&hm->st, b.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
@@ -1057,9 +1535,10 @@ static osmodi_status run_cg_profiled(osmodi_plan p, const Buffers<T>& b, int op,
         // count only launches that did work (the device skips the rest)
         const long long done_before = k_global - len;
         for (int k = 0; k < len; ++k) {
-            float ms_a = 0.f, ms_b = 0.f;
-            OSM_CUDA(cudaEventElapsedTime(&ms_a, p->events[2 * k], p->events[2 * k + 1]));
-            OSM_CUDA(cudaEventElapsedTime(&ms_b, p->events[2 * k + 1], p->events[2 * k + 2]));
+            float ms_a = 0.f, ms_b = 0.f, ms_m = 0.f;
+            OSM_CUDA(cudaEventElapsedTime(&ms_a, p->events[per * k], p->events[per * k + 1]));
+            OSM_CUDA(cudaEventElapsedTime(&ms_b, p->events[per * k + 1], p->events[per * k + 2]));
+            if (pre) OSM_CUDA(cudaEventElapsedTime(&ms_m, p->events[per * k + 2], p->events[per * k + 3]));
             const long long it_here = done_before + k;  // iteration index of this pair
             if (it_here <= hm->st.it) {
                 p->kstats[0] += ms_a;
@@ -1068,12 +1547,16 @@ static osmodi_status run_cg_profiled(osmodi_plan p, const Buffers<T>& b, int op,
             if (it_here < hm->st.it) {
                 p->kstats[2] += ms_b;
                 p->kstats[3] += 1;
+                if (pre && it_here + 1 < hm->st.it) {  // the preconditioner ran unless this update converged
+                    p->kstats[6] += ms_m;
+                    p->kstats[7] += 1;
+                }
             }
         }
         if (hm->st.status == kFinished) break;
     }
     *iters_out = hm->st.it;
-    return OSMODI_OK;
+    return hm->st.err ? OSMODI_E_TIMEOUT : OSMODI_OK;
 }
 
 // Direct launches in chunks of check_every iterations: no CUDA graph is
@@ -1088,7 +1571,7 @@ static osmodi_status run_cg_direct(osmodi_plan p, const Buffers<T>& b, int op, c
         if (hm->st.status == kFinished) break;
     }
     *iters_out = hm->st.it;
-    return OSMODI_OK;
+    return hm->st.err ? OSMODI_E_TIMEOUT : OSMODI_OK;
 }
 
 template <class T>
@@ -1138,7 +1621,7 @@ static osmodi_status run_cg(osmodi_plan p, const Buffers<T>& b, int op, void* ws
         if (hm->st.status == kFinished) break;
     }
     *iters_out = hm->st.it;
-    return OSMODI_OK;
+    return hm->st.err ? OSMODI_E_TIMEOUT : OSMODI_OK;
 }
 
 template <class T>
@@ -1181,6 +1664,117 @@ static osmodi_status comp_sums(osmodi_plan p, const T* v, double* sums, cudaStre
 static osmodi_status read_mirror(void* dst, const void* src, size_t n, cudaStream_t s) {
     OSM_CUDA(cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s));
     OSM_CUDA(cudaStreamSynchronize(s));
+    return OSMODI_OK;
+}
+
+// Host side of the Anderson mixing: which ring slots are active (oldest
+// first), the Gram matrix of their dF columns, and the small least-squares
+// solve.  Reset at the start of every refinement step (each step is a new
+// linear problem for the correction).
+struct AaHost {
+    int m = 0, k = 0;
+    std::vector<int> active;
+    double H[kAaMaxDepth][kAaMaxDepth] = {};
+    double rhs[kAaMaxDepth] = {};  // dF_c . f_k by slot c
+    void reset(int depth) {
+        m = depth;
+        k = 0;
+        active.clear();
+    }
+};
+
+// gamma minimising || f_k - dF gamma || over the active columns through the
+// normal equations (dF^T dF) gamma = dF^T f_k, by Cholesky.  While a pivot
+// falls below 1e-13 of the largest diagonal entry the oldest column is
+// dropped (the columns have become nearly dependent).
+static void aa_least_squares(AaHost& h, double* gamma) {
+    for (;;) {
+        const int n = (int)h.active.size();
+        if (n == 0) return;
+        double A[kAaMaxDepth][kAaMaxDepth], L[kAaMaxDepth][kAaMaxDepth] = {};
+        double dmax = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) A[i][j] = h.H[h.active[i]][h.active[j]];
+        for (int i = 0; i < n; ++i) dmax = std::max(dmax, A[i][i]);
+        bool ok = dmax > 0.0 && std::isfinite(dmax);
+        for (int j = 0; ok && j < n; ++j) {
+            double d = A[j][j];
+            for (int q = 0; q < j; ++q) d -= L[j][q] * L[j][q];
+            if (!(d > 1e-13 * dmax)) {
+                ok = false;
+                break;
+            }
+            L[j][j] = std::sqrt(d);
+            for (int i = j + 1; i < n; ++i) {
+                double v = A[i][j];
+                for (int q = 0; q < j; ++q) v -= L[i][q] * L[j][q];
+                L[i][j] = v / L[j][j];
+            }
+        }
+        if (!ok) {
+            h.active.erase(h.active.begin());
+            continue;
+        }
+        double y[kAaMaxDepth];
+        for (int i = 0; i < n; ++i) {
+            double v = h.rhs[h.active[i]];
+            for (int q = 0; q < i; ++q) v -= L[i][q] * y[q];
+            y[i] = v / L[i][i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double v = y[i];
+            for (int q = i + 1; q < n; ++q) v -= L[q][i] * gamma[q];
+            gamma[i] = v / L[i][i];
+        }
+        return;
+    }
+}
+
+// One mixing step after the inner solve left G(x_k) in gbuf: differences and
+// dot products on the device, least squares on the host, then gbuf and the
+// saved iterate become x_{k+1}.
+template <class T>
+static osmodi_status aa_step(osmodi_plan p, const Buffers<T>& b, AaHost& h, T* gbuf, HostMirror* hm, cudaStream_t s) {
+    AaArgs<T> a{};
+    a.xs = b.aa_xs;
+    a.g = gbuf;
+    a.f_prev = b.aa_fp;
+    a.g_prev = b.aa_gp;
+    a.dF = b.aa_dF;
+    a.dG = b.aa_dG;
+    a.n_box = p->n_box;
+    a.n_chunks = p->n_chunks;
+    a.jnew = -1;
+    if (h.k > 0) {
+        if ((int)h.active.size() == h.m) h.active.erase(h.active.begin());
+        int slot = 0;
+        while (std::find(h.active.begin(), h.active.end(), slot) != h.active.end()) ++slot;
+        a.jnew = slot;
+        h.active.push_back(slot);
+    }
+    a.n = (int)h.active.size();
+    for (int t = 0; t < a.n; ++t) a.cols[t] = h.active[t];
+    const int G = (int)std::min<int64_t>((p->n_chunks + 255) / 256, (int64_t)p->num_sms * 8);
+    k_aa_diff<T><<<G, 256, 0, s>>>(a, p->code8, b.aa_st, b.aa_partials);
+    OSM_CUDA(cudaGetLastError());
+    double gamma[kAaMaxDepth] = {};
+    if (a.jnew >= 0) {
+        OSM_TRY(read_mirror(&hm->aa, b.aa_st, sizeof(AaState), s));
+        for (int t = 0; t < a.n; ++t) {
+            const int c = a.cols[t];
+            h.H[c][a.jnew] = h.H[a.jnew][c] = hm->aa.dots[t];
+            h.rhs[c] = hm->aa.dots[kAaMaxDepth + t];
+        }
+        aa_least_squares(h, gamma);
+    }
+    a.n = (int)h.active.size();
+    for (int t = 0; t < a.n; ++t) {
+        a.cols[t] = h.active[t];
+        a.gamma[t] = gamma[t];
+    }
+    k_aa_mix<T><<<G, 256, 0, s>>>(a, gbuf, b.aa_xs);
+    OSM_CUDA(cudaGetLastError());
+    h.k += 1;
     return OSMODI_OK;
 }
 
@@ -1233,7 +1827,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
 
     osmodi_status status = OSMODI_OK;
     double eps = 0.0, eps_p = 0.0;
-    long long total_inner = 0;
+    long long total_inner = 0, mg_applies = 0;
     int steps = 0, outer_total = 0, residual_evals = 0;
     double* cur = b.p64a;
     double* nxt = b.p64b;
@@ -1272,13 +1866,20 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                 if (cont && !(last_dir_in_a)) {
                     OSM_CUDA(cudaMemcpyAsync(b.pA, b.pB, sizeof(T) * (size_t)p->n_box, cudaMemcpyDeviceToDevice, s));
                 }
+                const bool pre = precond_on(p, b, OP_L);
                 k_cg_init<T><<<G, TH, 0, s>>>(b.r, b.x, p->code8, p->label, comp_r, p->comp_count, multi ? 1 : 0,
                                               p->n_chunks, b.sc, b.st, stop_abs * stop_abs, rel * rel, budget,
-                                              b.partials + kSlotMisc * kMaxBlocks, cont ? 1 : 0);
+                                              b.partials + kSlotMisc * kMaxBlocks, cont ? 1 : 0, pre ? 1 : 0);
                 OSM_CUDA(cudaGetLastError());
+                if (pre) {
+                    launch_mg<T>(p, b, s);  // z_0 = B r_0, (r_0, z_0), the first direction
+                    OSM_CUDA(cudaGetLastError());
+                    mg_applies += 1;
+                }
                 long long it = 0;
                 OSM_TRY(run_cg<T>(p, b, OP_L, ws, s, hm, &it, noalloc));
                 total_inner += it;
+                if (pre) mg_applies += std::max<long long>(0, it - 1);
                 // iteration k (from 0 in each segment) writes its direction to pB
                 // when k is even, to pA when odd; the last one was k = it - 1
                 cont = it > 0;
@@ -1292,6 +1893,12 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                 const TableT<T> tab = table<T>(p);
                 double eps_step0 = -1.0;
                 T* e_cur = b.x;
+                AaHost aa;
+                if (p->opt.accel > 0) {
+                    aa.reset(p->opt.accel);
+                    OSM_CUDA(cudaMemsetAsync(b.aa_xs, 0, sizeof(T) * (size_t)p->n_box, s));  // x_0 = e = 0
+                    OSM_CUDA(cudaMemsetAsync(b.aa_st, 0, sizeof(AaState), s));                // reduction ticket
+                }
                 for (;;) {
                     // residual of the current outer iterate (and boundary refresh for Jacobi)
                     if (p->opt.inner == OSMODI_INNER_CG) {
@@ -1314,6 +1921,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                         long long it = 0;
                         OSM_TRY(run_cg<T>(p, b, OP_M, ws, s, hm, &it, noalloc));
                         total_inner += it;
+                        if (p->opt.accel > 0) OSM_TRY(aa_step<T>(p, b, aa, b.x, hm, s));
                     } else {
                         const int kf = p->opt.sweeps_per_pass;
                         for (int sw = 0; sw < p->opt.inner_max;) {
@@ -1341,6 +1949,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                         }
                         OSM_CUDA(cudaGetLastError());
                         total_inner += p->opt.inner_max;
+                        if (p->opt.accel > 0) OSM_TRY(aa_step<T>(p, b, aa, e_cur, hm, s));
                     }
                     outer_total++;
                 }
@@ -1390,7 +1999,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
         res->eps_P = eps_p;
         res->ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
         double apps = (double)total_inner + (double)residual_evals + (outer ? (double)outer_total : 0.0);
-        res->point_updates = apps * (double)p->n_valid;
+        res->point_updates = apps * (double)p->n_valid + (double)mg_applies * mg_updates_per_apply(p);
         res->seed_rel_dist = hm->sc.pnorm2 > 0 ? std::sqrt(hm->sc.dist2 / hm->sc.pnorm2) : 0.0;
     }
     return status;
@@ -1479,7 +2088,10 @@ static osmodi_status tune_impl(osmodi_plan p, void* ws, cudaStream_t s, const ch
             if (gb <= bps_b) cands.push_back({ga, gb, 1});
     if (p->ndim == 3)
         for (int gb : {4, 6, 8})
-            if (gb <= bps_b) cands.push_back({bps_a, gb, 0});
+            if (gb <= bps_b) {
+                cands.push_back({bps_a, gb, 0});
+                if (sizeof(T) == 4) cands.push_back({bps_a, gb, 2});  // TMA-staged planes
+            }
     cudaEvent_t e0, e1;
     OSM_CUDA(cudaEventCreate(&e0));
     OSM_CUDA(cudaEventCreate(&e1));
@@ -1495,8 +2107,10 @@ static osmodi_status tune_impl(osmodi_plan p, void* ws, cudaStream_t s, const ch
         k_fill_pattern<T><<<G, TH, 0, s>>>(b.r, p->code8, p->n_box);
         OSM_CUDA(cudaMemsetAsync(b.sc, 0, sizeof(Scalars), s));
         OSM_CUDA(cudaMemsetAsync(b.st, 0, sizeof(CgState), s));
+        const bool pre = precond_on(p, b, OP_L);
         k_cg_init<T><<<G, TH, 0, s>>>(b.r, b.x, p->code8, p->label, b.comp, p->comp_count, 0, p->n_chunks, b.sc, b.st,
-                                      0.0, 0.0, (long long)1 << 40, b.partials + kSlotMisc * kMaxBlocks);
+                                      0.0, 0.0, (long long)1 << 40, b.partials + kSlotMisc * kMaxBlocks, 0, pre ? 1 : 0);
+        if (pre) launch_mg<T>(p, b, s);
         if ((st = launch_cg_iters<T>(p, b, OP_L, 4, s)) != OSMODI_OK) break;
         OSM_CUDA(cudaEventRecord(e0, s));
         if ((st = launch_cg_iters<T>(p, b, OP_L, iters, s)) != OSMODI_OK) break;

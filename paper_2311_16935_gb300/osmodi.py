@@ -31,7 +31,7 @@ class osmodi_options(ctypes.Structure):
                 ("sweeps_per_pass", ctypes.c_int), ("max_refine", ctypes.c_int), ("record_history", ctypes.c_int),
                 ("threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("profile", ctypes.c_int),
                 ("slab", ctypes.c_int), ("flat_sweeps", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("reserved", ctypes.c_int * 1)]
+                ("accel", ctypes.c_int), ("precond", ctypes.c_int)]
 
 
 class osmodi_result(ctypes.Structure):
@@ -65,6 +65,21 @@ _SIGS = {
                                             ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_batched_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_void_p]),
+    "osmodi_source_incompressible": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                    ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                                    ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_source_rans": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_source_compressible": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                                  ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_batch_graph_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                                 ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_batch_graph_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_batch_graph_results": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_batch_graph_destroy": (None, [ctypes.c_void_p]),
     "osmodi_solve_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                             ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                             ctypes.c_void_p]),
@@ -150,7 +165,10 @@ def _check_cuda(t: torch.Tensor, name: str):
 def default_options(**overrides) -> osmodi_options:
     o = osmodi_options()
     lib().osmodi_default_options(ctypes.byref(o))
+    names = {f[0] for f in osmodi_options._fields_}
     for k, v in overrides.items():
+        if k not in names:
+            raise TypeError(f"unknown option {k!r}")
         setattr(o, k, v)
     return o
 
@@ -230,7 +248,8 @@ class Plan:
             raise OsmodiError(st, "osmodi_kernel_stats")
         v = list(out)
         return {"cg_apply_ms": v[0], "cg_apply_launches": int(v[1]), "cg_update_ms": v[2],
-                "cg_update_launches": int(v[3]), "residual64_ms": v[4], "residual64_launches": int(v[5])}
+                "cg_update_launches": int(v[3]), "residual64_ms": v[4], "residual64_launches": int(v[5]),
+                "precond_ms": v[6], "precond_applications": int(v[7])}
 
     def solve_noalloc(self, grad: torch.Tensor, p: torch.Tensor, tol: float, max_iter: int = 1 << 30, stream=None,
                       check=True) -> osmodi_result:
@@ -297,6 +316,57 @@ class Plan:
             raise OsmodiError(st, "osmodi_residual")
         return eps.value
 
+    # ---- source-term front ends (FP32 velocity data -> FP32 gradient) ----
+    def _vec(self, t, name, planes):
+        _check_cuda(t, name)
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            raise TypeError(f"{name} must be contiguous float32")
+        if t.numel() != planes * self.dims[0] * self.dims[1] * self.dims[2]:
+            raise ValueError(f"{name} must hold {planes} planes of the plan's grid")
+        return t.data_ptr()
+
+    def _grad_out(self, like):
+        return torch.empty((self.ndim,) + tuple(like.shape[1:]), dtype=torch.float32, device="cuda")
+
+    def source_incompressible(self, u, u_prev=None, u_next=None, dt=1.0, rho=1.0, mu=0.0, stream=None):
+        """osmodi_source_incompressible: f of Eq. 1 from the snapshot u (and
+        its neighbours in time, either may be None)."""
+        pu = self._vec(u, "u", self.ndim)
+        pp = self._vec(u_prev, "u_prev", self.ndim) if u_prev is not None else None
+        pn = self._vec(u_next, "u_next", self.ndim) if u_next is not None else None
+        out = self._grad_out(u)
+        st = lib().osmodi_source_incompressible(self.handle, pu, pp, pn, float(dt), float(rho), float(mu),
+                                                out.data_ptr(), _stream_ptr(stream))
+        if st != OK:
+            raise OsmodiError(st, "osmodi_source_incompressible")
+        return out
+
+    def source_rans(self, u_mean, stress, rho=1.0, stream=None):
+        """osmodi_source_rans: f of Eq. RANS_f."""
+        nst = 3 if self.ndim == 2 else 6
+        pu = self._vec(u_mean, "u_mean", self.ndim)
+        ps = self._vec(stress, "stress", nst)
+        out = self._grad_out(u_mean)
+        st = lib().osmodi_source_rans(self.handle, pu, ps, float(rho), out.data_ptr(), _stream_ptr(stream))
+        if st != OK:
+            raise OsmodiError(st, "osmodi_source_rans")
+        return out
+
+    def source_compressible(self, u_mean, stress, gamma, mach_inf, v_inf, t_inf, r_gas, stream=None):
+        """osmodi_source_compressible: (grad ln(P/P_inf), T) of Eq.
+        compressible-pressure."""
+        nst = 3 if self.ndim == 2 else 6
+        pu = self._vec(u_mean, "u_mean", self.ndim)
+        ps = self._vec(stress, "stress", nst)
+        out = self._grad_out(u_mean)
+        temp = torch.empty(tuple(u_mean.shape[1:]), dtype=torch.float32, device="cuda")
+        st = lib().osmodi_source_compressible(self.handle, pu, ps, float(gamma), float(mach_inf), float(v_inf),
+                                              float(t_inf), float(r_gas), out.data_ptr(), temp.data_ptr(),
+                                              _stream_ptr(stream))
+        if st != OK:
+            raise OsmodiError(st, "osmodi_source_compressible")
+        return out, temp
+
     def close(self):
         if getattr(self, "handle", None):
             lib().osmodi_destroy(self.handle)
@@ -343,6 +413,12 @@ class Batch:
         return st, list(res)
 
 
+    def capture(self, grads, ps, tol, max_iter=1 << 30, stream=None):
+        """osmodi_batch_graph_create: one solve of this batch captured as a
+        CUDA graph bound to these tensors (keep them alive, refill them in
+        place between launches)."""
+        return BatchGraph(self, grads, ps, tol, max_iter, stream)
+
     def autotune(self, grads, ps, stream=None):
         """osmodi_autotune_batched; returns the chosen tile depth."""
         count = len(self.plans)
@@ -355,6 +431,56 @@ class Batch:
         if st != OK:
             raise OsmodiError(st, "osmodi_autotune_batched")
         return depth.value
+
+
+class BatchGraph:
+    """A captured batched solve (osmodi_batch_graph_*)."""
+
+    def __init__(self, batch, grads, ps, tol, max_iter=1 << 30, stream=None):
+        count = len(batch.plans)
+        if len(grads) != count or len(ps) != count:
+            raise ValueError("one gradient and one pressure tensor per plan")
+        for g, p in zip(grads, ps):
+            _check_cuda(g, "grad")
+            _check_cuda(p, "p")
+        gdt = {_dtype_code(g) for g in grads}
+        pdt = {_dtype_code(p) for p in ps}
+        if len(gdt) != 1 or len(pdt) != 1:
+            raise TypeError("all gradients (and all pressures) must share one dtype")
+        self.batch, self.grads, self.ps = batch, list(grads), list(ps)  # the graph holds their addresses
+        ga = (ctypes.c_void_p * count)(*[g.data_ptr() for g in grads])
+        pa = (ctypes.c_void_p * count)(*[p.data_ptr() for p in ps])
+        ws = (batch.ws.data_ptr() + 255) // 256 * 256
+        h = ctypes.c_void_p()
+        st = lib().osmodi_batch_graph_create(count, batch._arr, ga, gdt.pop(), pa, pdt.pop(), float(tol),
+                                             int(min(max_iter, 2**31 - 1)), ws, _stream_ptr(stream), ctypes.byref(h))
+        if st != OK:
+            raise OsmodiError(st, "osmodi_batch_graph_create")
+        self.handle = h
+
+    def launch(self, stream=None):
+        st = lib().osmodi_batch_graph_launch(self.handle, _stream_ptr(stream))
+        if st != OK:
+            raise OsmodiError(st, "osmodi_batch_graph_launch")
+
+    def results(self, check=True):
+        """Waits for the last launch; returns (status, [osmodi_result])."""
+        res = (osmodi_result * len(self.grads))()
+        st = lib().osmodi_batch_graph_results(self.handle, res)
+        if check and st < 0 and st != E_NAN_INPUT:
+            raise OsmodiError(st, "osmodi_batch_graph_results")
+        return st, list(res)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().osmodi_batch_graph_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def osmodi_solve_batched(plans, grads, ps, tol, max_iter=1 << 30, stream=None):

@@ -1,0 +1,108 @@
+"""The multigrid-preconditioned CG solve (osmodi_options.precond = 1)
+against the oracle: the same fixed point to the same tolerance as plain CG,
+in far fewer iterations, on every grid shape the hierarchy meets (ragged
+sizes, masks with several components, one-cell-thick axes, grids too small
+for a coarse level).  Needs a GPU."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2311_16935_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def osm():
+    from paper_2311_16935_gb300 import build
+
+    build.build()
+    from paper_2311_16935_gb300 import osmodi
+
+    return osmodi
+
+
+def _rel(a, b, valid):
+    return float(np.linalg.norm(a[valid] - b[valid]) / max(np.linalg.norm(b[valid]), 1e-300))
+
+
+def _solve(osm, f, valid, spacing, tol, **opt):
+    plan = osm.Plan(valid.ndim, valid.shape[::-1], spacing, torch.from_numpy(valid.astype(np.uint8)).cuda(), **opt)
+    p = torch.zeros(valid.shape, dtype=torch.float64, device="cuda")
+    res = plan.solve(torch.from_numpy(np.ascontiguousarray(f)).cuda(), p, tol)
+    return plan, res, p.cpu().numpy()
+
+
+SHAPES = [((37, 53), (0.1, 0.13)), ((130, 9), (1.0, 1.0)), ((19, 23, 29), (1.0, 1.0, 1.0)),
+          ((17, 1, 33), (1.0, 1.0, 1.0)), ((9, 12, 40), (1.0, 1.3, 0.7))]
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+@pytest.mark.parametrize("case", range(len(SHAPES)))
+def test_preconditioned_matches_oracle(osm, case, precision):
+    shape, spacing = SHAPES[case]
+    rng = np.random.default_rng(60 + case)
+    valid = rng.random(shape) > 0.2  # salt-and-pepper: several components
+    f = rng.normal(size=(len(shape),) + shape)
+    if precision == 2:
+        f = f.astype(np.float32)
+    want = oracle.solve_direct(oracle.Grid(valid, spacing), f.astype(np.float64))
+    _, r0, p0 = _solve(osm, f, valid, spacing, 1e-12, precision=precision)
+    _, r1, p1 = _solve(osm, f, valid, spacing, 1e-12, precision=precision, precond=1)
+    assert r0.status == osm.OK and r1.status == osm.OK, (r0.as_dict(), r1.as_dict())
+    assert r1.eps_R <= 1e-12
+    assert _rel(p1, want, valid) < 1e-10
+    assert np.isnan(p1[~valid]).all()
+    assert r1.inner_iters < r0.inner_iters, (r1.inner_iters, r0.inner_iters)
+
+
+def test_preconditioned_configs_and_iteration_counts(osm):
+    """The 64^2 Lamb-Oseen and 128^3 sin-cos configurations to 1e-10 against
+    the oracle, each in a small fraction of plain CG's iterations."""
+    prob = inputs.lamb_oseen_2d(n=64)
+    valid = prob.mask.numpy().astype(bool)
+    f = prob.grad.numpy()
+    want = oracle.solve_direct(oracle.Grid(valid, prob.spacing), f)
+    _, r0, _ = _solve(osm, f, valid, prob.spacing, 1e-10, precision=0)
+    _, r1, got = _solve(osm, f, valid, prob.spacing, 1e-10, precision=0, precond=1)
+    assert r1.status == osm.OK and _rel(got, want, valid) < 1e-9
+    assert r1.inner_iters * 3 < r0.inner_iters, (r1.inner_iters, r0.inner_iters)
+
+    prob = inputs.sincos_3d(n=128)
+    valid = prob.mask.numpy().astype(bool)
+    f = prob.grad.numpy()
+    _, r0, _ = _solve(osm, f, valid, prob.spacing, 1e-12)
+    _, r1, got = _solve(osm, f, valid, prob.spacing, 1e-12, precond=1)
+    assert r1.status == osm.OK
+    want = oracle.solve_cg(oracle.Grid(valid, prob.spacing), f.astype(np.float64), tol=1e-14, maxit=20000)[0]
+    assert _rel(got, want, valid) < 1e-10
+    assert r1.inner_iters * 8 < r0.inner_iters, (r1.inner_iters, r0.inner_iters)
+
+
+def test_preconditioned_small_grid_and_noalloc(osm):
+    """A grid of at most 8 cells per axis has no coarse level (plain CG); the
+    allocation-free entry runs the preconditioned solve too."""
+    rng = np.random.default_rng(3)
+    valid = rng.random((6, 8)) > 0.2
+    f = rng.normal(size=(2, 6, 8))
+    want = oracle.solve_direct(oracle.Grid(valid, (1.0, 1.0)), f)
+    _, r, got = _solve(osm, f, valid, (1.0, 1.0), 1e-12, precision=0, precond=1)
+    assert r.status == osm.OK and _rel(got, want, valid) < 1e-10
+    valid = rng.random((40, 50)) > 0.1
+    f = rng.normal(size=(2, 40, 50))
+    want = oracle.solve_direct(oracle.Grid(valid, (1.0, 1.0)), f)
+    plan = osm.Plan(2, (50, 40), (1.0, 1.0), torch.from_numpy(valid.astype(np.uint8)).cuda(), precond=1)
+    p = torch.zeros((40, 50), dtype=torch.float64, device="cuda")
+    res = plan.solve_noalloc(torch.from_numpy(f).cuda(), p, 1e-12)
+    assert res.status == osm.OK and _rel(p.cpu().numpy(), want, valid) < 1e-10
+
+
+def test_preconditioner_timing_is_reported(osm):
+    prob = inputs.sincos_3d(n=48)
+    valid = prob.mask.numpy().astype(bool)
+    plan, res, _ = _solve(osm, prob.grad.numpy(), valid, prob.spacing, 1e-10, precond=1, profile=1)
+    ks = plan.kernel_stats()
+    assert res.status == osm.OK
+    assert ks["precond_applications"] > 0 and ks["precond_ms"] > 0
+    assert ks["precond_applications"] <= ks["cg_update_launches"]

@@ -227,6 +227,53 @@ def test_outer_scheme_history_matches_literal_algorithm(osm):
     assert _rel(got, P_lit, valid) < 1e-8
 
 
+@pytest.mark.parametrize("depth", [3, 8])
+def test_outer_anderson_history_matches_oracle(osm, depth):
+    """Anderson-mixed Algorithm 1 (deep inner CG on M) follows the oracle's
+    mixed iteration (exact LU inner solves, least squares by SVD) iterate by
+    iterate, needs far fewer outer iterations than Algorithm 1, and lands on
+    the same fixed point."""
+    rng = np.random.default_rng(9)
+    shape, spacing = (14, 19), (0.1, 0.13)
+    valid = rng.random(shape) > 0.15
+    f = rng.normal(size=(2,) + shape)
+    grid = oracle.Grid(valid, spacing)
+    want = oracle.solve_direct(grid, f)
+    P_aa, n_aa, er = oracle.solve_outer_anderson(grid, f, depth, tol=1e-11)
+    plan, res, got = _solve(osm, f, valid.astype(np.uint8), spacing, 1e-11, precision=0, scheme=1, inner=0,
+                            inner_tol=1e-14, inner_max=10000, record_history=1, accel=depth)
+    hist = plan.history()
+    assert res.status == osm.OK, res.as_dict()
+    # the normal equations on the device and the SVD least squares of the
+    # oracle agree to ~1e-9 over the first 40 iterations (rounding only)
+    m = min(30, len(er), len(hist) - 1)
+    np.testing.assert_allclose(np.array(hist[1:m + 1]), np.array(er[:m]), rtol=1e-6)
+    assert abs(res.outer_iters - n_aa) <= max(3, n_aa // 10)
+    _, n_lit, _, _ = oracle.solve_literal(grid, f, tol=1e-11)
+    assert res.outer_iters < n_lit / 4
+    assert _rel(got, want, valid) < 1e-9
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_outer_anderson_jacobi_refined(osm, ndim):
+    """Anderson mixing around FP32 Jacobi sweeps inside FP64 refinement:
+    the FP64 fixed point to 1e-10, with fewer outer iterations than the
+    unmixed sweeps."""
+    rng = np.random.default_rng(12 + ndim)
+    shape = (11, 13) if ndim == 2 else (7, 9, 10)
+    spacing = (0.1, 0.13) if ndim == 2 else (1.0, 1.0, 1.0)
+    valid = rng.random(shape) > 0.1
+    f = rng.normal(size=(ndim,) + shape).astype(np.float32)
+    want = oracle.solve_direct(oracle.Grid(valid, spacing), f.astype(np.float64))
+    _, res0, _ = _solve(osm, f, valid.astype(np.uint8), spacing, 1e-11, precision=2, scheme=1, inner=1, inner_max=4,
+                        max_iter=500000)
+    _, res, got = _solve(osm, f, valid.astype(np.uint8), spacing, 1e-11, precision=2, scheme=1, inner=1, inner_max=4,
+                         max_iter=500000, accel=6)
+    assert res.status == osm.OK and res0.status == osm.OK, (res.as_dict(), res0.as_dict())
+    assert _rel(got, want, valid) < 1e-10
+    assert res.outer_iters < res0.outer_iters / 3, (res.outer_iters, res0.outer_iters)
+
+
 def test_outer_jacobi_converges_to_fixed_point(osm):
     rng = np.random.default_rng(10)
     shape, spacing = (9, 12), (1.0, 1.0)
@@ -362,3 +409,23 @@ def test_fused_jacobi_sweeps_equal_single_sweeps(osm, ndim, precision):
                                 inner_max=3, sweeps_per_pass=spp, max_iter=40)
         outs.append(got)
     assert _rel(outs[1], outs[0], valid) < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(20, 37, 150), (9, 16, 128), (33, 5, 260)])
+def test_tma_staged_sweep_matches_flat(osm, shape):
+    """The TMA-staged stencil kernel (tiles of 128 x 16 cells, planes in a
+    shared-memory ring filled by bulk tensor copies) reaches the same answer
+    as the flat kernel, on ragged masked grids (partial tiles in x and y)."""
+    rng = np.random.default_rng(sum(shape))
+    valid = rng.random(shape) > 0.1
+    f = rng.normal(size=(3,) + shape).astype(np.float32)
+    grid = oracle.Grid(valid, (1.0, 1.0, 1.0))
+    outs = []
+    for variant in (1, 2):
+        plan, res, got = _solve(osm, f, valid.astype(np.uint8), (1.0, 1.0, 1.0), 1e-12, precision=2,
+                                flat_sweeps=variant, slab=8)
+        assert res.status == osm.OK, (variant, res.as_dict())
+        outs.append(got)
+    assert _rel(outs[1], outs[0], valid) < 1e-10
+    want, it, r = oracle.solve_cg(grid, f.astype(np.float64), tol=1e-14, maxit=20000)
+    assert _rel(outs[1], want, valid) < 1e-10

@@ -3,12 +3,14 @@
 
 One step = one complete solve of the 500^3 Gaussian-blob workload (125 M
 cells, FP32 gradients, 20 random blobs, 3 % noise) from P^0 = 0 to
-eps_R <= 1e-8: FP32 conjugate-gradient sweeps on the fixed-point system
-inside an FP64 iterative-refinement loop (FP64 residual, norms and
-constant removal).  value = (valid cells x stencil applications) / device
-time, summed over the timed steps.  Inputs (1.5 GB of gradients, 1 GB of
-pressure, ~5 GB of work vectors) are far larger than L2, so no flush is
-needed between steps.
+eps_R <= 1e-8: FP32 multigrid-preconditioned conjugate-gradient sweeps on
+the fixed-point system inside an FP64 iterative-refinement loop (FP64
+residual, norms and constant removal).  value = (valid cells x stencil
+applications, every multigrid level counted with its own cells) / device
+time, summed over the timed steps.  The same solve without the
+preconditioner and the same scheme in FP64 are timed beside it.  Inputs
+(1.5 GB of gradients, 1 GB of pressure, ~6 GB of work vectors) are far
+larger than L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--size n] [--no-e2e] [--no-cpu] [--no-fp64]
@@ -47,23 +49,26 @@ def _peaks():
 
 
 def _kernel_source_hash():
-    """Hash of the sources that define the timed sweep kernels."""
+    """Hash of the sources that define the timed solve's kernels."""
     h = hashlib.sha256()
-    for name in ("solve.cu", "stencil.cuh", "internal.cuh"):
+    for name in ("solve.cu", "mg.cu", "mg.cuh", "cg_state.cuh", "stencil.cuh", "internal.cuh"):
         with open(os.path.join(ROOT, "paper_2311_16935_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
+PROFILE = os.path.join(ROOT, "profiles", "solve_kernels_gaussian_blobs_3d_500.md")
+
+
 def _profiled_traffic(kernel: str, cells: int):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
-    to `cells` per launch; None if the summary is for other kernel sources."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_gaussian_blobs_3d.md")
-    if not os.path.exists(path):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (a line `dram_bytes_per_cell[<kernel>]: <value>`), scaled to `cells` per
+    launch; None if the summary was taken on other kernel sources."""
+    if not os.path.exists(PROFILE):
         return None
-    txt = open(path).read()
+    txt = open(PROFILE).read()
     m_hash = re.search(r"kernel_source_hash:\s*(\w+)", txt)
-    m_b = re.search(r"dram_bytes_per_cell:\s*([0-9.eE+-]+)", txt)
+    m_b = re.search(r"dram_bytes_per_cell\[" + re.escape(kernel) + r"\]:\s*([0-9.eE+-]+)", txt)
     if not m_hash or not m_b or m_hash.group(1) != _kernel_source_hash():
         return None
     return float(m_b.group(1)) * cells
@@ -203,6 +208,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-front", action="store_true")
     ap.add_argument("--batch-count", type=int, default=512)
@@ -234,7 +240,7 @@ def main():
     prob = inputs.gaussian_blobs_3d(n=(n, n, n), device="cuda", dtype=torch.float32)
     grad = prob.grad
     dims = (n, n, n)
-    plan = osm.Plan(3, dims, (1.0, 1.0, 1.0), None, precision=osm.FP32_REFINE, profile=1)
+    plan = osm.Plan(3, dims, (1.0, 1.0, 1.0), None, precision=osm.FP32_REFINE, precond=1, profile=1)
     info = plan.info()
     stream = torch.cuda.current_stream()
     p = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
@@ -249,7 +255,7 @@ def main():
     # timed region: K full solves
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     results = []
-    ka_ms = ka_n = kb_ms = kb_n = 0.0
+    ka_ms = ka_n = kb_ms = kb_n = mg_ms = mg_n = sw_ms = sw_n = 0.0
     barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
@@ -263,6 +269,11 @@ def main():
             ka_n += ks["cg_apply_launches"]
             kb_ms += ks["cg_update_ms"]
             kb_n += ks["cg_update_launches"]
+            mg_ms += ks["precond_ms"]
+            mg_n += ks["precond_applications"]
+            km = plan.kernel_stats_precond()
+            sw_ms += km["mg_sweep_ms"]
+            sw_n += km["mg_sweep_launches"]
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier()
@@ -273,56 +284,79 @@ def main():
     if any(r["status"] != osm.OK for r in results):
         raise SystemExit(f"solve did not converge: {results}")
 
-    # kernels per solve: the two CG kernels, one FP64 residual per refinement
-    # step plus the initial one, one CG initialisation per step, source and
-    # output (refine_steps counts the residual evaluations)
-    # roofline of the dominant kernel (the CG kernel applying the stencil):
-    # algorithmic bytes per cell = read r, p_old, x (3 x 4 B) + code (1 B) + write p_new, q, x (3 x 4 B)
+    # roofline of the dominant kernel: the multigrid fine-level sweep
+    # z_out = z + omega D^-1 (r - L z), two launches per V-cycle; algorithmic
+    # bytes per cell = read z, r (2 x 4 B) + code (1 B) + write z_out (4 B)
     cells = info["n_box"]
-    bytes_per_launch = 25.0 * cells
-    ka_avg = ka_ms / max(ka_n, 1)
-    achieved = bytes_per_launch / (ka_avg / 1e3) / 1e9
     peak, peak_kind = _peaks()
-    traffic = _profiled_traffic("k_cg_a", cells)
+    sw_avg = sw_ms / max(sw_n, 1)
+    sw_bytes = 13.0 * cells
+    # the CG kernel applying the stencil: read z (the preconditioned residual),
+    # p_old, x (3 x 4 B) + code (1 B); write p, q, x (3 x 4 B)
+    ka_avg = ka_ms / max(ka_n, 1)
     kb_avg = kb_ms / max(kb_n, 1)
 
     line = {"metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"gaussian_blobs_3d_{n}^3", "cells": n ** 3, "tol_eps_R": TOL,
-                       "precision": "fp32 sweeps + fp64 refinement", "scheme": "CG on the fixed-point system",
+                       "precision": "fp32 sweeps + fp64 refinement",
+                       "scheme": "multigrid-preconditioned CG on the fixed-point system",
                        "l2": "inputs and work vectors (>5 GB) exceed L2; no flush needed",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "time_to_tolerance_s": ms_max / args.steps / 1e3,
             "solves_per_s": args.steps * world / (ms_max / 1e3),
             "iterations": {"cg": results[-1]["inner_iters"], "refine_steps": results[-1]["refine_steps"],
                            "eps_R": results[-1]["eps_R"]},
-            "roofline": {"bound": "hbm", "kernel": "k_cg_a (stencil apply + p/x updates + p.q)",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_source": peak_kind, "traffic": traffic, "bytes_per_launch": bytes_per_launch,
-                         "avg_launch_ms": ka_avg,
-                         "second_kernel": {"name": "k_cg_b (r update + r.r)", "avg_launch_ms": kb_avg,
-                                           "achieved": 12.0 * cells / (kb_avg / 1e3) / 1e9 if kb_avg > 0 else None}},
-            "clocks": clocks, "gpu_launches": int(ka_n + kb_n + sum(2 * r["refine_steps"] + 1 for r in results))}
+            "roofline": {"bound": "hbm", "kernel": "k_mg_fine<sweep> (multigrid fine-level damped Jacobi sweep)",
+                         "achieved": sw_bytes / (sw_avg / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": sw_bytes / (sw_avg / 1e3) / 1e9 / peak, "peak_source": peak_kind,
+                         "traffic": _profiled_traffic("k_mg_fine_sweep", cells), "bytes_per_launch": sw_bytes,
+                         "avg_launch_ms": sw_avg, "launches_timed": sw_n,
+                         "other_kernels": [
+                             {"name": "k_cg_a (p = z + beta p_old, q = L p, x update, p.q)", "avg_launch_ms": ka_avg,
+                              "bytes_per_launch": 25.0 * cells,
+                              "achieved": 25.0 * cells / (ka_avg / 1e3) / 1e9 if ka_avg > 0 else None,
+                              "traffic": _profiled_traffic("k_cg_a", cells)},
+                             {"name": "k_cg_b (r update + r.r)", "avg_launch_ms": kb_avg, "bytes_per_launch": 12.0 * cells,
+                              "achieved": 12.0 * cells / (kb_avg / 1e3) / 1e9 if kb_avg > 0 else None,
+                              "traffic": _profiled_traffic("k_cg_b", cells)}]},
+            "clocks": clocks, "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
+            "preconditioner": {"levels": info.get("mg_levels"), "applications": mg_n,
+                               "avg_application_ms": mg_ms / max(mg_n, 1)}}
 
-    # plain FP64 solve of the same problem (time-to-tolerance comparison)
-    if not args.no_fp64:
-        plan64 = osm.Plan(3, dims, (1.0, 1.0, 1.0), None, precision=osm.FP64)
+    # the same solve in FP64 arithmetic throughout (same scheme), and the
+    # FP32+refinement solve without the preconditioner (time-to-tolerance
+    # comparisons on the same GPU)
+    def timed_solve(pl):
         p.zero_()
-        plan64.solve(grad, p, TOL)  # warm-up (graph capture)
+        pl.solve(grad, p, TOL)  # warm-up (graph capture)
         torch.cuda.synchronize()
         p.zero_()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        r64 = plan64.solve(grad, p, TOL)
+        rr = pl.solve(grad, p, TOL)
         t1.record(stream)
         torch.cuda.synchronize()
-        line["fp64_plain"] = {"time_to_tolerance_s": t0.elapsed_time(t1) / 1e3, "cg": r64.inner_iters,
-                              "eps_R": r64.eps_R, "status": r64.status,
-                              "speedup_fp32_refine": (t0.elapsed_time(t1) / 1e3) / line["time_to_tolerance_s"]}
+        return t0.elapsed_time(t1) / 1e3, rr
+
+    if not args.no_fp64:
+        plan64 = osm.Plan(3, dims, (1.0, 1.0, 1.0), None, precision=osm.FP64, precond=1)
+        t64, r64 = timed_solve(plan64)
+        line["fp64_plain"] = {"scheme": "same (multigrid-preconditioned CG), every vector and operation in FP64",
+                              "time_to_tolerance_s": t64, "cg": r64.inner_iters, "eps_R": r64.eps_R,
+                              "status": r64.status, "speedup_fp32_refine": t64 / line["time_to_tolerance_s"]}
         plan64.close()
         del plan64
+    if not args.no_cg:
+        plan_cg = osm.Plan(3, dims, (1.0, 1.0, 1.0), None, precision=osm.FP32_REFINE)
+        tcg, rcg = timed_solve(plan_cg)
+        line["cg_unpreconditioned"] = {"time_to_tolerance_s": tcg, "cg": rcg.inner_iters, "eps_R": rcg.eps_R,
+                                       "status": rcg.status, "GLUPS": rcg.point_updates / tcg / 1e9,
+                                       "speedup_preconditioned": tcg / line["time_to_tolerance_s"]}
+        plan_cg.close()
+        del plan_cg
 
     # end to end through the C interface with host buffers
     if not args.no_e2e:

@@ -92,10 +92,12 @@ typedef struct {
                             OUTER: max inner iterations (or sweeps) per outer iteration */
     double inner_tol;    /* FP32_REFINE: the FP32 CG runs until its residual has dropped
                             by this factor since the last FP64 residual replacement
-                            (default 0.1); the search direction carries over
+                            (default 0.1; 1e-4 with precond = 1, whose few
+                            iterations drift little); the search direction carries over
                             ("reliable updates").  OUTER+CG: relative tolerance of
                             each inner solve (default 1e-6) */
-    int check_every;     /* iterations between host convergence checks (default 64) */
+    int check_every;     /* iterations between host convergence checks (0 = default:
+                            64, or 8 with precond = 1) */
     int sweeps_per_pass; /* OUTER+JACOBI: Jacobi sweeps fused per pass, 1..4 (default 2) */
     int max_refine;      /* FP32_REFINE: max refinement steps (default 32) */
     int record_history;  /* OUTER: keep eps_R of every outer iteration (osmodi_history) */
@@ -140,6 +142,8 @@ typedef struct {
     double point_updates;    /* valid cells x stencil applications (GLUPS numerator) */
     double seed_rel_dist;    /* ||P0 - P|| / ||P|| over valid cells, both gauge-fixed
                                 (0 for a zero initial pressure) */
+    double kernel_launches;  /* kernels the call issued (including those of a captured
+                                chunk that found the iteration already finished) */
 } osmodi_result;
 
 /* Fill *opt with the defaults listed above. */
@@ -360,6 +364,12 @@ OSMODI_API osmodi_status osmodi_source_compressible(osmodi_plan plan, const floa
  * preconditioner (one application z = B r per CG iteration; 0 without it). */
 OSMODI_API osmodi_status osmodi_kernel_stats(osmodi_plan plan, double out[8]);
 
+/* Profile mode, multigrid preconditioner: out[0] / out[1] = total ms /
+ * launches of the fine-level plain sweep kernel (two launches per V-cycle,
+ * z += omega D^-1 (r - L z)); out[2] / out[3] = the fine-level residual
+ * kernel (t = r - L z, one per V-cycle).  CUDA events on the solve's stream. */
+OSMODI_API osmodi_status osmodi_kernel_stats_precond(osmodi_plan plan, double out[4]);
+
 /*
  * Autotuner.  osmodi_autotune times short bursts of CG iterations on this
  * plan (synthetic right-hand side, the caller's workspace) for every
@@ -386,6 +396,10 @@ OSMODI_API osmodi_status osmodi_autotune_batched(int count, const osmodi_plan* p
 /* Plan facts: out[0] nx, [1] ny, [2] nz, [3] valid cells, [4] connected
  * components, [5] padded row pitch, [6] padded cells, [7] launch blocks. */
 OSMODI_API osmodi_status osmodi_plan_info(osmodi_plan plan, int64_t out[8]);
+
+/* Coarse levels of the plan's multigrid preconditioner (0 when it is off or
+ * the grid has at most 8 cells per axis). */
+OSMODI_API int osmodi_precond_levels(osmodi_plan plan);
 
 /* The constants the plan uses: c[9] = c_jk row-major (x, y, z), F[3] = face
  * totals, a_tot (Eqs. cxx2D, Atot2D; Section 2.2.2). */

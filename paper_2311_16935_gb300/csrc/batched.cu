@@ -770,6 +770,7 @@ static osmodi_status finish_batched(int count, const BState* st, const BGlobal& 
             R.ms = ms;
             R.point_updates = ((double)S.it + (double)S.rounds + 1.0) * n_valid[i];
             R.seed_rel_dist = S.pnorm2 > 0 ? std::sqrt(S.dist2 / S.pnorm2) : 0.0;
+            R.kernel_launches = 1.0;  // the whole batch is one persistent launch
         }
     }
     return overall;

@@ -93,6 +93,9 @@ struct osmodi_plan_s {
     std::vector<cudaEvent_t> events;             // profile mode event pool
     void* tma_maps = nullptr;                    // tensor maps of the TMA-staged sweep (solve.cu)
     void* mg = nullptr;                          // multigrid hierarchy (mg.cu), when the preconditioner is on
+    double launches = 0;                         // kernels issued by the current / last solve
+    std::vector<cudaEvent_t> mg_events;          // profile mode: around the fine-level multigrid sweeps
+    double mg_kstats[4] = {0, 0, 0, 0};          // profile mode: fine sweep ms / launches, residual ms / launches
 };
 
 namespace osm {

@@ -21,8 +21,8 @@ namespace osm {
 
 namespace {
 
-constexpr float kOmega = 0.8f;   // Jacobi damping
-constexpr float kScale = 1.6f;   // coarse-correction scale (aggregation under-estimates the coarse operator)
+constexpr float kOmega = 0.85f;  // Jacobi damping
+constexpr float kScale = 1.8f;   // coarse-correction scale (aggregation under-estimates the coarse operator)
 constexpr int kNu = 2;           // sweeps before and after the coarse correction
 constexpr int kCoarseSweeps = 40;
 constexpr int kCoarsestMax = 8;  // cells per axis on the coarsest level
@@ -109,7 +109,7 @@ __global__ void k_mg_setup_dinv(Level c, unsigned long long* active) {
 // ---------------------------------------------------------------------------
 // level 0 (the plan's grid)
 // ---------------------------------------------------------------------------
-enum { M_SWEEP = 0, M_FIRST = 1, M_RESID = 2, M_PROLONG = 3 };
+enum { M_SWEEP = 0, M_FIRST = 1, M_RESID = 2 };
 
 template <class T>
 struct FineArgs {
@@ -118,6 +118,7 @@ struct FineArgs {
     int64_t cnx, cny;                         // level-1 dims (parents)
     T F[3];
     T omega, scale;
+    int idx32;                                // chunk indices fit 32-bit arithmetic
 };
 
 template <class T, int NDIM>
@@ -149,14 +150,20 @@ __device__ __forceinline__ void finish_rz(CgState* st, double rz) {
 // MODE M_FIRST:   out = omega D^-1 r                 (first sweep from zero)
 // MODE M_SWEEP:   out = z + omega D^-1 (r - L z)
 // MODE M_RESID:   out = r - L z                      (for the restriction)
-// MODE M_PROLONG: z' = z + scale * P zc, out = z' + omega D^-1 (r - L z')
 // DOT: reduce (r, out) and finish the CG state
 template <class T, int NDIM, int MODE, bool DOT>
 __global__ void __launch_bounds__(256) k_mg_fine(const T* __restrict__ z, const T* __restrict__ r,
-                                                 const T* __restrict__ zc, T* __restrict__ out,
+                                                 T* __restrict__ out,
                                                  const uint8_t* __restrict__ code8, FineArgs<T> g, CgState* st,
                                                  double* partials) {
     if (st->status != kRunning) return;
+    __shared__ T wd[64];  // omega / D for every face mask (0 for an isolated cell)
+    if (threadIdx.x < 64) {
+        const T d = diag0<T, NDIM>(threadIdx.x, 0, g.F);
+        wd[threadIdx.x] = d > T(0) ? g.omega / d : T(0);
+    }
+    __syncthreads();
+    auto wdiag = [&](uint32_t cw, int m) { return valid8(cw, m) ? wd[face_bits8(cw, m)] : T(0); };
     ChunkLoop L;
     double acc[1] = {0.0};
     for (int64_t base = L.base; base < g.n_chunks; base += L.stride) {
@@ -168,50 +175,10 @@ __global__ void __launch_bounds__(256) k_mg_fine(const T* __restrict__ z, const 
         V4<T> o;
         if (MODE == M_FIRST) {
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const T d = diag0<T, NDIM>(cw, m, g.F);
-                o.v[m] = (valid8(cw, m) && d > T(0)) ? g.omega * rv.v[m] / d : T(0);
-            }
+            for (int m = 0; m < 4; ++m) o.v[m] = wdiag(cw, m) * rv.v[m];
         } else {
-            // the chunk's row and plane (for the parents of MODE M_PROLONG)
-            const int64_t row = act ? ch / g.cpr : 0;
-            const int64_t ix = (ch - row * g.cpr) * 4;
-            const int64_t jy = NDIM == 3 ? row % g.ny : row;
-            const int64_t kz = NDIM == 3 ? row / g.ny : 0;
-            auto parent_row = [&](int64_t j, int64_t k) {
-                j = j < 0 ? 0 : (j >= g.ny ? g.ny - 1 : j);
-                k = k < 0 ? 0 : (k >= g.nz ? g.nz - 1 : k);
-                return zc + ((k >> 1) * g.cny + (j >> 1)) * g.cnx;
-            };
-            auto px_of = [&](int64_t i) {
-                i = i < 0 ? 0 : i;
-                const int64_t c = i >> 1;
-                return c >= g.cnx ? g.cnx - 1 : c;
-            };
-            auto f4 = [&](int64_t off) {
-                V4<T> v = ld4(z + i0 + off);
-                if (MODE == M_PROLONG) {
-                    // plane offsets first: with ny = 1 they equal the row
-                    // offsets, whose neighbours do not exist then
-                    int64_t j = jy, k = kz;
-                    if (NDIM == 3 && off == g.plane) ++k;
-                    else if (NDIM == 3 && off == -g.plane) --k;
-                    else if (off == g.px) ++j;
-                    else if (off == -g.px) --j;
-                    const T* cr = parent_row(j, k);
-                    const T a = g.scale * cr[px_of(ix)], b = g.scale * cr[px_of(ix + 2)];
-                    v.v[0] += a;
-                    v.v[1] += a;
-                    v.v[2] += b;
-                    v.v[3] += b;
-                }
-                return v;
-            };
-            auto f1 = [&](int64_t off) {
-                T v = z[i0 + off];
-                if (MODE == M_PROLONG) v += g.scale * parent_row(jy, kz)[px_of(ix + off)];
-                return v;
-            };
+            auto f4 = [&](int64_t off) { return ld4(z + i0 + off); };
+            auto f1 = [&](int64_t off) { return z[i0 + off]; };
             const V4<T> c = act ? f4(0) : zero4<T>();
             const Nbrs<T> nb = gather_clamped<T, NDIM>(c, i0, g.n_box, L.lane, g.px, g.plane, act, f4, f1);
 #pragma unroll
@@ -221,8 +188,8 @@ __global__ void __launch_bounds__(256) k_mg_fine(const T* __restrict__ z, const 
                 if (MODE == M_RESID) {
                     o.v[m] = valid8(cw, m) ? res : T(0);
                 } else {
-                    const T d = diag0<T, NDIM>(cw, m, g.F);
-                    o.v[m] = (valid8(cw, m) && d > T(0)) ? c.v[m] + g.omega * res / d : T(0);
+                    const T w = wdiag(cw, m);
+                    o.v[m] = w != T(0) ? c.v[m] + w * res : T(0);
                 }
             }
         }
@@ -242,13 +209,57 @@ __global__ void __launch_bounds__(256) k_mg_fine(const T* __restrict__ z, const 
     }
 }
 
+// prolongation, in place: z += scale * zc[parent] on the plan's grid (one
+// chunk per thread; the chunk's two x-parents in its row's parent row)
+template <class T, int NDIM>
+__global__ void __launch_bounds__(256) k_mg_fine_prolong(T* __restrict__ z, const T* __restrict__ zc, FineArgs<T> g,
+                                                         const CgState* st) {
+    if (st->status != kRunning) return;
+    for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < g.n_chunks;
+         ch += (int64_t)gridDim.x * blockDim.x) {
+        int64_t ix, jy, kz;
+        if (g.idx32) {
+            const uint32_t r32 = (uint32_t)ch / (uint32_t)g.cpr;
+            ix = ((uint32_t)ch - r32 * (uint32_t)g.cpr) * 4u;
+            jy = NDIM == 3 ? r32 % (uint32_t)g.ny : r32;
+            kz = NDIM == 3 ? r32 / (uint32_t)g.ny : 0;
+        } else {
+            const int64_t row = ch / g.cpr;
+            ix = (ch - row * g.cpr) * 4;
+            jy = NDIM == 3 ? row % g.ny : row;
+            kz = NDIM == 3 ? row / g.ny : 0;
+        }
+        if (ix >= g.nx) continue;  // a chunk of padding only (its values stay 0)
+        const T* cr = zc + ((kz >> 1) * g.cny + (jy >> 1)) * g.cnx;
+        const int64_t c0 = ix >> 1, c1 = (ix >> 1) + 1 < g.cnx ? (ix >> 1) + 1 : g.cnx - 1;
+        const T a = g.scale * cr[c0], b = g.scale * cr[c1];
+        V4<T> v = ld4c(z + ch * 4);
+        v.v[0] += a;
+        v.v[1] += a;
+        v.v[2] += b;
+        v.v[3] += b;
+        st4(z + ch * 4, v);
+    }
+}
+
 // restriction: rc[I] = sum of the (up to 8) children of t (row pitch `pitch`)
 template <class T>
 __global__ void k_mg_restrict(const T* __restrict__ t, int64_t fnx, int64_t fny, int64_t fnz, int64_t pitch,
                               T* __restrict__ rc, Level c, const CgState* st) {
     if (st->status != kRunning) return;
+    const bool i32 = c.n < (int64_t)(1u << 31);
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < c.n; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t I = q % c.nx, J = (q / c.nx) % c.ny, K = q / (c.nx * c.ny);
+        int64_t I, J, K;
+        if (i32) {
+            const uint32_t q32 = (uint32_t)q, nx32 = (uint32_t)c.nx, row = q32 / nx32;
+            I = q32 - row * nx32;
+            J = row % (uint32_t)c.ny;
+            K = row / (uint32_t)c.ny;
+        } else {
+            I = q % c.nx;
+            J = (q / c.nx) % c.ny;
+            K = q / (c.nx * c.ny);
+        }
         T s = T(0);
         const int dz = fnz > 1 ? 2 : 1;
         for (int b = 0; b < dz; ++b)
@@ -275,21 +286,30 @@ struct CoarseArgs {
 };
 
 template <class T, int MODE>
-__global__ void k_mg_coarse(const T* __restrict__ z, const T* __restrict__ r, const T* __restrict__ zc,
-                            T* __restrict__ out, CoarseArgs<T> a, const CgState* st) {
+__global__ void k_mg_coarse(const T* __restrict__ z, const T* __restrict__ r, T* __restrict__ out, CoarseArgs<T> a,
+                            const CgState* st) {
     if (st->status != kRunning) return;
     const Level& g = a.lv;
+    const bool i32 = g.n < (int64_t)(1u << 31);
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < g.n; q += (int64_t)gridDim.x * blockDim.x) {
         const T dv = (T)g.dinv[q];
         if (MODE == M_FIRST) {
             out[q] = dv * r[q];
             continue;
         }
-        const int64_t i = q % g.nx, j = (q / g.nx) % g.ny, k = q / (g.nx * g.ny);
+        int64_t i, j, k;
+        if (i32) {
+            const uint32_t q32 = (uint32_t)q, nx32 = (uint32_t)g.nx, row = q32 / nx32;
+            i = q32 - row * nx32;
+            j = row % (uint32_t)g.ny;
+            k = row / (uint32_t)g.ny;
+        } else {
+            i = q % g.nx;
+            j = (q / g.nx) % g.ny;
+            k = q / (g.nx * g.ny);
+        }
         auto zv = [&](int64_t ii, int64_t jj, int64_t kk) {
-            T v = z[(kk * g.ny + jj) * g.nx + ii];
-            if (MODE == M_PROLONG) v += a.scale * zc[((kk >> 1) * a.cny + (jj >> 1)) * a.cnx + (ii >> 1)];
-            return v;
+            return z[(kk * g.ny + jj) * g.nx + ii];
         };
         const T zc0 = zv(i, j, k);
         T az = T(0);
@@ -301,6 +321,28 @@ __global__ void k_mg_coarse(const T* __restrict__ z, const T* __restrict__ r, co
         if (k > 0) az += (T)g.wz[q - g.nx * g.ny] * (zc0 - zv(i, j, k - 1));
         const T res = r[q] - az;
         out[q] = MODE == M_RESID ? res : zc0 + dv * res;
+    }
+}
+
+// prolongation on a coarse level, in place: z += scale * zc[parent]
+template <class T>
+__global__ void k_mg_coarse_prolong(T* __restrict__ z, const T* __restrict__ zc, CoarseArgs<T> a, const CgState* st) {
+    if (st->status != kRunning) return;
+    const Level& g = a.lv;
+    const bool i32 = g.n < (int64_t)(1u << 31);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < g.n; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i, j, k;
+        if (i32) {
+            const uint32_t q32 = (uint32_t)q, nx32 = (uint32_t)g.nx, row = q32 / nx32;
+            i = q32 - row * nx32;
+            j = row % (uint32_t)g.ny;
+            k = row / (uint32_t)g.ny;
+        } else {
+            i = q % g.nx;
+            j = (q / g.nx) % g.ny;
+            k = q / (g.nx * g.ny);
+        }
+        z[q] += a.scale * zc[((k >> 1) * a.cny + (j >> 1)) * a.cnx + (i >> 1)];
     }
 }
 
@@ -395,26 +437,31 @@ T* vcycle_coarse(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, c
     const int G = grid_for(p, g.n);
     T* cur = v.a;
     T* oth = v.b;
-    k_mg_coarse<T, M_FIRST><<<G, 256, 0, s>>>(nullptr, v.r, nullptr, cur, a, st);
+    k_mg_coarse<T, M_FIRST><<<G, 256, 0, s>>>(nullptr, v.r, cur, a, st);
     for (int i = 1; i < kNu; ++i) {
-        k_mg_coarse<T, M_SWEEP><<<G, 256, 0, s>>>(cur, v.r, nullptr, oth, a, st);
+        k_mg_coarse<T, M_SWEEP><<<G, 256, 0, s>>>(cur, v.r, oth, a, st);
         std::swap(cur, oth);
     }
-    k_mg_coarse<T, M_RESID><<<G, 256, 0, s>>>(cur, v.r, nullptr, oth, a, st);
+    k_mg_coarse<T, M_RESID><<<G, 256, 0, s>>>(cur, v.r, oth, a, st);
     LevelVecs<T> vc = level_vecs<T>(h, base, l + 1);
     k_mg_restrict<T><<<grid_for(p, gc.n), 256, 0, s>>>(oth, g.nx, g.ny, g.nz, g.nx, vc.r, gc, st);
     T* zc = vcycle_coarse<T>(p, h, base, l + 1, st, s);
-    k_mg_coarse<T, M_PROLONG><<<G, 256, 0, s>>>(cur, v.r, zc, oth, a, st);
+    k_mg_coarse_prolong<T><<<G, 256, 0, s>>>(cur, zc, a, st);
+    k_mg_coarse<T, M_SWEEP><<<G, 256, 0, s>>>(cur, v.r, oth, a, st);
     std::swap(cur, oth);
     for (int i = 1; i < kNu; ++i) {
-        k_mg_coarse<T, M_SWEEP><<<G, 256, 0, s>>>(cur, v.r, nullptr, oth, a, st);
+        k_mg_coarse<T, M_SWEEP><<<G, 256, 0, s>>>(cur, v.r, oth, a, st);
         std::swap(cur, oth);
     }
     return cur;
 }
 
 template <class T, int NDIM>
-T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, double* partials, cudaStream_t s) {
+T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, double* partials, cudaStream_t s,
+            cudaEvent_t* ev) {
+    auto mark = [&](int i) {
+        if (ev) cudaEventRecord(ev[i], s);
+    };
     const Hier* h = hier_of(p);
     const Level& g1 = h->lv[0];
     FineArgs<T> f;
@@ -431,29 +478,38 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
     for (int a = 0; a < 3; ++a) f.F[a] = (T)p->k.F[a];
     f.omega = (T)kOmega;
     f.scale = (T)kScale;
+    f.idx32 = p->n_chunks < (int64_t)(1u << 31) ? 1 : 0;
     const int G = std::min(p->launch.blocks_b > 0 ? p->launch.blocks_b : p->num_sms * 4, kMaxBlocks);
+    // (fusing the first two sweeps into one pass was measured slower than the
+    // two passes: forming every neighbour's first-sweep value costs more
+    // instructions than the extra pass moves bytes)
     T* cur = w.zA;
     T* oth = w.zB;
-    k_mg_fine<T, NDIM, M_FIRST, false><<<G, 256, 0, s>>>(nullptr, r, nullptr, cur, p->code8, f, st, partials);
+    k_mg_fine<T, NDIM, M_FIRST, false><<<G, 256, 0, s>>>(nullptr, r, cur, p->code8, f, st, partials);
     for (int i = 1; i < kNu; ++i) {
-        k_mg_fine<T, NDIM, M_SWEEP, false><<<G, 256, 0, s>>>(cur, r, nullptr, oth, p->code8, f, st, partials);
+        if (i == 1) mark(0);
+        k_mg_fine<T, NDIM, M_SWEEP, false><<<G, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
+        if (i == 1) mark(1);
         std::swap(cur, oth);
     }
-    k_mg_fine<T, NDIM, M_RESID, false><<<G, 256, 0, s>>>(cur, r, nullptr, oth, p->code8, f, st, partials);
+    mark(4);
+    k_mg_fine<T, NDIM, M_RESID, false><<<G, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
+    mark(5);
     LevelVecs<T> v1 = level_vecs<T>(h, w.lv, 1);
     k_mg_restrict<T><<<grid_for(p, g1.n), 256, 0, s>>>(oth, p->nx, p->ny, p->nz, p->px, v1.r, g1, st);
     T* zc = vcycle_coarse<T>(p, h, w.lv, 1, st, s);
-    if (kNu == 1) {
-        k_mg_fine<T, NDIM, M_PROLONG, true><<<G, 256, 0, s>>>(cur, r, zc, oth, p->code8, f, st, partials);
-        return oth;
-    }
-    k_mg_fine<T, NDIM, M_PROLONG, false><<<G, 256, 0, s>>>(cur, r, zc, oth, p->code8, f, st, partials);
+    // the prolongation as its own in-place pass: fused into the sweep, every
+    // neighbour's parent lookup made that kernel twice as slow as the two apart
+    k_mg_fine_prolong<T, NDIM><<<G, 256, 0, s>>>(cur, zc, f, st);
+    mark(2);
+    k_mg_fine<T, NDIM, M_SWEEP, false><<<G, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
+    mark(3);
     std::swap(cur, oth);
     for (int i = 1; i < kNu; ++i) {
         if (i == kNu - 1)
-            k_mg_fine<T, NDIM, M_SWEEP, true><<<G, 256, 0, s>>>(cur, r, nullptr, oth, p->code8, f, st, partials);
+            k_mg_fine<T, NDIM, M_SWEEP, true><<<G, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
         else
-            k_mg_fine<T, NDIM, M_SWEEP, false><<<G, 256, 0, s>>>(cur, r, nullptr, oth, p->code8, f, st, partials);
+            k_mg_fine<T, NDIM, M_SWEEP, false><<<G, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
         std::swap(cur, oth);
     }
     return cur;
@@ -544,12 +600,41 @@ double mg_updates_per_apply(osmodi_plan p) {
     return u;
 }
 
-template <class T>
-T* mg_apply(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, double* partials, cudaStream_t s) {
-    return p->ndim == 2 ? apply_nd<T, 2>(p, r, w, st, partials, s) : apply_nd<T, 3>(p, r, w, st, partials, s);
+int mg_launches_per_apply(osmodi_plan p) {
+    const Hier* h = hier_of(p);
+    if (!h) return 0;
+    // per level above the coarsest: kNu pre-sweeps, residual, restriction,
+    // prolongation, kNu post-sweeps; then the coarsest
+    const int per = kNu + 1 + 1 + 1 + kNu;
+    return per * (int)h->lv.size() + 1;
 }
 
-template float* mg_apply<float>(osmodi_plan, const float*, const MgBuffers<float>&, CgState*, double*, cudaStream_t);
-template double* mg_apply<double>(osmodi_plan, const double*, const MgBuffers<double>&, CgState*, double*, cudaStream_t);
+template <class T>
+T* mg_apply(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, double* partials, cudaStream_t s,
+            cudaEvent_t* ev) {
+    return p->ndim == 2 ? apply_nd<T, 2>(p, r, w, st, partials, s, ev) : apply_nd<T, 3>(p, r, w, st, partials, s, ev);
+}
+
+// the fine V-cycle swaps its two buffers (kNu - 1) + kNu times (an odd
+// number): z always ends in zB
+template <class T>
+T* mg_result(const MgBuffers<T>& w) {
+    return w.zB;
+}
+template float* mg_result<float>(const MgBuffers<float>&);
+template double* mg_result<double>(const MgBuffers<double>&);
+
+template float* mg_apply<float>(osmodi_plan, const float*, const MgBuffers<float>&, CgState*, double*, cudaStream_t,
+                                cudaEvent_t*);
+template double* mg_apply<double>(osmodi_plan, const double*, const MgBuffers<double>&, CgState*, double*,
+                                  cudaStream_t, cudaEvent_t*);
 
 }  // namespace osm
+
+extern "C" int osmodi_precond_levels(osmodi_plan p) { return p ? osm::mg_levels(p) : 0; }
+
+extern "C" osmodi_status osmodi_kernel_stats_precond(osmodi_plan p, double out[4]) {
+    if (!p || !out) return OSMODI_E_INVALID;
+    for (int i = 0; i < 4; ++i) out[i] = p->mg_kstats[i];
+    return OSMODI_OK;
+}

@@ -25,6 +25,7 @@ bool mg_enabled(osmodi_plan p);
 int mg_levels(osmodi_plan p);                           // coarse levels (0 when off)
 size_t mg_level_bytes(osmodi_plan p, size_t tsize);     // workspace for the coarse-level vectors
 double mg_updates_per_apply(osmodi_plan p);             // valid cells x stencil applications of one B r
+int mg_launches_per_apply(osmodi_plan p);               // kernels one B r issues
 
 // two fine work vectors (padded box) and the coarse-level vectors
 template <class T>
@@ -36,9 +37,17 @@ struct MgBuffers {
 
 // z = B r on `s`; every kernel returns at once unless the CG state is
 // running.  The last fine-level kernel forms (r, z) and updates the state
-// (beta, rho; the first direction of a segment).  Returns the buffer (zA or
-// zB) that holds z.
+// (beta, rho; the first direction of a segment).  Returns the buffer that
+// holds z (always mg_result(w)).
+// ev (profile mode, else nullptr): six events recorded around the fine
+// level's two plain sweeps and its residual (before/after each)
 template <class T>
-T* mg_apply(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, double* partials, cudaStream_t s);
+T* mg_apply(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, double* partials, cudaStream_t s,
+            cudaEvent_t* ev = nullptr);
+
+// the buffer mg_apply leaves z in (fixed, so that captured CG iterations can
+// read it before the call that writes it)
+template <class T>
+T* mg_result(const MgBuffers<T>& w);
 
 }  // namespace osm

@@ -253,7 +253,7 @@ extern "C" void osmodi_default_options(osmodi_options* o) {
     o->inner = OSMODI_INNER_CG;
     o->inner_max = 1 << 20;
     o->inner_tol = -1.0;  // scheme-dependent default, resolved at create
-    o->check_every = 64;
+    o->check_every = 0;  // 64, or 8 with the preconditioner; resolved at create
     o->sweeps_per_pass = 2;
     o->flat_sweeps = 1;
     o->max_refine = 32;
@@ -293,6 +293,8 @@ static void free_plan_device(osmodi_plan p) {
     p->pinned = nullptr;
     for (auto ev : p->events) cudaEventDestroy(ev);
     p->events.clear();
+    for (auto ev : p->mg_events) cudaEventDestroy(ev);
+    p->mg_events.clear();
     if (p->tma_maps) std::free(p->tma_maps);  // plain struct of tensor maps
     p->tma_maps = nullptr;
     osm::mg_free(p);
@@ -326,8 +328,13 @@ extern "C" osmodi_status osmodi_create(int ndim, const int64_t dims[3], const do
     if (o.scheme != OSMODI_FPCG && o.scheme != OSMODI_OUTER) return OSMODI_E_INVALID;
     if (o.inner != OSMODI_INNER_CG && o.inner != OSMODI_INNER_JACOBI) return OSMODI_E_INVALID;
     if (o.inner_max < 1) o.inner_max = 1 << 20;
-    if (!(o.inner_tol > 0.0)) o.inner_tol = (o.scheme == OSMODI_OUTER) ? 1e-6 : 0.1;
-    if (o.check_every < 2) o.check_every = 64;
+    // FPCG with FP32 sweeps: plain CG drifts over long FP32 runs and works best
+    // with frequent FP64 residual replacements (0.1); the preconditioned CG
+    // needs few iterations and saves FP64 residuals with a deeper target
+    if (!(o.inner_tol > 0.0)) o.inner_tol = (o.scheme == OSMODI_OUTER) ? 1e-6 : (o.precond == 1 ? 1e-4 : 0.1);
+    // a preconditioned CG needs a few dozen iterations: check often, so that
+    // little of a captured chunk runs (as no-op launches) after convergence
+    if (o.check_every < 2) o.check_every = (o.precond == 1 && o.scheme == OSMODI_FPCG) ? 8 : 64;
     o.check_every += o.check_every & 1;  // even: the direction buffers alternate
     if (o.sweeps_per_pass < 1) o.sweeps_per_pass = 1;
     if (o.sweeps_per_pass > 4) o.sweeps_per_pass = 4;

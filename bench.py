@@ -211,6 +211,8 @@ def main():
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-front", action="store_true")
+    ap.add_argument("--no-many", action="store_true")
+    ap.add_argument("--streams", type=int, default=8)
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--ref-crop", type=int, default=100)
     ap.add_argument("--ref-iters", type=int, default=150)
@@ -446,6 +448,29 @@ def main():
                                "GLUPS": sum(r.point_updates for r in res_b) / (bms / 1e3) / 1e9,
                                "cg_iterations_min_mean_max": [min(its), float(sum(its)) / len(its), max(its)],
                                "launches": 1, "graph_captured": True, "tile_depth_chunks_per_thread": depth}
+        # the same snapshots, each solved by the multigrid-preconditioned CG,
+        # spread over host threads driving their own streams (osmodi_solve_many)
+        if not args.no_many:
+            plans_m = [osm.Plan(2, pr.dims, pr.spacing, pr.mask.cuda(), precond=1) for pr in probs]
+            many = osm.Many(plans_m, streams=args.streams)
+            for o in outs:
+                o.zero_()
+            many.solve(grads_b, outs, 1e-10)  # warm-up: every plan captures its CUDA graphs
+            for o in outs:
+                o.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st_m, res_m = many.solve(grads_b, outs, 1e-10)
+            dt_m = time.perf_counter() - t0
+            its_m = [r.inner_iters for r in res_m]
+            line["batched_piv"]["multistream_multigrid"] = {
+                "streams": many.streams, "status": st_m, "converged": int(sum(r.status == osm.OK for r in res_m)),
+                "seconds": dt_m, "timer": "host clock around the synchronous call (inputs resident)",
+                "solves_per_s": args.batch_count / dt_m,
+                "GLUPS": sum(r.point_updates for r in res_m) / dt_m / 1e9,
+                "cg_iterations_min_mean_max": [min(its_m), float(sum(its_m)) / len(its_m), max(its_m)],
+                "kernel_launches": int(sum(r.kernel_launches for r in res_m))}
+            del many, plans_m
         del batch, plans_b, probs, grads_b, outs
     if rank == 0 and world == 1 and not args.no_cpu:
         try:

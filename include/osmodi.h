@@ -245,6 +245,22 @@ OSMODI_API osmodi_status osmodi_solve_noalloc(osmodi_plan plan, const void* grad
                                               int p_dtype, double tol, int max_iter, void* stream,
                                               osmodi_result* res);
 
+/*
+ * Solve `count` independent problems, each by the single-problem path of
+ * osmodi_solve with its own plan's options (so a multigrid-preconditioned
+ * plan solves in a few dozen iterations), spread over `streams` (1..64)
+ * CUDA streams that as many host threads drive concurrently.  Problem i runs
+ * on stream i mod streams with workspaces[i mod streams], which must hold
+ * osmodi_workspace_bytes() of every plan assigned to it; a problem's plan is
+ * used by one thread only.  grads / ps / dtypes as osmodi_solve_batched.
+ * Synchronous: returns when every problem has finished.  Returns OK when all
+ * converged, NOT_CONVERGED if any did not, NAN_INPUT if one had non-finite
+ * input, else the first error (the others stop at their next problem).
+ */
+OSMODI_API osmodi_status osmodi_solve_many(int count, const osmodi_plan* plans, const void* const* grads, int grad_dtype,
+                                           void* const* ps, int p_dtype, double tol, int max_iter, int streams,
+                                           void* const* workspaces, osmodi_result* results);
+
 /* Workspace bytes for osmodi_solve_batched over these plans. */
 OSMODI_API size_t osmodi_batched_workspace_bytes(int count, const osmodi_plan* plans);
 

@@ -104,6 +104,8 @@ namespace osm {
 // error helpers
 // ---------------------------------------------------------------------------
 void set_cuda_error(cudaError_t e, const char* where);
+void set_error_text(const char* msg);  // the calling thread's error text
+const char* last_cuda_error();
 
 #define OSM_CUDA(call)                                        \
     do {                                                      \

@@ -18,7 +18,6 @@
 namespace osm {
 osmodi_status solve_into_scratch(osmodi_plan p, const void* grad, int gdt, void* pu, int pdt, double tol, int max_iter,
                                  void* scratch, cudaStream_t s, osmodi_result* res);
-void set_error_text(const char* msg);
 }  // namespace osm
 
 // The scratch.  Every GPU that loads this module holds it until the process

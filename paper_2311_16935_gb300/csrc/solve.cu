@@ -65,9 +65,21 @@ __global__ void k_source(const TG* __restrict__ f, const TP* __restrict__ p_in, 
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     int bad = 0;
     const int64_t sd[3] = {1, g.nx, g.nx * g.ny};
+    // per axis: -h_a F_a / 2 (the face coefficient of Eq. ExplicitEqn's sum)
+    double coef[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) coef[a] = -0.5 * g.h[a] * g.F[a];
+    const bool i32 = g.n_box < (int64_t)(1u << 31);
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < g.n_box; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = idx / g.px;
-        const int64_t i = idx - row * g.px;
+        int64_t row, i;
+        if (i32) {
+            const uint32_t r32 = (uint32_t)idx / (uint32_t)g.px;
+            row = r32;
+            i = (uint32_t)idx - r32 * (uint32_t)g.px;
+        } else {
+            row = idx / g.px;
+            i = idx - row * g.px;
+        }
         const unsigned cw = code8[idx];
         if (i >= g.nx || !(cw & 0x80u)) {
             b64[idx] = 0.0;
@@ -75,20 +87,22 @@ __global__ void k_source(const TG* __restrict__ f, const TP* __restrict__ p_in, 
             continue;
         }
         const int64_t d = row * g.nx + i;
+        // S_C = sum_a coef_a [b~_+ (f(+) + f(C)) - b~_- (f(-) + f(C))]: the
+        // cell's own component is converted once per axis
         double s = 0.0;
 #pragma unroll
-        for (int fc = 0; fc < 2 * NDIM; ++fc) {
-            if (!(cw & (1u << fc))) continue;
-            const int a = fc >> 1;
-            const double sgn = (fc & 1) ? -1.0 : 1.0;
-            const int64_t dn = d + ((fc & 1) ? -sd[a] : sd[a]);
+        for (int a = 0; a < NDIM; ++a) {
+            const unsigned bp = (cw >> (2 * a)) & 1u, bm = (cw >> (2 * a + 1)) & 1u;
+            if (!(bp | bm)) continue;
             const double fc_ = (double)f[a * g.n_dense + d];
-            const double fn_ = (double)f[a * g.n_dense + dn];
-            s -= sgn * g.h[a] * g.F[a] * 0.5 * (fn_ + fc_);
+            double t = 0.0;
+            if (bp) t += (double)f[a * g.n_dense + d + sd[a]] + fc_;
+            if (bm) t -= (double)f[a * g.n_dense + d - sd[a]] + fc_;
+            s = fma(coef[a], t, s);
         }
 #pragma unroll
         for (int a = 0; a < NDIM; ++a)
-            if (!isfinite((double)f[a * g.n_dense + d])) bad |= 1;
+            if (!isfinite(f[a * g.n_dense + d])) bad |= 1;  // in the input's own precision
         const double p0 = (double)p_in[d];
         if (!isfinite(p0)) bad |= 2;
         b64[idx] = s;

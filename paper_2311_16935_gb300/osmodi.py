@@ -66,6 +66,9 @@ _SIGS = {
                                             ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_batched_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_void_p]),
+    "osmodi_solve_many": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_source_incompressible": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                     ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                                     ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
@@ -495,6 +498,42 @@ class BatchGraph:
             self.close()
         except Exception:
             pass
+
+
+class Many:
+    """osmodi_solve_many over a fixed list of plans: one workspace per stream."""
+
+    def __init__(self, plans, streams=8):
+        self.plans = list(plans)
+        self.streams = max(1, min(int(streams), len(self.plans), 64))
+        self._arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        self.ws = []
+        for w in range(self.streams):
+            need = max(p.workspace_bytes() for p in self.plans[w::self.streams])
+            self.ws.append(torch.empty(need + 256, dtype=torch.uint8, device="cuda"))
+        self._ws_arr = (ctypes.c_void_p * self.streams)(*[(t.data_ptr() + 255) // 256 * 256 for t in self.ws])
+
+    def solve(self, grads, ps, tol, max_iter=1 << 30, check=True):
+        """Returns (status, [osmodi_result]); synchronous."""
+        count = len(self.plans)
+        if len(grads) != count or len(ps) != count:
+            raise ValueError("one gradient and one pressure tensor per plan")
+        for g, p in zip(grads, ps):
+            _check_cuda(g, "grad")
+            _check_cuda(p, "p")
+        gdt = {_dtype_code(g) for g in grads}
+        pdt = {_dtype_code(p) for p in ps}
+        if len(gdt) != 1 or len(pdt) != 1:
+            raise TypeError("all gradients (and all pressures) must share one dtype")
+        ga = (ctypes.c_void_p * count)(*[g.data_ptr() for g in grads])
+        pa = (ctypes.c_void_p * count)(*[p.data_ptr() for p in ps])
+        res = (osmodi_result * count)()
+        torch.cuda.current_stream().synchronize()  # inputs written on torch's stream are complete
+        st = lib().osmodi_solve_many(count, self._arr, ga, gdt.pop(), pa, pdt.pop(), float(tol),
+                                     int(min(max_iter, 2**31 - 1)), self.streams, self._ws_arr, res)
+        if check and st < 0 and st != E_NAN_INPUT:
+            raise OsmodiError(st, "osmodi_solve_many")
+        return st, list(res)
 
 
 def osmodi_solve_batched(plans, grads, ps, tol, max_iter=1 << 30, stream=None):

@@ -195,3 +195,32 @@ def test_captured_graph_replays_new_gradients(osm):
             assert r1.inner_iters == r2.inner_iters
             assert _rel(a, b.cpu().numpy(), valid) < 1e-12
     graph.close()
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_solve_many_streams_match_oracle(osm, precond):
+    """osmodi_solve_many: the single-problem solve of every plan spread over
+    four streams and host threads; each answer equals the oracle's and the
+    per-plan result of a plain osmodi_solve."""
+    inst = _random_instances(11, 9)
+    plans, grads, ps = [], [], []
+    for valid, spacing, f in inst:
+        plans.append(osm.Plan(2, valid.shape[::-1], spacing, torch.from_numpy(valid.astype(np.uint8)).cuda(),
+                              precond=precond))
+        grads.append(torch.from_numpy(f).float().cuda())
+        ps.append(torch.zeros(valid.shape, dtype=torch.float64, device="cuda"))
+    many = osm.Many(plans, streams=4)
+    for rep in range(2):  # the second pass replays every plan's captured graphs
+        for p in ps:
+            p.zero_()
+        st, res = many.solve(grads, ps, 1e-12)
+        assert st == osm.OK, [r.as_dict() for r in res]
+        for (valid, spacing, f), p, r in zip(inst, ps, res):
+            want = oracle.solve_direct(oracle.Grid(valid, spacing), np.asarray(f, np.float32).astype(np.float64))
+            assert r.status == osm.OK and r.eps_R <= 1e-12 and r.kernel_launches > 0
+            assert _rel(p.cpu().numpy(), want, valid) < 1e-9
+    # same iterations as one-by-one solves
+    for k in (0, 5, 10):
+        p1 = torch.zeros_like(ps[k])
+        r1 = plans[k].solve(grads[k], p1, 1e-12)
+        assert r1.inner_iters == res[k].inner_iters

@@ -396,6 +396,26 @@ __global__ void __launch_bounds__(kCoarsestThreads) k_mg_coarsest(const T* __res
 
 Hier* hier_of(osmodi_plan p) { return reinterpret_cast<Hier*>(p->mg); }
 
+// Resident 256-thread blocks per SM of a kernel (queried once per kernel).
+// Grid-stride kernels are launched with exactly one wave of resident blocks:
+// a grid of more blocks than fit at once leaves its last partial wave on
+// half-empty SMs (measured: 912 blocks of a 4-per-SM sweep ran as 1.5 waves).
+template <class K>
+int blocks_per_sm(K kernel) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 256, 0) != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return b;
+}
+
+template <class K>
+int wave_grid(osmodi_plan p, K kernel, int bps, int64_t work256) {
+    (void)kernel;
+    return (int)std::max<int64_t>(1, std::min<int64_t>({work256, (int64_t)p->num_sms * bps, (int64_t)kMaxBlocks}));
+}
+
 int grid_for(osmodi_plan p, int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)p->num_sms * 8));
 }
@@ -434,23 +454,31 @@ T* vcycle_coarse(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, c
     }
     const Level& gc = h->lv[l];
     CoarseArgs<T> a{g, gc.nx, gc.ny, (T)kScale};
-    const int G = grid_for(p, g.n);
+    const int64_t w256 = (g.n + 255) / 256;
+    static const int b_first = blocks_per_sm(k_mg_coarse<T, M_FIRST>);
+    static const int b_sweep = blocks_per_sm(k_mg_coarse<T, M_SWEEP>);
+    static const int b_resid = blocks_per_sm(k_mg_coarse<T, M_RESID>);
+    static const int b_prol = blocks_per_sm(k_mg_coarse_prolong<T>);
+    static const int b_restr = blocks_per_sm(k_mg_restrict<T>);
+    const int G_first = wave_grid(p, 0, b_first, w256), G_sweep = wave_grid(p, 0, b_sweep, w256);
+    const int G_resid = wave_grid(p, 0, b_resid, w256), G_prol = wave_grid(p, 0, b_prol, w256);
     T* cur = v.a;
     T* oth = v.b;
-    k_mg_coarse<T, M_FIRST><<<G, 256, 0, s>>>(nullptr, v.r, cur, a, st);
+    k_mg_coarse<T, M_FIRST><<<G_first, 256, 0, s>>>(nullptr, v.r, cur, a, st);
     for (int i = 1; i < kNu; ++i) {
-        k_mg_coarse<T, M_SWEEP><<<G, 256, 0, s>>>(cur, v.r, oth, a, st);
+        k_mg_coarse<T, M_SWEEP><<<G_sweep, 256, 0, s>>>(cur, v.r, oth, a, st);
         std::swap(cur, oth);
     }
-    k_mg_coarse<T, M_RESID><<<G, 256, 0, s>>>(cur, v.r, oth, a, st);
+    k_mg_coarse<T, M_RESID><<<G_resid, 256, 0, s>>>(cur, v.r, oth, a, st);
     LevelVecs<T> vc = level_vecs<T>(h, base, l + 1);
-    k_mg_restrict<T><<<grid_for(p, gc.n), 256, 0, s>>>(oth, g.nx, g.ny, g.nz, g.nx, vc.r, gc, st);
+    k_mg_restrict<T><<<wave_grid(p, 0, b_restr, (gc.n + 255) / 256), 256, 0, s>>>(oth, g.nx, g.ny, g.nz, g.nx, vc.r, gc,
+                                                                                   st);
     T* zc = vcycle_coarse<T>(p, h, base, l + 1, st, s);
-    k_mg_coarse_prolong<T><<<G, 256, 0, s>>>(cur, zc, a, st);
-    k_mg_coarse<T, M_SWEEP><<<G, 256, 0, s>>>(cur, v.r, oth, a, st);
+    k_mg_coarse_prolong<T><<<G_prol, 256, 0, s>>>(cur, zc, a, st);
+    k_mg_coarse<T, M_SWEEP><<<G_sweep, 256, 0, s>>>(cur, v.r, oth, a, st);
     std::swap(cur, oth);
     for (int i = 1; i < kNu; ++i) {
-        k_mg_coarse<T, M_SWEEP><<<G, 256, 0, s>>>(cur, v.r, oth, a, st);
+        k_mg_coarse<T, M_SWEEP><<<G_sweep, 256, 0, s>>>(cur, v.r, oth, a, st);
         std::swap(cur, oth);
     }
     return cur;
@@ -479,37 +507,48 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
     f.omega = (T)kOmega;
     f.scale = (T)kScale;
     f.idx32 = p->n_chunks < (int64_t)(1u << 31) ? 1 : 0;
-    const int G = std::min(p->launch.blocks_b > 0 ? p->launch.blocks_b : p->num_sms * 4, kMaxBlocks);
+    // one wave of resident blocks per kernel (each mode has its own register count)
+    const int64_t w256 = (p->n_chunks + 255) / 256;
+    static const int b_first = blocks_per_sm(k_mg_fine<T, NDIM, M_FIRST, false>);
+    static const int b_sweep = blocks_per_sm(k_mg_fine<T, NDIM, M_SWEEP, false>);
+    static const int b_dot = blocks_per_sm(k_mg_fine<T, NDIM, M_SWEEP, true>);
+    static const int b_resid = blocks_per_sm(k_mg_fine<T, NDIM, M_RESID, false>);
+    static const int b_prol = blocks_per_sm(k_mg_fine_prolong<T, NDIM>);
+    const int G_first = wave_grid(p, 0, b_first, w256), G_sweep = wave_grid(p, 0, b_sweep, w256);
+    const int G_dot = wave_grid(p, 0, b_dot, w256), G_resid = wave_grid(p, 0, b_resid, w256);
+    const int G_prol = wave_grid(p, 0, b_prol, w256);
     // (fusing the first two sweeps into one pass was measured slower than the
     // two passes: forming every neighbour's first-sweep value costs more
     // instructions than the extra pass moves bytes)
     T* cur = w.zA;
     T* oth = w.zB;
-    k_mg_fine<T, NDIM, M_FIRST, false><<<G, 256, 0, s>>>(nullptr, r, cur, p->code8, f, st, partials);
+    k_mg_fine<T, NDIM, M_FIRST, false><<<G_first, 256, 0, s>>>(nullptr, r, cur, p->code8, f, st, partials);
     for (int i = 1; i < kNu; ++i) {
         if (i == 1) mark(0);
-        k_mg_fine<T, NDIM, M_SWEEP, false><<<G, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
+        k_mg_fine<T, NDIM, M_SWEEP, false><<<G_sweep, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
         if (i == 1) mark(1);
         std::swap(cur, oth);
     }
     mark(4);
-    k_mg_fine<T, NDIM, M_RESID, false><<<G, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
+    k_mg_fine<T, NDIM, M_RESID, false><<<G_resid, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
     mark(5);
     LevelVecs<T> v1 = level_vecs<T>(h, w.lv, 1);
-    k_mg_restrict<T><<<grid_for(p, g1.n), 256, 0, s>>>(oth, p->nx, p->ny, p->nz, p->px, v1.r, g1, st);
+    static const int b_restr = blocks_per_sm(k_mg_restrict<T>);
+    k_mg_restrict<T><<<wave_grid(p, 0, b_restr, (g1.n + 255) / 256), 256, 0, s>>>(oth, p->nx, p->ny, p->nz, p->px, v1.r,
+                                                                                  g1, st);
     T* zc = vcycle_coarse<T>(p, h, w.lv, 1, st, s);
     // the prolongation as its own in-place pass: fused into the sweep, every
     // neighbour's parent lookup made that kernel twice as slow as the two apart
-    k_mg_fine_prolong<T, NDIM><<<G, 256, 0, s>>>(cur, zc, f, st);
+    k_mg_fine_prolong<T, NDIM><<<G_prol, 256, 0, s>>>(cur, zc, f, st);
     mark(2);
-    k_mg_fine<T, NDIM, M_SWEEP, false><<<G, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
+    k_mg_fine<T, NDIM, M_SWEEP, false><<<G_sweep, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
     mark(3);
     std::swap(cur, oth);
     for (int i = 1; i < kNu; ++i) {
         if (i == kNu - 1)
-            k_mg_fine<T, NDIM, M_SWEEP, true><<<G, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
+            k_mg_fine<T, NDIM, M_SWEEP, true><<<G_dot, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
         else
-            k_mg_fine<T, NDIM, M_SWEEP, false><<<G, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
+            k_mg_fine<T, NDIM, M_SWEEP, false><<<G_sweep, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
         std::swap(cur, oth);
     }
     return cur;

@@ -87,17 +87,21 @@ __global__ void k_source(const TG* __restrict__ f, const TP* __restrict__ p_in, 
             continue;
         }
         const int64_t d = row * g.nx + i;
-        // S_C = sum_a coef_a [b~_+ (f(+) + f(C)) - b~_- (f(-) + f(C))]: the
-        // cell's own component is converted once per axis
+        // S_C = sum_a coef_a [b~_+ (f(+) + f(C)) - b~_- (f(-) + f(C))].  With
+        // both faces valid the bracket is f(+) - f(-): the sum or difference
+        // of two FP32 values within a factor 2^29 of each other is exact in
+        // FP64, so this is the same number (to FP64 rounding otherwise) with
+        // fewer FP64 instructions (FP64 throughput bounds this kernel)
         double s = 0.0;
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {
             const unsigned bp = (cw >> (2 * a)) & 1u, bm = (cw >> (2 * a + 1)) & 1u;
             if (!(bp | bm)) continue;
-            const double fc_ = (double)f[a * g.n_dense + d];
-            double t = 0.0;
-            if (bp) t += (double)f[a * g.n_dense + d + sd[a]] + fc_;
-            if (bm) t -= (double)f[a * g.n_dense + d - sd[a]] + fc_;
+            const TG* fa = f + a * g.n_dense + d;
+            double t;
+            if (bp & bm) t = (double)fa[sd[a]] - (double)fa[-sd[a]];
+            else if (bp) t = (double)fa[sd[a]] + (double)fa[0];
+            else t = -((double)fa[-sd[a]] + (double)fa[0]);
             s = fma(coef[a], t, s);
         }
 #pragma unroll
@@ -1745,6 +1749,18 @@ static osmodi_status comp_sums(osmodi_plan p, const T* v, double* sums, cudaStre
     return OSMODI_OK;
 }
 
+// One wave of resident 256-thread blocks of a grid-stride kernel: a grid of
+// more blocks than fit at once runs a partial last wave on few SMs.
+template <class K>
+static int one_wave(osmodi_plan p, K kernel, int64_t n_items) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 256, 0) != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n_items + 255) / 256, (int64_t)p->num_sms * b));
+}
+
 static osmodi_status read_mirror(void* dst, const void* src, size_t n, cudaStream_t s) {
     OSM_CUDA(cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s));
     OSM_CUDA(cudaStreamSynchronize(s));
@@ -1891,8 +1907,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
     // 1. source and initial pressure
     SrcGeo sg{p->px, p->nx, p->ny, p->nz, p->n_dense, p->n_box, {p->k.F[0], p->k.F[1], p->k.F[2]}, {p->h[0], p->h[1], p->h[2]}};
     {
-        const int GS = (int)std::min<int64_t>((p->n_box + 255) / 256, (int64_t)p->num_sms * 8);
-#define OSM_SRC(ND, TG, TP) k_source<ND, TG, TP><<<GS, 256, 0, s>>>((const TG*)grad, (const TP*)pu, p->code8, b.b64, b.p64a, sg, b.sc, b.partials + kSlotMisc * kMaxBlocks)
+#define OSM_SRC(ND, TG, TP) k_source<ND, TG, TP><<<one_wave(p, k_source<ND, TG, TP>, p->n_box), 256, 0, s>>>((const TG*)grad, (const TP*)pu, p->code8, b.b64, b.p64a, sg, b.sc, b.partials + kSlotMisc * kMaxBlocks)
         if (p->ndim == 2) {
             if (gdt == OSMODI_F32 && pdt == OSMODI_F32) OSM_SRC(2, float, float);
             else if (gdt == OSMODI_F32) OSM_SRC(2, float, double);
@@ -2084,12 +2099,11 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
     // gauge and output
     if (multi) OSM_TRY(comp_sums<double>(p, cur, comp_p, s));
     {
-        const int GS = (int)std::min<int64_t>((p->n_box + 255) / 256, (int64_t)p->num_sms * 8);
         if (pdt == OSMODI_F32)
-            k_output<float><<<GS, 256, 0, s>>>(cur, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0,
+            k_output<float><<<one_wave(p, k_output<float>, p->n_box), 256, 0, s>>>(cur, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0,
                                                (float*)pu, p->px, p->nx, p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks);
         else
-            k_output<double><<<GS, 256, 0, s>>>(cur, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0,
+            k_output<double><<<one_wave(p, k_output<double>, p->n_box), 256, 0, s>>>(cur, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0,
                                                 (double*)pu, p->px, p->nx, p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks);
         OSM_CUDA(cudaGetLastError());
         p->launches += 1;

@@ -123,10 +123,11 @@ typedef struct {
                             Same fixed point; far fewer outer iterations.  Adds
                             2m + 3 work vectors to the workspace. */
     int precond;         /* FPCG: 1 = multigrid-preconditioned CG (aggregation of 2x2(x2)
-                            cells per level, Galerkin coarse weights, damped Jacobi
-                            smoothing; a fixed symmetric operator, so CG still converges
-                            to the same fixed point in far fewer iterations); 0 = plain
-                            CG.  Built at plan creation (about 2 B of device memory per
+                            cells per level, Galerkin coarse weights, symmetric red-black
+                            SOR smoothing: red then black before the coarse correction,
+                            black then red after; a fixed symmetric operator, so CG still
+                            converges to the same fixed point in far fewer iterations);
+                            0 = plain CG.  Built at plan creation (about 2 B of device memory per
                             cell); grids of at most 8 cells per axis use plain CG.
                             Not part of the paper's method. */
 } osmodi_options;

@@ -6,11 +6,13 @@
 // the fixed point.  Aggregation of 2 x 2 (x 2) cells per level with the
 // Galerkin coarse operator of piecewise-constant interpolation -- the coarse
 // face weight is the sum of the fine face weights between two aggregates, so
-// every level is again a weighted graph Laplacian on a regular grid -- damped
-// Jacobi smoothing, the coarse correction scaled by a constant, and damped
-// Jacobi sweeps on the coarsest grid.  Pre- and post-smoothing are the same
-// number of sweeps and the coarsest solve is a fixed polynomial in D^-1 A, so
-// z = B r is a fixed symmetric positive (semi)definite operator, as CG needs.
+// every level is again a weighted graph Laplacian on a regular grid --
+// red-black SOR smoothing (one red-then-black sweep before the coarse
+// correction, its adjoint black-then-red after), the coarse correction scaled
+// by a constant, and red-black sweeps in both orders on the coarsest grid
+// (damped Jacobi is kept as the alternative smoother).  Post-smoothing is the
+// adjoint of pre-smoothing and the coarsest solve is symmetric, so z = B r is
+// a fixed symmetric positive (semi)definite operator, as CG needs.
 #pragma once
 
 #include "cg_state.cuh"

@@ -130,6 +130,8 @@ typedef struct {
                             0 = plain CG.  Built at plan creation (about 2 B of device memory per
                             cell); grids of at most 8 cells per axis use plain CG.
                             Not part of the paper's method. */
+    int zero_start;      /* 1 = start from P^0 = 0 without reading p: p is output only
+                            (saves reading it, e.g. from host memory); 0 = p holds P^0 */
 } osmodi_options;
 
 typedef struct {
@@ -142,7 +144,7 @@ typedef struct {
     double ms;               /* wall-clock of the call (host timer around the stream) */
     double point_updates;    /* valid cells x stencil applications (GLUPS numerator) */
     double seed_rel_dist;    /* ||P0 - P|| / ||P|| over valid cells, both gauge-fixed
-                                (0 for a zero initial pressure) */
+                                (1 for a zero initial pressure) */
     double kernel_launches;  /* kernels the call issued (including those of a captured
                                 chunk that found the iteration already finished) */
 } osmodi_result;
@@ -192,6 +194,11 @@ OSMODI_API size_t osmodi_workspace_bytes(osmodi_plan plan);
  *   stream      all work is ordered on it; the call synchronises the stream
  *               to read convergence flags and fill *res
  *   res         may be NULL
+ * grad_dev and p_dev may be device or managed memory, or page-locked host
+ * memory (cudaHostAlloc / cudaHostRegister, unified addressing): the source
+ * kernel then reads the gradient and P^0 and the output kernel writes P
+ * directly over the host link, with no staging copies.  Any other host
+ * pointer is refused with E_INVALID.
  * Returns OK (eps_R <= tol), NOT_CONVERGED, E_NAN_INPUT, E_DIVERGED,
  * E_WORKSPACE, E_INVALID or E_CUDA.  A plan is not thread-safe: one solve at
  * a time per plan.
@@ -397,6 +404,10 @@ OSMODI_API osmodi_status osmodi_kernel_stats_precond(osmodi_plan plan, double ou
  * NULL-safe) keyed by GPU name, ndim, log2 of the cell count and precision.
  * Plans created with options.autotune = 1 read that cache.  ms_out (may be
  * NULL) receives the best time per CG iteration.  Synchronous.
+ * For an OUTER plan with Jacobi inner sweeps it instead times 24 sweeps of
+ * the plan's operator with 1, 2, 3 and 4 sweeps fused per pass, keeps the
+ * fastest in options.sweeps_per_pass (ms_out: time per sweep) and caches it
+ * the same way.
  *
  * osmodi_autotune_batched picks the tile depth of osmodi_solve_batched (1, 2,
  * 4 or 8 chunks of 4 cells per thread) by timing the batched solve capped at

@@ -909,6 +909,7 @@ static osmodi_status check_batch(int count, const osmodi_plan* plans, const void
     for (int i = 0; i < count; ++i) {
         if (!plans[i] || !grads[i] || !ps[i]) return OSMODI_E_INVALID;
         if (plans[i]->ndim != ndim || plans[i]->device != dev) return OSMODI_E_INVALID;
+        if (!user_buffer_ok(grads[i], dev) || !user_buffer_ok(ps[i], dev)) return OSMODI_E_INVALID;
         if (plans[i]->n_chunks > (int64_t)kTileThreads * (int64_t)(1 << 30)) return OSMODI_E_INVALID;
     }
     if (plans[0]->opt.scheme != OSMODI_FPCG) return OSMODI_E_UNSUPPORTED;

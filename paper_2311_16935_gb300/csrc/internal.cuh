@@ -105,6 +105,10 @@ namespace osm {
 // ---------------------------------------------------------------------------
 void set_cuda_error(cudaError_t e, const char* where);
 void set_error_text(const char* msg);  // the calling thread's error text
+// A caller buffer the kernels may read and write: device memory of `dev`,
+// managed memory, or page-locked host memory mapped at the same address
+// (unified addressing).  Unregistered host memory is refused.
+bool user_buffer_ok(const void* ptr, int dev);
 const char* last_cuda_error();
 
 #define OSM_CUDA(call)                                        \

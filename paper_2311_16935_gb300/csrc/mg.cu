@@ -1,12 +1,15 @@
 // Multigrid preconditioner (see mg.cuh for what it computes and why it keeps
-// CG's requirements).  The smoother is red-black SOR (kRedBlack); the damped
-// Jacobi variant is kept beside it (measured at 500^3: 18 CG iterations and
-// 75.9 ms per solve with Jacobi, 15 and 68.9 ms with red-black).  Level 0 is the plan's own grid: padded box, 4-cell
-// chunks, face weights b~_j F_j read from the 1-byte codes, the same
-// neighbour gather as the CG kernels.  Levels >= 1 are dense boxes with
-// explicit FP32 weights to the +x / +y / +z neighbour (0 when the aggregates
-// share no valid face) and omega / diagonal; one thread per cell.  The
-// coarsest level (at most 8 cells per axis) is swept by one block.
+// CG's requirements).  The smoother depends on the dimension: red-black SOR
+// on 3-D grids (measured at 500^3: 15 CG iterations and 68.9 ms per solve,
+// against 18 and 75.9 ms with damped Jacobi), damped Jacobi on 2-D grids
+// (on the 2-D PIV snapshots Jacobi with a coarse scale of 2.0 needed 11
+// iterations, red-black 12 to 21 depending on omega and scale).  Level 0 is
+// the plan's own grid: padded box, 4-cell chunks, face weights b~_j F_j read
+// from the 1-byte codes, the same neighbour gather as the CG kernels.  Levels
+// >= 1 are dense boxes with explicit FP32 weights to the +x / +y / +z
+// neighbour (0 when the aggregates share no valid face) and omega / diagonal;
+// one thread per cell.  The coarsest level (at most 8 cells per axis) is
+// swept by one block.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,10 +26,11 @@ namespace osm {
 
 namespace {
 
-constexpr bool kRedBlack = true;  // smoother: symmetric red-black SOR (else damped Jacobi)
 constexpr float kOmega = 0.85f;    // Jacobi damping
 constexpr float kOmegaRB = 1.2f;   // red-black over-relaxation
-constexpr float kScale = 1.8f;   // coarse-correction scale (aggregation under-estimates the coarse operator)
+// coarse-correction scale (aggregation under-estimates the coarse operator)
+constexpr float kScaleRB = 1.8f;      // with red-black smoothing (3-D)
+constexpr float kScaleJacobi = 2.0f;  // with damped Jacobi (2-D)
 constexpr int kNu = 2;           // sweeps before and after the coarse correction
 constexpr int kCoarseSweeps = 40;
 constexpr int kCoarsestMax = 8;  // cells per axis on the coarsest level
@@ -467,7 +471,7 @@ __global__ void k_mg_coarse_prolong(T* __restrict__ z, const T* __restrict__ zc,
 
 // coarsest level, one block: kCoarseSweeps sweeps from zero (red-black: half
 // of them red-then-black, half black-then-red; Jacobi: damped Jacobi)
-template <class T>
+template <class T, bool RB>
 __global__ void __launch_bounds__(kCoarsestThreads) k_mg_coarsest(const T* __restrict__ r, T* __restrict__ out, Level g,
                                                                   const CgState* st) {
     if (st->status != kRunning) return;
@@ -481,7 +485,7 @@ __global__ void __launch_bounds__(kCoarsestThreads) k_mg_coarsest(const T* __res
         j = (q / g.nx) % g.ny;
         k = q / (g.nx * g.ny);
         rq = r[q];
-        dv = (T)(kRedBlack ? kOmegaRB : kOmega) * (T)g.dinv[q];
+        dv = (T)(RB ? kOmegaRB : kOmega) * (T)g.dinv[q];
         wxp = i + 1 < g.nx ? (T)g.wx[q] : T(0);
         wxm = i > 0 ? (T)g.wx[q - 1] : T(0);
         wyp = j + 1 < g.ny ? (T)g.wy[q] : T(0);
@@ -501,7 +505,7 @@ __global__ void __launch_bounds__(kCoarsestThreads) k_mg_coarsest(const T* __res
         if (wzm != T(0)) az += wzm * (c - zz[q - sz]);
         return az;
     };
-    if (kRedBlack) {
+    if (RB) {
         // kCoarseSweeps / 2 red-black sweeps, then as many black-red ones
         // (the reverse order keeps the operator symmetric), in place
         const int col = act ? (int)((i + j + k) & 1) : 2;
@@ -549,6 +553,10 @@ __global__ void __launch_bounds__(kCoarsestThreads) k_mg_coarsest(const T* __res
 }
 
 Hier* hier_of(osmodi_plan p) { return reinterpret_cast<Hier*>(p->mg); }
+
+// the smoother of a plan: red-black SOR on 3-D grids, damped Jacobi on 2-D
+bool red_black(osmodi_plan p) { return p->ndim == 3; }
+float coarse_scale(osmodi_plan p) { return red_black(p) ? kScaleRB : kScaleJacobi; }
 
 // Resident 256-thread blocks per SM of a kernel (queried once per kernel).
 // Grid-stride kernels are launched with exactly one wave of resident blocks:
@@ -602,12 +610,16 @@ template <class T>
 T* vcycle_coarse(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, cudaStream_t s) {
     const Level& g = h->lv[l - 1];
     LevelVecs<T> v = level_vecs<T>(h, base, l);
+    const bool rb = red_black(p);
     if (l == (int)h->lv.size()) {
-        k_mg_coarsest<T><<<1, kCoarsestThreads, 0, s>>>(v.r, v.a, g, st);
+        if (rb)
+            k_mg_coarsest<T, true><<<1, kCoarsestThreads, 0, s>>>(v.r, v.a, g, st);
+        else
+            k_mg_coarsest<T, false><<<1, kCoarsestThreads, 0, s>>>(v.r, v.a, g, st);
         return v.a;
     }
     const Level& gc = h->lv[l];
-    CoarseArgs<T> a{g, gc.nx, gc.ny, (T)kScale, (T)(kRedBlack ? kOmegaRB : kOmega)};
+    CoarseArgs<T> a{g, gc.nx, gc.ny, (T)coarse_scale(p), (T)(rb ? kOmegaRB : kOmega)};
     const int64_t w256 = (g.n + 255) / 256;
     static const int b_first = blocks_per_sm(k_mg_coarse<T, M_FIRST>);
     static const int b_sweep = blocks_per_sm(k_mg_coarse<T, M_SWEEP>);
@@ -616,7 +628,7 @@ T* vcycle_coarse(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, c
     static const int b_restr = blocks_per_sm(k_mg_restrict<T>);
     const int G_first = wave_grid(p, 0, b_first, w256), G_sweep = wave_grid(p, 0, b_sweep, w256);
     const int G_resid = wave_grid(p, 0, b_resid, w256), G_prol = wave_grid(p, 0, b_prol, w256);
-    if (kRedBlack) {
+    if (rb) {
         static const int b_rb = blocks_per_sm(k_mg_coarse_rb<T, 1, false>);
         const int G_rb = wave_grid(p, 0, b_rb, w256);
         LevelVecs<T> vc = level_vecs<T>(h, base, l + 1);
@@ -674,7 +686,7 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
     f.cny = g1.ny;
     for (int a = 0; a < 3; ++a) f.F[a] = (T)p->k.F[a];
     f.omega = (T)kOmega;
-    f.scale = (T)kScale;
+    f.scale = (T)coarse_scale(p);
     f.idx32 = p->n_chunks < (int64_t)(1u << 31) ? 1 : 0;
     // one wave of resident blocks per kernel (each mode has its own register count)
     const int64_t w256 = (p->n_chunks + 255) / 256;
@@ -689,7 +701,7 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
     // (fusing the first two sweeps into one pass was measured slower than the
     // two passes: forming every neighbour's first-sweep value costs more
     // instructions than the extra pass moves bytes)
-    if (kRedBlack) {
+    if (red_black(p)) {
         f.omega = (T)kOmegaRB;
         static const int b_rb = blocks_per_sm(k_mg_fine_rb<T, NDIM, 1, false, false>);
         static const int b_rbd = blocks_per_sm(k_mg_fine_rb<T, NDIM, 0, false, true>);
@@ -827,10 +839,11 @@ double mg_updates_per_apply(osmodi_plan p) {
     // fine and intermediate levels: (nu - 1) + 1 (residual) + nu sweeps with a
     // stencil application each; the coarsest: kCoarseSweeps - 1
     // red-black: three half-sweeps (1.5 applications) and the residual per level
-    const double per = kRedBlack ? 2.5 : 2.0 * kNu;
+    const bool rb = red_black(p);
+    const double per = rb ? 2.5 : 2.0 * kNu;
     double u = per * (double)p->n_valid;
     for (size_t q = 0; q < h->lv.size(); ++q)
-        u += (q + 1 == h->lv.size() ? (double)kCoarseSweeps - (kRedBlack ? 0.5 : 1.0) : per) * h->lv[q].active;
+        u += (q + 1 == h->lv.size() ? (double)kCoarseSweeps - (rb ? 0.5 : 1.0) : per) * h->lv[q].active;
     return u;
 }
 
@@ -852,11 +865,11 @@ T* mg_apply(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
 // red-black smoothing updates z in place in zA; the Jacobi V-cycle swaps its
 // two buffers (kNu - 1) + kNu times (an odd number) and ends in zB
 template <class T>
-T* mg_result(const MgBuffers<T>& w) {
-    return kRedBlack ? w.zA : w.zB;
+T* mg_result(osmodi_plan p, const MgBuffers<T>& w) {
+    return red_black(p) ? w.zA : w.zB;
 }
-template float* mg_result<float>(const MgBuffers<float>&);
-template double* mg_result<double>(const MgBuffers<double>&);
+template float* mg_result<float>(osmodi_plan, const MgBuffers<float>&);
+template double* mg_result<double>(osmodi_plan, const MgBuffers<double>&);
 
 template float* mg_apply<float>(osmodi_plan, const float*, const MgBuffers<float>&, CgState*, double*, cudaStream_t,
                                 cudaEvent_t*);

@@ -7,10 +7,11 @@
 // Galerkin coarse operator of piecewise-constant interpolation -- the coarse
 // face weight is the sum of the fine face weights between two aggregates, so
 // every level is again a weighted graph Laplacian on a regular grid --
-// red-black SOR smoothing (one red-then-black sweep before the coarse
-// correction, its adjoint black-then-red after), the coarse correction scaled
-// by a constant, and red-black sweeps in both orders on the coarsest grid
-// (damped Jacobi is kept as the alternative smoother).  Post-smoothing is the
+// smoothing by red-black SOR on 3-D grids (one red-then-black sweep before
+// the coarse correction, its adjoint black-then-red after) and by two damped
+// Jacobi sweeps before and after on 2-D grids, the coarse correction scaled
+// by a constant, and the same smoother run for many sweeps on the coarsest
+// grid.  Post-smoothing is the
 // adjoint of pre-smoothing and the coarsest solve is symmetric, so z = B r is
 // a fixed symmetric positive (semi)definite operator, as CG needs.
 #pragma once
@@ -50,6 +51,6 @@ T* mg_apply(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
 // the buffer mg_apply leaves z in (fixed, so that captured CG iterations can
 // read it before the call that writes it)
 template <class T>
-T* mg_result(const MgBuffers<T>& w);
+T* mg_result(osmodi_plan p, const MgBuffers<T>& w);
 
 }  // namespace osm

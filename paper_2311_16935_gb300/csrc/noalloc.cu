@@ -62,6 +62,7 @@ extern "C" osmodi_status osmodi_solve_noalloc(osmodi_plan p, const void* grad, i
     int dev = -1;
     OSM_CUDA(cudaGetDevice(&dev));
     if (dev != p->device || dev < 0 || dev >= kMaxDevices) return OSMODI_E_INVALID;
+    if (!osm::user_buffer_ok(grad, dev) || !osm::user_buffer_ok(pu, dev)) return OSMODI_E_INVALID;
     void* scratch = nullptr;
     cudaError_t e = scratch_address(dev, &scratch);
     if (e != cudaSuccess) {

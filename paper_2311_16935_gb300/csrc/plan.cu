@@ -29,6 +29,16 @@ const char* last_cuda_error() { return g_last_cuda_error.c_str(); }
 
 void set_error_text(const char* msg) { g_last_cuda_error = msg; }
 
+bool user_buffer_ok(const void* ptr, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev;
+    return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeHost && a.devicePointer == ptr);
+}
+
 // ---------------------------------------------------------------------------
 // Constants
 // ---------------------------------------------------------------------------

@@ -107,7 +107,7 @@ __global__ void k_source(const TG* __restrict__ f, const TP* __restrict__ p_in, 
 #pragma unroll
         for (int a = 0; a < NDIM; ++a)
             if (!isfinite(f[a * g.n_dense + d])) bad |= 1;  // in the input's own precision
-        const double p0 = (double)p_in[d];
+        const double p0 = p_in ? (double)p_in[d] : 0.0;  // null: P^0 = 0, not read
         if (!isfinite(p0)) bad |= 2;
         b64[idx] = s;
         p64[idx] = p0;
@@ -147,12 +147,11 @@ __global__ void __launch_bounds__(512) k_residual_zero_start(const double* __res
 }
 
 // ---------------------------------------------------------------------------
-// FP64 residual of the refinement loop: p_out = p_in + e (if e), r = b - L p,
-// reductions ||r||^2, sum r, sum p.
+// FP64 residual of the refinement loop: r = b - L p (the correction was
+// folded into p by k_fold), reductions ||r||^2, sum r, sum p.
 // ---------------------------------------------------------------------------
-template <class TI, int NDIM, bool HAS_E>
-__global__ void __launch_bounds__(512) k_residual(const double* __restrict__ p_in, const TI* __restrict__ e,
-                                                  double* __restrict__ p_out, const double* __restrict__ b64,
+template <class TI, int NDIM>
+__global__ void __launch_bounds__(512) k_residual(const double* __restrict__ p_in, const double* __restrict__ b64,
                                                   TI* __restrict__ r_out, const uint8_t* __restrict__ code8,
                                                   Geo<double> g, Scalars* sc, double* partials) {
     __shared__ double dtab[64];  // sum of F over the faces set in a 6-bit face mask
@@ -169,32 +168,15 @@ __global__ void __launch_bounds__(512) k_residual(const double* __restrict__ p_i
         const bool act = ch < g.n_chunks;
         const int64_t i0 = ch * 4;
         const uint32_t cw = act ? *reinterpret_cast<const uint32_t*>(code8 + i0) : 0u;
-        V4<double> c = act ? ld4(p_in + i0) : zero4<double>();
-        if (HAS_E && act) {
-            V4<TI> ev = ld4(e + i0);
-#pragma unroll
-            for (int m = 0; m < 4; ++m) c.v[m] += (double)ev.v[m];
-        }
+        const V4<double> c = act ? ld4(p_in + i0) : zero4<double>();
         unsigned fm[4], any = 0;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             fm[m] = face_bits8(cw, m);
             any |= fm[m];
         }
-        auto f4 = [&](int64_t off) {
-            V4<double> v = ld4(p_in + i0 + off);
-            if (HAS_E) {
-                V4<TI> w = ld4(e + i0 + off);
-#pragma unroll
-                for (int m = 0; m < 4; ++m) v.v[m] += (double)w.v[m];
-            }
-            return v;
-        };
-        auto f1 = [&](int64_t off) {
-            double v = p_in[i0 + off];
-            if (HAS_E) v += (double)e[i0 + off];
-            return v;
-        };
+        auto f4 = [&](int64_t off) { return ld4(p_in + i0 + off); };
+        auto f1 = [&](int64_t off) { return p_in[i0 + off]; };
         Nbrs<double> nb = gather<double, NDIM>(c, any, fm[0] & 2u, fm[3] & 1u, L.lane, g.px, g.plane, f4, f1);
         if (act) {
             const V4<double> bv = ld4(b64 + i0);
@@ -220,7 +202,6 @@ __global__ void __launch_bounds__(512) k_residual(const double* __restrict__ p_i
                 acc[1] += r;
                 acc[2] += c.v[m];
             }
-            if (HAS_E) st4(p_out + i0, c);
             st4(r_out + i0, rv);
         }
     }
@@ -229,6 +210,19 @@ __global__ void __launch_bounds__(512) k_residual(const double* __restrict__ p_i
         sc->rnorm2 = tot[0];
         sc->rsum = tot[1];
         sc->psum = tot[2];
+    }
+}
+
+// p64 += e (the FP32 correction), in place; cells outside the valid set hold
+// e = 0
+template <class TI>
+__global__ void __launch_bounds__(256) k_fold(double* __restrict__ p64, const TI* __restrict__ e, int64_t n_chunks) {
+    for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < n_chunks; ch += (int64_t)gridDim.x * blockDim.x) {
+        V4<double> pv = ld4c(p64 + ch * 4);
+        const V4<TI> ev = ld4(e + ch * 4);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) pv.v[m] += (double)ev.v[m];
+        st4(p64 + ch * 4, pv);
     }
 }
 
@@ -1188,7 +1182,7 @@ template <class TP>
 __global__ void k_output(const double* __restrict__ p64, const uint8_t* __restrict__ code8, const int32_t* __restrict__ label,
                          const double* __restrict__ comp_p, const double* __restrict__ comp_p0,
                          const double* __restrict__ comp_cnt, int multi, TP* __restrict__ p_user, int64_t px, int64_t nx,
-                         int64_t n_box, Scalars* sc, double* partials) {
+                         int64_t n_box, Scalars* sc, double* partials, int zero0 = 0) {
     const double m1 = multi ? 0.0 : sc->psum / comp_cnt[0];
     const double m01 = multi ? 0.0 : sc->p0sum / comp_cnt[0];
     double acc[2] = {0.0, 0.0};
@@ -1208,7 +1202,7 @@ __global__ void k_output(const double* __restrict__ p64, const uint8_t* __restri
             m0 = comp_p0[l] / comp_cnt[l];
         }
         const double v = p64[idx] - m;
-        const double v0 = (double)p_user[d] - m0;
+        const double v0 = zero0 ? 0.0 : (double)p_user[d] - m0;  // zero start: P^0 is not read
         acc[0] += (v0 - v) * (v0 - v);
         acc[1] += v * v;
         p_user[d] = (TP)v;
@@ -1273,9 +1267,9 @@ int tuned_blocks_per_sm(int ndim, int threads) {
     int bps = 0;
     cudaError_t e;
     if (ndim == 2)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_residual<float, 2, true>, threads, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_residual<float, 2>, threads, 0);
     else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_residual<float, 3, true>, threads, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_residual<float, 3>, threads, 0);
     if (e != cudaSuccess || bps < 1) {
         cudaGetLastError();
         bps = 2048 / threads;
@@ -1305,7 +1299,7 @@ void sweep_blocks_per_sm(int ndim, bool fp64, int* bps_a, int* bps_b) {
 
 template <class T>
 struct Buffers {
-    double *p64a, *p64b, *b64;
+    double *p64a, *b64;
     T *r, *x, *q, *pA, *pB;
     T *rc, *rhs, *e2;  // OUTER extras
     T *mgA, *mgB;       // FPCG with the multigrid preconditioner: V-cycle buffers (z ends in mg_result)
@@ -1327,7 +1321,6 @@ static size_t carve(osmodi_plan p, void* ws, Buffers<T>* b) {
     const size_t n = (size_t)p->n_box;
     Buffers<T> t{};
     t.p64a = w.take<double>(n);
-    t.p64b = w.take<double>(n);
     t.b64 = w.take<double>(n);
     t.r = w.take<T>(n);
     t.x = w.take<T>(n);
@@ -1530,9 +1523,9 @@ static bool precond_on(osmodi_plan p, const Buffers<T>& b, int op) {
 }
 
 template <class T>
-static Buffers<T> a_operands(const Buffers<T>& b, bool pre) {
+static Buffers<T> a_operands(osmodi_plan p, const Buffers<T>& b, bool pre) {
     Buffers<T> ba = b;
-    if (pre) ba.r = mg_result<T>(MgBuffers<T>{b.mgA, b.mgB, b.mg_lv});
+    if (pre) ba.r = mg_result<T>(p, MgBuffers<T>{b.mgA, b.mgB, b.mg_lv});
     return ba;
 }
 
@@ -1552,7 +1545,7 @@ template <class T>
 static osmodi_status launch_cg_iters(osmodi_plan p, const Buffers<T>& b, int op, int iters, cudaStream_t s) {
     const int GB = p->launch.blocks_b;
     const bool pre = precond_on(p, b, op);
-    const Buffers<T> ba = a_operands(b, pre);
+    const Buffers<T> ba = a_operands(p, b, pre);
     for (int k = 0; k < iters; ++k) {
         const T* po = (k & 1) ? b.pB : b.pA;
         T* pn = (k & 1) ? b.pA : b.pB;
@@ -1582,7 +1575,7 @@ static osmodi_status run_cg_profiled(osmodi_plan p, const Buffers<T>& b, int op,
                                      long long* iters_out) {
     const int len = p->opt.check_every;
     const bool pre = precond_on(p, b, op);
-    const Buffers<T> ba = a_operands(b, pre);
+    const Buffers<T> ba = a_operands(p, b, pre);
     const int per = pre ? 3 : 2;  // events per iteration
     OSM_TRY(ensure_events(p, (size_t)(per * len + 1)));
     while (pre && p->mg_events.size() < (size_t)(6 * len)) {  // six per V-cycle (fine sweeps and residual)
@@ -1712,21 +1705,16 @@ static osmodi_status run_cg(osmodi_plan p, const Buffers<T>& b, int op, void* ws
 }
 
 template <class T>
-static osmodi_status launch_residual(osmodi_plan p, const Buffers<T>& b, const double* p_in, const T* e, double* p_out,
-                                     T* r_out, cudaStream_t s, bool prof) {
+static osmodi_status launch_residual(osmodi_plan p, const Buffers<T>& b, const double* p_in, T* r_out, cudaStream_t s,
+                                     bool prof) {
     const int G = p->launch.blocks, TH = p->launch.threads;
     if (prof) {
         OSM_TRY(ensure_events(p, 2));
         OSM_CUDA(cudaEventRecord(p->events[0], s));
     }
     const Geo<double> g = geo<double>(p);
-    if (p->ndim == 2) {
-        if (e) k_residual<T, 2, true><<<G, TH, 0, s>>>(p_in, e, p_out, b.b64, r_out, p->code8, g, b.sc, b.partials + kSlotRes * kMaxBlocks);
-        else k_residual<T, 2, false><<<G, TH, 0, s>>>(p_in, e, p_out, b.b64, r_out, p->code8, g, b.sc, b.partials + kSlotRes * kMaxBlocks);
-    } else {
-        if (e) k_residual<T, 3, true><<<G, TH, 0, s>>>(p_in, e, p_out, b.b64, r_out, p->code8, g, b.sc, b.partials + kSlotRes * kMaxBlocks);
-        else k_residual<T, 3, false><<<G, TH, 0, s>>>(p_in, e, p_out, b.b64, r_out, p->code8, g, b.sc, b.partials + kSlotRes * kMaxBlocks);
-    }
+    if (p->ndim == 2) k_residual<T, 2><<<G, TH, 0, s>>>(p_in, b.b64, r_out, p->code8, g, b.sc, b.partials + kSlotRes * kMaxBlocks);
+    else k_residual<T, 3><<<G, TH, 0, s>>>(p_in, b.b64, r_out, p->code8, g, b.sc, b.partials + kSlotRes * kMaxBlocks);
     OSM_CUDA(cudaGetLastError());
     if (prof) {
         OSM_CUDA(cudaEventRecord(p->events[1], s));
@@ -1764,6 +1752,33 @@ static int one_wave(osmodi_plan p, K kernel, int64_t n_items) {
 static osmodi_status read_mirror(void* dst, const void* src, size_t n, cudaStream_t s) {
     OSM_CUDA(cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s));
     OSM_CUDA(cudaStreamSynchronize(s));
+    return OSMODI_OK;
+}
+
+// One pass of k Jacobi sweeps on M~ e = rhs (k = 1: the plain sweep kernel;
+// k > 1: the fused ghost-zone kernel), e_in -> e_out.
+template <class T>
+static osmodi_status launch_jacobi_pass(osmodi_plan p, const T* e_in, T* e_out, const T* rhs, int k, cudaStream_t s) {
+    const int G = p->launch.blocks, TH = p->launch.threads;
+    const Geo<T> g = geo<T>(p);
+    const TableT<T> tab = table<T>(p);
+    if (k == 1) {
+        if (p->ndim == 2) k_jacobi<T, 2><<<G, TH, 0, s>>>(e_in, e_out, rhs, p->code32, g, tab);
+        else k_jacobi<T, 3><<<G, TH, 0, s>>>(e_in, e_out, rhs, p->code32, g, tab);
+    } else {
+        const int tz = p->ndim == 3 ? 4 : 1, hz = p->ndim == 3 ? k : 0;
+        const size_t cells = (size_t)(JTX + 2 * k) * (JTY + 2 * k) * (tz + 2 * hz);
+        const size_t smem = cells * (3 * sizeof(T) + sizeof(uint32_t));
+        dim3 grid((unsigned)((p->px + JTX - 1) / JTX), (unsigned)((p->ny + JTY - 1) / JTY), (unsigned)((p->nz + tz - 1) / tz));
+        if (p->ndim == 2) {
+            OSM_CUDA(cudaFuncSetAttribute(k_jacobi_fused<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_jacobi_fused<T, 2><<<grid, 256, smem, s>>>(e_in, e_out, rhs, p->code32, p->px, p->ny, p->nz, k, tab);
+        } else {
+            OSM_CUDA(cudaFuncSetAttribute(k_jacobi_fused<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_jacobi_fused<T, 3><<<grid, 256, smem, s>>>(e_in, e_out, rhs, p->code32, p->px, p->ny, p->nz, k, tab);
+        }
+    }
+    OSM_CUDA(cudaGetLastError());
     return OSMODI_OK;
 }
 
@@ -1907,7 +1922,8 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
     // 1. source and initial pressure
     SrcGeo sg{p->px, p->nx, p->ny, p->nz, p->n_dense, p->n_box, {p->k.F[0], p->k.F[1], p->k.F[2]}, {p->h[0], p->h[1], p->h[2]}};
     {
-#define OSM_SRC(ND, TG, TP) k_source<ND, TG, TP><<<one_wave(p, k_source<ND, TG, TP>, p->n_box), 256, 0, s>>>((const TG*)grad, (const TP*)pu, p->code8, b.b64, b.p64a, sg, b.sc, b.partials + kSlotMisc * kMaxBlocks)
+        const void* p_in = p->opt.zero_start ? nullptr : pu;
+#define OSM_SRC(ND, TG, TP) k_source<ND, TG, TP><<<one_wave(p, k_source<ND, TG, TP>, p->n_box), 256, 0, s>>>((const TG*)grad, (const TP*)p_in, p->code8, b.b64, b.p64a, sg, b.sc, b.partials + kSlotMisc * kMaxBlocks)
         if (p->ndim == 2) {
             if (gdt == OSMODI_F32 && pdt == OSMODI_F32) OSM_SRC(2, float, float);
             else if (gdt == OSMODI_F32) OSM_SRC(2, float, double);
@@ -1934,7 +1950,6 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
     bool zero_start = false;
     int steps = 0, outer_total = 0, residual_evals = 0;
     double* cur = b.p64a;
-    double* nxt = b.p64b;
     const int prec = p->opt.precision;
     const bool outer = p->opt.scheme == OSMODI_OUTER;
     T* rtarget = outer ? b.rc : b.r;
@@ -1943,7 +1958,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
         // S = 0: the answer is a constant on every component; P = 0 after the gauge
         k_fill_zero_f64<<<G, TH, 0, s>>>(cur, p->n_box);
         OSM_CUDA(cudaGetLastError());
-        OSM_TRY(launch_residual<T>(p, b, cur, nullptr, nullptr, rtarget, s, prof));
+        OSM_TRY(launch_residual<T>(p, b, cur, rtarget, s, prof));
         p->launches += 2;
         residual_evals++;
         OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
@@ -1955,7 +1970,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
             k_residual_zero_start<T><<<G, TH, 0, s>>>(b.b64, rtarget, p->n_chunks, b.sc);
             OSM_CUDA(cudaGetLastError());
         } else {
-            OSM_TRY(launch_residual<T>(p, b, cur, nullptr, nullptr, rtarget, s, prof));
+            OSM_TRY(launch_residual<T>(p, b, cur, rtarget, s, prof));
         }
         p->launches += 1;
         residual_evals++;
@@ -2045,23 +2060,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                         for (int sw = 0; sw < p->opt.inner_max;) {
                             T* e_next = (e_cur == b.x) ? b.e2 : b.x;
                             const int k = std::min(kf, p->opt.inner_max - sw);
-                            if (k == 1) {
-                                if (p->ndim == 2) k_jacobi<T, 2><<<G, TH, 0, s>>>(e_cur, e_next, b.rhs, p->code32, g, tab);
-                                else k_jacobi<T, 3><<<G, TH, 0, s>>>(e_cur, e_next, b.rhs, p->code32, g, tab);
-                            } else {
-                                const int tz = p->ndim == 3 ? 4 : 1, hz = p->ndim == 3 ? k : 0;
-                                const size_t cells = (size_t)(JTX + 2 * k) * (JTY + 2 * k) * (tz + 2 * hz);
-                                const size_t smem = cells * (3 * sizeof(T) + sizeof(uint32_t));
-                                dim3 grid((unsigned)((p->px + JTX - 1) / JTX), (unsigned)((p->ny + JTY - 1) / JTY),
-                                          (unsigned)((p->nz + tz - 1) / tz));
-                                if (p->ndim == 2) {
-                                    OSM_CUDA(cudaFuncSetAttribute(k_jacobi_fused<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                                    k_jacobi_fused<T, 2><<<grid, 256, smem, s>>>(e_cur, e_next, b.rhs, p->code32, p->px, p->ny, p->nz, k, tab);
-                                } else {
-                                    OSM_CUDA(cudaFuncSetAttribute(k_jacobi_fused<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                                    k_jacobi_fused<T, 3><<<grid, 256, smem, s>>>(e_cur, e_next, b.rhs, p->code32, p->px, p->ny, p->nz, k, tab);
-                                }
-                            }
+                            OSM_TRY(launch_jacobi_pass<T>(p, e_cur, e_next, b.rhs, k, s));
                             e_cur = e_next;
                             sw += k;
                             p->launches += 1;
@@ -2074,11 +2073,15 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                 }
                 if (e_cur != b.x) OSM_CUDA(cudaMemcpyAsync(b.x, e_cur, sizeof(T) * (size_t)p->n_box, cudaMemcpyDeviceToDevice, s));
             }
-            // p64 += e ; new FP64 residual
-            OSM_TRY(launch_residual<T>(p, b, cur, b.x, nxt, rtarget, s, prof));
-            p->launches += 1;
+            // p64 += e in place (pointwise), then the new FP64 residual of p64
+            // alone: adding e inside the stencil kernel repeated the FP64 add
+            // for every cell that loads a neighbour, and FP64 throughput, not
+            // memory, bounds that kernel
+            k_fold<T><<<one_wave(p, k_fold<T>, p->n_box), 256, 0, s>>>(cur, b.x, p->n_chunks);
+            OSM_CUDA(cudaGetLastError());
+            OSM_TRY(launch_residual<T>(p, b, cur, rtarget, s, prof));
+            p->launches += 2;
             residual_evals++;
-            std::swap(cur, nxt);
             OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
             const double eps_new = std::sqrt(hm->sc.rnorm2) / bnorm;
             steps++;
@@ -2101,10 +2104,12 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
     {
         if (pdt == OSMODI_F32)
             k_output<float><<<one_wave(p, k_output<float>, p->n_box), 256, 0, s>>>(cur, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0,
-                                               (float*)pu, p->px, p->nx, p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks);
+                                               (float*)pu, p->px, p->nx, p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks,
+                                               p->opt.zero_start);
         else
             k_output<double><<<one_wave(p, k_output<double>, p->n_box), 256, 0, s>>>(cur, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0,
-                                                (double*)pu, p->px, p->nx, p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks);
+                                                (double*)pu, p->px, p->nx, p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks,
+                                                p->opt.zero_start);
         OSM_CUDA(cudaGetLastError());
         p->launches += 1;
     }
@@ -2191,13 +2196,66 @@ void apply_tuned(osmodi_plan p) {
     char k[512];
     int ga, gb, fl;
     double ms;
-    while (std::fscanf(f, "%511s %d %d %d %lf", k, &ga, &gb, &fl, &ms) == 5)
+    const std::string jkey = key + "|jacobi";
+    while (std::fscanf(f, "%511s %d %d %d %lf", k, &ga, &gb, &fl, &ms) == 5) {
         if (key == k) set_geometry(p, ga, gb, fl);
+        if (jkey == k && ga >= 1 && ga <= 4) p->opt.sweeps_per_pass = ga;
+    }
     std::fclose(f);
+}
+
+// OUTER + Jacobi plans: the number of sweeps fused per pass (1..4), timed on
+// 24 sweeps of the plan's own operator (every k divides 24), cached under the
+// plan's key with the suffix "|jacobi"
+template <class T>
+static osmodi_status tune_sweeps(osmodi_plan p, void* ws, cudaStream_t s, const char* path, double* ms_out) {
+    Buffers<T> b;
+    carve<T>(p, ws, &b);
+    const int G = p->launch.blocks, TH = p->launch.threads;
+    k_fill_pattern<T><<<G, TH, 0, s>>>(b.rhs, p->code8, p->n_box);
+    OSM_CUDA(cudaMemsetAsync(b.x, 0, sizeof(T) * (size_t)p->n_box, s));
+    cudaEvent_t e0, e1;
+    OSM_CUDA(cudaEventCreate(&e0));
+    OSM_CUDA(cudaEventCreate(&e1));
+    double best = 1e300;
+    int pick = p->opt.sweeps_per_pass;
+    osmodi_status st = OSMODI_OK;
+    for (int k = 1; k <= 4 && st == OSMODI_OK; ++k) {
+        for (int rep = 0; rep < 2 && st == OSMODI_OK; ++rep) {  // the first repetition warms up
+            if ((st = launch_jacobi_pass<T>(p, b.x, b.e2, b.rhs, k, s)) != OSMODI_OK) break;
+            OSM_CUDA(cudaEventRecord(e0, s));
+            T* cur = b.e2;
+            T* nxt = b.x;
+            for (int sw = 0; sw < 24 && st == OSMODI_OK; sw += k) {
+                st = launch_jacobi_pass<T>(p, cur, nxt, b.rhs, k, s);
+                std::swap(cur, nxt);
+            }
+            OSM_CUDA(cudaEventRecord(e1, s));
+            OSM_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            OSM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep == 1 && ms / 24 < best) {
+                best = ms / 24;
+                pick = k;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != OSMODI_OK) return st;
+    p->opt.sweeps_per_pass = pick;
+    if (ms_out) *ms_out = best;
+    std::FILE* f = std::fopen(cache_file(path).c_str(), "a");
+    if (f) {
+        std::fprintf(f, "%s|jacobi %d 0 0 %.6f\n", cache_key(p).c_str(), pick, best);
+        std::fclose(f);
+    }
+    return OSMODI_OK;
 }
 
 template <class T>
 static osmodi_status tune_impl(osmodi_plan p, void* ws, cudaStream_t s, const char* path, double* ms_out) {
+    if (p->opt.scheme == OSMODI_OUTER && p->opt.inner == OSMODI_INNER_JACOBI) return tune_sweeps<T>(p, ws, s, path, ms_out);
     Buffers<T> b;
     carve<T>(p, ws, &b);
     int bps_a = 0, bps_b = 0;
@@ -2293,6 +2351,10 @@ extern "C" osmodi_status osmodi_solve(osmodi_plan p, const void* grad, int gdt, 
     int dev = -1;
     OSM_CUDA(cudaGetDevice(&dev));
     if (dev != p->device) return OSMODI_E_INVALID;
+    if (!user_buffer_ok(grad, dev) || !user_buffer_ok(pu, dev)) {
+        set_error_text("osmodi_solve: gradient and pressure must be device, managed or page-locked host memory");
+        return OSMODI_E_INVALID;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     osmodi_status st = p->opt.precision == OSMODI_FP64
                            ? solve_impl<double>(p, grad, gdt, pu, pdt, tol, max_iter, ws, s, res)

@@ -31,7 +31,7 @@ class osmodi_options(ctypes.Structure):
                 ("sweeps_per_pass", ctypes.c_int), ("max_refine", ctypes.c_int), ("record_history", ctypes.c_int),
                 ("threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("profile", ctypes.c_int),
                 ("slab", ctypes.c_int), ("flat_sweeps", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("accel", ctypes.c_int), ("precond", ctypes.c_int)]
+                ("accel", ctypes.c_int), ("precond", ctypes.c_int), ("zero_start", ctypes.c_int)]
 
 
 class osmodi_result(ctypes.Structure):
@@ -168,6 +168,14 @@ def _check_cuda(t: torch.Tensor, name: str):
         raise ValueError(f"{name} must be a contiguous CUDA tensor")
 
 
+def _check_solve_buffer(t: torch.Tensor, name: str):
+    """A contiguous CUDA tensor, or a contiguous page-locked host tensor (the
+    kernels then read / write it over the host link; osmodi_solve checks the
+    pointer as well)."""
+    if not t.is_contiguous() or not (t.is_cuda or (t.device.type == "cpu" and t.is_pinned())):
+        raise ValueError(f"{name} must be a contiguous CUDA tensor or a pinned host tensor")
+
+
 def default_options(**overrides) -> osmodi_options:
     o = osmodi_options()
     lib().osmodi_default_options(ctypes.byref(o))
@@ -238,9 +246,10 @@ class Plan:
 
     def solve(self, grad: torch.Tensor, p: torch.Tensor, tol: float, max_iter: int = 1 << 30, stream=None,
               check=True) -> osmodi_result:
-        """osmodi_solve: p holds P^0 on entry and the pressure on return."""
-        _check_cuda(grad, "grad")
-        _check_cuda(p, "p")
+        """osmodi_solve: p holds P^0 on entry and the pressure on return.
+        grad and p may be CUDA tensors or pinned host tensors."""
+        _check_solve_buffer(grad, "grad")
+        _check_solve_buffer(p, "p")
         res = osmodi_result()
         st = lib().osmodi_solve(self.handle, grad.data_ptr(), _dtype_code(grad), p.data_ptr(), _dtype_code(p),
                                 float(tol), int(min(max_iter, 2**31 - 1)), self._ws_ptr(), _stream_ptr(stream),

@@ -60,9 +60,9 @@ def blob_problem(n, seed, device="cuda", noise=0.03):
                                     dtype=torch.float32)
 
 
-def make_pairs(count, n, seed0=1000, tol=1e-8, device="cuda"):
+def make_pairs(count, n, seed0=1000, tol=1e-8, device="cuda", precond=1):
     """Gradient fields and their converged pressures (targets)."""
-    plan = osm.Plan(3, (n, n, n), (1.0, 1.0, 1.0), None, precision=osm.FP32_REFINE)
+    plan = osm.Plan(3, (n, n, n), (1.0, 1.0, 1.0), None, precision=osm.FP32_REFINE, precond=precond)
     pairs = []
     for i in range(count):
         prob = blob_problem(n, seed0 + i, device)
@@ -124,53 +124,82 @@ def seeded_solve(params, grad, n, tol, plan=None, net=None):
 
 
 def run_experiment(pairs=2000, train_n=128, epochs=4, lr=1e-3, batch=8, eval_n=256, eval_count=16, tol=1e-10,
-                   log=print):
+                   log=print, params=None):
     """The network-seeded workload: train on `pairs` method-solved fields at
-    train_n^3, then solve `eval_count` held-out fields at eval_n^3 to `tol`
-    from the network's guess and from zero.  Returns a result dict."""
-    t0 = time.perf_counter()
-    data = make_pairs(pairs, train_n, tol=1e-8)
-    torch.cuda.synchronize()
-    t_pairs = time.perf_counter() - t0
-    log(f"{pairs} training pairs at {train_n}^3 solved in {t_pairs:.1f} s")
-    t1 = time.perf_counter()
-    params, hist = train(data, train_n, epochs=epochs, lr=lr, batch=batch, log=log)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t1
-    del data
-    torch.cuda.empty_cache()
-    plan = osm.Plan(3, (eval_n,) * 3, (1.0, 1.0, 1.0), None, precision=osm.FP32_REFINE)
+    train_n^3 (or take trained `params`), then solve `eval_count` held-out
+    fields at eval_n^3 to `tol` from the network's guess and from zero, with
+    the plain CG and with the multigrid-preconditioned CG.  Returns a result
+    dict (and the parameters under "params")."""
+    t_pairs = t_train = 0.0
+    hist = []
+    if params is None:
+        t0 = time.perf_counter()
+        data = make_pairs(pairs, train_n, tol=1e-8)
+        torch.cuda.synchronize()
+        t_pairs = time.perf_counter() - t0
+        log(f"{pairs} training pairs at {train_n}^3 solved in {t_pairs:.1f} s")
+        t1 = time.perf_counter()
+        params, hist = train(data, train_n, epochs=epochs, lr=lr, batch=batch, log=log)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t1
+        del data
+        torch.cuda.empty_cache()
+    plans = {"cg": osm.Plan(3, (eval_n,) * 3, (1.0, 1.0, 1.0), None, precision=osm.FP32_REFINE),
+             "mg": osm.Plan(3, (eval_n,) * 3, (1.0, 1.0, 1.0), None, precision=osm.FP32_REFINE, precond=1)}
+    # the plain FP64 solve (every vector and operation in FP64, same
+    # preconditioned scheme, zero start): the time-to-tolerance reference
+    plan64 = osm.Plan(3, (eval_n,) * 3, (1.0, 1.0, 1.0), None, precision=osm.FP64, precond=1)
     net = osm.Net((eval_n,) * 3, train=False)
     net.set_params(params)
     rows = []
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     for i in range(eval_count):
         prob = blob_problem(eval_n, 50000 + i)
-        p = torch.empty((eval_n,) * 3, dtype=torch.float64, device="cuda")
-        plan.solve(prob.grad, torch.zeros_like(p), tol)  # warm (graph capture)
+        row = dict(field=i)
+        for name, plan in plans.items():
+            p = torch.empty((eval_n,) * 3, dtype=torch.float64, device="cuda")
+            plan.solve(prob.grad, torch.zeros_like(p), tol)  # warm (graph capture)
+            ev[0].record()
+            net.forward(prob.grad, None, 1.0, p)
+            ev[1].record()
+            r_seed = plan.solve(prob.grad, p, tol)
+            ev[2].record()
+            p0 = torch.zeros_like(p)
+            r_zero = plan.solve(prob.grad, p0, tol)
+            ev[3].record()
+            torch.cuda.synchronize()
+            row.update({f"{name}_seed_rel_dist": r_seed.seed_rel_dist, f"{name}_it_seeded": r_seed.inner_iters,
+                        f"{name}_it_zero": r_zero.inner_iters, "ms_net": ev[0].elapsed_time(ev[1]),
+                        f"{name}_ms_seeded_solve": ev[1].elapsed_time(ev[2]),
+                        f"{name}_ms_zero_solve": ev[2].elapsed_time(ev[3]),
+                        f"{name}_ok": r_seed.status == osm.OK and r_zero.status == osm.OK})
+        p64 = torch.zeros((eval_n,) * 3, dtype=torch.float64, device="cuda")
+        plan64.solve(prob.grad, p64, tol)  # warm
+        p64.zero_()
         ev[0].record()
-        net.forward(prob.grad, None, 1.0, p)
+        r64 = plan64.solve(prob.grad, p64, tol)
         ev[1].record()
-        r_seed = plan.solve(prob.grad, p, tol)
-        ev[2].record()
-        p0 = torch.zeros_like(p)
-        r_zero = plan.solve(prob.grad, p0, tol)
-        ev[3].record()
         torch.cuda.synchronize()
-        rows.append(dict(field=i, seed_rel_dist=r_seed.seed_rel_dist, cg_seeded=r_seed.inner_iters,
-                         cg_zero=r_zero.inner_iters, ms_net=ev[0].elapsed_time(ev[1]),
-                         ms_seeded_solve=ev[1].elapsed_time(ev[2]), ms_zero_solve=ev[2].elapsed_time(ev[3]),
-                         eps_seeded=r_seed.eps_R, eps_zero=r_zero.eps_R,
-                         ok=r_seed.status == osm.OK and r_zero.status == osm.OK))
+        row.update({"fp64_it_zero": r64.inner_iters, "fp64_ms_zero_solve": ev[0].elapsed_time(ev[1]),
+                    "fp64_ok": r64.status == osm.OK})
+        rows.append(row)
         log(str(rows[-1]))
-    plan.close()
+    plan64.close()
+    for plan in plans.values():
+        plan.close()
     net.close()
     mean = lambda k: float(np.mean([r[k] for r in rows]))
-    return dict(pairs=pairs, train_n=train_n, epochs=epochs, lr=lr, batch=batch, eval_n=eval_n, eval_count=eval_count,
-                tol=tol, seconds_pairs=t_pairs, seconds_train=t_train, loss_history=hist,
-                mean_seed_rel_dist=mean("seed_rel_dist"), mean_cg_seeded=mean("cg_seeded"),
-                mean_cg_zero=mean("cg_zero"), mean_ms_seeded_total=mean("ms_net") + mean("ms_seeded_solve"),
-                mean_ms_zero=mean("ms_zero_solve"), all_converged=all(r["ok"] for r in rows), fields=rows)
+    out = dict(pairs=pairs, train_n=train_n, epochs=epochs, lr=lr, batch=batch, eval_n=eval_n, eval_count=eval_count,
+               tol=tol, seconds_pairs=t_pairs, seconds_train=t_train, loss_history=hist, ms_net=mean("ms_net"),
+               all_converged=all(r["cg_ok"] and r["mg_ok"] and r["fp64_ok"] for r in rows), fields=rows,
+               fp64=dict(mean_it_zero=mean("fp64_it_zero"), mean_ms_zero=mean("fp64_ms_zero_solve")))
+    for name in plans:
+        out[name] = dict(mean_seed_rel_dist=mean(f"{name}_seed_rel_dist"), mean_it_seeded=mean(f"{name}_it_seeded"),
+                         mean_it_zero=mean(f"{name}_it_zero"),
+                         mean_ms_seeded_total=mean("ms_net") + mean(f"{name}_ms_seeded_solve"),
+                         mean_ms_zero=mean(f"{name}_ms_zero_solve"))
+    out["params"] = [float(v) for v in np.asarray(params, dtype=np.float32)]
+    return out
 
 
 if __name__ == "__main__":
@@ -187,13 +216,18 @@ if __name__ == "__main__":
     ap.add_argument("--eval-count", type=int, default=16)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--params", default=None, help="JSON written by an earlier run: reuse its trained parameters")
     a = ap.parse_args()
     from . import build
 
     build.build()
-    res = run_experiment(a.pairs, a.train_n, a.epochs, a.lr, a.batch, a.eval_n, a.eval_count, a.tol)
+    params = None
+    if a.params:
+        with open(a.params) as fh:
+            params = np.asarray(json.load(fh)["params"], dtype=np.float32)
+    res = run_experiment(a.pairs, a.train_n, a.epochs, a.lr, a.batch, a.eval_n, a.eval_count, a.tol, params=params)
     txt = json.dumps(res)
-    print(txt)
+    print(json.dumps({k: v for k, v in res.items() if k not in ("fields", "params")}))
     if a.out:
         with open(a.out, "w") as fh:
             fh.write(txt + "\n")

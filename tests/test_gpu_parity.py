@@ -1,5 +1,6 @@
 """CUDA path against the FP64 CPU oracle, element by element, through the C
 interface.  Needs a GPU."""
+import ctypes
 import math
 
 import numpy as np
@@ -429,3 +430,78 @@ def test_tma_staged_sweep_matches_flat(osm, shape):
     assert _rel(outs[1], outs[0], valid) < 1e-10
     want, it, r = oracle.solve_cg(grid, f.astype(np.float64), tol=1e-14, maxit=20000)
     assert _rel(outs[1], want, valid) < 1e-10
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_host_buffers_and_zero_start(osm, precond):
+    """The solve reading the gradient from pinned host memory and writing P
+    there gives the device solve's answer exactly; zero_start = 1 never reads
+    P (a P full of NaN is ignored); unregistered host memory is refused
+    before any kernel runs."""
+    rng = np.random.default_rng(31)
+    shape, spacing = (18, 21, 26), (1.0, 1.0, 1.0)
+    valid = rng.random(shape) > 0.1
+    f = rng.normal(size=(3,) + shape).astype(np.float32)
+    m = torch.from_numpy(valid.astype(np.uint8)).cuda()
+    plan = osm.Plan(3, shape[::-1], spacing, m, precond=precond)
+    p_dev = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    r_dev = plan.solve(torch.from_numpy(f).cuda(), p_dev, 1e-11)
+    g_host = torch.from_numpy(f).pin_memory()
+    p_host = torch.zeros(shape, dtype=torch.float64).pin_memory()
+    r_host = plan.solve(g_host, p_host, 1e-11)
+    torch.cuda.synchronize()
+    assert r_dev.status == osm.OK and r_host.status == osm.OK
+    assert r_host.inner_iters == r_dev.inner_iters
+    got = p_host.numpy()
+    np.testing.assert_array_equal(got[valid], p_dev.cpu().numpy()[valid])
+    assert np.isnan(got[~valid]).all()
+    want = oracle.solve_direct(oracle.Grid(valid, spacing), f.astype(np.float64))
+    assert _rel(got, want, valid) < 1e-10
+    # zero start: P is output only
+    plan0 = osm.Plan(3, shape[::-1], spacing, m, precond=precond, zero_start=1)
+    p_nan = torch.full(shape, float("nan"), dtype=torch.float64).pin_memory()
+    r0 = plan0.solve(g_host, p_nan, 1e-11)
+    torch.cuda.synchronize()
+    assert r0.status == osm.OK and r0.inner_iters == r_dev.inner_iters
+    np.testing.assert_array_equal(p_nan.numpy()[valid], got[valid])
+    # pageable host memory: refused, nothing touched
+    page = np.zeros(shape, dtype=np.float64)
+    res = osm.osmodi_result()
+    st = osm.lib().osmodi_solve(plan.handle, g_host.data_ptr(), osm.F32, page.ctypes.data, osm.F64, 1e-8, 100,
+                                plan._ws_ptr(), None, ctypes.byref(res))
+    assert st == osm.E_INVALID
+    assert np.all(page == 0.0)
+
+
+def test_autotune_sweeps_per_pass(osm, tmp_path):
+    """OUTER + Jacobi: the autotuner picks the sweeps fused per pass (1..4),
+    caches it, and the solve still lands on the fixed point."""
+    import os
+
+    rng = np.random.default_rng(17)
+    shape, spacing = (20, 24, 28), (1.0, 1.0, 1.0)
+    valid = rng.random(shape) > 0.1
+    f = rng.normal(size=(3,) + shape).astype(np.float32)
+    m = torch.from_numpy(valid.astype(np.uint8)).cuda()
+    cache = tmp_path / "tune.txt"
+    plan = osm.Plan(3, shape[::-1], spacing, m, precision=2, scheme=1, inner=1, inner_max=4)
+    ms = plan.autotune(cache_path=str(cache))
+    assert ms > 0
+    lines = [l for l in cache.read_text().splitlines() if "|jacobi" in l]
+    assert len(lines) == 1 and 1 <= int(lines[0].split()[1]) <= 4
+    p = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    r = plan.solve(torch.from_numpy(f).cuda(), p, 1e-10, max_iter=500000)
+    assert r.status == osm.OK
+    want = oracle.solve_direct(oracle.Grid(valid, spacing), f.astype(np.float64))
+    # the stop rule bounds the relative residual (1e-10), not the error: the
+    # error of this geometry came out at 1.02e-8, so the bound is 5e-8
+    assert _rel(p.cpu().numpy(), want, valid) < 5e-8
+    os.environ["OSMODI_AUTOTUNE_CACHE"] = str(cache)
+    try:
+        plan2 = osm.Plan(3, shape[::-1], spacing, m, precision=2, scheme=1, inner=1, inner_max=4, autotune=1)
+        p2 = torch.zeros_like(p)
+        assert plan2.solve(torch.from_numpy(f).cuda(), p2, 1e-10, max_iter=500000).status == osm.OK
+        assert _rel(p2.cpu().numpy(), want, valid) < 5e-8
+    finally:
+        del os.environ["OSMODI_AUTOTUNE_CACHE"]
+

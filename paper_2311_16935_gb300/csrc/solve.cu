@@ -32,6 +32,7 @@
 #include <cuda.h>
 
 #include "cg_state.cuh"
+#include "ff.cuh"
 #include "internal.cuh"
 #include "mg.cuh"
 #include "stencil.cuh"
@@ -39,6 +40,8 @@
 namespace osm {
 
 enum { OP_L = 0, OP_M = 1 };
+// smallest tolerance the float-float refinement is used for
+constexpr double kFFMinTol = 1e-9;
 // reduction partials: one range of kMaxBlocks doubles per slot
 enum { kSlotA = 0, kSlotB = 1, kSlotRes = 2 /* 3 slots */, kSlotMisc = 5 /* 3 slots */, kPartialSlots = 8 };
 
@@ -223,6 +226,273 @@ __global__ void __launch_bounds__(256) k_fold(double* __restrict__ p64, const TI
 #pragma unroll
         for (int m = 0; m < 4; ++m) pv.v[m] += (double)ev.v[m];
         st4(p64 + ch * 4, pv);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The refinement loop of the FP32 precisions in float-float arithmetic (see
+// ff.cuh): the iterate P and the source b are pairs of FP32 arrays, hi at
+// [0, n_box) and lo at [n_box, 2 n_box) of the same 8 bytes per cell that an
+// FP64 array takes.  Same arithmetic as the FP64 kernels above, carried to
+// about 48 bits; the FP64 precision keeps the FP64 kernels.
+// ---------------------------------------------------------------------------
+struct SrcGeoFF {
+    int64_t px, nx, ny, nz, n_dense, n_box;
+    FF coef[3];  // -h_a F_a / 2 (the face coefficient of Eq. ExplicitEqn's sum)
+};
+
+// b = A_tot S and P^0 as pairs; norms and sums as k_source
+template <int NDIM, class TG, class TP>
+__global__ void k_source_ff(const TG* __restrict__ f, const TP* __restrict__ p_in, const uint8_t* __restrict__ code8,
+                            float* __restrict__ bh, float* __restrict__ ph, SrcGeoFF g, Scalars* sc,
+                            double* partials) {
+    float* bl = bh + g.n_box;
+    float* pl = ph + g.n_box;
+    FFAcc a_b2, a_p0, a_b;
+    unsigned n_p0 = 0;
+    int bad = 0;
+    const int64_t sd[3] = {1, g.nx, g.nx * g.ny};
+    const bool i32 = g.n_box < (int64_t)(1u << 31);
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < g.n_box; idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t row, i;
+        if (i32) {
+            const uint32_t r32 = (uint32_t)idx / (uint32_t)g.px;
+            row = r32;
+            i = (uint32_t)idx - r32 * (uint32_t)g.px;
+        } else {
+            row = idx / g.px;
+            i = idx - row * g.px;
+        }
+        const unsigned cw = code8[idx];
+        if (i >= g.nx || !(cw & 0x80u)) {
+            bh[idx] = 0.f;
+            bl[idx] = 0.f;
+            ph[idx] = 0.f;
+            pl[idx] = 0.f;
+            continue;
+        }
+        const int64_t d = row * g.nx + i;
+        FF s{0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const unsigned bp = (cw >> (2 * a)) & 1u, bm = (cw >> (2 * a + 1)) & 1u;
+            if (!(bp | bm)) continue;
+            const TG* fa = f + a * g.n_dense + d;
+            FF t;
+            if constexpr (sizeof(TG) == 4) {
+                // the sum or difference of two FP32 values is exact as a pair
+                if (bp & bm) t = ff_sum2(fa[sd[a]], -fa[-sd[a]]);
+                else if (bp) t = ff_sum2(fa[sd[a]], fa[0]);
+                else t = ff_sum2(-fa[-sd[a]], -fa[0]);
+            } else {
+                double td;
+                if (bp & bm) td = (double)fa[sd[a]] - (double)fa[-sd[a]];
+                else if (bp) td = (double)fa[sd[a]] + (double)fa[0];
+                else td = -((double)fa[-sd[a]] + (double)fa[0]);
+                t = ff_from_double(td);
+            }
+            s = ff_add(s, ff_mul(g.coef[a], t));
+        }
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a)
+            if (!isfinite(f[a * g.n_dense + d])) bad |= 1;  // in the input's own precision
+        FF p0{0.f, 0.f};
+        if (p_in) {
+            const TP v = p_in[d];
+            if (!isfinite(v)) bad |= 2;
+            if constexpr (sizeof(TP) == 4) p0 = FF{v, 0.f};
+            else p0 = ff_from_double(v);
+        }
+        bh[idx] = s.hi;
+        bl[idx] = s.lo;
+        ph[idx] = p0.hi;
+        pl[idx] = p0.lo;
+        a_b2.add(s.hi * s.hi);
+        a_p0.add(p0.hi);
+        a_p0.add(p0.lo);
+        a_b.add(s.hi);
+        a_b.add(s.lo);
+        n_p0 += p0.hi != 0.f ? 1u : 0u;
+    }
+    if (bad) atomicOr(&sc->nan_flag, bad);
+    double acc[4] = {a_b2.value(), a_p0.value(), a_b.value(), (double)n_p0};
+    double tot[4];
+    if (grid_sum<4>(acc, partials, &sc->t_src, tot) && threadIdx.x == 0) {
+        sc->bnorm2 = tot[0];
+        sc->p0sum = tot[1];
+        sc->bsum = tot[2];
+        sc->p0nz = tot[3];
+    }
+}
+
+// zero initial pressure: r = b rounded to FP32; the residual norms are b's
+__global__ void __launch_bounds__(256) k_residual_zero_start_ff(const float* __restrict__ bh, float* __restrict__ r_out,
+                                                                int64_t n_chunks, int64_t n_box, Scalars* sc) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->rnorm2 = sc->bnorm2;
+        sc->rsum = sc->bsum;
+        sc->psum = 0.0;
+    }
+    const float* bl = bh + n_box;
+    for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < n_chunks; ch += (int64_t)gridDim.x * blockDim.x) {
+        const V4<float> h = ld4(bh + ch * 4), l = ld4(bl + ch * 4);
+        V4<float> rv;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) rv.v[m] = __fadd_rn(h.v[m], l.v[m]);
+        st4(r_out + ch * 4, rv);
+    }
+}
+
+struct GeoFF {
+    int64_t px, plane, n_chunks, n_box;
+    FF F[3];
+};
+
+// r = b - L p as pairs, rounded to FP32 for the inner solve; (L p)_C =
+// sum_a F_a sum_{valid faces on axis a} (p_C - p_n), every difference formed
+// exactly from the pairs.  Reductions ||r||^2, sum r (of the FP32 r the inner
+// solve sees) and sum p.
+template <int NDIM>
+__global__ void __launch_bounds__(256) k_residual_ff(const float* __restrict__ ph, const float* __restrict__ bh,
+                                                     float* __restrict__ r_out, const uint8_t* __restrict__ code8,
+                                                     GeoFF g, Scalars* sc, double* partials) {
+    const float* pl = ph + g.n_box;
+    const float* bl = bh + g.n_box;
+    ChunkLoop L;
+    FFAcc a_r2, a_r, a_p;
+    for (int64_t base = L.base; base < g.n_chunks; base += L.stride) {
+        const int64_t ch = base + L.lane;
+        const bool act = ch < g.n_chunks;
+        const int64_t i0 = ch * 4;
+        const uint32_t cw = act ? *reinterpret_cast<const uint32_t*>(code8 + i0) : 0u;
+        const V4<float> ch4 = act ? ld4(ph + i0) : zero4<float>();
+        const V4<float> cl4 = act ? ld4(pl + i0) : zero4<float>();
+        unsigned fm[4], any = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            fm[m] = face_bits8(cw, m);
+            any |= fm[m];
+        }
+        auto h4 = [&](int64_t off) { return ld4(ph + i0 + off); };
+        auto h1 = [&](int64_t off) { return ph[i0 + off]; };
+        auto l4 = [&](int64_t off) { return ld4(pl + i0 + off); };
+        auto l1 = [&](int64_t off) { return pl[i0 + off]; };
+        const Nbrs<float> nh = gather<float, NDIM>(ch4, any, fm[0] & 2u, fm[3] & 1u, L.lane, g.px, g.plane, h4, h1);
+        const Nbrs<float> nl = gather<float, NDIM>(cl4, any, fm[0] & 2u, fm[3] & 1u, L.lane, g.px, g.plane, l4, l1);
+        if (act) {
+            const V4<float> b_h = ld4(bh + i0), b_l = ld4(bl + i0);
+            V4<float> rv;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const unsigned f = fm[m];
+                const FF c{ch4.v[m], cl4.v[m]};
+                auto dif = [&](unsigned bit, float nhv, float nlv) {
+                    return (f & bit) ? ff_diff(c, FF{nhv, nlv}) : FF{0.f, 0.f};
+                };
+                const FF sx = ff_add(dif(1u, nh.e.v[m], nl.e.v[m]), dif(2u, nh.w.v[m], nl.w.v[m]));
+                const FF sy = ff_add(dif(4u, nh.n.v[m], nl.n.v[m]), dif(8u, nh.s.v[m], nl.s.v[m]));
+                FF lp = ff_add(ff_mul(g.F[0], sx), ff_mul(g.F[1], sy));
+                if (NDIM == 3) {
+                    const FF sz = ff_add(dif(16u, nh.f.v[m], nl.f.v[m]), dif(32u, nh.b.v[m], nl.b.v[m]));
+                    lp = ff_add(lp, ff_mul(g.F[2], sz));
+                }
+                const FF r = ff_add(FF{b_h.v[m], b_l.v[m]}, FF{-lp.hi, -lp.lo});
+                const float rf = __fadd_rn(r.hi, r.lo);
+                rv.v[m] = rf;
+                a_r2.add(rf * rf);
+                a_r.add(rf);
+                a_p.add(c.hi);
+                a_p.add(c.lo);
+            }
+            st4(r_out + i0, rv);
+        }
+    }
+    double acc[3] = {a_r2.value(), a_r.value(), a_p.value()};
+    double tot[3];
+    if (grid_sum<3>(acc, partials, &sc->t_res, tot) && threadIdx.x == 0) {
+        sc->rnorm2 = tot[0];
+        sc->rsum = tot[1];
+        sc->psum = tot[2];
+    }
+}
+
+// p += e for the pair iterate, in place (e = 0 outside the valid set)
+__global__ void __launch_bounds__(256) k_fold_ff(float* __restrict__ ph, const float* __restrict__ e, int64_t n_chunks,
+                                                 int64_t n_box) {
+    float* pl = ph + n_box;
+    for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < n_chunks; ch += (int64_t)gridDim.x * blockDim.x) {
+        V4<float> h = ld4c(ph + ch * 4), l = ld4c(pl + ch * 4);
+        const V4<float> ev = ld4(e + ch * 4);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            float s, t;
+            two_sum(h.v[m], ev.v[m], s, t);
+            t = __fadd_rn(t, l.v[m]);
+            fast_two_sum(s, t, h.v[m], l.v[m]);
+        }
+        st4(ph + ch * 4, h);
+        st4(pl + ch * 4, l);
+    }
+}
+
+// output of the pair iterate: as k_output (P = hi + lo - mean, exact in FP64)
+template <class TP>
+__global__ void k_output_ff(const float* __restrict__ ph, const uint8_t* __restrict__ code8,
+                            const int32_t* __restrict__ label, const double* __restrict__ comp_p,
+                            const double* __restrict__ comp_p0, const double* __restrict__ comp_cnt, int multi,
+                            TP* __restrict__ p_user, int64_t px, int64_t nx, int64_t n_box, Scalars* sc,
+                            double* partials, int zero0) {
+    const float* pl = ph + n_box;
+    const double m1 = multi ? 0.0 : sc->psum / comp_cnt[0];
+    const double m01 = multi ? 0.0 : sc->p0sum / comp_cnt[0];
+    FFAcc a_d, a_v;
+    const bool i32 = n_box < (int64_t)(1u << 31);
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n_box; idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t row, i;
+        if (i32) {
+            const uint32_t r32 = (uint32_t)idx / (uint32_t)px;
+            row = r32;
+            i = (uint32_t)idx - r32 * (uint32_t)px;
+        } else {
+            row = idx / px;
+            i = idx - row * px;
+        }
+        if (i >= nx) continue;
+        const int64_t d = row * nx + i;
+        if (!(code8[idx] & 0x80u)) {
+            p_user[d] = (TP)NAN;
+            continue;
+        }
+        double m = m1, m0 = m01;
+        if (multi) {
+            const int32_t l = label[idx];
+            m = comp_p[l] / comp_cnt[l];
+            m0 = comp_p0[l] / comp_cnt[l];
+        }
+        const double v = ((double)ph[idx] - m) + (double)pl[idx];
+        // the seed distance is a reported statistic: FP32 terms suffice
+        const float dv = zero0 ? -(float)v : (float)(((double)p_user[d] - m0) - v);
+        a_d.add(dv * dv);
+        a_v.add((float)v * (float)v);
+        p_user[d] = (TP)v;
+    }
+    double acc[2] = {a_d.value(), a_v.value()};
+    double tot[2];
+    if (grid_sum<2>(acc, partials, &sc->t_out, tot) && threadIdx.x == 0) {
+        sc->dist2 = tot[0];
+        sc->pnorm2 = tot[1];
+    }
+}
+
+// per-component sums of the pair iterate
+__global__ void k_comp_sums_ff(const float* __restrict__ ph, const int32_t* __restrict__ label, int64_t n_box,
+                               double* sums) {
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n_box; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t l = label[idx];
+        if (l >= 0) {
+            const double x = (double)ph[idx] + (double)ph[n_box + idx];
+            if (x != 0.0) atomicAdd(&sums[l], x);
+        }
     }
 }
 
@@ -1704,17 +1974,57 @@ static osmodi_status run_cg(osmodi_plan p, const Buffers<T>& b, int op, void* ws
     return hm->st.err ? OSMODI_E_TIMEOUT : OSMODI_OK;
 }
 
+// One wave of resident 256-thread blocks of a grid-stride kernel: a grid of
+// more blocks than fit at once runs a partial last wave on few SMs.
+template <class K>
+static int one_wave(osmodi_plan p, K kernel, int64_t n_items) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 256, 0) != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n_items + 255) / 256, (int64_t)p->num_sms * b));
+}
+
+// the iterate and the source of the FP32 precisions as float-float pairs
+// (hi half, lo half of the FP64-sized buffers)
+static GeoFF geo_ff(osmodi_plan p) {
+    GeoFF g{};
+    g.px = p->px;
+    g.plane = p->px * p->ny;
+    g.n_chunks = p->n_chunks;
+    g.n_box = p->n_box;
+    for (int a = 0; a < 3; ++a) g.F[a] = ff_from_double(p->k.F[a]);
+    return g;
+}
+
+// residual of the refinement loop: float-float for the FP32 precisions, FP64
+// for the FP64 precision
 template <class T>
 static osmodi_status launch_residual(osmodi_plan p, const Buffers<T>& b, const double* p_in, T* r_out, cudaStream_t s,
-                                     bool prof) {
+                                     bool prof, bool ff) {
     const int G = p->launch.blocks, TH = p->launch.threads;
     if (prof) {
         OSM_TRY(ensure_events(p, 2));
         OSM_CUDA(cudaEventRecord(p->events[0], s));
     }
-    const Geo<double> g = geo<double>(p);
-    if (p->ndim == 2) k_residual<T, 2><<<G, TH, 0, s>>>(p_in, b.b64, r_out, p->code8, g, b.sc, b.partials + kSlotRes * kMaxBlocks);
-    else k_residual<T, 3><<<G, TH, 0, s>>>(p_in, b.b64, r_out, p->code8, g, b.sc, b.partials + kSlotRes * kMaxBlocks);
+    if (ff) {
+        const GeoFF gf = geo_ff(p);
+        const float* ph = reinterpret_cast<const float*>(p_in);
+        const float* bh = reinterpret_cast<const float*>(b.b64);
+        float* r = reinterpret_cast<float*>(r_out);  // ff is only chosen for FP32 vectors
+        double* part = b.partials + kSlotRes * kMaxBlocks;
+        if (p->ndim == 2)
+            k_residual_ff<2><<<one_wave(p, k_residual_ff<2>, p->n_chunks), 256, 0, s>>>(ph, bh, r, p->code8, gf,
+                                                                                       b.sc, part);
+        else
+            k_residual_ff<3><<<one_wave(p, k_residual_ff<3>, p->n_chunks), 256, 0, s>>>(ph, bh, r, p->code8, gf,
+                                                                                       b.sc, part);
+    } else {
+        const Geo<double> g = geo<double>(p);
+        if (p->ndim == 2) k_residual<T, 2><<<G, TH, 0, s>>>(p_in, b.b64, r_out, p->code8, g, b.sc, b.partials + kSlotRes * kMaxBlocks);
+        else k_residual<T, 3><<<G, TH, 0, s>>>(p_in, b.b64, r_out, p->code8, g, b.sc, b.partials + kSlotRes * kMaxBlocks);
+    }
     OSM_CUDA(cudaGetLastError());
     if (prof) {
         OSM_CUDA(cudaEventRecord(p->events[1], s));
@@ -1737,16 +2047,19 @@ static osmodi_status comp_sums(osmodi_plan p, const T* v, double* sums, cudaStre
     return OSMODI_OK;
 }
 
-// One wave of resident 256-thread blocks of a grid-stride kernel: a grid of
-// more blocks than fit at once runs a partial last wave on few SMs.
-template <class K>
-static int one_wave(osmodi_plan p, K kernel, int64_t n_items) {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 256, 0) != cudaSuccess || b < 1) {
-        cudaGetLastError();
-        b = 1;
+// per-component sums of the iterate (float-float pairs for the FP32
+// precisions, FP64 otherwise)
+static osmodi_status comp_sums_iterate(osmodi_plan p, const double* it, double* sums, cudaStream_t s, bool ff) {
+    if (ff) {
+        OSM_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * (size_t)p->n_comp, s));
+        const int G = std::min<int64_t>((p->n_box + 255) / 256, (int64_t)p->num_sms * 8);
+        k_comp_sums_ff<<<G, 256, 0, s>>>(reinterpret_cast<const float*>(it), p->label, p->n_box, sums);
+        OSM_CUDA(cudaGetLastError());
+        p->launches += 1;
+        return OSMODI_OK;
+    } else {
+        return comp_sums<double>(p, it, sums, s);
     }
-    return (int)std::max<int64_t>(1, std::min<int64_t>((n_items + 255) / 256, (int64_t)p->num_sms * b));
 }
 
 static osmodi_status read_mirror(void* dst, const void* src, size_t n, cudaStream_t s) {
@@ -1921,9 +2234,28 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
 
     // 1. source and initial pressure
     SrcGeo sg{p->px, p->nx, p->ny, p->nz, p->n_dense, p->n_box, {p->k.F[0], p->k.F[1], p->k.F[2]}, {p->h[0], p->h[1], p->h[2]}};
+    // float-float refinement for the FP32 precisions down to kFFMinTol (its
+    // residual floor, a few 2^-48 of |F p| against |b|, stays far below that);
+    // tighter tolerances and the FP64 precision refine in FP64
+    const bool ff = sizeof(T) == 4 && tol >= kFFMinTol;
     {
         const void* p_in = p->opt.zero_start ? nullptr : pu;
-#define OSM_SRC(ND, TG, TP) k_source<ND, TG, TP><<<one_wave(p, k_source<ND, TG, TP>, p->n_box), 256, 0, s>>>((const TG*)grad, (const TP*)p_in, p->code8, b.b64, b.p64a, sg, b.sc, b.partials + kSlotMisc * kMaxBlocks)
+        SrcGeoFF sgf{p->px, p->nx, p->ny, p->nz, p->n_dense, p->n_box, {}};
+        for (int a = 0; a < 3; ++a) sgf.coef[a] = ff_from_double(-0.5 * p->h[a] * p->k.F[a]);
+        float* bh = reinterpret_cast<float*>(b.b64);
+        float* ph = reinterpret_cast<float*>(b.p64a);
+        (void)bh;
+        (void)ph;
+#define OSM_SRC(ND, TG, TP)                                                                                             \
+    do {                                                                                                                \
+        if (ff)                                                                                                         \
+            k_source_ff<ND, TG, TP><<<one_wave(p, k_source_ff<ND, TG, TP>, p->n_box), 256, 0, s>>>(                     \
+                (const TG*)grad, (const TP*)p_in, p->code8, bh, ph, sgf, b.sc, b.partials + kSlotMisc * kMaxBlocks);    \
+        else                                                                                                            \
+            k_source<ND, TG, TP><<<one_wave(p, k_source<ND, TG, TP>, p->n_box), 256, 0, s>>>(                           \
+                (const TG*)grad, (const TP*)p_in, p->code8, b.b64, b.p64a, sg, b.sc,                                    \
+                b.partials + kSlotMisc * kMaxBlocks);                                                                   \
+    } while (0)
         if (p->ndim == 2) {
             if (gdt == OSMODI_F32 && pdt == OSMODI_F32) OSM_SRC(2, float, float);
             else if (gdt == OSMODI_F32) OSM_SRC(2, float, double);
@@ -1942,7 +2274,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
     OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
     if (hm->sc.nan_flag) return OSMODI_E_NAN_INPUT;
     const double bnorm = std::sqrt(hm->sc.bnorm2);
-    if (multi) OSM_TRY(comp_sums<double>(p, b.p64a, comp_p0, s));
+    if (multi) OSM_TRY(comp_sums_iterate(p, b.p64a, comp_p0, s, ff));
 
     osmodi_status status = OSMODI_OK;
     double eps = 0.0, eps_p = 0.0;
@@ -1958,7 +2290,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
         // S = 0: the answer is a constant on every component; P = 0 after the gauge
         k_fill_zero_f64<<<G, TH, 0, s>>>(cur, p->n_box);
         OSM_CUDA(cudaGetLastError());
-        OSM_TRY(launch_residual<T>(p, b, cur, rtarget, s, prof));
+        OSM_TRY(launch_residual<T>(p, b, cur, rtarget, s, prof, ff));
         p->launches += 2;
         residual_evals++;
         OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
@@ -1967,10 +2299,15 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
         zero_start = hm->sc.p0nz == 0.0;
         if (zero_start) {
             // zero initial pressure: the residual is b
-            k_residual_zero_start<T><<<G, TH, 0, s>>>(b.b64, rtarget, p->n_chunks, b.sc);
+            if (ff)
+                k_residual_zero_start_ff<<<one_wave(p, k_residual_zero_start_ff, p->n_chunks), 256, 0, s>>>(
+                    reinterpret_cast<const float*>(b.b64), reinterpret_cast<float*>(rtarget), p->n_chunks, p->n_box,
+                    b.sc);
+            else
+                k_residual_zero_start<T><<<G, TH, 0, s>>>(b.b64, rtarget, p->n_chunks, b.sc);
             OSM_CUDA(cudaGetLastError());
         } else {
-            OSM_TRY(launch_residual<T>(p, b, cur, rtarget, s, prof));
+            OSM_TRY(launch_residual<T>(p, b, cur, rtarget, s, prof, ff));
         }
         p->launches += 1;
         residual_evals++;
@@ -2077,9 +2414,13 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
             // alone: adding e inside the stencil kernel repeated the FP64 add
             // for every cell that loads a neighbour, and FP64 throughput, not
             // memory, bounds that kernel
-            k_fold<T><<<one_wave(p, k_fold<T>, p->n_box), 256, 0, s>>>(cur, b.x, p->n_chunks);
+            if (ff)
+                k_fold_ff<<<one_wave(p, k_fold_ff, p->n_chunks), 256, 0, s>>>(
+                    reinterpret_cast<float*>(cur), reinterpret_cast<const float*>(b.x), p->n_chunks, p->n_box);
+            else
+                k_fold<T><<<one_wave(p, k_fold<T>, p->n_chunks), 256, 0, s>>>(cur, b.x, p->n_chunks);
             OSM_CUDA(cudaGetLastError());
-            OSM_TRY(launch_residual<T>(p, b, cur, rtarget, s, prof));
+            OSM_TRY(launch_residual<T>(p, b, cur, rtarget, s, prof, ff));
             p->launches += 2;
             residual_evals++;
             OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
@@ -2100,8 +2441,20 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
     if (status == OSMODI_E_DIVERGED) return status;
 
     // gauge and output
-    if (multi) OSM_TRY(comp_sums<double>(p, cur, comp_p, s));
-    {
+    if (multi) OSM_TRY(comp_sums_iterate(p, cur, comp_p, s, ff));
+    if (ff) {
+        const float* ph = reinterpret_cast<const float*>(cur);
+        if (pdt == OSMODI_F32)
+            k_output_ff<float><<<one_wave(p, k_output_ff<float>, p->n_box), 256, 0, s>>>(
+                ph, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0, (float*)pu, p->px, p->nx,
+                p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks, p->opt.zero_start);
+        else
+            k_output_ff<double><<<one_wave(p, k_output_ff<double>, p->n_box), 256, 0, s>>>(
+                ph, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0, (double*)pu, p->px, p->nx,
+                p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks, p->opt.zero_start);
+        OSM_CUDA(cudaGetLastError());
+        p->launches += 1;
+    } else {
         if (pdt == OSMODI_F32)
             k_output<float><<<one_wave(p, k_output<float>, p->n_box), 256, 0, s>>>(cur, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0,
                                                (float*)pu, p->px, p->nx, p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks,

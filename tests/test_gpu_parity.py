@@ -505,3 +505,48 @@ def test_autotune_sweeps_per_pass(osm, tmp_path):
     finally:
         del os.environ["OSMODI_AUTOTUNE_CACHE"]
 
+
+
+FF_CASES = [
+    # (shape, spacing, mask density, P0 offset, gradient dtype, output dtype)
+    ((37, 53), (0.1, 0.13), 0.85, None, np.float32, torch.float64),
+    ((61, 47), (1.0, 1.0), 0.6, 3.0, np.float64, torch.float64),      # several components, seeded
+    ((19, 23, 29), (1.0, 1.3, 0.7), 0.9, None, np.float32, torch.float32),
+    ((33, 17, 45), (0.5, 0.5, 0.5), 0.7, -20.0, np.float32, torch.float64),
+]
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+@pytest.mark.parametrize("case", range(len(FF_CASES)))
+def test_float_float_refinement(osm, case, precond):
+    """The FP32 precisions refine in float-float arithmetic at tolerances >=
+    1e-9: the eps_R they report must be the FP64 residual of the pressure they
+    return (the oracle's Eq. ResidualMomentum), within the float-float
+    arithmetic's floor, and below the tolerance."""
+    shape, spacing, dens, off, gdt, pdt = FF_CASES[case]
+    rng = np.random.default_rng(90 + case)
+    valid = rng.random(shape) > 1.0 - dens
+    grid = oracle.Grid(valid, spacing)
+    f = rng.normal(size=(len(shape),) + shape).astype(gdt)
+    p0 = None
+    if off is not None:
+        p0 = off + 0.1 * rng.normal(size=shape)
+    for tol in (1e-8, 1e-9):
+        plan, res, got = _solve(osm, f, valid.astype(np.uint8), spacing, tol, p0=p0, pdtype=pdt, precision=2,
+                                precond=precond)
+        assert res.status == osm.OK, res.as_dict()
+        assert np.isnan(got[~valid]).all()
+        true_eps = oracle.residual(grid, f.astype(np.float64), np.where(valid, got, 0.0))
+        if pdt == torch.float64:
+            assert true_eps <= tol * 1.05, (true_eps, tol)
+            assert abs(true_eps - res.eps_R) <= 0.02 * res.eps_R + 1e-12, (true_eps, res.eps_R)
+        else:
+            # FP32 output: rounding P to FP32 moves the residual by ~1e-7 of
+            # |F P| / |S|; the reported eps_R is that of the FP64 iterate
+            assert res.eps_R <= tol
+        # the gauge: zero mean on every component
+        lab, _ = oracle.labels(grid)
+        rtol = 1e-9 if pdt == torch.float64 else 1e-6
+        for c in np.unique(lab[lab >= 0]):
+            sel = lab == c
+            assert abs(got[sel].mean()) <= rtol * np.abs(got[valid]).max() + 1e-12

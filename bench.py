@@ -51,7 +51,7 @@ def _peaks():
 def _kernel_source_hash():
     """Hash of the sources that define the timed solve's kernels."""
     h = hashlib.sha256()
-    for name in ("solve.cu", "mg.cu", "mg.cuh", "cg_state.cuh", "stencil.cuh", "internal.cuh"):
+    for name in ("solve.cu", "mg.cu", "mg.cuh", "cg_state.cuh", "stencil.cuh", "internal.cuh", "ff.cuh"):
         with open(os.path.join(ROOT, "paper_2311_16935_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -305,8 +305,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"gaussian_blobs_3d_{n}^3", "cells": n ** 3, "tol_eps_R": TOL,
-                       "precision": "fp32 sweeps + fp64 refinement",
-                       "scheme": "multigrid-preconditioned CG on the fixed-point system (red-black SOR smoothing)",
+                       "precision": "fp32 sweeps + float-float (48-bit) refinement",
+                       "scheme": "multigrid-preconditioned CG on the fixed-point system (two red-black SOR "
+                                 "sweeps before and after the coarse correction)",
                        "glups_counting": "valid cells x stencil applications on every level; a red-black "
                                          "half-sweep counts half",
                        "l2": "inputs and work vectors (>5 GB) exceed L2; no flush needed",
@@ -327,7 +328,13 @@ def main():
                               "traffic": _profiled_traffic("k_cg_a", cells)},
                              {"name": "k_cg_b (r update + r.r)", "avg_launch_ms": kb_avg, "bytes_per_launch": 12.0 * cells,
                               "achieved": 12.0 * cells / (kb_avg / 1e3) / 1e9 if kb_avg > 0 else None,
-                              "traffic": _profiled_traffic("k_cg_b", cells)}]},
+                              "traffic": _profiled_traffic("k_cg_b", cells)},
+                             # float-float residual of the refinement loop: read
+                             # P (hi, lo: 8 B), b (8 B), code (1 B); write r (4 B)
+                             {"name": "k_residual_ff (r = b - L P in float-float, norms)",
+                              "avg_launch_ms": r64_ms / max(r64_n, 1), "bytes_per_launch": 21.0 * cells,
+                              "achieved": 21.0 * cells / (r64_ms / max(r64_n, 1) / 1e3) / 1e9 if r64_ms > 0 else None,
+                              "traffic": _profiled_traffic("k_residual_ff", cells)}]},
             "clocks": clocks, "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
             "preconditioner": {"levels": info.get("mg_levels"), "applications": mg_n,
                                "avg_application_ms": mg_ms / max(mg_n, 1)},
@@ -336,8 +343,8 @@ def main():
             # convergence checks)
             "time_breakdown_ms_per_solve": {
                 "preconditioner": mg_ms / args.steps, "cg_apply": ka_ms / args.steps,
-                "cg_update": kb_ms / args.steps, "fp64_residual": r64_ms / args.steps,
-                "fp64_residual_launches": r64_n / args.steps,
+                "cg_update": kb_ms / args.steps, "refinement_residual": r64_ms / args.steps,
+                "refinement_residual_launches": r64_n / args.steps,
                 "rest": ms_max / args.steps - (mg_ms + ka_ms + kb_ms + r64_ms) / args.steps}}
 
     # the same solve in FP64 arithmetic throughout (same scheme), and the

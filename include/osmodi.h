@@ -123,15 +123,22 @@ typedef struct {
                             Same fixed point; far fewer outer iterations.  Adds
                             2m + 3 work vectors to the workspace. */
     int precond;         /* FPCG: 1 = multigrid-preconditioned CG (aggregation of 2x2(x2)
-                            cells per level, Galerkin coarse weights, symmetric red-black
-                            SOR smoothing: red then black before the coarse correction,
-                            black then red after; a fixed symmetric operator, so CG still
-                            converges to the same fixed point in far fewer iterations);
+                            cells per level, Galerkin coarse weights; symmetric smoothing:
+                            3-D red-black SOR, red then black before the coarse correction,
+                            black then red after; 2-D damped Jacobi; a fixed symmetric
+                            operator, so CG still converges to the same fixed point in far
+                            fewer iterations);
                             0 = plain CG.  Built at plan creation (about 2 B of device memory per
                             cell); grids of at most 8 cells per axis use plain CG.
                             Not part of the paper's method. */
     int zero_start;      /* 1 = start from P^0 = 0 without reading p: p is output only
                             (saves reading it, e.g. from host memory); 0 = p holds P^0 */
+    int mg_sweeps;       /* precond = 1: smoothing sweeps before and after the coarse
+                            correction on every level (3-D: red-black sweeps; 2-D: damped
+                            Jacobi sweeps), 1..8; 0 = the default, 2 */
+    double mg_scale;     /* precond = 1: scale of the coarse correction, (0, 4]; 0 = the
+                            default, 2.0.  Any positive scale keeps the preconditioner
+                            symmetric positive definite; it changes the iteration count */
 } osmodi_options;
 
 typedef struct {

@@ -1,15 +1,18 @@
 // Multigrid preconditioner (see mg.cuh for what it computes and why it keeps
-// CG's requirements).  The smoother depends on the dimension: red-black SOR
-// on 3-D grids (measured at 500^3: 15 CG iterations and 68.9 ms per solve,
-// against 18 and 75.9 ms with damped Jacobi), damped Jacobi on 2-D grids
-// (on the 2-D PIV snapshots Jacobi with a coarse scale of 2.0 needed 11
-// iterations, red-black 12 to 21 depending on omega and scale).  Level 0 is
-// the plan's own grid: padded box, 4-cell chunks, face weights b~_j F_j read
-// from the 1-byte codes, the same neighbour gather as the CG kernels.  Levels
-// >= 1 are dense boxes with explicit FP32 weights to the +x / +y / +z
-// neighbour (0 when the aggregates share no valid face) and omega / diagonal;
-// one thread per cell.  The coarsest level (at most 8 cells per axis) is
-// swept by one block.
+// CG's requirements).  The smoother depends on the dimension: two red-black
+// SOR sweeps before and after the coarse correction on 3-D grids, two damped
+// Jacobi sweeps on 2-D grids, the coarse correction scaled by 2.0 in both.
+// Measured at 500^3 (solve to 1e-8): one red-black sweep, scale 1.8: 15 CG
+// iterations, 57.0 ms; one sweep, 2.0: 14, 53.5 ms; two sweeps, 1.8: 12,
+// 70.5 ms; two sweeps, 2.0: 7, 45.0 ms; two sweeps, 2.2: 11, 65.4 ms; three
+// sweeps, 2.0: 6, 52.1 ms (damped Jacobi, two sweeps, 1.8: 18 iterations).
+// On the 2-D PIV snapshots (numpy model of the same V-cycle) Jacobi with
+// scale 2.0 needed 11 iterations, red-black 12 to 21.  Level 0 is the plan's
+// own grid: padded box, 4-cell chunks, face weights b~_j F_j read from the
+// 1-byte codes, the same neighbour gather as the CG kernels.  Levels >= 1 are
+// dense boxes with explicit FP32 weights to the +x / +y / +z neighbour (0
+// when the aggregates share no valid face) and 1 / diagonal; one thread per
+// cell.  The coarsest level (at most 8 cells per axis) is swept by one block.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,9 +32,11 @@ namespace {
 constexpr float kOmega = 0.85f;    // Jacobi damping
 constexpr float kOmegaRB = 1.2f;   // red-black over-relaxation
 // coarse-correction scale (aggregation under-estimates the coarse operator)
-constexpr float kScaleRB = 1.8f;      // with red-black smoothing (3-D)
+constexpr float kScaleRB = 2.0f;      // with red-black smoothing (3-D)
 constexpr float kScaleJacobi = 2.0f;  // with damped Jacobi (2-D)
-constexpr int kNu = 2;           // sweeps before and after the coarse correction
+// default sweeps before and after the coarse correction on every level
+constexpr int kNu = 2;    // damped Jacobi (2-D)
+constexpr int kNuRB = 2;  // red-black (3-D)
 constexpr int kCoarseSweeps = 40;
 constexpr int kCoarsestMax = 8;  // cells per axis on the coarsest level
 constexpr int kCoarsestThreads = 512;
@@ -322,6 +327,71 @@ __global__ void __launch_bounds__(256) k_mg_fine_prolong(T* __restrict__ z, cons
     }
 }
 
+// Fine-level residual and restriction in one pass: rc[I] = sum over the (up
+// to 8) children C of I of (r - L z)_C (0 outside the valid set), without
+// the residual vector in between.  A thread takes one chunk column of one
+// parent row: x-chunk cx of the 2 (3-D: 4) fine rows of parent row (J, K),
+// whose cells have the parents 2 cx and 2 cx + 1.  Lanes of a warp take
+// consecutive cx, so the west / east shuffles of the neighbour gather see the
+// adjacent chunk of the same fine row; where a warp crosses into the next
+// parent row the shuffled values belong to faces whose bits are 0 (the first
+// and last cell of a padded row have no west / east face).
+template <class T, int NDIM>
+__global__ void __launch_bounds__(256) k_mg_fine_resid_restrict(const T* __restrict__ z, const T* __restrict__ r,
+                                                                const uint8_t* __restrict__ code8, FineArgs<T> g,
+                                                                T* __restrict__ rc, const CgState* st) {
+    if (st->status != kRunning) return;
+    const int64_t cnz = NDIM == 3 ? (g.nz + 1) / 2 : 1;
+    const int64_t n_slots = g.cny * cnz * g.cpr;
+    ChunkLoop L;
+    for (int64_t base = L.base; base < n_slots; base += L.stride) {
+        const int64_t sl = base + L.lane;
+        const bool act = sl < n_slots;
+        int64_t cx = 0, J = 0, K = 0;
+        if (act) {
+            if (g.idx32) {
+                const uint32_t prow = (uint32_t)sl / (uint32_t)g.cpr;
+                cx = (uint32_t)sl - prow * (uint32_t)g.cpr;
+                J = NDIM == 3 ? prow % (uint32_t)g.cny : prow;
+                K = NDIM == 3 ? prow / (uint32_t)g.cny : 0;
+            } else {
+                const int64_t prow = sl / g.cpr;
+                cx = sl - prow * g.cpr;
+                J = NDIM == 3 ? prow % g.cny : prow;
+                K = NDIM == 3 ? prow / g.cny : 0;
+            }
+        }
+        T s0 = T(0), s1 = T(0);
+#pragma unroll
+        for (int b = 0; b < (NDIM == 3 ? 2 : 1); ++b) {
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const int64_t j = 2 * J + a, k = 2 * K + b;
+                const bool ra = act && j < g.ny && k < g.nz;
+                const int64_t i0 = ra ? ((k * g.ny + j) * g.cpr + cx) * 4 : 0;
+                const uint32_t cw = ra ? __ldg(reinterpret_cast<const uint32_t*>(code8 + i0)) : 0u;
+                const V4<T> rv = ra ? ld4(r + i0) : zero4<T>();
+                auto f4 = [&](int64_t off) { return ld4(z + i0 + off); };
+                auto f1 = [&](int64_t off) { return z[i0 + off]; };
+                const V4<T> c = ra ? f4(0) : zero4<T>();
+                const Nbrs<T> nb = gather_clamped<T, NDIM>(c, i0, g.n_box, L.lane, g.px, g.plane, ra, f4, f1);
+                T t[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    t[m] = valid8(cw, m) ? rv.v[m] - apply_L<T, NDIM>(face_bits8(cw, m), c, nb, m, g.F) : T(0);
+                s0 += t[0] + t[1];
+                s1 += t[2] + t[3];
+            }
+        }
+        if (act) {
+            T* row = rc + (K * g.cny + J) * g.cnx;
+            const int64_t I = 2 * cx;
+            if (I < g.cnx) row[I] = s0;
+            if (I + 1 < g.cnx) row[I + 1] = s1;
+        }
+    }
+}
+
 // restriction: rc[I] = sum of the (up to 8) children of t (row pitch `pitch`)
 template <class T>
 __global__ void k_mg_restrict(const T* __restrict__ t, int64_t fnx, int64_t fny, int64_t fnz, int64_t pitch,
@@ -556,7 +626,11 @@ Hier* hier_of(osmodi_plan p) { return reinterpret_cast<Hier*>(p->mg); }
 
 // the smoother of a plan: red-black SOR on 3-D grids, damped Jacobi on 2-D
 bool red_black(osmodi_plan p) { return p->ndim == 3; }
-float coarse_scale(osmodi_plan p) { return red_black(p) ? kScaleRB : kScaleJacobi; }
+// options.mg_scale / options.mg_sweeps, else the defaults of the smoother
+float coarse_scale(osmodi_plan p) {
+    return p->opt.mg_scale > 0.0 ? (float)p->opt.mg_scale : (red_black(p) ? kScaleRB : kScaleJacobi);
+}
+int sweeps(osmodi_plan p) { return p->opt.mg_sweeps > 0 ? p->opt.mg_sweeps : (red_black(p) ? kNuRB : kNu); }
 
 // Resident 256-thread blocks per SM of a kernel (queried once per kernel).
 // Grid-stride kernels are launched with exactly one wave of resident blocks:
@@ -611,6 +685,7 @@ T* vcycle_coarse(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, c
     const Level& g = h->lv[l - 1];
     LevelVecs<T> v = level_vecs<T>(h, base, l);
     const bool rb = red_black(p);
+    const int nu = sweeps(p);
     if (l == (int)h->lv.size()) {
         if (rb)
             k_mg_coarsest<T, true><<<1, kCoarsestThreads, 0, s>>>(v.r, v.a, g, st);
@@ -634,19 +709,25 @@ T* vcycle_coarse(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, c
         LevelVecs<T> vc = level_vecs<T>(h, base, l + 1);
         k_mg_coarse_rb<T, 0, true><<<G_rb, 256, 0, s>>>(v.a, v.r, a, st);   // red from zero
         k_mg_coarse_rb<T, 1, false><<<G_rb, 256, 0, s>>>(v.a, v.r, a, st);  // black
+        for (int i = 1; i < nu; ++i) {
+            k_mg_coarse_rb<T, 0, false><<<G_rb, 256, 0, s>>>(v.a, v.r, a, st);
+            k_mg_coarse_rb<T, 1, false><<<G_rb, 256, 0, s>>>(v.a, v.r, a, st);
+        }
         k_mg_coarse<T, M_RESID><<<G_resid, 256, 0, s>>>(v.a, v.r, v.b, a, st);
         k_mg_restrict<T><<<wave_grid(p, 0, b_restr, (gc.n + 255) / 256), 256, 0, s>>>(v.b, g.nx, g.ny, g.nz, g.nx, vc.r,
                                                                                        gc, st);
         T* zc = vcycle_coarse<T>(p, h, base, l + 1, st, s);
         k_mg_coarse_prolong<T><<<G_prol, 256, 0, s>>>(v.a, zc, a, st);
-        k_mg_coarse_rb<T, 1, false><<<G_rb, 256, 0, s>>>(v.a, v.r, a, st);  // black
-        k_mg_coarse_rb<T, 0, false><<<G_rb, 256, 0, s>>>(v.a, v.r, a, st);  // red
+        for (int i = 0; i < nu; ++i) {  // the adjoint: black then red
+            k_mg_coarse_rb<T, 1, false><<<G_rb, 256, 0, s>>>(v.a, v.r, a, st);
+            k_mg_coarse_rb<T, 0, false><<<G_rb, 256, 0, s>>>(v.a, v.r, a, st);
+        }
         return v.a;
     }
     T* cur = v.a;
     T* oth = v.b;
     k_mg_coarse<T, M_FIRST><<<G_first, 256, 0, s>>>(nullptr, v.r, cur, a, st);
-    for (int i = 1; i < kNu; ++i) {
+    for (int i = 1; i < nu; ++i) {
         k_mg_coarse<T, M_SWEEP><<<G_sweep, 256, 0, s>>>(cur, v.r, oth, a, st);
         std::swap(cur, oth);
     }
@@ -658,7 +739,7 @@ T* vcycle_coarse(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, c
     k_mg_coarse_prolong<T><<<G_prol, 256, 0, s>>>(cur, zc, a, st);
     k_mg_coarse<T, M_SWEEP><<<G_sweep, 256, 0, s>>>(cur, v.r, oth, a, st);
     std::swap(cur, oth);
-    for (int i = 1; i < kNu; ++i) {
+    for (int i = 1; i < nu; ++i) {
         k_mg_coarse<T, M_SWEEP><<<G_sweep, 256, 0, s>>>(cur, v.r, oth, a, st);
         std::swap(cur, oth);
     }
@@ -673,6 +754,7 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
     };
     const Hier* h = hier_of(p);
     const Level& g1 = h->lv[0];
+    const int nu = sweeps(p);
     FineArgs<T> f;
     f.px = p->px;
     f.plane = p->px * p->ny;
@@ -693,11 +775,13 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
     static const int b_first = blocks_per_sm(k_mg_fine<T, NDIM, M_FIRST, false>);
     static const int b_sweep = blocks_per_sm(k_mg_fine<T, NDIM, M_SWEEP, false>);
     static const int b_dot = blocks_per_sm(k_mg_fine<T, NDIM, M_SWEEP, true>);
-    static const int b_resid = blocks_per_sm(k_mg_fine<T, NDIM, M_RESID, false>);
+    static const int b_rr = blocks_per_sm(k_mg_fine_resid_restrict<T, NDIM>);
     static const int b_prol = blocks_per_sm(k_mg_fine_prolong<T, NDIM>);
     const int G_first = wave_grid(p, 0, b_first, w256), G_sweep = wave_grid(p, 0, b_sweep, w256);
-    const int G_dot = wave_grid(p, 0, b_dot, w256), G_resid = wave_grid(p, 0, b_resid, w256);
-    const int G_prol = wave_grid(p, 0, b_prol, w256);
+    const int G_dot = wave_grid(p, 0, b_dot, w256), G_prol = wave_grid(p, 0, b_prol, w256);
+    // one thread per chunk column of a parent row (2 or 4 chunks)
+    const int G_rr = wave_grid(p, 0, b_rr, (p->n_chunks / (NDIM == 3 ? 4 : 2) + 255) / 256 + 1);
+    LevelVecs<T> v1 = level_vecs<T>(h, w.lv, 1);
     // (fusing the first two sweeps into one pass was measured slower than the
     // two passes: forming every neighbour's first-sweep value costs more
     // instructions than the extra pass moves bytes)
@@ -706,19 +790,25 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
         static const int b_rb = blocks_per_sm(k_mg_fine_rb<T, NDIM, 1, false, false>);
         static const int b_rbd = blocks_per_sm(k_mg_fine_rb<T, NDIM, 0, false, true>);
         const int G_rb = wave_grid(p, 0, b_rb, w256), G_rbd = wave_grid(p, 0, b_rbd, w256);
+        static const int b_red = blocks_per_sm(k_mg_fine_rb<T, NDIM, 0, false, false>);
+        const int G_red = wave_grid(p, 0, b_red, w256);
         k_mg_fine_rb<T, NDIM, 0, true, false><<<G_first, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);  // red from 0
         mark(0);
         k_mg_fine_rb<T, NDIM, 1, false, false><<<G_rb, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);   // black
         mark(1);
+        for (int i = 1; i < nu; ++i) {
+            k_mg_fine_rb<T, NDIM, 0, false, false><<<G_red, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);
+            k_mg_fine_rb<T, NDIM, 1, false, false><<<G_rb, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);
+        }
         mark(4);
-        k_mg_fine<T, NDIM, M_RESID, false><<<G_resid, 256, 0, s>>>(w.zA, r, w.zB, p->code8, f, st, partials);
+        k_mg_fine_resid_restrict<T, NDIM><<<G_rr, 256, 0, s>>>(w.zA, r, p->code8, f, v1.r, st);
         mark(5);
-        LevelVecs<T> v1 = level_vecs<T>(h, w.lv, 1);
-        static const int b_restr = blocks_per_sm(k_mg_restrict<T>);
-        k_mg_restrict<T><<<wave_grid(p, 0, b_restr, (g1.n + 255) / 256), 256, 0, s>>>(w.zB, p->nx, p->ny, p->nz, p->px,
-                                                                                      v1.r, g1, st);
         T* zc = vcycle_coarse<T>(p, h, w.lv, 1, st, s);
         k_mg_fine_prolong<T, NDIM><<<G_prol, 256, 0, s>>>(w.zA, zc, f, st);
+        for (int i = 1; i < nu; ++i) {  // the adjoint: black then red
+            k_mg_fine_rb<T, NDIM, 1, false, false><<<G_rb, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);
+            k_mg_fine_rb<T, NDIM, 0, false, false><<<G_red, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);
+        }
         mark(2);
         k_mg_fine_rb<T, NDIM, 1, false, false><<<G_rb, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);   // black
         mark(3);
@@ -728,19 +818,15 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
     T* cur = w.zA;
     T* oth = w.zB;
     k_mg_fine<T, NDIM, M_FIRST, false><<<G_first, 256, 0, s>>>(nullptr, r, cur, p->code8, f, st, partials);
-    for (int i = 1; i < kNu; ++i) {
+    for (int i = 1; i < nu; ++i) {
         if (i == 1) mark(0);
         k_mg_fine<T, NDIM, M_SWEEP, false><<<G_sweep, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
         if (i == 1) mark(1);
         std::swap(cur, oth);
     }
     mark(4);
-    k_mg_fine<T, NDIM, M_RESID, false><<<G_resid, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
+    k_mg_fine_resid_restrict<T, NDIM><<<G_rr, 256, 0, s>>>(cur, r, p->code8, f, v1.r, st);
     mark(5);
-    LevelVecs<T> v1 = level_vecs<T>(h, w.lv, 1);
-    static const int b_restr = blocks_per_sm(k_mg_restrict<T>);
-    k_mg_restrict<T><<<wave_grid(p, 0, b_restr, (g1.n + 255) / 256), 256, 0, s>>>(oth, p->nx, p->ny, p->nz, p->px, v1.r,
-                                                                                  g1, st);
     T* zc = vcycle_coarse<T>(p, h, w.lv, 1, st, s);
     // the prolongation as its own in-place pass: fused into the sweep, every
     // neighbour's parent lookup made that kernel twice as slow as the two apart
@@ -749,8 +835,8 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
     k_mg_fine<T, NDIM, M_SWEEP, false><<<G_sweep, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
     mark(3);
     std::swap(cur, oth);
-    for (int i = 1; i < kNu; ++i) {
-        if (i == kNu - 1)
+    for (int i = 1; i < nu; ++i) {
+        if (i == nu - 1)
             k_mg_fine<T, NDIM, M_SWEEP, true><<<G_dot, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
         else
             k_mg_fine<T, NDIM, M_SWEEP, false><<<G_sweep, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
@@ -839,8 +925,11 @@ double mg_updates_per_apply(osmodi_plan p) {
     // fine and intermediate levels: (nu - 1) + 1 (residual) + nu sweeps with a
     // stencil application each; the coarsest: kCoarseSweeps - 1
     // red-black: three half-sweeps (1.5 applications) and the residual per level
+    // red-black, nu sweeps: 2 nu - 1 stencil half-sweeps before (the first
+    // red one starts from zero), the residual, 2 nu half-sweeps after
     const bool rb = red_black(p);
-    const double per = rb ? 2.5 : 2.0 * kNu;
+    const int nu = sweeps(p);
+    const double per = rb ? 2.0 * nu + 0.5 : 2.0 * nu;
     double u = per * (double)p->n_valid;
     for (size_t q = 0; q < h->lv.size(); ++q)
         u += (q + 1 == h->lv.size() ? (double)kCoarseSweeps - (rb ? 0.5 : 1.0) : per) * h->lv[q].active;
@@ -850,10 +939,14 @@ double mg_updates_per_apply(osmodi_plan p) {
 int mg_launches_per_apply(osmodi_plan p) {
     const Hier* h = hier_of(p);
     if (!h) return 0;
-    // per level above the coarsest: kNu pre-sweeps, residual, restriction,
-    // prolongation, kNu post-sweeps; then the coarsest
-    const int per = kNu + 1 + 1 + 1 + kNu;
-    return per * (int)h->lv.size() + 1;
+    // per level above the coarsest: the pre-sweeps (Jacobi: kNu launches;
+    // red-black: two half-sweeps per sweep), residual, restriction,
+    // prolongation, the post-sweeps; the fine level's residual and
+    // restriction are one kernel; then the coarsest
+    const bool rb = red_black(p);
+    const int nu = sweeps(p);
+    const int per = rb ? 4 * nu + 3 : 2 * nu + 3;
+    return per * (int)h->lv.size();
 }
 
 template <class T>
@@ -863,7 +956,7 @@ T* mg_apply(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
 }
 
 // red-black smoothing updates z in place in zA; the Jacobi V-cycle swaps its
-// two buffers (kNu - 1) + kNu times (an odd number) and ends in zB
+// two buffers (nu - 1) + nu times (an odd number) and ends in zB
 template <class T>
 T* mg_result(osmodi_plan p, const MgBuffers<T>& w) {
     return red_black(p) ? w.zA : w.zB;

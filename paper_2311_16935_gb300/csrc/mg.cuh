@@ -7,11 +7,11 @@
 // Galerkin coarse operator of piecewise-constant interpolation -- the coarse
 // face weight is the sum of the fine face weights between two aggregates, so
 // every level is again a weighted graph Laplacian on a regular grid --
-// smoothing by red-black SOR on 3-D grids (one red-then-black sweep before
-// the coarse correction, its adjoint black-then-red after) and by two damped
-// Jacobi sweeps before and after on 2-D grids, the coarse correction scaled
-// by a constant, and the same smoother run for many sweeps on the coarsest
-// grid.  Post-smoothing is the
+// smoothing by red-black SOR on 3-D grids (two red-then-black sweeps before
+// the coarse correction, their adjoint, black-then-red, after) and by two
+// damped Jacobi sweeps before and after on 2-D grids, the coarse correction
+// scaled by a constant, and the same smoother run for many sweeps on the
+// coarsest grid.  Post-smoothing is the
 // adjoint of pre-smoothing and the coarsest solve is symmetric, so z = B r is
 // a fixed symmetric positive (semi)definite operator, as CG needs.
 #pragma once

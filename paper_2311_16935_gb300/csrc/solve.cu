@@ -300,8 +300,12 @@ __global__ void k_source_ff(const TG* __restrict__ f, const TP* __restrict__ p_i
         if (p_in) {
             const TP v = p_in[d];
             if (!isfinite(v)) bad |= 2;
-            if constexpr (sizeof(TP) == 4) p0 = FF{v, 0.f};
-            else p0 = ff_from_double(v);
+            if constexpr (sizeof(TP) == 4) {
+                p0 = FF{v, 0.f};
+            } else {
+                // a zero start needs no FP64 arithmetic (the test is on the bits)
+                if ((__double_as_longlong(v) << 1) != 0) p0 = ff_from_double(v);
+            }
         }
         bh[idx] = s.hi;
         bl[idx] = s.lo;
@@ -445,6 +449,7 @@ __global__ void k_output_ff(const float* __restrict__ ph, const uint8_t* __restr
     const float* pl = ph + n_box;
     const double m1 = multi ? 0.0 : sc->psum / comp_cnt[0];
     const double m01 = multi ? 0.0 : sc->p0sum / comp_cnt[0];
+    const FF m1f = ff_from_double(m1);
     FFAcc a_d, a_v;
     const bool i32 = n_box < (int64_t)(1u << 31);
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n_box; idx += (int64_t)gridDim.x * blockDim.x) {
@@ -463,17 +468,21 @@ __global__ void k_output_ff(const float* __restrict__ ph, const uint8_t* __restr
             p_user[d] = (TP)NAN;
             continue;
         }
-        double m = m1, m0 = m01;
+        FF mf = m1f;
+        double m0 = m01;
         if (multi) {
             const int32_t l = label[idx];
-            m = comp_p[l] / comp_cnt[l];
+            mf = ff_from_double(comp_p[l] / comp_cnt[l]);
             m0 = comp_p0[l] / comp_cnt[l];
         }
-        const double v = ((double)ph[idx] - m) + (double)pl[idx];
+        // P - mean as a pair (FP32 arithmetic), then the one FP64 addition
+        // that forms the output value
+        const FF vf = ff_add(FF{ph[idx], pl[idx]}, FF{-mf.hi, -mf.lo});
+        const double v = (double)vf.hi + (double)vf.lo;
         // the seed distance is a reported statistic: FP32 terms suffice
-        const float dv = zero0 ? -(float)v : (float)(((double)p_user[d] - m0) - v);
+        const float dv = zero0 ? -vf.hi : (float)(((double)p_user[d] - m0) - v);
         a_d.add(dv * dv);
-        a_v.add((float)v * (float)v);
+        a_v.add(vf.hi * vf.hi);
         p_user[d] = (TP)v;
     }
     double acc[2] = {a_d.value(), a_v.value()};
@@ -2338,8 +2347,20 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                 OSM_CUDA(cudaGetLastError());
                 p->launches += 1;
                 if (pre) {
+                    if (prof) {
+                        OSM_TRY(ensure_events(p, 2));
+                        OSM_CUDA(cudaEventRecord(p->events[0], s));
+                    }
                     launch_mg<T>(p, b, s);  // z_0 = B r_0, (r_0, z_0), the first direction
                     OSM_CUDA(cudaGetLastError());
+                    if (prof) {  // the segment's first application counts with the others
+                        OSM_CUDA(cudaEventRecord(p->events[1], s));
+                        OSM_CUDA(cudaEventSynchronize(p->events[1]));
+                        float ms = 0.f;
+                        OSM_CUDA(cudaEventElapsedTime(&ms, p->events[0], p->events[1]));
+                        p->kstats[6] += ms;
+                        p->kstats[7] += 1;
+                    }
                     mg_applies += 1;
                     p->launches += mg_launches_per_apply(p);
                 }
@@ -2442,27 +2463,29 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
 
     // gauge and output
     if (multi) OSM_TRY(comp_sums_iterate(p, cur, comp_p, s, ff));
+    // an all-zero P^0 (read or not) needs no second read for the seed distance
+    const int zero0 = (p->opt.zero_start || hm->sc.p0nz == 0.0) ? 1 : 0;
     if (ff) {
         const float* ph = reinterpret_cast<const float*>(cur);
         if (pdt == OSMODI_F32)
             k_output_ff<float><<<one_wave(p, k_output_ff<float>, p->n_box), 256, 0, s>>>(
                 ph, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0, (float*)pu, p->px, p->nx,
-                p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks, p->opt.zero_start);
+                p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks, zero0);
         else
             k_output_ff<double><<<one_wave(p, k_output_ff<double>, p->n_box), 256, 0, s>>>(
                 ph, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0, (double*)pu, p->px, p->nx,
-                p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks, p->opt.zero_start);
+                p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks, zero0);
         OSM_CUDA(cudaGetLastError());
         p->launches += 1;
     } else {
         if (pdt == OSMODI_F32)
             k_output<float><<<one_wave(p, k_output<float>, p->n_box), 256, 0, s>>>(cur, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0,
                                                (float*)pu, p->px, p->nx, p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks,
-                                               p->opt.zero_start);
+                                               zero0);
         else
             k_output<double><<<one_wave(p, k_output<double>, p->n_box), 256, 0, s>>>(cur, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0,
                                                 (double*)pu, p->px, p->nx, p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks,
-                                                p->opt.zero_start);
+                                                zero0);
         OSM_CUDA(cudaGetLastError());
         p->launches += 1;
     }

@@ -31,7 +31,8 @@ class osmodi_options(ctypes.Structure):
                 ("sweeps_per_pass", ctypes.c_int), ("max_refine", ctypes.c_int), ("record_history", ctypes.c_int),
                 ("threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("profile", ctypes.c_int),
                 ("slab", ctypes.c_int), ("flat_sweeps", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("accel", ctypes.c_int), ("precond", ctypes.c_int), ("zero_start", ctypes.c_int)]
+                ("accel", ctypes.c_int), ("precond", ctypes.c_int), ("zero_start", ctypes.c_int),
+                ("mg_sweeps", ctypes.c_int), ("mg_scale", ctypes.c_double)]
 
 
 class osmodi_result(ctypes.Structure):

@@ -44,6 +44,8 @@ constexpr int kCoarsestThreads = 512;
 struct Level {
     int64_t nx, ny, nz, n;
     float *wx, *wy, *wz, *dinv;
+    uint32_t* wc;   // packed fine-face counts (null when a count can exceed 10 bits)
+    float F[3];     // the fine F_a: weight = count * F_a
     double active;  // cells with a nonzero diagonal
 };
 
@@ -392,24 +394,40 @@ __global__ void __launch_bounds__(256) k_mg_fine_resid_restrict(const T* __restr
     }
 }
 
+// ---------------------------------------------------------------------------
+// levels >= 1 (dense boxes), one thread per cell in grid-stride loops of one
+// wave.  A level's face weights are integer counts of fine faces times the
+// fine F_a; where the counts fit 10 bits (3-D: levels 1-4, 2-D: levels 1-9)
+// they are read as one packed 32-bit word per cell (count_x | count_y << 10
+// | count_z << 20) and the diagonal is formed from the six counts: 4 bytes
+// per cell instead of the 16 of three FP32 weights and 1 / D.
+// ---------------------------------------------------------------------------
+template <class F>
+__device__ __forceinline__ void for_cells(int64_t nx, int64_t ny, int64_t nz, F f) {
+    const int64_t n = nx * ny * nz;
+    const bool i32 = n < (int64_t)(1u << 31);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i, j, k;
+        if (i32) {
+            const uint32_t q32 = (uint32_t)q, row = q32 / (uint32_t)nx;
+            i = q32 - row * (uint32_t)nx;
+            j = row % (uint32_t)ny;
+            k = row / (uint32_t)ny;
+        } else {
+            i = q % nx;
+            j = (q / nx) % ny;
+            k = q / (nx * ny);
+        }
+        f(i, j, k, q);
+    }
+}
+
 // restriction: rc[I] = sum of the (up to 8) children of t (row pitch `pitch`)
 template <class T>
 __global__ void k_mg_restrict(const T* __restrict__ t, int64_t fnx, int64_t fny, int64_t fnz, int64_t pitch,
                               T* __restrict__ rc, Level c, const CgState* st) {
     if (st->status != kRunning) return;
-    const bool i32 = c.n < (int64_t)(1u << 31);
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < c.n; q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t I, J, K;
-        if (i32) {
-            const uint32_t q32 = (uint32_t)q, nx32 = (uint32_t)c.nx, row = q32 / nx32;
-            I = q32 - row * nx32;
-            J = row % (uint32_t)c.ny;
-            K = row / (uint32_t)c.ny;
-        } else {
-            I = q % c.nx;
-            J = (q / c.nx) % c.ny;
-            K = q / (c.nx * c.ny);
-        }
+    for_cells(c.nx, c.ny, c.nz, [&](int64_t I, int64_t J, int64_t K, int64_t q) {
         T s = T(0);
         const int dz = fnz > 1 ? 2 : 1;
         for (int b = 0; b < dz; ++b)
@@ -422,57 +440,80 @@ __global__ void k_mg_restrict(const T* __restrict__ t, int64_t fnx, int64_t fny,
                 if (i + 1 < fnx) s += row[i + 1];
             }
         rc[q] = s;
-    }
+    });
 }
 
-// ---------------------------------------------------------------------------
-// levels >= 1 (dense, explicit weights)
-// ---------------------------------------------------------------------------
 template <class T>
 struct CoarseArgs {
     Level lv;
     int64_t cnx, cny;  // the next coarser level (parents)
     T scale;
-    T omega;           // smoother weight (dinv holds 1 / D)
+    T omega;           // smoother weight
 };
 
-template <class T, int MODE>
-__global__ void k_mg_coarse(const T* __restrict__ z, const T* __restrict__ r, T* __restrict__ out, CoarseArgs<T> a,
-                            const CgState* st) {
+// the six face weights and omega / D of cell q of a coarse level
+template <class T>
+struct CoarseRow {
+    T xp, xm, yp, ym, zp, zm, wd;
+};
+
+template <class T, bool PACKED>
+__device__ __forceinline__ CoarseRow<T> coarse_row(const Level& g, T omega, int64_t i, int64_t j, int64_t k,
+                                                   int64_t q) {
+    CoarseRow<T> c;
+    if (PACKED) {
+        const uint32_t w = __ldg(g.wc + q);
+        c.xp = (T)((float)(w & 1023u) * g.F[0]);
+        c.yp = (T)((float)((w >> 10) & 1023u) * g.F[1]);
+        c.zp = (T)((float)(w >> 20) * g.F[2]);
+        c.xm = i > 0 ? (T)((float)(__ldg(g.wc + q - 1) & 1023u) * g.F[0]) : T(0);
+        c.ym = j > 0 ? (T)((float)((__ldg(g.wc + q - g.nx) >> 10) & 1023u) * g.F[1]) : T(0);
+        c.zm = k > 0 ? (T)((float)(__ldg(g.wc + q - g.nx * g.ny) >> 20) * g.F[2]) : T(0);
+        const T d = c.xp + c.xm + c.yp + c.ym + c.zp + c.zm;
+        c.wd = d > T(0) ? omega / d : T(0);
+    } else {
+        c.xp = i + 1 < g.nx ? (T)g.wx[q] : T(0);
+        c.xm = i > 0 ? (T)g.wx[q - 1] : T(0);
+        c.yp = j + 1 < g.ny ? (T)g.wy[q] : T(0);
+        c.ym = j > 0 ? (T)g.wy[q - g.nx] : T(0);
+        c.zp = k + 1 < g.nz ? (T)g.wz[q] : T(0);
+        c.zm = k > 0 ? (T)g.wz[q - g.nx * g.ny] : T(0);
+        c.wd = omega * (T)g.dinv[q];
+    }
+    return c;
+}
+
+// (A z)_q from the row (zero weights skip their neighbour's load)
+template <class T>
+__device__ __forceinline__ T coarse_az(const CoarseRow<T>& c, const T* z, T zc0, int64_t q, int64_t sy, int64_t sz) {
+    T az = T(0);
+    if (c.xp != T(0)) az += c.xp * (zc0 - z[q + 1]);
+    if (c.xm != T(0)) az += c.xm * (zc0 - z[q - 1]);
+    if (c.yp != T(0)) az += c.yp * (zc0 - z[q + sy]);
+    if (c.ym != T(0)) az += c.ym * (zc0 - z[q - sy]);
+    if (c.zp != T(0)) az += c.zp * (zc0 - z[q + sz]);
+    if (c.zm != T(0)) az += c.zm * (zc0 - z[q - sz]);
+    return az;
+}
+
+// MODE M_FIRST: out = omega D^-1 r; M_SWEEP: out = z + omega D^-1 (r - A z);
+// M_RESID: out = r - A z
+template <class T, int MODE, bool PACKED>
+__global__ void k_mg_coarse(const T* __restrict__ z, const T* __restrict__ r,
+                                                            T* __restrict__ out, CoarseArgs<T> a, const CgState* st) {
     if (st->status != kRunning) return;
     const Level& g = a.lv;
-    const bool i32 = g.n < (int64_t)(1u << 31);
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < g.n; q += (int64_t)gridDim.x * blockDim.x) {
-        const T dv = a.omega * (T)g.dinv[q];
+    const int64_t sy = g.nx, sz = g.nx * g.ny;
+    for_cells(g.nx, g.ny, g.nz, [&](int64_t i, int64_t j, int64_t k, int64_t q) {
+        const CoarseRow<T> c = coarse_row<T, PACKED>(g, a.omega, i, j, k, q);
         if (MODE == M_FIRST) {
-            out[q] = dv * r[q];
-            continue;
+            out[q] = c.wd * r[q];
+            return;
         }
-        int64_t i, j, k;
-        if (i32) {
-            const uint32_t q32 = (uint32_t)q, nx32 = (uint32_t)g.nx, row = q32 / nx32;
-            i = q32 - row * nx32;
-            j = row % (uint32_t)g.ny;
-            k = row / (uint32_t)g.ny;
-        } else {
-            i = q % g.nx;
-            j = (q / g.nx) % g.ny;
-            k = q / (g.nx * g.ny);
-        }
-        auto zv = [&](int64_t ii, int64_t jj, int64_t kk) {
-            return z[(kk * g.ny + jj) * g.nx + ii];
-        };
-        const T zc0 = zv(i, j, k);
-        T az = T(0);
-        if (i + 1 < g.nx) az += (T)g.wx[q] * (zc0 - zv(i + 1, j, k));
-        if (i > 0) az += (T)g.wx[q - 1] * (zc0 - zv(i - 1, j, k));
-        if (j + 1 < g.ny) az += (T)g.wy[q] * (zc0 - zv(i, j + 1, k));
-        if (j > 0) az += (T)g.wy[q - g.nx] * (zc0 - zv(i, j - 1, k));
-        if (k + 1 < g.nz) az += (T)g.wz[q] * (zc0 - zv(i, j, k + 1));
-        if (k > 0) az += (T)g.wz[q - g.nx * g.ny] * (zc0 - zv(i, j, k - 1));
-        const T res = r[q] - az;
-        out[q] = MODE == M_RESID ? res : zc0 + dv * res;
-    }
+        const T zc0 = z[q];
+        const T res = r[q] - coarse_az(c, z, zc0, q, sy, sz);
+        out[q] = MODE == M_RESID ? res : zc0 + c.wd * res;
+    });
 }
 
 // Red-black half-sweep on a coarse level, in place: cells of colour COLOR
@@ -480,62 +521,47 @@ __global__ void k_mg_coarse(const T* __restrict__ z, const T* __restrict__ r, T*
 // on red cells and 0 on black ones (the red half-sweep from zero).  The cells
 // a half-sweep writes are read by no other thread of it (their neighbours
 // are all of the other colour).
-template <class T, int COLOR, bool FIRST>
-__global__ void k_mg_coarse_rb(T* z, const T* __restrict__ r, CoarseArgs<T> a, const CgState* st) {
+template <class T, int COLOR, bool FIRST, bool PACKED>
+__global__ void k_mg_coarse_rb(T* z, const T* __restrict__ r, CoarseArgs<T> a,
+                                                               const CgState* st) {
     if (st->status != kRunning) return;
     const Level& g = a.lv;
-    const bool i32 = g.n < (int64_t)(1u << 31);
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < g.n; q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i, j, k;
-        if (i32) {
-            const uint32_t q32 = (uint32_t)q, nx32 = (uint32_t)g.nx, row = q32 / nx32;
-            i = q32 - row * nx32;
-            j = row % (uint32_t)g.ny;
-            k = row / (uint32_t)g.ny;
-        } else {
-            i = q % g.nx;
-            j = (q / g.nx) % g.ny;
-            k = q / (g.nx * g.ny);
-        }
+    const int64_t sy = g.nx, sz = g.nx * g.ny;
+    for_cells(g.nx, g.ny, g.nz, [&](int64_t i, int64_t j, int64_t k, int64_t q) {
         const int col = (int)((i + j + k) & 1);
-        const T dv = a.omega * (T)g.dinv[q];
         if (FIRST) {
-            z[q] = col == 0 ? dv * r[q] : T(0);
-            continue;
+            if (col == 0) {
+                const CoarseRow<T> c = coarse_row<T, PACKED>(g, a.omega, i, j, k, q);
+                z[q] = c.wd * r[q];
+            } else {
+                z[q] = T(0);
+            }
+            return;
         }
-        if (col != COLOR) continue;
-        auto zv = [&](int64_t ii, int64_t jj, int64_t kk) { return z[(kk * g.ny + jj) * g.nx + ii]; };
+        if (col != COLOR) return;
+        const CoarseRow<T> c = coarse_row<T, PACKED>(g, a.omega, i, j, k, q);
         const T zc0 = z[q];
-        T az = T(0);
-        if (i + 1 < g.nx) az += (T)g.wx[q] * (zc0 - zv(i + 1, j, k));
-        if (i > 0) az += (T)g.wx[q - 1] * (zc0 - zv(i - 1, j, k));
-        if (j + 1 < g.ny) az += (T)g.wy[q] * (zc0 - zv(i, j + 1, k));
-        if (j > 0) az += (T)g.wy[q - g.nx] * (zc0 - zv(i, j - 1, k));
-        if (k + 1 < g.nz) az += (T)g.wz[q] * (zc0 - zv(i, j, k + 1));
-        if (k > 0) az += (T)g.wz[q - g.nx * g.ny] * (zc0 - zv(i, j, k - 1));
-        z[q] = zc0 + dv * (r[q] - az);
-    }
+        z[q] = zc0 + c.wd * (r[q] - coarse_az(c, z, zc0, q, sy, sz));
+    });
 }
 
 // prolongation on a coarse level, in place: z += scale * zc[parent]
 template <class T>
-__global__ void k_mg_coarse_prolong(T* __restrict__ z, const T* __restrict__ zc, CoarseArgs<T> a, const CgState* st) {
+__global__ void k_mg_coarse_prolong(T* __restrict__ z, const T* __restrict__ zc,
+                                                                    CoarseArgs<T> a, const CgState* st) {
     if (st->status != kRunning) return;
     const Level& g = a.lv;
-    const bool i32 = g.n < (int64_t)(1u << 31);
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < g.n; q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i, j, k;
-        if (i32) {
-            const uint32_t q32 = (uint32_t)q, nx32 = (uint32_t)g.nx, row = q32 / nx32;
-            i = q32 - row * nx32;
-            j = row % (uint32_t)g.ny;
-            k = row / (uint32_t)g.ny;
-        } else {
-            i = q % g.nx;
-            j = (q / g.nx) % g.ny;
-            k = q / (g.nx * g.ny);
-        }
+    for_cells(g.nx, g.ny, g.nz, [&](int64_t i, int64_t j, int64_t k, int64_t q) {
         z[q] += a.scale * zc[((k >> 1) * a.cny + (j >> 1)) * a.cnx + (i >> 1)];
+    });
+}
+
+// counts of a level's face weights, packed (weights are sums of the fine
+// F_a, so weight / F_a is within 1e-4 of an integer count)
+__global__ void k_mg_pack(Level c) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < c.n; q += (int64_t)gridDim.x * blockDim.x) {
+        auto cnt = [&](float w, float F) -> uint32_t { return F > 0.f ? (uint32_t)__float2int_rn(w / F) : 0u; };
+        c.wc[q] = cnt(c.wx[q], c.F[0]) | (cnt(c.wy[q], c.F[1]) << 10) | (cnt(c.wz[q], c.F[2]) << 20);
     }
 }
 
@@ -679,13 +705,15 @@ LevelVecs<T> level_vecs(const Hier* h, char* base, int l) {
     return v;
 }
 
+template <class T, bool PACKED>
+T* vcycle_body(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, cudaStream_t s);
+
 // V-cycle on level l >= 1; returns the buffer holding z_l
 template <class T>
 T* vcycle_coarse(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, cudaStream_t s) {
     const Level& g = h->lv[l - 1];
     LevelVecs<T> v = level_vecs<T>(h, base, l);
     const bool rb = red_black(p);
-    const int nu = sweeps(p);
     if (l == (int)h->lv.size()) {
         if (rb)
             k_mg_coarsest<T, true><<<1, kCoarsestThreads, 0, s>>>(v.r, v.a, g, st);
@@ -693,54 +721,59 @@ T* vcycle_coarse(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, c
             k_mg_coarsest<T, false><<<1, kCoarsestThreads, 0, s>>>(v.r, v.a, g, st);
         return v.a;
     }
+    return g.wc ? vcycle_body<T, true>(p, h, base, l, st, s) : vcycle_body<T, false>(p, h, base, l, st, s);
+}
+
+template <class T, bool PACKED>
+T* vcycle_body(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, cudaStream_t s) {
+    const Level& g = h->lv[l - 1];
+    LevelVecs<T> v = level_vecs<T>(h, base, l);
+    const bool rb = red_black(p);
+    const int nu = sweeps(p);
     const Level& gc = h->lv[l];
+    LevelVecs<T> vc = level_vecs<T>(h, base, l + 1);
     CoarseArgs<T> a{g, gc.nx, gc.ny, (T)coarse_scale(p), (T)(rb ? kOmegaRB : kOmega)};
+    // one wave of resident 256-thread blocks per kernel (queried once each)
+    static const int b_rb = blocks_per_sm(k_mg_coarse_rb<T, 1, false, PACKED>);
+    static const int b_sw = blocks_per_sm(k_mg_coarse<T, M_SWEEP, PACKED>);
+    static const int b_rs = blocks_per_sm(k_mg_coarse<T, M_RESID, PACKED>);
+    static const int b_pr = blocks_per_sm(k_mg_coarse_prolong<T>);
+    static const int b_re = blocks_per_sm(k_mg_restrict<T>);
     const int64_t w256 = (g.n + 255) / 256;
-    static const int b_first = blocks_per_sm(k_mg_coarse<T, M_FIRST>);
-    static const int b_sweep = blocks_per_sm(k_mg_coarse<T, M_SWEEP>);
-    static const int b_resid = blocks_per_sm(k_mg_coarse<T, M_RESID>);
-    static const int b_prol = blocks_per_sm(k_mg_coarse_prolong<T>);
-    static const int b_restr = blocks_per_sm(k_mg_restrict<T>);
-    const int G_first = wave_grid(p, 0, b_first, w256), G_sweep = wave_grid(p, 0, b_sweep, w256);
-    const int G_resid = wave_grid(p, 0, b_resid, w256), G_prol = wave_grid(p, 0, b_prol, w256);
+    const int Grb = wave_grid(p, 0, b_rb, w256), Gsw = wave_grid(p, 0, b_sw, w256);
+    const int Grs = wave_grid(p, 0, b_rs, w256), Gpr = wave_grid(p, 0, b_pr, w256);
+    const int Gre = wave_grid(p, 0, b_re, (gc.n + 255) / 256);
+    const int B = 256;
     if (rb) {
-        static const int b_rb = blocks_per_sm(k_mg_coarse_rb<T, 1, false>);
-        const int G_rb = wave_grid(p, 0, b_rb, w256);
-        LevelVecs<T> vc = level_vecs<T>(h, base, l + 1);
-        k_mg_coarse_rb<T, 0, true><<<G_rb, 256, 0, s>>>(v.a, v.r, a, st);   // red from zero
-        k_mg_coarse_rb<T, 1, false><<<G_rb, 256, 0, s>>>(v.a, v.r, a, st);  // black
+        k_mg_coarse_rb<T, 0, true, PACKED><<<Grb, B, 0, s>>>(v.a, v.r, a, st);   // red from zero
+        k_mg_coarse_rb<T, 1, false, PACKED><<<Grb, B, 0, s>>>(v.a, v.r, a, st);  // black
         for (int i = 1; i < nu; ++i) {
-            k_mg_coarse_rb<T, 0, false><<<G_rb, 256, 0, s>>>(v.a, v.r, a, st);
-            k_mg_coarse_rb<T, 1, false><<<G_rb, 256, 0, s>>>(v.a, v.r, a, st);
+            k_mg_coarse_rb<T, 0, false, PACKED><<<Grb, B, 0, s>>>(v.a, v.r, a, st);
+            k_mg_coarse_rb<T, 1, false, PACKED><<<Grb, B, 0, s>>>(v.a, v.r, a, st);
         }
-        k_mg_coarse<T, M_RESID><<<G_resid, 256, 0, s>>>(v.a, v.r, v.b, a, st);
-        k_mg_restrict<T><<<wave_grid(p, 0, b_restr, (gc.n + 255) / 256), 256, 0, s>>>(v.b, g.nx, g.ny, g.nz, g.nx, vc.r,
-                                                                                       gc, st);
+        k_mg_coarse<T, M_RESID, PACKED><<<Grs, B, 0, s>>>(v.a, v.r, v.b, a, st);
+        k_mg_restrict<T><<<Gre, B, 0, s>>>(v.b, g.nx, g.ny, g.nz, g.nx, vc.r, gc, st);
         T* zc = vcycle_coarse<T>(p, h, base, l + 1, st, s);
-        k_mg_coarse_prolong<T><<<G_prol, 256, 0, s>>>(v.a, zc, a, st);
+        k_mg_coarse_prolong<T><<<Gpr, B, 0, s>>>(v.a, zc, a, st);
         for (int i = 0; i < nu; ++i) {  // the adjoint: black then red
-            k_mg_coarse_rb<T, 1, false><<<G_rb, 256, 0, s>>>(v.a, v.r, a, st);
-            k_mg_coarse_rb<T, 0, false><<<G_rb, 256, 0, s>>>(v.a, v.r, a, st);
+            k_mg_coarse_rb<T, 1, false, PACKED><<<Grb, B, 0, s>>>(v.a, v.r, a, st);
+            k_mg_coarse_rb<T, 0, false, PACKED><<<Grb, B, 0, s>>>(v.a, v.r, a, st);
         }
         return v.a;
     }
     T* cur = v.a;
     T* oth = v.b;
-    k_mg_coarse<T, M_FIRST><<<G_first, 256, 0, s>>>(nullptr, v.r, cur, a, st);
+    k_mg_coarse<T, M_FIRST, PACKED><<<Gsw, B, 0, s>>>(nullptr, v.r, cur, a, st);
     for (int i = 1; i < nu; ++i) {
-        k_mg_coarse<T, M_SWEEP><<<G_sweep, 256, 0, s>>>(cur, v.r, oth, a, st);
+        k_mg_coarse<T, M_SWEEP, PACKED><<<Gsw, B, 0, s>>>(cur, v.r, oth, a, st);
         std::swap(cur, oth);
     }
-    k_mg_coarse<T, M_RESID><<<G_resid, 256, 0, s>>>(cur, v.r, oth, a, st);
-    LevelVecs<T> vc = level_vecs<T>(h, base, l + 1);
-    k_mg_restrict<T><<<wave_grid(p, 0, b_restr, (gc.n + 255) / 256), 256, 0, s>>>(oth, g.nx, g.ny, g.nz, g.nx, vc.r, gc,
-                                                                                   st);
+    k_mg_coarse<T, M_RESID, PACKED><<<Grs, B, 0, s>>>(cur, v.r, oth, a, st);
+    k_mg_restrict<T><<<Gre, B, 0, s>>>(oth, g.nx, g.ny, g.nz, g.nx, vc.r, gc, st);
     T* zc = vcycle_coarse<T>(p, h, base, l + 1, st, s);
-    k_mg_coarse_prolong<T><<<G_prol, 256, 0, s>>>(cur, zc, a, st);
-    k_mg_coarse<T, M_SWEEP><<<G_sweep, 256, 0, s>>>(cur, v.r, oth, a, st);
-    std::swap(cur, oth);
-    for (int i = 1; i < nu; ++i) {
-        k_mg_coarse<T, M_SWEEP><<<G_sweep, 256, 0, s>>>(cur, v.r, oth, a, st);
+    k_mg_coarse_prolong<T><<<Gpr, B, 0, s>>>(cur, zc, a, st);
+    for (int i = 0; i < nu; ++i) {
+        k_mg_coarse<T, M_SWEEP, PACKED><<<Gsw, B, 0, s>>>(cur, v.r, oth, a, st);
         std::swap(cur, oth);
     }
     return cur;
@@ -863,8 +896,14 @@ osmodi_status mg_build(osmodi_plan p, cudaStream_t s) {
         nz = c.nz;
     }
     if (lv.empty()) return OSMODI_OK;  // grid already coarse: plain CG
+    // a level-l face joins at most 2^(l (ndim - 1)) fine faces: the counts
+    // fit the packed 10-bit fields while l (ndim - 1) <= 9
+    auto packable = [&](size_t q) { return (int)(q + 1) * (p->ndim - 1) <= 9; };
     size_t bytes = 0;
-    for (const Level& c : lv) bytes += 4 * ((c.n * sizeof(float) + 255) & ~size_t(255));
+    for (size_t q = 0; q < lv.size(); ++q) {
+        const size_t one = (lv[q].n * sizeof(float) + 255) & ~size_t(255);
+        bytes += (packable(q) ? 5 : 4) * one;
+    }
     Hier* h = new (std::nothrow) Hier;
     if (!h) return OSMODI_E_NOMEM;
     unsigned long long* cnt = nullptr;
@@ -875,13 +914,16 @@ osmodi_status mg_build(osmodi_plan p, cudaStream_t s) {
         return OSMODI_E_NOMEM;
     }
     char* b = reinterpret_cast<char*>(h->mem);
-    for (Level& c : lv) {
+    for (size_t q = 0; q < lv.size(); ++q) {
+        Level& c = lv[q];
         const size_t one = (c.n * sizeof(float) + 255) & ~size_t(255);
         c.wx = reinterpret_cast<float*>(b);
         c.wy = reinterpret_cast<float*>(b + one);
         c.wz = reinterpret_cast<float*>(b + 2 * one);
         c.dinv = reinterpret_cast<float*>(b + 3 * one);
-        b += 4 * one;
+        c.wc = packable(q) ? reinterpret_cast<uint32_t*>(b + 4 * one) : nullptr;
+        for (int a = 0; a < 3; ++a) c.F[a] = (float)p->k.F[a];
+        b += (packable(q) ? 5 : 4) * one;
     }
     h->lv = lv;
     p->mg = h;
@@ -890,6 +932,8 @@ osmodi_status mg_build(osmodi_plan p, cudaStream_t s) {
     k_mg_setup_fine<<<grid_for(p, lv[0].n), 256, 0, s>>>(p->code8, fd, lv[0]);
     for (size_t q = 1; q < lv.size(); ++q) k_mg_setup_coarse<<<grid_for(p, lv[q].n), 256, 0, s>>>(lv[q - 1], lv[q]);
     for (size_t q = 0; q < lv.size(); ++q) k_mg_setup_dinv<<<grid_for(p, lv[q].n), 256, 0, s>>>(lv[q], cnt + q);
+    for (size_t q = 0; q < lv.size(); ++q)
+        if (lv[q].wc) k_mg_pack<<<grid_for(p, lv[q].n), 256, 0, s>>>(lv[q]);
     OSM_CUDA(cudaGetLastError());
     std::vector<unsigned long long> hc(lv.size());
     OSM_CUDA(cudaMemcpyAsync(hc.data(), cnt, sizeof(unsigned long long) * lv.size(), cudaMemcpyDeviceToHost, s));

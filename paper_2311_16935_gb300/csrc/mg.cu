@@ -496,6 +496,43 @@ __device__ __forceinline__ T coarse_az(const CoarseRow<T>& c, const T* z, T zc0,
     return az;
 }
 
+// Packed level: omega / D and (A z)_q with every load issued at once (the
+// four count words and the six neighbour values; one memory round trip).
+// Addresses are clamped to the box; a face on the box boundary has count 0,
+// and the word before the first cell of a row / plane belongs to a cell
+// whose +x / +y count is 0, so only the box start needs a mask.
+template <class T, bool AZ>
+__device__ __forceinline__ void packed_cell(const Level& g, const T* z, T omega, int64_t q, int64_t sy, int64_t sz,
+                                            T& wd, T& az, T& zc0) {
+    const int64_t n = g.n;
+    const int64_t qxm = q >= 1 ? q - 1 : q, qym = q >= sy ? q - sy : q, qzm = q >= sz ? q - sz : q;
+    const uint32_t w0 = __ldg(g.wc + q), w1 = __ldg(g.wc + qxm), w2 = __ldg(g.wc + qym), w3 = __ldg(g.wc + qzm);
+    T zxp = T(0), zxm = T(0), zyp = T(0), zym = T(0), zzp = T(0), zzm = T(0);
+    zc0 = T(0);
+    if (AZ) {
+        const int64_t qxp = q + 1 < n ? q + 1 : q, qyp = q + sy < n ? q + sy : q, qzp = q + sz < n ? q + sz : q;
+        zc0 = z[q];
+        zxp = z[qxp];
+        zxm = z[qxm];
+        zyp = z[qyp];
+        zym = z[qym];
+        zzp = z[qzp];
+        zzm = z[qzm];
+    }
+    const T xp = (T)((float)(w0 & 1023u) * g.F[0]), yp = (T)((float)((w0 >> 10) & 1023u) * g.F[1]);
+    const T zp = (T)((float)(w0 >> 20) * g.F[2]);
+    const T xm = q >= 1 ? (T)((float)(w1 & 1023u) * g.F[0]) : T(0);
+    const T ym = q >= sy ? (T)((float)((w2 >> 10) & 1023u) * g.F[1]) : T(0);
+    const T zm = q >= sz ? (T)((float)(w3 >> 20) * g.F[2]) : T(0);
+    const T d = xp + xm + yp + ym + zp + zm;
+    wd = d > T(0) ? omega / d : T(0);
+    if (AZ)
+        az = xp * (zc0 - zxp) + xm * (zc0 - zxm) + yp * (zc0 - zyp) + ym * (zc0 - zym) + zp * (zc0 - zzp) +
+             zm * (zc0 - zzm);
+    else
+        az = T(0);
+}
+
 // MODE M_FIRST: out = omega D^-1 r; M_SWEEP: out = z + omega D^-1 (r - A z);
 // M_RESID: out = r - A z
 template <class T, int MODE, bool PACKED>
@@ -505,6 +542,13 @@ __global__ void k_mg_coarse(const T* __restrict__ z, const T* __restrict__ r,
     const Level& g = a.lv;
     const int64_t sy = g.nx, sz = g.nx * g.ny;
     for_cells(g.nx, g.ny, g.nz, [&](int64_t i, int64_t j, int64_t k, int64_t q) {
+        if (PACKED) {
+            T wd, az, zc0;
+            const T rq = r[q];
+            packed_cell<T, MODE != M_FIRST>(g, z, a.omega, q, sy, sz, wd, az, zc0);
+            out[q] = MODE == M_FIRST ? wd * rq : (MODE == M_RESID ? rq - az : zc0 + wd * (rq - az));
+            return;
+        }
         const CoarseRow<T> c = coarse_row<T, PACKED>(g, a.omega, i, j, k, q);
         if (MODE == M_FIRST) {
             out[q] = c.wd * r[q];
@@ -531,14 +575,29 @@ __global__ void k_mg_coarse_rb(T* z, const T* __restrict__ r, CoarseArgs<T> a,
         const int col = (int)((i + j + k) & 1);
         if (FIRST) {
             if (col == 0) {
-                const CoarseRow<T> c = coarse_row<T, PACKED>(g, a.omega, i, j, k, q);
-                z[q] = c.wd * r[q];
+                T wd;
+                if (PACKED) {
+                    T az, zc0;
+                    const T rq = r[q];
+                    packed_cell<T, false>(g, z, a.omega, q, sy, sz, wd, az, zc0);
+                    z[q] = wd * rq;
+                } else {
+                    const CoarseRow<T> c = coarse_row<T, PACKED>(g, a.omega, i, j, k, q);
+                    z[q] = c.wd * r[q];
+                }
             } else {
                 z[q] = T(0);
             }
             return;
         }
         if (col != COLOR) return;
+        if (PACKED) {
+            T wd, az, zc0;
+            const T rq = r[q];
+            packed_cell<T, true>(g, z, a.omega, q, sy, sz, wd, az, zc0);
+            z[q] = zc0 + wd * (rq - az);
+            return;
+        }
         const CoarseRow<T> c = coarse_row<T, PACKED>(g, a.omega, i, j, k, q);
         const T zc0 = z[q];
         z[q] = zc0 + c.wd * (r[q] - coarse_az(c, z, zc0, q, sy, sz));

@@ -263,42 +263,53 @@ __global__ void k_source_ff(const TG* __restrict__ f, const TP* __restrict__ p_i
             row = idx / g.px;
             i = idx - row * g.px;
         }
+        // every load is issued before the code word is looked at (one memory
+        // round trip per cell instead of two); neighbour offsets are clamped
+        // to the array, and values at missing faces are never used
+        const bool in_row = i < g.nx;
+        const int64_t d = in_row ? row * g.nx + i : 0;
         const unsigned cw = code8[idx];
-        if (i >= g.nx || !(cw & 0x80u)) {
+        TG fc[NDIM], fp[NDIM], fm[NDIM];
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const TG* fa = f + a * g.n_dense + d;
+            fc[a] = fa[0];
+            fp[a] = d + sd[a] < g.n_dense ? fa[sd[a]] : fc[a];
+            fm[a] = d >= sd[a] ? fa[-sd[a]] : fc[a];
+        }
+        const TP v = p_in ? p_in[d] : TP(0);
+        if (!in_row || !(cw & 0x80u)) {
             bh[idx] = 0.f;
             bl[idx] = 0.f;
             ph[idx] = 0.f;
             pl[idx] = 0.f;
             continue;
         }
-        const int64_t d = row * g.nx + i;
         FF s{0.f, 0.f};
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {
             const unsigned bp = (cw >> (2 * a)) & 1u, bm = (cw >> (2 * a + 1)) & 1u;
             if (!(bp | bm)) continue;
-            const TG* fa = f + a * g.n_dense + d;
             FF t;
             if constexpr (sizeof(TG) == 4) {
                 // the sum or difference of two FP32 values is exact as a pair
-                if (bp & bm) t = ff_sum2(fa[sd[a]], -fa[-sd[a]]);
-                else if (bp) t = ff_sum2(fa[sd[a]], fa[0]);
-                else t = ff_sum2(-fa[-sd[a]], -fa[0]);
+                if (bp & bm) t = ff_sum2(fp[a], -fm[a]);
+                else if (bp) t = ff_sum2(fp[a], fc[a]);
+                else t = ff_sum2(-fm[a], -fc[a]);
             } else {
                 double td;
-                if (bp & bm) td = (double)fa[sd[a]] - (double)fa[-sd[a]];
-                else if (bp) td = (double)fa[sd[a]] + (double)fa[0];
-                else td = -((double)fa[-sd[a]] + (double)fa[0]);
+                if (bp & bm) td = (double)fp[a] - (double)fm[a];
+                else if (bp) td = (double)fp[a] + (double)fc[a];
+                else td = -((double)fm[a] + (double)fc[a]);
                 t = ff_from_double(td);
             }
             s = ff_add(s, ff_mul(g.coef[a], t));
         }
 #pragma unroll
         for (int a = 0; a < NDIM; ++a)
-            if (!isfinite(f[a * g.n_dense + d])) bad |= 1;  // in the input's own precision
+            if (!isfinite(fc[a])) bad |= 1;  // in the input's own precision
         FF p0{0.f, 0.f};
         if (p_in) {
-            const TP v = p_in[d];
             if (!isfinite(v)) bad |= 2;
             if constexpr (sizeof(TP) == 4) {
                 p0 = FF{v, 0.f};
@@ -464,7 +475,11 @@ __global__ void k_output_ff(const float* __restrict__ ph, const uint8_t* __restr
         }
         if (i >= nx) continue;
         const int64_t d = row * nx + i;
-        if (!(code8[idx] & 0x80u)) {
+        // loads first (one memory round trip per cell)
+        const unsigned cw = code8[idx];
+        const float h = ph[idx], lo = pl[idx];
+        const TP pu0 = zero0 ? TP(0) : p_user[d];
+        if (!(cw & 0x80u)) {
             p_user[d] = (TP)NAN;
             continue;
         }
@@ -477,10 +492,10 @@ __global__ void k_output_ff(const float* __restrict__ ph, const uint8_t* __restr
         }
         // P - mean as a pair (FP32 arithmetic), then the one FP64 addition
         // that forms the output value
-        const FF vf = ff_add(FF{ph[idx], pl[idx]}, FF{-mf.hi, -mf.lo});
+        const FF vf = ff_add(FF{h, lo}, FF{-mf.hi, -mf.lo});
         const double v = (double)vf.hi + (double)vf.lo;
         // the seed distance is a reported statistic: FP32 terms suffice
-        const float dv = zero0 ? -vf.hi : (float)(((double)p_user[d] - m0) - v);
+        const float dv = zero0 ? -vf.hi : (float)(((double)pu0 - m0) - v);
         a_d.add(dv * dv);
         a_v.add(vf.hi * vf.hi);
         p_user[d] = (TP)v;

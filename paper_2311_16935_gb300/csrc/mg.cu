@@ -909,7 +909,9 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
     }
     T* cur = w.zA;
     T* oth = w.zB;
+    if (nu == 1) mark(0);  // profile: time the one pre-sweep there is
     k_mg_fine<T, NDIM, M_FIRST, false><<<G_first, 256, 0, s>>>(nullptr, r, cur, p->code8, f, st, partials);
+    if (nu == 1) mark(1);
     for (int i = 1; i < nu; ++i) {
         if (i == 1) mark(0);
         k_mg_fine<T, NDIM, M_SWEEP, false><<<G_sweep, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
@@ -924,14 +926,13 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
     // neighbour's parent lookup made that kernel twice as slow as the two apart
     k_mg_fine_prolong<T, NDIM><<<G_prol, 256, 0, s>>>(cur, zc, f, st);
     mark(2);
-    k_mg_fine<T, NDIM, M_SWEEP, false><<<G_sweep, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
-    mark(3);
-    std::swap(cur, oth);
-    for (int i = 1; i < nu; ++i) {
+    // nu post-sweeps; the last one also forms (r, z) and finishes the CG state
+    for (int i = 0; i < nu; ++i) {
         if (i == nu - 1)
             k_mg_fine<T, NDIM, M_SWEEP, true><<<G_dot, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
         else
             k_mg_fine<T, NDIM, M_SWEEP, false><<<G_sweep, 256, 0, s>>>(cur, r, oth, p->code8, f, st, partials);
+        if (i == 0) mark(3);
         std::swap(cur, oth);
     }
     return cur;

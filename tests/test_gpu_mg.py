@@ -106,3 +106,19 @@ def test_preconditioner_timing_is_reported(osm):
     assert res.status == osm.OK
     assert ks["precond_applications"] > 0 and ks["precond_ms"] > 0
     assert ks["precond_applications"] <= ks["cg_update_launches"]
+
+
+@pytest.mark.parametrize("sweeps,scale", [(1, 1.8), (3, 2.0), (2, 1.0), (1, 3.5)])
+def test_smoothing_options_keep_the_fixed_point(osm, sweeps, scale):
+    """options.mg_sweeps / mg_scale change the preconditioner, never the
+    answer: any positive scale keeps it symmetric positive definite, so CG
+    reaches the oracle's fixed point (3-D red-black and 2-D Jacobi)."""
+    for shape, spacing in (((21, 26, 30), (1.0, 1.1, 0.9)), ((45, 61), (0.2, 0.2))):
+        rng = np.random.default_rng(7 + sweeps)
+        valid = rng.random(shape) > 0.15
+        f = rng.normal(size=(len(shape),) + shape)
+        want = oracle.solve_direct(oracle.Grid(valid, spacing), f)
+        _, res, got = _solve(osm, f, valid, spacing, 1e-12, precision=0, precond=1, mg_sweeps=sweeps,
+                             mg_scale=scale)
+        assert res.status == osm.OK, res.as_dict()
+        assert _rel(got, want, valid) < 1e-10

@@ -128,7 +128,7 @@ typedef struct {
                             black then red after; 2-D damped Jacobi; a fixed symmetric
                             operator, so CG still converges to the same fixed point in far
                             fewer iterations);
-                            0 = plain CG.  Built at plan creation (about 2 B of device memory per
+                            0 = plain CG.  Built at plan creation (about 2.5 B of device memory per
                             cell); grids of at most 8 cells per axis use plain CG.
                             Not part of the paper's method. */
     int zero_start;      /* 1 = start from P^0 = 0 without reading p: p is output only

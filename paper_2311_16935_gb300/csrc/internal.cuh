@@ -2,15 +2,18 @@
 //
 // Data layout in device memory (every vector the iterations touch):
 //   a padded box of px x ny x nz cells, px = nx rounded up to a multiple of 4,
-//   x fastest.  Cells with i >= nx are padding: their codes are 0 (missing),
+//   x fastest.  Cells with i >= nx are padding: their codes mark them missing,
 //   so they never contribute.  Four consecutive cells of a row form one
 //   "chunk" that a thread loads with one 16-byte (FP32) or two 16-byte (FP64)
 //   accesses; a chunk never straddles two rows.
 //
 // Per-cell neighbour codes (built once per plan from the mask, Section 2.2):
 //   code8  bit f (f = 0..5 for E, W, N, S, F, B) = face neighbour f valid,
-//          bit 7 = the cell itself valid; 0 for missing cells.  Enough for the
-//          fixed-point operator, whose off-diagonal entries are b~_j F_j/A_tot.
+//          bit 6 = (j + k) mod 2 of the cell's row (the red-black colour of
+//          the row's even cells; set on every cell, missing or not),
+//          bit 7 = the cell itself valid; readers mask the bits they use.
+//          Enough for the fixed-point operator, whose off-diagonal entries
+//          are b~_j F_j/A_tot.
 //   code32 five bits per face f at bits 5f..5f+4: ray-count class k of that
 //          face, 0 if the neighbour is missing, else
 //          k = 1 + s_lo + 3 s_hi + 9 far, where s_lo / s_hi count the valid

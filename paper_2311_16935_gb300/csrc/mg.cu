@@ -249,17 +249,9 @@ __global__ void __launch_bounds__(256) k_mg_fine_rb(T* z, const T* __restrict__ 
         const int64_t i0 = ch * 4;
         const uint32_t cw = act ? __ldg(reinterpret_cast<const uint32_t*>(code8 + i0)) : 0u;
         const V4<T> rv = act ? ld4(r + i0) : zero4<T>();
-        // colour of the chunk's first cell (its x index is a multiple of 4)
-        int par = 0;
-        if (act) {
-            if (g.idx32) {
-                const uint32_t row = (uint32_t)ch / (uint32_t)g.cpr;
-                par = NDIM == 3 ? (int)((row % (uint32_t)g.ny + row / (uint32_t)g.ny) & 1u) : (int)(row & 1u);
-            } else {
-                const int64_t row = ch / g.cpr;
-                par = NDIM == 3 ? (int)((row % g.ny + row / g.ny) & 1) : (int)(row & 1);
-            }
-        }
+        // colour of the chunk's first cell (its x index is a multiple of 4):
+        // bit 6 of its code byte holds (j + k) mod 2
+        const int par = (int)((cw >> 6) & 1u);
         V4<T> o;
         if (FIRST) {
 #pragma unroll

@@ -204,10 +204,12 @@ __global__ void k_build_codes(MaskView mv, int64_t px, int64_t n_box, uint8_t* c
         int64_t row = idx / px;
         int64_t i = idx - row * px;
         int64_t j = row % mv.ny, k = row / mv.ny;
-        uint8_t c8 = 0;
+        // bit 6 of every byte: (j + k) mod 2, the red-black colour of the
+        // row's even cells (the colour of a 4-cell chunk's first cell)
+        uint8_t c8 = (uint8_t)(((j + k) & 1) << 6);
         uint32_t c32 = 0;
         if (i < mv.nx && mv.at(i, j, k)) {
-            c8 = 0x80;
+            c8 |= 0x80;
             c32 = 0x80000000u;
             ++local;
             for (int f = 0; f < 2 * NDIM; ++f) {

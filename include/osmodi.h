@@ -139,6 +139,11 @@ typedef struct {
     double mg_scale;     /* precond = 1: scale of the coarse correction, (0, 4]; 0 = the
                             default, 2.0.  Any positive scale keeps the preconditioner
                             symmetric positive definite; it changes the iteration count */
+    int refine_ff;       /* FP32 precisions: 1 = carry the refinement loop (P, b, the
+                            residual r = b - L P, the fold P += e, the output) in
+                            float-float arithmetic (pairs of FP32 numbers, about 48
+                            bits) at tolerances >= 1e-9, FP64 below; 0 (default) = FP64
+                            throughout the refinement loop */
 } osmodi_options;
 
 typedef struct {

@@ -355,6 +355,7 @@ extern "C" osmodi_status osmodi_create(int ndim, const int64_t dims[3], const do
     if (o.accel < 0 || o.accel > kAaMaxDepth) return OSMODI_E_INVALID;
     if (o.precond != 0 && o.precond != 1) return OSMODI_E_INVALID;
     if (o.mg_sweeps < 0 || o.mg_sweeps > 8 || !(o.mg_scale >= 0.0 && o.mg_scale <= 4.0)) return OSMODI_E_INVALID;
+    if (o.refine_ff != 0 && o.refine_ff != 1) return OSMODI_E_INVALID;
 
     osmodi_plan p = new (std::nothrow) osmodi_plan_s();
     if (!p) return OSMODI_E_NOMEM;

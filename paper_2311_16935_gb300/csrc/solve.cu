@@ -2258,10 +2258,10 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
 
     // 1. source and initial pressure
     SrcGeo sg{p->px, p->nx, p->ny, p->nz, p->n_dense, p->n_box, {p->k.F[0], p->k.F[1], p->k.F[2]}, {p->h[0], p->h[1], p->h[2]}};
-    // float-float refinement for the FP32 precisions down to kFFMinTol (its
-    // residual floor, a few 2^-48 of |F p| against |b|, stays far below that);
-    // tighter tolerances and the FP64 precision refine in FP64
-    const bool ff = sizeof(T) == 4 && tol >= kFFMinTol;
+    // float-float refinement (options.refine_ff) for the FP32 precisions
+    // down to kFFMinTol (its residual floor, a few 2^-48 of |F p| against
+    // |b|, stays far below that); otherwise, and by default, FP64
+    const bool ff = sizeof(T) == 4 && p->opt.refine_ff == 1 && tol >= kFFMinTol;
     {
         const void* p_in = p->opt.zero_start ? nullptr : pu;
         SrcGeoFF sgf{p->px, p->nx, p->ny, p->nz, p->n_dense, p->n_box, {}};

@@ -32,7 +32,7 @@ class osmodi_options(ctypes.Structure):
                 ("threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("profile", ctypes.c_int),
                 ("slab", ctypes.c_int), ("flat_sweeps", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("accel", ctypes.c_int), ("precond", ctypes.c_int), ("zero_start", ctypes.c_int),
-                ("mg_sweeps", ctypes.c_int), ("mg_scale", ctypes.c_double)]
+                ("mg_sweeps", ctypes.c_int), ("mg_scale", ctypes.c_double), ("refine_ff", ctypes.c_int)]
 
 
 class osmodi_result(ctypes.Structure):

@@ -65,7 +65,7 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
     assert lib.osmodi_create(2, dims, sp, None, ctypes.byref(o), None, ctypes.byref(h)) == osmodi.E_INVALID
     # multigrid smoothing sweeps 1..8 and coarse scale (0, 4] (0 = default)
     for field, value in (("mg_sweeps", 9), ("mg_sweeps", -1), ("mg_scale", -0.5), ("mg_scale", 4.5),
-                         ("mg_scale", float("nan"))):
+                         ("mg_scale", float("nan")), ("refine_ff", 2)):
         lib.osmodi_default_options(ctypes.byref(o))
         setattr(o, field, value)
         assert lib.osmodi_create(2, dims, sp, None, ctypes.byref(o), None, ctypes.byref(h)) == osmodi.E_INVALID
@@ -86,6 +86,7 @@ def test_default_options(lib):
     assert o.precision == osmodi.FP32_REFINE and o.scheme == osmodi.FPCG
     assert o.check_every >= 0 and o.max_refine >= 1
     assert o.mg_sweeps == 0 and o.mg_scale == 0.0 and o.zero_start == 0 and o.precond == 0
+    assert o.refine_ff == 0  # FP64 refinement unless asked
 
 
 def test_product_does_not_import_oracle():

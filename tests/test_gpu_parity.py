@@ -519,10 +519,10 @@ FF_CASES = [
 @pytest.mark.parametrize("precond", [0, 1])
 @pytest.mark.parametrize("case", range(len(FF_CASES)))
 def test_float_float_refinement(osm, case, precond):
-    """The FP32 precisions refine in float-float arithmetic at tolerances >=
-    1e-9: the eps_R they report must be the FP64 residual of the pressure they
-    return (the oracle's Eq. ResidualMomentum), within the float-float
-    arithmetic's floor, and below the tolerance."""
+    """With options.refine_ff the FP32 precisions refine in float-float
+    arithmetic at tolerances >= 1e-9: the eps_R they report must be the FP64
+    residual of the pressure they return (the oracle's Eq. ResidualMomentum),
+    within the float-float arithmetic's floor, and below the tolerance."""
     shape, spacing, dens, off, gdt, pdt = FF_CASES[case]
     rng = np.random.default_rng(90 + case)
     valid = rng.random(shape) > 1.0 - dens
@@ -533,7 +533,7 @@ def test_float_float_refinement(osm, case, precond):
         p0 = off + 0.1 * rng.normal(size=shape)
     for tol in (1e-8, 1e-9):
         plan, res, got = _solve(osm, f, valid.astype(np.uint8), spacing, tol, p0=p0, pdtype=pdt, precision=2,
-                                precond=precond)
+                                precond=precond, refine_ff=1)
         assert res.status == osm.OK, res.as_dict()
         assert np.isnan(got[~valid]).all()
         true_eps = oracle.residual(grid, f.astype(np.float64), np.where(valid, got, 0.0))

@@ -46,17 +46,20 @@ def test_sincos_128_full(osm):
 
 
 def test_blobs_500_full_residual_and_crop(osm):
-    """500^3 blobs (the benchmark's workload, same launch configuration): the
+    """500^3 blobs (the benchmark's workload and launch configuration: FP32
+    sweeps with the multigrid preconditioner inside the FP64 refinement): the
     oracle's independent per-cell FP64 evaluation of eps_R over all 125 M
     cells confirms the reported eps_R <= 1e-8; sampled cells agree
     individually; a 100^3 crop of the same generator matches the oracle's
-    solve to 1e-10."""
+    solve to 1e-10, with and without the preconditioner."""
     n = 500
     prob = inputs.gaussian_blobs_3d(n=(n, n, n), device="cuda", dtype=torch.float32)
-    plan = osm.Plan(3, (n, n, n), (1.0, 1.0, 1.0), None, precision=osm.FP32_REFINE)
+    plan = osm.Plan(3, (n, n, n), (1.0, 1.0, 1.0), None, precision=osm.FP32_REFINE, precond=1)
     p = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
     res = plan.solve(prob.grad, p, 1e-8)
     assert res.status == osm.OK and res.eps_R <= 1e-8
+    assert res.inner_iters < 40  # the multigrid-preconditioned iteration count, not plain CG's thousands
+    plan.close()
     f = prob.grad.cpu().double().numpy()
     P = p.cpu().numpy()
     del prob, p
@@ -77,13 +80,14 @@ def test_blobs_500_full_residual_and_crop(osm):
     params = inputs.blob_params(20, (n, n, n), (5.0, 40.0), 4)
     crop = inputs.gaussian_blobs_3d(n=(c, c, c), origin=(200, 200, 200), box=(n, n, n), params=params, device="cpu",
                                     dtype=torch.float32)
-    planc = osm.Plan(3, (c, c, c), (1.0, 1.0, 1.0), None, precision=osm.FP32_REFINE)
-    pc = torch.zeros((c, c, c), dtype=torch.float64, device="cuda")
-    rc = planc.solve(crop.grad.cuda(), pc, 1e-12)
-    assert rc.status == osm.OK
     gridc = oracle.Grid(np.ones((c, c, c), bool), (1.0, 1.0, 1.0))
     want, it, r = oracle.solve_cg(gridc, crop.grad.double().numpy(), tol=1e-14, maxit=20000)
-    assert _rel(pc.cpu().numpy(), want, gridc.valid) <= 1e-10
+    for precond in (0, 1):
+        planc = osm.Plan(3, (c, c, c), (1.0, 1.0, 1.0), None, precision=osm.FP32_REFINE, precond=precond)
+        pc = torch.zeros((c, c, c), dtype=torch.float64, device="cuda")
+        rc = planc.solve(crop.grad.cuda(), pc, 1e-12)
+        assert rc.status == osm.OK
+        assert _rel(pc.cpu().numpy(), want, gridc.valid) <= 1e-10
 
 
 def test_piv_batch_full_size_instances(osm):
@@ -102,3 +106,21 @@ def test_piv_batch_full_size_instances(osm):
         want, it, e = oracle.solve_cg(grid, pr.grad.double().numpy(), tol=1e-14, maxit=40000)
         assert _rel(p.cpu().numpy(), want, valid) <= 1e-9
         assert r.eps_R <= 1e-11
+
+
+def test_piv_full_size_instances_multigrid_streams(osm):
+    """The same full-size PIV instances through the benchmark's second PIV
+    path: osmodi_solve_many with the multigrid preconditioner (2-D damped
+    Jacobi smoothing) on several streams, each against the oracle."""
+    probs = [inputs.piv_snapshot_2d(i) for i in range(6)]
+    plans = [osm.Plan(2, pr.dims, pr.spacing, pr.mask.cuda(), precond=1) for pr in probs]
+    grads = [pr.grad.cuda() for pr in probs]
+    ps = [torch.zeros(pr.mask.shape, dtype=torch.float64, device="cuda") for pr in probs]
+    st, res = osm.Many(plans, streams=3).solve(grads, ps, 1e-11)
+    assert st == osm.OK
+    for pr, p, r in zip(probs, ps, res):
+        valid = pr.mask.numpy().astype(bool)
+        grid = oracle.Grid(valid, pr.spacing)
+        want, it, e = oracle.solve_cg(grid, pr.grad.double().numpy(), tol=1e-14, maxit=40000)
+        assert _rel(p.cpu().numpy(), want, valid) <= 1e-9
+        assert r.eps_R <= 1e-11 and r.inner_iters < 200

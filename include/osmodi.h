@@ -272,7 +272,9 @@ OSMODI_API osmodi_status osmodi_solve_noalloc(osmodi_plan plan, const void* grad
  * CUDA streams that as many host threads drive concurrently.  Problem i runs
  * on stream i mod streams with workspaces[i mod streams], which must hold
  * osmodi_workspace_bytes() of every plan assigned to it; a problem's plan is
- * used by one thread only.  grads / ps / dtypes as osmodi_solve_batched.
+ * used by one thread only: a plan listed more than once must appear only at
+ * indices that map to the same stream (else OSMODI_E_INVALID, nothing run).
+ * grads / ps / dtypes as osmodi_solve_batched.
  * Synchronous: returns when every problem has finished.  Returns OK when all
  * converged, NOT_CONVERGED if any did not, NAN_INPUT if one had non-finite
  * input, else the first error (the others stop at their next problem).

@@ -12,6 +12,7 @@
 #include <cstring>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.cuh"
@@ -28,6 +29,16 @@ extern "C" osmodi_status osmodi_solve_many(int count, const osmodi_plan* plans, 
         if (plans[i]->device != dev) return OSMODI_E_INVALID;
     }
     const int K = streams < count ? streams : count;
+    // a plan holds per-solve host state (its mirror, graphs, events): one
+    // plan listed twice must land on the same stream, whose thread solves
+    // its problems one after the other
+    {
+        std::unordered_map<osmodi_plan, int> stream_of;
+        for (int i = 0; i < count; ++i) {
+            auto it = stream_of.emplace(plans[i], i % K).first;
+            if (it->second != i % K) return OSMODI_E_INVALID;
+        }
+    }
     for (int w = 0; w < K; ++w) {
         if (!workspaces[w]) return OSMODI_E_WORKSPACE;
         // the workspace of stream w must fit every problem it takes

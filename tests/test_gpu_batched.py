@@ -224,3 +224,28 @@ def test_solve_many_streams_match_oracle(osm, precond):
         p1 = torch.zeros_like(ps[k])
         r1 = plans[k].solve(grads[k], p1, 1e-12)
         assert r1.inner_iters == res[k].inner_iters
+
+
+def test_solve_many_rejects_a_plan_shared_across_streams(osm):
+    """A plan carries per-solve host state: listed twice, it must map to one
+    stream (indices congruent mod the stream count), else nothing runs."""
+    inst = _random_instances(3, 4)
+    plans = [osm.Plan(2, v.shape[::-1], sp, torch.from_numpy(v.astype(np.uint8)).cuda()) for v, sp, _ in inst]
+    grads = [torch.from_numpy(f).float().cuda() for _, _, f in inst]
+
+    def buffers(order):  # each problem's gradient and a pressure of its plan's shape
+        return ([grads[k] for k in order],
+                [torch.zeros(inst[k][0].shape, dtype=torch.float64, device="cuda") for k in order])
+
+    # plans[0] at indices 0 and 1 on two streams: rejected
+    g_bad, p_bad = buffers([0, 0, 1])
+    st, _ = osm.Many([plans[0], plans[0], plans[1]], streams=2).solve(g_bad, p_bad, 1e-10, check=False)
+    assert st == osm.E_INVALID
+    # plans[0] at indices 0 and 2 on two streams (both on stream 0): solved in turn
+    g_ok, p_ok = buffers([0, 1, 0])
+    st, res = osm.Many([plans[0], plans[1], plans[0]], streams=2).solve(g_ok, p_ok, 1e-10)
+    assert st == osm.OK and all(r.status == osm.OK for r in res)
+    # the same problem solved twice in turn: the same answer, bit for bit
+    # (missing cells are NaN in both)
+    assert torch.equal(torch.isnan(p_ok[0]), torch.isnan(p_ok[2]))
+    assert torch.equal(torch.nan_to_num(p_ok[0], nan=0.0), torch.nan_to_num(p_ok[2], nan=0.0))

@@ -98,3 +98,31 @@ def test_product_does_not_import_oracle():
                 txt = open(os.path.join(dirpath, fn)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", txt, re.M), fn
                 assert "liboracle" not in txt, fn
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: a missing libosmodi.so is an ImportError at the first
+    call, not a silent substitute."""
+    from paper_2311_16935_gb300 import osmodi
+
+    monkeypatch.setattr(osmodi, "LIB_PATH", str(tmp_path / "libosmodi_missing.so"))
+    monkeypatch.setattr(osmodi, "_lib", None)
+    with pytest.raises(ImportError):
+        osmodi.default_options()
+
+
+def test_binding_argument_checks(lib):
+    """Host-side checks of the binding, before any device work."""
+    import torch
+    from paper_2311_16935_gb300 import osmodi
+
+    with pytest.raises(TypeError):
+        osmodi.default_options(no_such_option=1)
+    o = osmodi.default_options(precond=1, mg_sweeps=3, mg_scale=1.5, refine_ff=1, zero_start=1)
+    assert (o.precond, o.mg_sweeps, o.mg_scale, o.refine_ff, o.zero_start) == (1, 3, 1.5, 1, 1)
+    with pytest.raises(ValueError):
+        osmodi._check_cuda(torch.zeros(4), "grad")  # a host tensor is not a device buffer
+    with pytest.raises(ValueError):
+        osmodi._check_solve_buffer(torch.zeros(4), "grad")  # nor is unpinned host memory
+    with pytest.raises(ValueError):
+        osmodi._check_solve_buffer(torch.zeros(4, 4).t(), "grad")  # nor a strided view

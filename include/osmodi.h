@@ -152,7 +152,8 @@ typedef struct {
     int64_t inner_iters;     /* CG iterations or Jacobi sweeps, all steps together */
     int refine_steps;        /* FP64 residual evaluations r = b - A p */
     double eps_R;            /* Eq. ResidualMomentum of the returned pressure, in FP64 */
-    double eps_P;            /* OUTER: Eq. ResidualPressure of the last outer iteration */
+    double eps_P;            /* OUTER: Eq. ResidualPressure of the last outer iteration
+                                (FPCG: 0, the scheme has no outer iterates) */
     double ms;               /* wall-clock of the call (host timer around the stream) */
     double point_updates;    /* valid cells x stencil applications (GLUPS numerator) */
     double seed_rel_dist;    /* ||P0 - P|| / ||P|| over valid cells, both gauge-fixed
@@ -250,9 +251,11 @@ OSMODI_API osmodi_status osmodi_solve_batched(int count, const osmodi_plan* plan
  * default FP32_REFINE / FPCG options that admits grids of up to about
  * 350,000 cells (e.g. 512 x 512 in 2D, 64^3 in 3D).
  *
- * The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress) and keeps it; make that first call before any
- * stream capture on that device.  All calls share the one array, which keeps
+ * osmodi_create looks the array's device address up on the plan's device
+ * (cudaGetSymbolAddress, which also loads the array there) and keeps it, so
+ * the solve itself finds the scratch ready; create plans before any stream
+ * capture on that device.  (Should that look-up have failed, the first solve
+ * on the device retries it.)  All calls share the one array, which keeps
  * the previous call's contents (every value the solve needs zeroed is
  * cleared at the start of each call).  Calls whose GPU work overlaps -- on
  * two streams, from two threads or on plans that share a device -- race on
@@ -323,8 +326,17 @@ OSMODI_API osmodi_status osmodi_batch_graph_results(osmodi_batch_graph graph, os
 OSMODI_API void osmodi_batch_graph_destroy(osmodi_batch_graph graph);
 
 /* eps_R of every outer iteration of the plan's last OUTER solve with
- * record_history set; copies min(cap, n) values, returns n. */
+ * record_history set; copies min(cap, n) values, returns n.  Entry 0 of each
+ * refinement step is the residual of its starting iterate, entry k the
+ * residual after k outer iterations of Algorithm 1. */
 OSMODI_API int osmodi_history(osmodi_plan plan, double* out_host, int cap);
+
+/* eps_P of Eq. ResidualPressure, ||P^{n+1} - P^n||_2 / ||P^{n+1}||_2 over the
+ * valid cells (P ungauged: the refinement's iterate plus the outer iterate),
+ * at the same evaluations as osmodi_history; NaN at the first entry of each
+ * refinement step (no previous outer iterate).  Copies min(cap, n) values to
+ * host memory, returns n. */
+OSMODI_API int osmodi_history_pressure(osmodi_plan plan, double* out_host, int cap);
 
 /*
  * Step-level entry points (the pieces of the solve, for checking each one
@@ -493,6 +505,29 @@ OSMODI_API void osmodi_net_destroy(osmodi_net net);
 OSMODI_API const char* osmodi_status_string(int status);
 /* Text of the last CUDA error seen by this thread (empty if none). */
 OSMODI_API const char* osmodi_last_cuda_error(void);
+
+/*
+ * Test knobs, for exercising the failure statuses without a GPU fault (no
+ * counterpart in the paper).  Process-wide; every later call reads them.
+ * Returns the previous value; OSMODI_DEBUG_DEFAULT restores the default.
+ *
+ * OSMODI_DEBUG_BARRIER_SPINS: polls (each followed by a ~64 ns sleep) a grid
+ *   barrier of the batched persistent kernel makes before it gives up, sets
+ *   the batch's error flag and lets every block return (the call then
+ *   reports OSMODI_E_TIMEOUT).  Default (0): 2^25, about 2 s.
+ * OSMODI_DEBUG_SKIP_BARRIER_BLOCK: the block of the batched persistent
+ *   kernel with this index returns before its first grid barrier, so the
+ *   other blocks' barrier runs out of polls.  Default (-1): none.
+ * OSMODI_DEBUG_CORRECTION_SCALE: osmodi_solve multiplies each refinement
+ *   step's correction by this factor before adding it (0: no scaling); a
+ *   large factor makes the residual grow and the solve report
+ *   OSMODI_E_DIVERGED.
+ */
+#define OSMODI_DEBUG_BARRIER_SPINS 1
+#define OSMODI_DEBUG_SKIP_BARRIER_BLOCK 2
+#define OSMODI_DEBUG_CORRECTION_SCALE 3
+#define OSMODI_DEBUG_DEFAULT (-0x7fffffffffffffffLL)
+OSMODI_API long long osmodi_debug_set(int knob, long long value);
 
 #ifdef __cplusplus
 }

@@ -31,6 +31,11 @@ What it computes, each piece written from the paper:
                             the ray integral (Eq. AE_Interior's (s, theta) integral,
                             classifying each ray by tracing it back one cell)
 * ``monte_carlo_constants_3d`` the 3D c_jk by Monte-Carlo ray tracing
+* ``rotating_ray_solve_2d``  whole straight rays at finite ray density (the
+                            rotating-parallel-ray integration whose limit of
+                            infinitely many rays the method takes), iterated;
+                            a trend check against the fixed point, not parity
+* ``pressure_update``       Eq. ResidualPressure
 
 Pressure is defined up to a constant (Eq. 1); every solve here returns the
 answer with zero mean on each connected component of valid cells and NaN on
@@ -332,7 +337,8 @@ def residual_at(grid: Grid, f, P, flat_idx) -> np.ndarray:
 
 
 def pressure_update(P_new, P_old, valid) -> float:
-    """eps_P of Eq. ResidualPressure over valid cells."""
+    """eps_P of Eq. ResidualPressure: ||P^{n+1} - P^n||_2 / ||P^{n+1}||_2, the
+    L2 norms over the valid cells; 0 when P^{n+1} = 0 there."""
     v = np.asarray(valid, dtype=bool)
     a = np.asarray(P_new)[v]
     b = np.asarray(P_old)[v]
@@ -419,8 +425,7 @@ def solve_literal(grid: Grid, f, tol: float = 1e-10, max_outer: int = 100000, P0
         Pn1 = lu.solve(Wnv @ P + Sv)
         n += 1
         er = 0.0 if snorm == 0 else float(np.linalg.norm(K @ Pn1 - Sv) / snorm)
-        nrm = np.linalg.norm(Pn1)
-        ep = 0.0 if nrm == 0 else float(np.linalg.norm(Pn1 - P) / nrm)
+        ep = pressure_update(Pn1, P, np.ones(Pn1.size, dtype=bool))
         if history:
             eps_r.append(er)
             eps_p.append(ep)
@@ -676,3 +681,134 @@ def brute_force_update_2d(grid: Grid, f, P_n, P_np1, n_t: int = 200, n_theta: in
                     num += m * (src + step)
             out[j, i] = num / den
     return out
+
+
+# --------------------------------------------------------------------------
+# Whole straight rays (the rotating-parallel-ray integration the method takes
+# to the limit of infinitely many rays, Section "Limit of Infinite Rays")
+# --------------------------------------------------------------------------
+
+def _line_cells_2d(x0, y0, ux, uy, nx, ny, hx, hy):
+    """Cells crossed, in order, by the line (x0, y0) + t (ux, uy), t over all
+    reals.  Cell (i, j) is the rectangle of half-widths hx/2, hy/2 about the
+    node (i hx, j hy).  Each piece of the line between two consecutive grid
+    lines lies in one cell, found from the piece's midpoint."""
+    lo = (-0.5 * hx, -0.5 * hy)
+    hi = ((nx - 0.5) * hx, (ny - 0.5) * hy)
+    t0, t1 = -np.inf, np.inf
+    for p, u, a, b in ((x0, ux, lo[0], hi[0]), (y0, uy, lo[1], hi[1])):
+        if u == 0.0:
+            if not a < p < b:
+                return []
+            continue
+        ta, tb = (a - p) / u, (b - p) / u
+        t0, t1 = max(t0, min(ta, tb)), min(t1, max(ta, tb))
+    if not t1 > t0:
+        return []
+    ts = [t0, t1]
+    if ux != 0.0:
+        ts += [t for t in (((k - 0.5) * hx - x0) / ux for k in range(nx + 1)) if t0 < t < t1]
+    if uy != 0.0:
+        ts += [t for t in (((k - 0.5) * hy - y0) / uy for k in range(ny + 1)) if t0 < t < t1]
+    ts.sort()
+    cells = []
+    for a, b in zip(ts[:-1], ts[1:]):
+        if b - a <= 1e-12 * (t1 - t0):
+            continue
+        tm = 0.5 * (a + b)
+        i = min(max(int(math.floor((x0 + tm * ux) / hx + 0.5)), 0), nx - 1)
+        j = min(max(int(math.floor((y0 + tm * uy) / hy + 0.5)), 0), ny - 1)
+        if not cells or cells[-1] != (i, j):
+            cells.append((i, j))
+    return cells
+
+
+def rotating_ray_map_2d(grid: Grid, f, n_theta: int, ds: float):
+    """The averaging map of whole straight rays: P^{n+1} = R P^n + c.
+
+    Lines at n_theta midpoint angles theta in [0, 2 pi) (each line traversed
+    in the direction theta, so every line is also run backwards by theta +
+    pi) and parallel offsets s spaced ds apart cover the grid.  Along a line,
+    a ray starts at its first valid cell after a missing one (or after
+    entering the array) with that cell's previous iterate P^n, and crossing
+    the face from cell A into cell B adds the path step of Eq.
+    PressureIntegrator1, (x_B - x_A)_a (f_a(A) + f_a(B)) / 2 along the face's
+    axis a.  Each cell's new value is the mean, over every ray through it
+    (each the same measure ds dtheta), of the ray's value there.
+    Returns (R, c, vidx): R (valid x valid) and c on the valid cells vidx.
+    Lines through a cell corner exactly (measure zero) are skipped."""
+    if grid.ndim != 2:
+        raise ValueError("2D only")
+    nx, ny = int(grid.dims[0]), int(grid.dims[1])
+    hx, hy = float(grid.h[0]), float(grid.h[1])
+    valid = grid.valid
+    f = np.asarray(f, dtype=np.float64)
+    vidx = np.flatnonzero(valid.reshape(-1))
+    pos = -np.ones(grid.n, dtype=np.int64)
+    pos[vidx] = np.arange(vidx.size)
+    R = np.zeros((vidx.size, vidx.size))
+    c = np.zeros(vidx.size)
+    cnt = np.zeros(vidx.size)
+    xc, yc = 0.5 * (nx - 1) * hx, 0.5 * (ny - 1) * hy
+    rad = 0.5 * math.hypot(nx * hx, ny * hy) + max(hx, hy)
+    n_s = int(math.ceil(2 * rad / ds))
+    for it in range(n_theta):
+        th = (it + 0.5) * 2 * math.pi / n_theta
+        ux, uy = math.cos(th), math.sin(th)
+        for ks in range(n_s):
+            s = -rad + (ks + 0.5) * ds
+            cells = _line_cells_2d(xc - s * uy, yc + s * ux, ux, uy, nx, ny, hx, hy)
+            if any(abs(a[0] - b[0]) + abs(a[1] - b[1]) != 1 for a, b in zip(cells[:-1], cells[1:])):
+                continue  # passes through a corner
+            start, acc, prev = -1, 0.0, None
+            for i, j in cells:
+                if not valid[j, i]:
+                    start, prev = -1, None
+                    continue
+                q = pos[j * nx + i]
+                if start < 0:
+                    start, acc = q, 0.0
+                else:
+                    pi_, pj_ = prev
+                    if pi_ != i:
+                        acc += (i - pi_) * hx * 0.5 * (f[0, pj_, pi_] + f[0, j, i])
+                    else:
+                        acc += (j - pj_) * hy * 0.5 * (f[1, pj_, pi_] + f[1, j, i])
+                R[q, start] += 1.0
+                c[q] += acc
+                cnt[q] += 1.0
+                prev = (i, j)
+    seen = cnt > 0
+    R[seen] /= cnt[seen, None]
+    c[seen] /= cnt[seen]
+    return R, c, vidx
+
+
+def rotating_ray_solve_2d(grid: Grid, f, n_theta: int, ds: float, tol: float = 1e-13, max_iter: int = 100000):
+    """Iterate the whole-ray average P^{n+1} = R P^n + c (rotating_ray_map_2d)
+    from P^0 = 0 until the gauged iterate stops changing.  The map moves the
+    per-component constant by a fixed amount per iteration when c has a
+    component along R's stationary distribution, so each iterate is gauged
+    (per-component mean removed); the gauged iterates converge.
+    Returns (P gauged with NaN on missing cells, iterations)."""
+    R, c, vidx = rotating_ray_map_2d(grid, f, n_theta, ds)
+    lab, nc = labels(grid)
+    labv = lab.reshape(-1)[vidx]
+    members = [labv == k for k in range(nc)]
+
+    def gauge_v(x):
+        for m in members:
+            x[m] -= x[m].mean()
+        return x
+
+    P = np.zeros(vidx.size)
+    n = 0
+    for n in range(1, max_iter + 1):
+        Pn = gauge_v(R @ P + c)
+        done = np.linalg.norm(Pn - P) <= tol * max(np.linalg.norm(Pn), 1e-300)
+        P = Pn
+        if done:
+            break
+    out = np.full(grid.n, np.nan)
+    out[vidx] = P
+    return out.reshape(grid.valid.shape), n

@@ -83,10 +83,13 @@ struct BParams {
     int count, ntiles, max_refine, cpt;
     long long max_iter, inner_max;
     double tol, inner_tol;
+    long long spin_limit;  // polls of a grid barrier before it gives up (OSMODI_DEBUG_BARRIER_SPINS)
+    int skip_block;        // test hook: this block leaves before the first barrier (-1: none)
+    int pad2;
 };
 
 // ---- bounded grid barrier (the cooperative launch guarantees co-residency) ----
-__device__ bool grid_barrier(BGlobal* gl) {
+__device__ bool grid_barrier(BGlobal* gl, long long spin_limit) {
     __syncthreads();
     __shared__ int ok;
     if (threadIdx.x == 0) {
@@ -105,7 +108,7 @@ __device__ bool grid_barrier(BGlobal* gl) {
             long long spins = 0;
             while (*gen == g) {
                 if (*(volatile int*)&gl->error) break;
-                if (++spins > (1LL << 25)) {  // about 2 s with the sleep below
+                if (++spins > spin_limit) {  // default 2^25: about 2 s with the sleep below
                     atomicExch(&gl->error, 1);
                     break;
                 }
@@ -231,7 +234,10 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_batched(BParams P) {
             S->p0sum = tot[1];
         }
     }
-    if (!grid_barrier(P.gl)) return;
+    // test hook (osmodi_debug_set): one block leaves without arriving, so the
+    // others' first barrier runs out of polls and reports the time-out
+    if ((int)blockIdx.x == P.skip_block) return;
+    if (!grid_barrier(P.gl, P.spin_limit)) return;
 
     // ===== refinement rounds =====
     for (int round = 0;; ++round) {
@@ -321,7 +327,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_batched(BParams P) {
                 }
             }
         }
-        if (!grid_barrier(P.gl)) return;
+        if (!grid_barrier(P.gl, P.spin_limit)) return;
         if (snap_of(P.gl, 1) == 0) break;
 
         // --- phase I: remove the constant, x = 0, CG start or continuation
@@ -391,7 +397,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_batched(BParams P) {
                 }
             }
         }
-        if (!grid_barrier(P.gl)) return;
+        if (!grid_barrier(P.gl, P.spin_limit)) return;
 
         // --- a CG segment: phases A and B until no instance is live
         while (snap_of(P.gl, 0) > 0) {
@@ -480,7 +486,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_batched(BParams P) {
                     }
                 }
             }
-            if (!grid_barrier(P.gl)) return;
+            if (!grid_barrier(P.gl, P.spin_limit)) return;
             // phase B: r -= alpha q, r.r, stopping test
             for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x) {
                 const BTile tl = P.tiles[t];
@@ -518,7 +524,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_batched(BParams P) {
                         S->status = kConv;
                 }
             }
-            if (!grid_barrier(P.gl)) return;
+            if (!grid_barrier(P.gl, P.spin_limit)) return;
         }
     }
 
@@ -716,6 +722,9 @@ static osmodi_status prepare_batched(int count, const osmodi_plan* plans, const 
     P->inner_max = o.inner_max;
     P->tol = tol;
     P->inner_tol = o.precision == OSMODI_FP32_REFINE ? o.inner_tol : 0.0;
+    const long long spins = debug_knob(OSMODI_DEBUG_BARRIER_SPINS);
+    P->spin_limit = spins > 0 ? spins : (1LL << 25);
+    P->skip_block = (int)debug_knob(OSMODI_DEBUG_SKIP_BARRIER_BLOCK);
     OSM_CUDA(cudaMemcpyAsync((void*)P->inst, L->inst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, s));
     OSM_CUDA(cudaMemcpyAsync((void*)P->tiles, L->tiles.data(), sizeof(BTile) * L->tiles.size(), cudaMemcpyHostToDevice, s));
     return OSMODI_OK;

@@ -90,7 +90,8 @@ struct osmodi_plan_s {
     double* comp_count = nullptr; // n_comp valid-cell counts (device)
     osm::Launch launch;
     osm::GraphCache graphs[4];
-    std::vector<double> history;
+    std::vector<double> history;    // OUTER: eps_R per residual evaluation
+    std::vector<double> history_p;  // OUTER: eps_P at the same evaluations (NaN where undefined)
     void* pinned = nullptr;  // 4 KB page-locked host mirror of the device scalars
     double kstats[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // profile mode: ms / launches per kernel kind
     std::vector<cudaEvent_t> events;             // profile mode event pool
@@ -272,6 +273,10 @@ struct ChunkLoop {
 // host helpers
 // ---------------------------------------------------------------------------
 Constants make_constants(int ndim, const double h[3]);
+// resolves the allocation-free solve's device scratch on `dev` (noalloc.cu)
+void noalloc_prepare(int dev);
+// current value of a test knob set by osmodi_debug_set (plan.cu)
+long long debug_knob(int knob);
 ClassTable make_class_table(int ndim, const Constants& k);
 
 struct Workspace {

@@ -41,7 +41,9 @@ extern "C" osmodi_status osmodi_solve_many(int count, const osmodi_plan* plans, 
     }
     for (int w = 0; w < K; ++w) {
         if (!workspaces[w]) return OSMODI_E_WORKSPACE;
-        // the workspace of stream w must fit every problem it takes
+        // the caller sizes workspaces[w] for every problem of stream w (this
+        // interface takes no sizes, so a short one cannot be detected here);
+        // only plans that report no workspace size are refused
         for (int i = w; i < count; i += K)
             if (osmodi_workspace_bytes(plans[i]) == 0) return OSMODI_E_INVALID;
     }

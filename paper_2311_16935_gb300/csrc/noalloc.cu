@@ -32,7 +32,9 @@ std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch on the current device, looked up once per
-// device (the first call on each device does this set-up).
+// device.  Plan creation does this set-up (osm::noalloc_prepare): looking the
+// symbol up loads this module, and with it the array, on that device, which
+// under lazy module loading would otherwise happen inside the first solve.
 cudaError_t scratch_address(int dev, void** out) {
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_ptr[dev]) {
@@ -46,6 +48,18 @@ cudaError_t scratch_address(int dev, void** out) {
 }
 
 }  // namespace
+
+namespace osm {
+// Called by osmodi_create with the plan's device current: resolves (and so
+// loads) the scratch on that device once, so that osmodi_solve_noalloc finds
+// it ready and allocates nothing.  A failure here is not an error of plan
+// creation; the solve reports it if it persists.
+void noalloc_prepare(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) return;
+    void* ptr = nullptr;
+    if (scratch_address(dev, &ptr) != cudaSuccess) cudaGetLastError();
+}
+}  // namespace osm
 
 extern "C" osmodi_status osmodi_solve_noalloc(osmodi_plan p, const void* grad, int gdt, void* pu, int pdt, double tol,
                                               int max_iter, void* stream, osmodi_result* res) {
@@ -61,8 +75,14 @@ extern "C" osmodi_status osmodi_solve_noalloc(osmodi_plan p, const void* grad, i
     }
     int dev = -1;
     OSM_CUDA(cudaGetDevice(&dev));
-    if (dev != p->device || dev < 0 || dev >= kMaxDevices) return OSMODI_E_INVALID;
-    if (!osm::user_buffer_ok(grad, dev) || !osm::user_buffer_ok(pu, dev)) return OSMODI_E_INVALID;
+    if (dev != p->device || dev < 0 || dev >= kMaxDevices) {
+        osm::set_error_text("osmodi_solve_noalloc: the current device is not the plan's device");
+        return OSMODI_E_INVALID;
+    }
+    if (!osm::user_buffer_ok(grad, dev) || !osm::user_buffer_ok(pu, dev)) {
+        osm::set_error_text("osmodi_solve_noalloc: gradient and pressure must be device, managed or page-locked host memory");
+        return OSMODI_E_INVALID;
+    }
     void* scratch = nullptr;
     cudaError_t e = scratch_address(dev, &scratch);
     if (e != cudaSuccess) {

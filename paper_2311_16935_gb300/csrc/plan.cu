@@ -4,6 +4,8 @@
 // which cells hold data (Section 2.2), so they are encoded once per plan.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -382,6 +384,7 @@ extern "C" osmodi_status osmodi_create(int ndim, const int64_t dims[3], const do
     if (e != cudaSuccess) { set_cuda_error(e, "cudaGetDevice"); return fail(OSMODI_E_CUDA); }
     e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     if (e != cudaSuccess) { set_cuda_error(e, "cudaDeviceGetAttribute"); return fail(OSMODI_E_CUDA); }
+    noalloc_prepare(p->device);  // the allocation-free solve's scratch, loaded now rather than in a solve
 
     if (cudaMalloc(&p->code8, (size_t)p->n_box) != cudaSuccess) { cudaGetLastError(); return fail(OSMODI_E_NOMEM); }
     if (cudaMalloc(&p->code32, (size_t)p->n_box * 4) != cudaSuccess) { cudaGetLastError(); return fail(OSMODI_E_NOMEM); }
@@ -545,5 +548,26 @@ extern "C" int osmodi_history(osmodi_plan p, double* out, int cap) {
     if (!p) return 0;
     int n = (int)p->history.size();
     if (out && cap > 0) std::memcpy(out, p->history.data(), sizeof(double) * (size_t)std::min(n, cap));
+    return n;
+}
+
+namespace osm {
+namespace {
+std::atomic<long long> g_knobs[4] = {{0}, {0}, {-1}, {0}};
+long long knob_default(int k) { return k == OSMODI_DEBUG_SKIP_BARRIER_BLOCK ? -1 : 0; }
+}  // namespace
+long long debug_knob(int knob) { return knob >= 1 && knob <= 3 ? g_knobs[knob].load() : 0; }
+}  // namespace osm
+
+extern "C" long long osmodi_debug_set(int knob, long long value) {
+    if (knob < 1 || knob > 3) return 0;
+    if (value == OSMODI_DEBUG_DEFAULT) value = osm::knob_default(knob);
+    return osm::g_knobs[knob].exchange(value);
+}
+
+extern "C" int osmodi_history_pressure(osmodi_plan p, double* out, int cap) {
+    if (!p) return 0;
+    int n = (int)p->history_p.size();
+    if (out && cap > 0) std::memcpy(out, p->history_p.data(), sizeof(double) * (size_t)std::min(n, cap));
     return n;
 }

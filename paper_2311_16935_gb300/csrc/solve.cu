@@ -48,6 +48,7 @@ enum { kSlotA = 0, kSlotB = 1, kSlotRes = 2 /* 3 slots */, kSlotMisc = 5 /* 3 sl
 struct Scalars {
     double bnorm2, p0sum, rnorm2, rsum, psum, dist2, pnorm2, outer_r2;
     double bsum, p0nz;  // sum of b; valid cells with a nonzero initial pressure
+    double outer_dp2, outer_pn2;  // OUTER: ||P^n - P^{n-1}||^2 and ||P^n||^2 (Eq. ResidualPressure)
     int nan_flag, pad;
     unsigned t_src, t_res, t_out, t_init, t_outer, t_misc, pad2, pad3;
 };
@@ -1146,16 +1147,60 @@ __global__ void __launch_bounds__(512) k_cg_b(T* __restrict__ r, const T* __rest
     }
 }
 
+// x *= a (the correction-scale test knob)
+template <class T>
+__global__ void k_scale(T* x, T a, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] *= a;
+}
+
 // ---------------------------------------------------------------------------
 // OUTER scheme pieces (Algorithm 1 applied to the correction equation).
 // ---------------------------------------------------------------------------
+// The pieces of eps_P (Eq. ResidualPressure) for the outer iterate P^n =
+// p + e^n of the current refinement step (p: the refinement's FP64 iterate,
+// or a float-float pair with hi in the first n_box floats and lo in the
+// second): ||e^n - e^{n-1}||^2 and ||p + e^n||^2 over the valid cells of a
+// chunk; e_prev (e^{n-1}) is overwritten with e^n.
+struct PrevIter {
+    const void* p;     // the refinement's iterate
+    int ff;            // p holds float-float pairs
+    int64_t n_box;
+};
+
+template <class T>
+__device__ __forceinline__ void pressure_update_chunk(const V4<T>& c, T* __restrict__ e_prev, int64_t i0,
+                                                      const PrevIter& pv, const bool (&valid)[4], double& dp2,
+                                                      double& pn2) {
+    const V4<T> ep = ld4c(e_prev + i0);
+    double pc[4];
+    if (pv.ff) {
+        const float* ph = reinterpret_cast<const float*>(pv.p);
+        const V4<float> hi = ld4(ph + i0), lo = ld4(ph + pv.n_box + i0);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) pc[m] = (double)hi.v[m] + (double)lo.v[m];
+    } else {
+        const V4<double> pd = ld4(reinterpret_cast<const double*>(pv.p) + i0);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) pc[m] = pd.v[m];
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        if (!valid[m]) continue;
+        const double d = (double)c.v[m] - (double)ep.v[m], q = pc[m] + (double)c.v[m];
+        dp2 += d * d;
+        pn2 += q * q;
+    }
+    st4(e_prev + i0, c);
+}
+
 // r_cg = rc - L e  (the residual of e^n; also the warm-started inner CG's
-// first residual, since M~ e^{n+1} = W~^n e^n + rc)
+// first residual, since M~ e^{n+1} = W~^n e^n + rc), and the pieces of eps_P
 template <class T, int NDIM>
 __global__ void __launch_bounds__(512) k_outer_res(const T* __restrict__ e, const T* __restrict__ rc, T* __restrict__ r_cg,
-                                                   const uint8_t* __restrict__ code8, Geo<T> g, Scalars* sc, double* partials) {
+                                                   const uint8_t* __restrict__ code8, Geo<T> g, Scalars* sc, double* partials,
+                                                   T* __restrict__ e_prev, PrevIter pv) {
     ChunkLoop L;
-    double acc[1] = {0.0};
+    double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t base = L.base; base < g.n_chunks; base += L.stride) {
         const int64_t ch = base + L.lane;
         const bool act = ch < g.n_chunks;
@@ -1182,10 +1227,16 @@ __global__ void __launch_bounds__(512) k_outer_res(const T* __restrict__ e, cons
             }
             st4(r_cg + i0, o);
             acc[0] += (double)part;
+            const bool valid[4] = {valid8(cw, 0), valid8(cw, 1), valid8(cw, 2), valid8(cw, 3)};
+            pressure_update_chunk(c, e_prev, i0, pv, valid, acc[1], acc[2]);
         }
     }
-    double tot[1];
-    if (grid_sum<1>(acc, partials, &sc->t_outer, tot) && threadIdx.x == 0) sc->outer_r2 = tot[0];
+    double tot[3];
+    if (grid_sum<3>(acc, partials, &sc->t_outer, tot) && threadIdx.x == 0) {
+        sc->outer_r2 = tot[0];
+        sc->outer_dp2 = tot[1];
+        sc->outer_pn2 = tot[2];
+    }
 }
 
 // Boundary refresh (Eq. MatrixEquation's right-hand side): rhs = W~^n e + rc,
@@ -1193,12 +1244,12 @@ __global__ void __launch_bounds__(512) k_outer_res(const T* __restrict__ e, cons
 template <class T, int NDIM>
 __global__ void __launch_bounds__(512) k_outer_rhs(const T* __restrict__ e, const T* __restrict__ rc, T* __restrict__ rhs,
                                                    const uint32_t* __restrict__ code32, Geo<T> g, TableT<T> tabv,
-                                                   Scalars* sc, double* partials) {
+                                                   Scalars* sc, double* partials, T* __restrict__ e_prev, PrevIter pv) {
     __shared__ T tab[3][kClasses];
     for (int t = threadIdx.x; t < 3 * kClasses; t += blockDim.x) tab[t / kClasses][t % kClasses] = tabv.anp1[t / kClasses][t % kClasses];
     __syncthreads();
     ChunkLoop L;
-    double acc[1] = {0.0};
+    double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t base = L.base; base < g.n_chunks; base += L.stride) {
         const int64_t ch = base + L.lane;
         const bool act = ch < g.n_chunks;
@@ -1248,10 +1299,16 @@ __global__ void __launch_bounds__(512) k_outer_rhs(const T* __restrict__ e, cons
             }
             st4(rhs + i0, o);
             acc[0] += (double)part;
+            const bool valid[4] = {(w32.x >> 31) != 0u, (w32.y >> 31) != 0u, (w32.z >> 31) != 0u, (w32.w >> 31) != 0u};
+            pressure_update_chunk(c, e_prev, i0, pv, valid, acc[1], acc[2]);
         }
     }
-    double tot[1];
-    if (grid_sum<1>(acc, partials, &sc->t_outer, tot) && threadIdx.x == 0) sc->outer_r2 = tot[0];
+    double tot[3];
+    if (grid_sum<3>(acc, partials, &sc->t_outer, tot) && threadIdx.x == 0) {
+        sc->outer_r2 = tot[0];
+        sc->outer_dp2 = tot[1];
+        sc->outer_pn2 = tot[2];
+    }
 }
 
 // One Jacobi sweep on M~ e = rhs:  e_out = (sum_j A_j^{n+1} e_in_j + rhs) / A_tot
@@ -1596,6 +1653,7 @@ struct Buffers {
     double *p64a, *b64;
     T *r, *x, *q, *pA, *pB;
     T *rc, *rhs, *e2;  // OUTER extras
+    T* eprev;           // OUTER: the previous outer iterate's correction (for eps_P)
     T *mgA, *mgB;       // FPCG with the multigrid preconditioner: V-cycle buffers (z ends in mg_result)
     char* mg_lv;        // coarse-level vectors
     T *aa_xs, *aa_fp, *aa_gp, *aa_dF, *aa_dG;  // OUTER with Anderson mixing
@@ -1628,6 +1686,7 @@ static size_t carve(osmodi_plan p, void* ws, Buffers<T>* b) {
     }
     if (p->opt.scheme == OSMODI_OUTER) {
         t.rc = w.take<T>(n);
+        t.eprev = w.take<T>(n);
         if (p->opt.inner == OSMODI_INNER_JACOBI) {
             t.rhs = w.take<T>(n);
             t.e2 = w.take<T>(n);
@@ -1688,18 +1747,19 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// Looked up once; a function-local static initialised from a lambda is
+// thread-safe (osmodi_solve_many solves from several threads at once).
 static EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
         void* ptr = nullptr;
         cudaDriverEntryPointQueryResult q;
+        EncodeTiledFn f = nullptr;
         if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &ptr, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+            f = reinterpret_cast<EncodeTiledFn>(ptr);
         cudaGetLastError();
-    }
+        return f;
+    }();
     return fn;
 }
 
@@ -1752,11 +1812,13 @@ static bool launch_cg_a_tma(osmodi_plan p, const Buffers<float>& b, const float*
     g.slab = p->launch.slab > 0 ? p->launch.slab : 16;
     g.n_items = (long long)g.n_tx * g.n_ty * ((g.nz + g.slab - 1) / g.slab);
     for (int a = 0; a < 3; ++a) g.F[a] = (float)p->k.F[a];
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_cg_a_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmem);
-        attr = true;
-    }
+    static const bool attr = []() {  // once, thread-safe
+        const bool ok = cudaFuncSetAttribute(k_cg_a_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmem) ==
+                        cudaSuccess;
+        cudaGetLastError();
+        return ok;
+    }();
+    if (!attr) return false;
     const int grid = (int)std::min<long long>(g.n_items, (long long)p->num_sms * 2);
     const CUtensorMap& mpo = (po == b.pA) ? t->pA : t->pB;
     k_cg_a_tma<<<grid, 256, kTmaSmem, s>>>(t->r, mpo, p->code8, po, pn, b.q, b.x, g, b.st, b.partials);
@@ -2248,6 +2310,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
     double* comp_p = b.comp + std::max<int64_t>(1, p->n_comp);
     double* comp_p0 = b.comp + 2 * std::max<int64_t>(1, p->n_comp);
     p->history.clear();
+    p->history_p.clear();
     for (double& v : p->kstats) v = 0.0;
     for (double& v : p->mg_kstats) v = 0.0;
     p->launches = 0;
@@ -2397,6 +2460,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                 const TableT<T> tab = table<T>(p);
                 double eps_step0 = -1.0;
                 T* e_cur = b.x;
+                OSM_CUDA(cudaMemsetAsync(b.eprev, 0, sizeof(T) * (size_t)p->n_box, s));  // e^0 = 0
                 AaHost aa;
                 if (p->opt.accel > 0) {
                     aa.reset(p->opt.accel);
@@ -2405,19 +2469,30 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                 }
                 for (;;) {
                     // residual of the current outer iterate (and boundary refresh for Jacobi)
+                    const PrevIter pv{cur, ff ? 1 : 0, p->n_box};
+                    double* part3 = b.partials + kSlotMisc * kMaxBlocks;
                     if (p->opt.inner == OSMODI_INNER_CG) {
-                        if (p->ndim == 2) k_outer_res<T, 2><<<G, TH, 0, s>>>(e_cur, b.rc, b.r, p->code8, g, b.sc, b.partials + kSlotMisc * kMaxBlocks);
-                        else k_outer_res<T, 3><<<G, TH, 0, s>>>(e_cur, b.rc, b.r, p->code8, g, b.sc, b.partials + kSlotMisc * kMaxBlocks);
+                        if (p->ndim == 2) k_outer_res<T, 2><<<G, TH, 0, s>>>(e_cur, b.rc, b.r, p->code8, g, b.sc, part3, b.eprev, pv);
+                        else k_outer_res<T, 3><<<G, TH, 0, s>>>(e_cur, b.rc, b.r, p->code8, g, b.sc, part3, b.eprev, pv);
                     } else {
-                        if (p->ndim == 2) k_outer_rhs<T, 2><<<G, TH, 0, s>>>(e_cur, b.rc, b.rhs, p->code32, g, tab, b.sc, b.partials + kSlotMisc * kMaxBlocks);
-                        else k_outer_rhs<T, 3><<<G, TH, 0, s>>>(e_cur, b.rc, b.rhs, p->code32, g, tab, b.sc, b.partials + kSlotMisc * kMaxBlocks);
+                        if (p->ndim == 2) k_outer_rhs<T, 2><<<G, TH, 0, s>>>(e_cur, b.rc, b.rhs, p->code32, g, tab, b.sc, part3, b.eprev, pv);
+                        else k_outer_rhs<T, 3><<<G, TH, 0, s>>>(e_cur, b.rc, b.rhs, p->code32, g, tab, b.sc, part3, b.eprev, pv);
                     }
                     OSM_CUDA(cudaGetLastError());
                     p->launches += 1;
                     OSM_TRY(read_mirror(&hm->sc, b.sc, sizeof(Scalars), s));
                     const double eps_o = std::sqrt(hm->sc.outer_r2) / bnorm;
+                    // eps_P of this outer iterate; none at a step's first
+                    // evaluation (e = 0, no previous outer iterate in the step)
+                    const bool has_prev = eps_step0 >= 0;
+                    const double eps_po = has_prev ? (hm->sc.outer_pn2 > 0 ? std::sqrt(hm->sc.outer_dp2 / hm->sc.outer_pn2) : 0.0)
+                                                   : std::nan("");
+                    if (has_prev) eps_p = eps_po;
                     if (eps_step0 < 0) eps_step0 = eps_o;
-                    if (p->opt.record_history) p->history.push_back(eps_o);
+                    if (p->opt.record_history) {
+                        p->history.push_back(eps_o);
+                        p->history_p.push_back(eps_po);
+                    }
                     const double target = std::max(0.5 * tol, rel * eps_step0);
                     if (eps_o <= target || outer_total >= max_iter || !std::isfinite(eps_o)) break;
                     if (p->opt.inner == OSMODI_INNER_CG) {
@@ -2445,6 +2520,11 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                     outer_total++;
                 }
                 if (e_cur != b.x) OSM_CUDA(cudaMemcpyAsync(b.x, e_cur, sizeof(T) * (size_t)p->n_box, cudaMemcpyDeviceToDevice, s));
+            }
+            // test knob: scale the correction (drives the divergence check)
+            if (const long long cs = debug_knob(OSMODI_DEBUG_CORRECTION_SCALE)) {
+                k_scale<T><<<G, TH, 0, s>>>(b.x, (T)cs, p->n_box);
+                OSM_CUDA(cudaGetLastError());
             }
             // p64 += e in place (pointwise), then the new FP64 residual of p64
             // alone: adding e inside the stencil kernel repeated the FP64 add

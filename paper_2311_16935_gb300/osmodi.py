@@ -22,6 +22,8 @@ E_INVALID, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_DIVERGED, E_TIMEOUT, E_EMPTY, E_NAN
 F32, F64 = 0, 1
 FP64, FP32, FP32_REFINE = 0, 1, 2
 FPCG, OUTER = 0, 1
+DEBUG_BARRIER_SPINS, DEBUG_SKIP_BARRIER_BLOCK, DEBUG_CORRECTION_SCALE = 1, 2, 3
+DEBUG_DEFAULT = -0x7fffffffffffffff
 INNER_CG, INNER_JACOBI = 0, 1
 
 
@@ -89,6 +91,8 @@ _SIGS = {
                                             ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                             ctypes.c_void_p]),
     "osmodi_history": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "osmodi_history_pressure": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "osmodi_debug_set": (ctypes.c_longlong, [ctypes.c_int, ctypes.c_longlong]),
     "osmodi_ray_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_source": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -305,6 +309,12 @@ class Plan:
         n = lib().osmodi_history(self.handle, None, 0)
         buf = (ctypes.c_double * max(n, 1))()
         lib().osmodi_history(self.handle, buf, n)
+        return list(buf)[:n]
+
+    def history_pressure(self):
+        n = lib().osmodi_history_pressure(self.handle, None, 0)
+        buf = (ctypes.c_double * max(n, 1))()
+        lib().osmodi_history_pressure(self.handle, buf, n)
         return list(buf)[:n]
 
     def ray_counts(self, stream=None) -> torch.Tensor:
@@ -656,3 +666,8 @@ def osmodi_solve(plan: Plan, grad, p, tol, max_iter=1 << 30, stream=None) -> osm
 
 def osmodi_destroy(plan: Plan):
     plan.close()
+
+
+def debug_set(knob: int, value: int) -> int:
+    """osmodi_debug_set: set a test knob, return its previous value."""
+    return int(lib().osmodi_debug_set(int(knob), int(value)))

@@ -65,15 +65,21 @@ def test_blobs_500_full_residual_and_crop(osm):
     del prob, p
     torch.cuda.empty_cache()
     grid = oracle.Grid(np.ones((n, n, n), bool), (1.0, 1.0, 1.0))
-    eps = oracle.residual(grid, f, P)
+    num, den = oracle.residual_norms(grid, f, P)
+    eps = float(np.sqrt(num / den))
     assert eps <= 1e-8
     assert eps == pytest.approx(res.eps_R, rel=1e-3)
-    # sampled cells: the per-cell residual evaluated by the oracle is small
-    # relative to the per-cell source
+    # sampled cells, one by one: the oracle's per-cell residual ((I - T) P -
+    # S)_C against the source's per-cell scale RMS(S) = ||S|| / sqrt(N): the
+    # sample's RMS is the global one (eps_R RMS(S)) within a factor 3, and no
+    # sampled cell exceeds 30 tol RMS(S)
+    rms_s = float(np.sqrt(den / n ** 3))
     rng = np.random.default_rng(0)
     idx = rng.integers(0, n ** 3, size=2000)
     r_at = oracle.residual_at(grid, f, P, idx)
     assert np.isfinite(r_at).all()
+    assert float(np.sqrt(np.mean(r_at ** 2))) <= 3.0 * eps * rms_s
+    assert float(np.abs(r_at).max()) <= 30.0 * 1e-8 * rms_s
     del f, P
     # crop
     c = 100
@@ -90,11 +96,14 @@ def test_blobs_500_full_residual_and_crop(osm):
         assert _rel(pc.cpu().numpy(), want, gridc.valid) <= 1e-10
 
 
+PIV_SAMPLE = list(range(0, 512, 16))  # 32 of the 512 snapshots, spread over the workload
+
+
 def test_piv_batch_full_size_instances(osm):
-    """The first instances of the 512-snapshot PIV workload at full size
-    through the batched persistent solve (tolerance 1e-10), each against the
-    oracle's FP64 solve."""
-    probs = [inputs.piv_snapshot_2d(i) for i in range(6)]
+    """32 instances of the 512-snapshot PIV workload (every 16th), at full
+    size, through the batched persistent solve (tolerance 1e-11), each
+    against the oracle's FP64 solve."""
+    probs = [inputs.piv_snapshot_2d(i) for i in PIV_SAMPLE]
     plans = [osm.Plan(2, pr.dims, pr.spacing, pr.mask.cuda()) for pr in probs]
     grads = [pr.grad.cuda() for pr in probs]
     ps = [torch.zeros(pr.mask.shape, dtype=torch.float64, device="cuda") for pr in probs]
@@ -109,10 +118,10 @@ def test_piv_batch_full_size_instances(osm):
 
 
 def test_piv_full_size_instances_multigrid_streams(osm):
-    """The same full-size PIV instances through the benchmark's second PIV
+    """The same 32 full-size PIV instances through the benchmark's second PIV
     path: osmodi_solve_many with the multigrid preconditioner (2-D damped
     Jacobi smoothing) on several streams, each against the oracle."""
-    probs = [inputs.piv_snapshot_2d(i) for i in range(6)]
+    probs = [inputs.piv_snapshot_2d(i) for i in PIV_SAMPLE]
     plans = [osm.Plan(2, pr.dims, pr.spacing, pr.mask.cuda(), precond=1) for pr in probs]
     grads = [pr.grad.cuda() for pr in probs]
     ps = [torch.zeros(pr.mask.shape, dtype=torch.float64, device="cuda") for pr in probs]

@@ -224,8 +224,46 @@ def test_outer_scheme_history_matches_literal_algorithm(osm):
     m = min(100, len(er), len(hist) - 1)
     assert m > 10
     np.testing.assert_allclose(np.array(hist[1:m + 1]), np.array(er[:m]), rtol=1e-6)
+    # eps_P (Eq. ResidualPressure) at the same iterations; undefined at P^0
+    hp = plan.history_pressure()
+    assert len(hp) == len(hist) and np.isnan(hp[0])
+    np.testing.assert_allclose(np.array(hp[1:m + 1]), np.array(ep[:m]), rtol=1e-6)
+    assert res.eps_P == hp[-1] and 0 < res.eps_P < 1e-6
     assert res.status == osm.OK
     assert _rel(got, P_lit, valid) < 1e-8
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_outer_jacobi_eps_P_matches_its_iterates(osm, ndim):
+    """OUTER with Jacobi inner sweeps (FP64): the reported eps_P history is
+    Eq. ResidualPressure of the scheme's own iterates.  The GPU's outer map
+    here is k Jacobi sweeps on M, so the oracle replays that map (M's
+    off-diagonal part and W^n from oracle.operators, FP64) from P^0 = 0 and
+    computes eps_P with oracle.pressure_update."""
+    rng = np.random.default_rng(30 + ndim)
+    shape = (9, 11) if ndim == 2 else (5, 6, 7)
+    spacing = (0.1, 0.13) if ndim == 2 else (1.0, 1.0, 1.0)
+    valid = rng.random(shape) > 0.1
+    f = rng.normal(size=(ndim,) + shape)
+    grid = oracle.Grid(valid, spacing)
+    k = 3
+    plan, res, got = _solve(osm, f, valid.astype(np.uint8), spacing, 1e-7, precision=0, scheme=1, inner=1,
+                            inner_max=k, sweeps_per_pass=1, record_history=1, max_iter=60)
+    hp = plan.history_pressure()
+    assert np.isnan(hp[0]) and len(hp) > 20
+    W1, Wn = oracle.operators(grid)
+    v = np.flatnonzero(valid.reshape(-1))
+    W1v, Wnv = W1[v][:, v], Wn[v][:, v]
+    S = oracle.source(grid, f).reshape(-1)[v]
+    P = np.zeros(v.size)
+    for it in range(1, 21):
+        rhs = Wnv @ P + S
+        e = P.copy()
+        for _ in range(k):  # Jacobi on (I - W1) e = rhs, warm-started from P^n
+            e = W1v @ e + rhs
+        want = oracle.pressure_update(e, P, np.ones(v.size, bool))
+        assert hp[it] == pytest.approx(want, rel=1e-9), it
+        P = e
 
 
 @pytest.mark.parametrize("depth", [3, 8])

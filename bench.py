@@ -48,30 +48,30 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic_gaussian_blobs_3d.json")
+
+
 def _kernel_source_hash():
-    """Hash of the sources that define the timed solve's kernels."""
-    h = hashlib.sha256()
-    for name in ("solve.cu", "mg.cu", "mg.cuh", "cg_state.cuh", "stencil.cuh", "internal.cuh", "ff.cuh"):
-        with open(os.path.join(ROOT, "paper_2311_16935_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+    from paper_2311_16935_gb300 import profile_traffic
 
-
-PROFILE = os.path.join(ROOT, "profiles", "solve_kernels_gaussian_blobs_3d_500.md")
+    return profile_traffic.kernel_source_hash()
 
 
 def _profiled_traffic(kernel: str, cells: int):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary
-    (a line `dram_bytes_per_cell[<kernel>]: <value>`), scaled to `cells` per
-    launch; None if the summary was taken on other kernel sources."""
-    if not os.path.exists(PROFILE):
+    """DRAM bytes per launch of `kernel` (name up to its template arguments)
+    from the machine-written ncu summary, scaled to `cells` per launch; None
+    when the summary was taken on other kernel sources or lacks the kernel."""
+    try:
+        with open(TRAFFIC) as fh:
+            d = json.load(fh)
+    except Exception:
         return None
-    txt = open(PROFILE).read()
-    m_hash = re.search(r"kernel_source_hash:\s*(\w+)", txt)
-    m_b = re.search(r"dram_bytes_per_cell\[" + re.escape(kernel) + r"\]:\s*([0-9.eE+-]+)", txt)
-    if not m_hash or not m_b or m_hash.group(1) != _kernel_source_hash():
+    if d.get("kernel_source_hash") != _kernel_source_hash():
         return None
-    return float(m_b.group(1)) * cells
+    hits = [v for k, v in d.get("kernels", {}).items() if k == kernel or k.startswith(kernel + "<")]
+    if len(hits) != 1:
+        return None
+    return hits[0]["dram_bytes_per_cell"] * cells
 
 
 class Clocks:
@@ -128,29 +128,74 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _cpu_baseline(size_crop=100, max_seconds=20.0):
-    """The oracle (FP64 CG, as written) on the host cores, on a crop of the
-    same Gaussian-blob workload; GLUPS = valid cells x iterations / time."""
-    import numpy as np
-
-    import oracle
+def _crop_problem(c=100):
+    """The c^3 crop at (200, 200, 200) of the 500^3 Gaussian-blob field (same
+    blob parameters), FP32 gradients on the host."""
     from paper_2311_16935_gb300 import inputs
 
     params = inputs.blob_params(20, (500, 500, 500), (5.0, 40.0), 4)
-    c = size_crop
-    prob = inputs.gaussian_blobs_3d(n=(c, c, c), origin=(200, 200, 200), box=(500, 500, 500), params=params,
+    return inputs.gaussian_blobs_3d(n=(c, c, c), origin=(200, 200, 200), box=(500, 500, 500), params=params,
                                     device="cpu", dtype=torch_float32())
+
+
+def _host_bytes_available():
+    try:
+        return os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError, AttributeError):
+        return 0
+
+
+def _cpu_baseline(grad_full_host=None, gpu_plain_cg_iters=None, size_crop=100, timed_iters=50):
+    """The oracle (FP64 CG, as written) on the host cores.
+
+    (1) measured: the 100^3 crop of the same Gaussian-blob field solved to
+        eps_R <= 1e-8; value = cells x (iterations + 2) / time, in GLUPS.
+    (2) extrapolated: the full 500^3 field, `timed_iters` CG iterations timed
+        (the difference of a 1 + timed_iters and a 1-iteration run, so the
+        set-up is not counted), times the iteration count of the same
+        unpreconditioned CG on the GPU to the same tolerance (the same
+        algorithm in exact arithmetic), plus the measured set-up."""
+    import numpy as np
+
+    import oracle
+
+    c = size_crop
+    prob = _crop_problem(c)
     grid = oracle.Grid(np.ones((c, c, c), bool), (1.0, 1.0, 1.0))
     f = prob.grad.double().numpy()
-    # bound the sample: time a capped number of CG iterations
     t0 = time.perf_counter()
     P, it, res = oracle.solve_cg(grid, f, tol=TOL, maxit=100000)
     dt = time.perf_counter() - t0
     threads = oracle.num_threads()
-    glups = grid.n * (it + 2) / dt / 1e9
-    return {"value": glups, "unit": "GLUPS", "cores": threads, "kind": "oracle",
-            "sample": f"oracle FP64 CG (ray-count operator) on a {c}^3 crop of the 500^3 blob field to eps_R<={TOL}: "
-                      f"{it} iterations in {dt:.1f} s", "seconds": dt}
+    out = {"value": grid.n * (it + 2) / dt / 1e9, "unit": "GLUPS", "cores": threads, "kind": "oracle",
+           "sample": f"oracle FP64 CG (ray-count operator) on a {c}^3 crop of the 500^3 blob field to eps_R<={TOL}: "
+                     f"{it} iterations in {dt:.2f} s",
+           "crop_time_to_tolerance_s": dt, "crop_iterations": it}
+    if grad_full_host is not None and gpu_plain_cg_iters:
+        n3 = grad_full_host.shape[1:]
+        cells = int(np.prod(n3))
+        # the oracle's ray-count array (14 doubles per cell), gradients, source,
+        # pressure and CG vectors: about 200 B per cell
+        if _host_bytes_available() < 220 * cells:
+            out["full_size"] = {"skipped": f"host memory: {_host_bytes_available() / 1e9:.0f} GB available, "
+                                           f"~{220 * cells / 1e9:.0f} GB needed"}
+            return out
+        gridf = oracle.Grid(np.ones(tuple(n3), bool), (1.0, 1.0, 1.0))
+        ff = grad_full_host.double().numpy()
+        t0 = time.perf_counter()
+        oracle.solve_cg(gridf, ff, tol=TOL, maxit=1)
+        t1 = time.perf_counter()
+        oracle.solve_cg(gridf, ff, tol=TOL, maxit=1 + timed_iters)
+        t2 = time.perf_counter()
+        per_it = max((t2 - t1) - (t1 - t0), 1e-9) / timed_iters
+        setup = max((t1 - t0) - per_it, 0.0)
+        out["full_size"] = {"kind": "extrapolated", "cells": cells, "timed_iterations": timed_iters,
+                            "seconds_per_iteration": per_it, "setup_s": setup,
+                            "iterations_to_tolerance": int(gpu_plain_cg_iters),
+                            "iteration_count_source": "the same unpreconditioned CG on the GPU (this run)",
+                            "time_to_tolerance_s": setup + per_it * gpu_plain_cg_iters,
+                            "GLUPS": cells * gpu_plain_cg_iters / (setup + per_it * gpu_plain_cg_iters) / 1e9}
+    return out
 
 
 def torch_float32():
@@ -216,6 +261,8 @@ def main():
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--ref-crop", type=int, default=100)
     ap.add_argument("--ref-iters", type=int, default=150)
+    ap.add_argument("--cpu-full", type=int, default=1,
+                    help="1: also time 50 oracle CG iterations at the full size (extrapolated baseline)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -288,18 +335,41 @@ def main():
     if any(r["status"] != osm.OK for r in results):
         raise SystemExit(f"solve did not converge: {results}")
 
-    # roofline of the dominant kernel: the multigrid fine-level red-black
-    # half-sweep z <- z + omega D^-1 (r - L z) on one colour, in place (two
-    # black half-sweeps per V-cycle are timed); algorithmic bytes per cell =
-    # read z, r (2 x 4 B) + code (1 B) + write z (4 B)
+    # roofline of the dominant kernel: the multigrid fine-level fused
+    # red-black sweep (one full sweep per launch: every cell updated once,
+    # out of place).  Algorithmic bytes per point update: read z_in, r
+    # (2 x 4 B) + code (1 B), write z_out (4 B) = 13 B; updates per launch =
+    # the cells of the padded box (padding cells are written too).  Two
+    # launches per V-cycle are timed with CUDA events on the solve's stream.
     cells = info["n_box"]
     peak, peak_kind = _peaks()
     sw_avg = sw_ms / max(sw_n, 1)
-    sw_bytes = 13.0 * cells
+    per_update = 13.0
+    sw_bytes = per_update * cells
+    sw_traffic = _profiled_traffic("k_mg_fine_rb_fused", cells)
     # the CG kernel applying the stencil: read z (the preconditioned residual),
     # p_old, x (3 x 4 B) + code (1 B); write p, q, x (3 x 4 B)
     ka_avg = ka_ms / max(ka_n, 1)
     kb_avg = kb_ms / max(kb_n, 1)
+    r64_avg = r64_ms / max(r64_n, 1)
+    # FP64 refinement residual r = b - L P: bounded by min(HBM, FP64).  Per
+    # cell: read P, b (2 x 8 B) + code (1 B), write r (4 B) = 21 B, and 11 FP64
+    # instructions (3 neighbour sums, F_x s_x, two FMAs for F_y s_y, F_z s_z,
+    # the FMA D p - t, b - Lp, the FP32 conversion, r^2 into the sum and the
+    # sums of r and P), of which 4 are fused multiply-adds: 15 FP64 flops
+    try:
+        fp64_gflops = osm.probe_fp64()
+    except Exception:
+        fp64_gflops = None
+    res_fp64 = None
+    if fp64_gflops and r64_ms > 0:
+        inst_rate = fp64_gflops / 2.0 * 1e9          # FP64 FMA instructions/s (one per pipe slot)
+        t_fp64 = 11.0 * cells / inst_rate             # s per launch at the FP64 instruction peak
+        t_hbm = 21.0 * cells / (peak * 1e9)
+        res_fp64 = {"fp64_peak_gflops_measured": fp64_gflops, "fp64_instructions_per_cell": 11,
+                    "fp64_flops_per_cell": 15, "bound_ms_fp64": t_fp64 * 1e3, "bound_ms_hbm": t_hbm * 1e3,
+                    "bound": "fp64" if t_fp64 > t_hbm else "hbm",
+                    "frac_of_bound": max(t_fp64, t_hbm) / (r64_avg / 1e3)}
 
     line = {"metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -316,11 +386,14 @@ def main():
             "solves_per_s": args.steps * world / (ms_max / 1e3),
             "iterations": {"cg": results[-1]["inner_iters"], "refine_steps": results[-1]["refine_steps"],
                            "eps_R": results[-1]["eps_R"]},
-            "roofline": {"bound": "hbm", "kernel": "k_mg_fine_rb<black> (multigrid fine-level red-black half-sweep)",
+            "roofline": {"bound": "hbm",
+                         "kernel": "k_mg_fine_rb_fused (multigrid fine-level red-black sweep, both colours in one pass)",
                          "achieved": sw_bytes / (sw_avg / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": sw_bytes / (sw_avg / 1e3) / 1e9 / peak, "peak_source": peak_kind,
-                         "traffic": _profiled_traffic("k_mg_fine_rb", cells), "bytes_per_launch": sw_bytes,
-                         "avg_launch_ms": sw_avg, "launches_timed": sw_n,
+                         "traffic": sw_traffic,
+                         "traffic_per_cell": sw_traffic / cells if sw_traffic else None,
+                         "algorithmic_bytes_per_update": per_update, "updates_per_launch": cells,
+                         "bytes_per_launch": sw_bytes, "avg_launch_ms": sw_avg, "launches_timed": sw_n,
                          "other_kernels": [
                              {"name": "k_cg_a (p = z + beta p_old, q = L p, x update, p.q)", "avg_launch_ms": ka_avg,
                               "bytes_per_launch": 25.0 * cells,
@@ -329,13 +402,11 @@ def main():
                              {"name": "k_cg_b (r update + r.r)", "avg_launch_ms": kb_avg, "bytes_per_launch": 12.0 * cells,
                               "achieved": 12.0 * cells / (kb_avg / 1e3) / 1e9 if kb_avg > 0 else None,
                               "traffic": _profiled_traffic("k_cg_b", cells)},
-                             # FP64 residual of the refinement loop: read P (8 B),
-                             # b (8 B), code (1 B); write r (4 B); bound by the
-                             # FP64 units, not by memory
                              {"name": "k_residual (r = b - L P in FP64, norms)",
-                              "avg_launch_ms": r64_ms / max(r64_n, 1), "bytes_per_launch": 21.0 * cells,
-                              "achieved": 21.0 * cells / (r64_ms / max(r64_n, 1) / 1e3) / 1e9 if r64_ms > 0 else None,
-                              "traffic": _profiled_traffic("k_residual", cells)}]},
+                              "avg_launch_ms": r64_avg, "bytes_per_launch": 21.0 * cells,
+                              "achieved": 21.0 * cells / (r64_avg / 1e3) / 1e9 if r64_ms > 0 else None,
+                              "traffic": _profiled_traffic("k_residual", cells),
+                              "fp64_roofline": res_fp64}]},
             "clocks": clocks, "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
             "preconditioner": {"levels": info.get("mg_levels"), "applications": mg_n,
                                "avg_application_ms": mg_ms / max(mg_n, 1)},
@@ -396,6 +467,42 @@ def main():
                                        "speedup_preconditioned": tcg / line["time_to_tolerance_s"]}
         plan_cg.close()
         del plan_cg
+
+    # the same solve by the V-cycle of one-colour half-sweeps (two passes per
+    # red-black sweep on the plan's grid) instead of the fused sweeps
+    if not args.no_fp64:
+        osm.debug_set(osm.DEBUG_MG_UNFUSED, 1)
+        try:
+            plan_u = osm.Plan(3, dims, (1.0, 1.0, 1.0), None, precision=osm.FP32_REFINE, precond=1)
+            tu, ru = timed_solve(plan_u)
+            plan_u.close()
+            del plan_u
+        finally:
+            osm.debug_set(osm.DEBUG_MG_UNFUSED, osm.DEBUG_DEFAULT)
+        line["half_sweep_vcycle"] = {"time_to_tolerance_s": tu, "cg": ru.inner_iters, "eps_R": ru.eps_R,
+                                     "status": ru.status,
+                                     "fused_speedup": tu / line.get("time_to_tolerance_unprofiled_s", tu)}
+
+    # the CPU baseline's 100^3 crop of the same field, solved on the GPU by the
+    # benchmark's own configuration (time to the same tolerance)
+    crop = _crop_problem(100)
+    plan_c = osm.Plan(3, (100, 100, 100), (1.0, 1.0, 1.0), None, precision=osm.FP32_REFINE, precond=1)
+    gc_dev = crop.grad.cuda()
+    pc_dev = torch.zeros((100, 100, 100), dtype=torch.float64, device="cuda")
+    plan_c.solve(gc_dev, pc_dev, TOL)  # warm-up
+    torch.cuda.synchronize()
+    pc_dev.zero_()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    rc_ = plan_c.solve(gc_dev, pc_dev, TOL)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    line["crop_gpu"] = {"workload": "gaussian_blobs_3d 100^3 crop (the CPU baseline's sample)",
+                        "time_to_tolerance_s": c0.elapsed_time(c1) / 1e3, "cg": rc_.inner_iters,
+                        "eps_R": rc_.eps_R, "status": rc_.status}
+    plan_c.close()
+    del plan_c, gc_dev, pc_dev, crop
+    grad_host = grad.cpu() if (rank == 0 and world == 1 and not args.no_cpu and args.cpu_full) else None
 
     # end to end through the C interface with host buffers: the gradient and
     # P^0 live in page-locked host memory and P is returned there; the solve's
@@ -518,7 +625,13 @@ def main():
         del batch, plans_b, probs, grads_b, outs
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
-            line["cpu_baseline"] = _cpu_baseline()
+            cg_its = line.get("cg_unpreconditioned", {}).get("cg")
+            line["cpu_baseline"] = _cpu_baseline(grad_host if args.cpu_full else None, cg_its)
+            if "crop_gpu" in line:
+                cb = line["cpu_baseline"]
+                line["crop_gpu"]["cpu_oracle_time_to_tolerance_s"] = cb["crop_time_to_tolerance_s"]
+                line["crop_gpu"]["speedup_vs_cpu_oracle"] = (cb["crop_time_to_tolerance_s"] /
+                                                             line["crop_gpu"]["time_to_tolerance_s"])
         except Exception as exc:  # the baseline is context, never the measurement
             line["cpu_baseline"] = {"error": str(exc)}
     line["kernel_source_hash"] = _kernel_source_hash()

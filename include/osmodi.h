@@ -487,6 +487,10 @@ OSMODI_API osmodi_status osmodi_net_set_params(osmodi_net net, const float* para
 OSMODI_API osmodi_status osmodi_net_get_params(osmodi_net net, float* params_host);
 /* accumulated parameter gradients (training nets) */
 OSMODI_API osmodi_status osmodi_net_get_grads(osmodi_net net, float* grads_host);
+/* OSMODI_E_TIMEOUT (and the flag cleared) if a tensor-core wait of an
+ * earlier network call gave up, else OSMODI_OK; synchronous.  get_output and
+ * get_grads report the same. */
+OSMODI_API osmodi_status osmodi_net_status(osmodi_net net);
 /* the normalised network output of the last forward (nx*ny*nz floats) */
 OSMODI_API osmodi_status osmodi_net_get_output(osmodi_net net, float* out_host);
 /* P^0 = network output * s into p_dev (0 on missing cells); asynchronous */
@@ -507,6 +511,29 @@ OSMODI_API const char* osmodi_status_string(int status);
 OSMODI_API const char* osmodi_last_cuda_error(void);
 
 /*
+ * Tensor-core GEMM step (no counterpart in the paper: the contraction the
+ * seed network's convolutions are built from, exposed to check it against a
+ * reference product): D = A B^T with A 128 x K and B N x K in BF16 (row-major,
+ * K contiguous, 16-byte aligned), D 128 x N in FP32 (row-major), on the
+ * tcgen05 tensor cores with the accumulator in tensor memory.  N and K
+ * multiples of 16, 16 <= N, K <= 256.  *err_dev (device int, caller-zeroed)
+ * is set to 1 if the MMAs did not complete within the kernel's bounded wait.
+ * Asynchronous on `stream`.
+ */
+OSMODI_API osmodi_status osmodi_tc_gemm(const void* A_dev, const void* B_dev, float* D_dev, int N, int K,
+                                        int* err_dev, void* stream);
+
+/*
+ * Measured FP64 arithmetic peak of the current device (no counterpart in
+ * the paper; the second roofline of the FP64 refinement kernels): the best
+ * of five timed launches (CUDA events on `stream`) of a kernel whose threads
+ * run eight independent FP64 fused multiply-add chains, one wave of resident
+ * blocks.  *gflops_out = 2 x FMAs / time in GFLOP/s; *ms_out (may be NULL)
+ * = that launch's time.  Synchronous; allocates nothing.
+ */
+OSMODI_API osmodi_status osmodi_probe_fp64(double* gflops_out, double* ms_out, void* stream);
+
+/*
  * Test knobs, for exercising the failure statuses without a GPU fault (no
  * counterpart in the paper).  Process-wide; every later call reads them.
  * Returns the previous value; OSMODI_DEBUG_DEFAULT restores the default.
@@ -522,10 +549,21 @@ OSMODI_API const char* osmodi_last_cuda_error(void);
  *   step's correction by this factor before adding it (0: no scaling); a
  *   large factor makes the residual grow and the solve report
  *   OSMODI_E_DIVERGED.
+ * OSMODI_DEBUG_MG_UNFUSED: how the 3-D multigrid preconditioner smooths the
+ *   plan's own grid, the same arithmetic in each case, for comparisons:
+ *   0 (default) fused one-pass red-black sweeps with their input planes
+ *   staged by TMA (FP32; FP64 plans use 2); 1 one-colour half-sweeps in
+ *   place (two passes per sweep); 2 fused one-pass sweeps reading their
+ *   inputs with ordinary loads.
+ * OSMODI_DEBUG_NET_WMMA: nonzero runs the seed network's convolutions on the
+ *   warp-level (wmma) tensor-core path instead of tcgen05; the same
+ *   products, for comparisons.  Default (0): tcgen05.
  */
 #define OSMODI_DEBUG_BARRIER_SPINS 1
 #define OSMODI_DEBUG_SKIP_BARRIER_BLOCK 2
 #define OSMODI_DEBUG_CORRECTION_SCALE 3
+#define OSMODI_DEBUG_MG_UNFUSED 4
+#define OSMODI_DEBUG_NET_WMMA 5
 #define OSMODI_DEBUG_DEFAULT (-0x7fffffffffffffffLL)
 OSMODI_API long long osmodi_debug_set(int knob, long long value);
 

@@ -277,6 +277,13 @@ Constants make_constants(int ndim, const double h[3]);
 void noalloc_prepare(int dev);
 // current value of a test knob set by osmodi_debug_set (plan.cu)
 long long debug_knob(int knob);
+// a CUtensorMap (written to `map`, 64-byte aligned storage of 128 bytes) for
+// tiled loads of bx x by x 1 boxes from a px x ny x nz FP32 array (solve.cu)
+bool tensor_map_3d_f32(void* map, const void* ptr, int64_t px, int64_t ny, int64_t nz, uint32_t bx, uint32_t by);
+// a CUtensorMap for tiled loads from a BF16 array of `rank` dimensions
+// (dims innermost first; strides_bytes of dims 1 .. rank-1; box per dim)
+bool tensor_map_bf16(void* map, const void* ptr, int rank, const uint64_t* dims, const uint64_t* strides_bytes,
+                     const uint32_t* box);
 ClassTable make_class_table(int ndim, const Constants& k);
 
 struct Workspace {

@@ -13,6 +13,7 @@
 // dense boxes with explicit FP32 weights to the +x / +y / +z neighbour (0
 // when the aggregates share no valid face) and 1 / diagonal; one thread per
 // cell.  The coarsest level (at most 8 cells per axis) is swept by one block.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,9 +50,17 @@ struct Level {
     double active;  // cells with a nonzero diagonal
 };
 
+// tensor maps of the TMA-staged fine sweep, for the buffers they were made for
+struct alignas(64) RbMaps {
+    CUtensorMap zA, zB, r;
+    const void* key[3] = {nullptr, nullptr, nullptr};
+    bool ok = false;
+};
+
 struct Hier {
     std::vector<Level> lv;  // lv[0] = level 1 (the first coarse level)
     void* mem = nullptr;
+    RbMaps* maps = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -281,6 +290,541 @@ __global__ void __launch_bounds__(256) k_mg_fine_rb(T* z, const T* __restrict__ 
                 acc[0] += (double)part;
             }
         }
+    }
+    if (DOT) {
+        double tot[1];
+        if (grid_sum<1>(acc, partials, &st->ticketM, tot) && threadIdx.x == 0) finish_rz(st, tot[0]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused red-black sweep, out of place, marching in z.
+//
+// One full sweep -- the cells of colour FC ((i + j + k) mod 2 == FC) first,
+// then the other colour, each z += omega D^-1 (r - L z) -- in one pass: z_in
+// is read once, z_out written once, so a sweep moves the 13 B per cell of one
+// half-sweep instead of twice that.  A block owns an xy tile of CX x RY
+// chunks (4 cells each) and walks a slab of planes in z.  At plane step k it
+// updates colour FC on plane k + 1 from z_in (the tile plus a one-chunk /
+// one-row halo ring, which the neighbouring tiles also compute, so no block
+// waits for another), keeps that plane in a 4-slot shared-memory ring, and
+// then updates the other colour on plane k from the ring (planes k - 1, k,
+// k + 1) and writes plane k of z_out.  Reading z_in and writing z_out never
+// alias, so the halo values every block reads are the sweep's inputs
+// whichever block runs first.  FROM_ZERO: z_in = 0 (the first sweep of a
+// V-cycle: colour FC gets omega D^-1 r, read no z).  DOT: reduce (r, z_out)
+// over the tile interiors and finish the CG state.
+// ---------------------------------------------------------------------------
+// One red-black update z + w (r - L z) of a cell from its value, its six
+// neighbours (east, west, north, south, front, back), r, its face bits and
+// w = omega / D (0 for a missing or isolated cell).
+template <class T>
+__device__ __forceinline__ T rb_cell(T cm, T e, T wv, T n, T sv, T f, T b, T r, unsigned fm, T w, T Fx, T Fy, T Fz) {
+    T lz = T(0);
+    if (fm & 1u) lz += Fx * (cm - e);
+    if (fm & 2u) lz += Fx * (cm - wv);
+    if (fm & 4u) lz += Fy * (cm - n);
+    if (fm & 8u) lz += Fy * (cm - sv);
+    if (fm & 16u) lz += Fz * (cm - f);
+    if (fm & 32u) lz += Fz * (cm - b);
+    return w != T(0) ? cm + w * (r - lz) : T(0);
+}
+// the same for a valid cell with all six faces valid (no tests; wf = omega /
+// (2 Fx + 2 Fy + 2 Fz)): most cells of most grids, about a third of the
+// instructions
+template <class T>
+__device__ __forceinline__ T rb_cell_full(T cm, T e, T wv, T n, T sv, T f, T b, T r, T wf, T Fx, T Fy, T Fz) {
+    const T c2 = cm + cm;
+    const T lz = Fx * (c2 - (e + wv)) + Fy * (c2 - (n + sv)) + Fz * (c2 - (f + b));
+    return cm + wf * (r - lz);
+}
+// every cell of a chunk valid with six valid faces (the colour bit ignored)
+__device__ __forceinline__ bool chunk_full(uint32_t cw) { return (cw & 0xBFBFBFBFu) == 0xBFBFBFBFu; }
+
+struct RbArgs {
+    int64_t px, plane;      // padded row pitch, px * ny
+    int cpr, ny, nz;        // chunks per padded row, rows, planes
+    int tiles_x, tiles_y;   // tiles per plane (interior (CX - 2) x (RY - 2) chunks)
+    int slab;               // planes per work item
+    long long n_items;      // tiles_x * tiles_y * slabs
+    float F[3];
+    float omega;
+};
+
+template <class T, int CX, int RY, int FC, bool FROM_ZERO, bool DOT>
+__global__ void __launch_bounds__(CX * RY) k_mg_fine_rb_fused(const T* __restrict__ zin, T* __restrict__ zout,
+                                                             const T* __restrict__ r,
+                                                             const uint8_t* __restrict__ code8, RbArgs g,
+                                                             CgState* st, double* partials) {
+    constexpr int NT = CX * RY;
+    if (st->status != kRunning) return;
+    __shared__ T wd[64];             // omega / D for every face mask (0 for an isolated cell)
+    __shared__ V4<T> ring[4][NT];    // plane q of the half-updated z in slot q & 3
+    if (threadIdx.x < 64) {
+        const unsigned fm = threadIdx.x;
+        const T d = (T)g.F[0] * (T)((fm & 1u) + ((fm >> 1) & 1u)) + (T)g.F[1] * (T)(((fm >> 2) & 1u) + ((fm >> 3) & 1u)) +
+                    (T)g.F[2] * (T)(((fm >> 4) & 1u) + ((fm >> 5) & 1u));
+        wd[threadIdx.x] = d > T(0) ? (T)g.omega / d : T(0);
+    }
+    const int t = threadIdx.x, lx = t % CX, ly = t / CX;
+    const T Fx = (T)g.F[0], Fy = (T)g.F[1], Fz = (T)g.F[2];
+    double acc[1] = {0.0};
+    for (long long item = blockIdx.x; item < g.n_items; item += gridDim.x) {
+        const int tx = (int)(item % g.tiles_x);
+        const int ty = (int)((item / g.tiles_x) % g.tiles_y);
+        const int sl = (int)(item / ((long long)g.tiles_x * g.tiles_y));
+        const int c = tx * (CX - 2) - 1 + lx, j = ty * (RY - 2) - 1 + ly;
+        const bool inr = c >= 0 && c < g.cpr && j >= 0 && j < g.ny;
+        const bool interior = inr && lx >= 1 && lx <= CX - 2 && ly >= 1 && ly <= RY - 2;
+        const int k0 = sl * g.slab, k1 = min(g.nz, k0 + g.slab);
+        const int64_t col = (int64_t)j * g.px + 4 * (int64_t)c;  // offset of the chunk within a plane
+        __syncthreads();  // the previous item's readers are done with the ring (and wd is set)
+        // colour FC on plane q into ring slot q & 3; returns r and the code word of the chunk
+        auto first_colour = [&](int q, V4<T>& rv, uint32_t& cw) {
+            V4<T> o = zero4<T>();
+            rv = zero4<T>();
+            cw = 0u;
+            if (inr && q >= 0 && q < g.nz) {
+                const int64_t i0 = (int64_t)q * g.plane + col;
+                cw = __ldg(reinterpret_cast<const uint32_t*>(code8 + i0));
+                rv = ld4(r + i0);
+                const int par = (int)((cw >> 6) & 1u);
+                if (FROM_ZERO) {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        o.v[m] = ((m + par) & 1) == FC && valid8(cw, m) ? wd[face_bits8(cw, m)] * rv.v[m] : T(0);
+                } else {
+                    // every load issued at an in-range address (clamped to the chunk
+                    // itself where a neighbour is outside the box; its face bit is 0)
+                    const int64_t on = j + 1 < g.ny ? g.px : 0, os = j > 0 ? -g.px : 0;
+                    const int64_t of = q + 1 < g.nz ? g.plane : 0, ob = q > 0 ? -g.plane : 0;
+                    const V4<T> zc = ld4(zin + i0), zn = ld4(zin + i0 + on), zs = ld4(zin + i0 + os);
+                    const V4<T> zf = ld4(zin + i0 + of), zb = ld4(zin + i0 + ob);
+                    const T xw = zin[c > 0 ? i0 - 1 : i0], xe = zin[c + 1 < g.cpr ? i0 + 4 : i0];
+                    const T wv[4] = {xw, zc.v[0], zc.v[1], zc.v[2]};
+                    const T ev[4] = {zc.v[1], zc.v[2], zc.v[3], xe};
+                    if (chunk_full(cw)) {
+                        const T wf = wd[63];
+#pragma unroll
+                        for (int m = 0; m < 4; ++m)
+                            o.v[m] = ((m + par) & 1) != FC ? zc.v[m]
+                                                          : rb_cell_full(zc.v[m], ev[m], wv[m], zn.v[m], zs.v[m], zf.v[m],
+                                                                         zb.v[m], rv.v[m], wf, Fx, Fy, Fz);
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            if (((m + par) & 1) != FC) {
+                                o.v[m] = zc.v[m];
+                                continue;
+                            }
+                            const unsigned fm = face_bits8(cw, m);
+                            const T w = valid8(cw, m) ? wd[fm] : T(0);
+                            o.v[m] = rb_cell(zc.v[m], ev[m], wv[m], zn.v[m], zs.v[m], zf.v[m], zb.v[m], rv.v[m], fm, w,
+                                             Fx, Fy, Fz);
+                        }
+                    }
+                }
+            }
+            ring[q & 3][t] = o;
+        };
+        V4<T> r_cur, r_nxt;
+        uint32_t c_cur = 0u, c_nxt = 0u;
+        if (k0 > 0) first_colour(k0 - 1, r_nxt, c_nxt);
+        first_colour(k0, r_cur, c_cur);
+        for (int k = k0; k < k1; ++k) {
+            first_colour(k + 1, r_nxt, c_nxt);  // zeros beyond the last plane
+            __syncthreads();
+            if (interior) {
+                // the other colour on plane k, from planes k - 1, k, k + 1 of the ring
+                const V4<T> o = ring[k & 3][t];
+                const V4<T> zn = ring[k & 3][t + CX], zs = ring[k & 3][t - CX];
+                const V4<T> zf = ring[(k + 1) & 3][t], zb = ring[(k + 3) & 3][t];
+                const T xw = ring[k & 3][t - 1].v[3], xe = ring[k & 3][t + 1].v[0];
+                const T wv[4] = {xw, o.v[0], o.v[1], o.v[2]};
+                const T ev[4] = {o.v[1], o.v[2], o.v[3], xe};
+                const uint32_t cw = c_cur;
+                const int par = (int)((cw >> 6) & 1u);
+                V4<T> out;
+                if (chunk_full(cw)) {
+                    const T wf = wd[63];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        out.v[m] = ((m + par) & 1) == FC ? o.v[m]
+                                                         : rb_cell_full(o.v[m], ev[m], wv[m], zn.v[m], zs.v[m], zf.v[m],
+                                                                        zb.v[m], r_cur.v[m], wf, Fx, Fy, Fz);
+                } else {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        if (((m + par) & 1) == FC) {
+                            out.v[m] = o.v[m];
+                            continue;
+                        }
+                        const unsigned fm = face_bits8(cw, m);
+                        const T w = valid8(cw, m) ? wd[fm] : T(0);
+                        out.v[m] = rb_cell(o.v[m], ev[m], wv[m], zn.v[m], zs.v[m], zf.v[m], zb.v[m], r_cur.v[m], fm, w,
+                                           Fx, Fy, Fz);
+                    }
+                }
+                st4(zout + (int64_t)k * g.plane + col, out);
+                if (DOT) {
+                    T part = T(0);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) part += r_cur.v[m] * out.v[m];
+                    acc[0] += (double)part;
+                }
+            }
+            r_cur = r_nxt;
+            c_cur = c_nxt;
+        }
+    }
+    if (DOT) {
+        double tot[1];
+        if (grid_sum<1>(acc, partials, &st->ticketM, tot) && threadIdx.x == 0) finish_rz(st, tot[0]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The fused red-black sweep with its input planes staged by TMA (FP32, the
+// default).  Same sweep as k_mg_fine_rb_fused; what changes is how the
+// planes arrive: a block of 512 threads owns a tile of 128 x 16 cells and a
+// slab of planes, and a ring of RS shared-memory stages holds, per plane, the
+// z_in box (136 x 20 cells: 4-cell / 2-row halo) and the r box (136 x 18),
+// each one cp.async.bulk.tensor.3d load completing on the stage's mbarrier.
+// Planes k .. k + 2 are resident while k + 3 .. k + RS - 1 are in flight
+// (about 100 KB per SM), so the bytes in flight do not depend on registers,
+// and the code words of a plane are loaded one step before they are used.  At step k the
+// block updates colour FC on plane k + 1 (the tile, the row above and below
+// it and the cell left and right of each row) into a 4-slot ring of
+// half-updated planes, then the other colour on plane k from that ring, and
+// stores plane k of z_out.  Copies that fall outside the box are zero-filled
+// (their code is "missing", so they stay 0).  Every mbarrier wait is
+// bounded; a wait that gives up sets st->err, lets the copies in flight land
+// and leaves the block.
+// ---------------------------------------------------------------------------
+constexpr int RTX = 128, RTY = 16, RHX = 4;     // tile (cells), x halo of the boxes
+constexpr int RBX = RTX + 2 * RHX;              // 136 box columns
+constexpr int RZY = RTY + 4, RRY = RTY + 2;     // z box rows (2-row halo), r box rows (1-row halo)
+constexpr int RZB = RBX * RZY * 4;              // 10880
+constexpr int RRB = RBX * RRY * 4;              // 9792
+constexpr int RSTAGE = RZB + (RRB + 127) / 128 * 128;  // 20736
+constexpr int RS = 8;                           // stages (planes k .. k + 2 resident, k + 3 .. k + 7 in flight)
+constexpr int RSLOT = RBX * RRY * 4;            // one half-updated plane (18 rows)
+constexpr int kRbTmaSmem = RS * RSTAGE + 4 * RSLOT + 128;
+
+struct RbTmaGeo {
+    int64_t px, plane;
+    int nx4, ny, nz, n_tx, n_ty, slab;
+    long long n_items;
+    float F[3];
+    float omega;
+};
+
+__device__ __forceinline__ uint32_t rb_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+template <int FC, bool FROM_ZERO, bool DOT>
+__global__ void __launch_bounds__(512, 1) k_mg_fine_rb_tma(const __grid_constant__ CUtensorMap tm_z,
+                                                          const __grid_constant__ CUtensorMap tm_r,
+                                                          const uint8_t* __restrict__ code8, float* __restrict__ zout,
+                                                          RbTmaGeo g, CgState* st, double* partials) {
+    if (st->status != kRunning) return;
+    extern __shared__ __align__(128) unsigned char rsm[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(rsm) + 127) & ~uintptr_t(127));
+    float* slots = reinterpret_cast<float*>(base + RS * RSTAGE);
+    __shared__ __align__(8) uint64_t bars[RS];
+    __shared__ float wd[64];
+    __shared__ int abort_flag;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t < 64) {
+        const unsigned fm = t;
+        const float d = g.F[0] * (float)((fm & 1u) + ((fm >> 1) & 1u)) + g.F[1] * (float)(((fm >> 2) & 1u) + ((fm >> 3) & 1u)) +
+                        g.F[2] * (float)(((fm >> 4) & 1u) + ((fm >> 5) & 1u));
+        wd[t] = d > 0.f ? g.omega / d : 0.f;
+    }
+    if (t == 0) {
+        for (int i = 0; i < RS; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(rb_smem(&bars[i])), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    __syncthreads();
+    unsigned uses[RS], issued[RS];
+#pragma unroll
+    for (int i = 0; i < RS; ++i) uses[i] = issued[i] = 0;
+    const unsigned tx_bytes = FROM_ZERO ? (unsigned)RRB : (unsigned)(RZB + RRB);
+    double acc[1] = {0.0};
+    const float Fx = g.F[0], Fy = g.F[1], Fz = g.F[2];
+    for (long long item = blockIdx.x; item < g.n_items; item += gridDim.x) {
+        const int tx = (int)(item % g.n_tx);
+        const long long rest = item / g.n_tx;
+        const int ty = (int)(rest % g.n_ty);
+        const int sl = (int)(rest / g.n_ty);
+        const int x0 = tx * RTX, y0 = ty * RTY;
+        const int k0 = sl * g.slab, k1 = min(g.nz, k0 + g.slab);
+        // plane P lives in stage (P - (k0 - 2)) mod RS
+        auto stage_of = [&](int P) { return (P - k0 + 2 + 2 * RS) % RS; };
+        auto issue = [&](int P) {
+            if (P < 0 || P >= g.nz) return;
+            const int si = stage_of(P);
+            issued[si] += 1;
+            if (t != 0) return;
+            unsigned char* sb = base + si * RSTAGE;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(rb_smem(&bars[si])), "r"(tx_bytes)
+                         : "memory");
+            if (!FROM_ZERO)
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+                        rb_smem(sb)),
+                    "l"(&tm_z), "r"(x0 - RHX), "r"(y0 - 2), "r"(P), "r"(rb_smem(&bars[si]))
+                    : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+                    rb_smem(sb + RZB)),
+                "l"(&tm_r), "r"(x0 - RHX), "r"(y0 - 1), "r"(P), "r"(rb_smem(&bars[si]))
+                : "memory");
+        };
+        auto wait = [&](int P) {
+            if (P < 0 || P >= g.nz) return;
+            const int si = stage_of(P);
+            const unsigned parity = uses[si] & 1u;
+            long long spins = 0;
+            for (;;) {
+                uint32_t ok;
+                asm volatile(
+                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                    : "=r"(ok)
+                    : "r"(rb_smem(&bars[si])), "r"(parity)
+                    : "memory");
+                if (ok) break;
+                if (++spins > (1LL << 22)) {
+                    atomicExch(&abort_flag, 1);
+                    return;
+                }
+                __nanosleep(32);
+            }
+            uses[si] += 1;
+        };
+        auto zbox = [&](int P) { return reinterpret_cast<const float*>(base + stage_of(P) * RSTAGE); };
+        auto rbox = [&](int P) { return reinterpret_cast<const float*>(base + stage_of(P) * RSTAGE + RZB); };
+        auto slot = [&](int P) { return slots + (size_t)(P & 3) * (RBX * RRY); };
+        auto code_at = [&](int q, int y, int x) -> uint32_t {  // 4 code bytes of the chunk at (x, y, q), 0 outside
+            if (y < 0 || y >= g.ny || x < 0 || x >= 4 * g.nx4) return 0u;
+            return __ldg(reinterpret_cast<const uint32_t*>(code8 + (int64_t)q * g.plane + (int64_t)y * g.px + x));
+        };
+        // colour FC on plane q for the chunk at tile row ry (-1 .. 16), chunk cx
+        auto first_chunk = [&](int q, int ry, int cx, uint32_t cw) {
+            const int bz = (ry + 2) * RBX + RHX + 4 * cx, br = (ry + 1) * RBX + RHX + 4 * cx;
+            const float4 r4 = *reinterpret_cast<const float4*>(rbox(q) + br);
+            const float* rv = reinterpret_cast<const float*>(&r4);
+            const int par = (int)((cw >> 6) & 1u);
+            float4 o;
+            float* ov = reinterpret_cast<float*>(&o);
+            if (FROM_ZERO) {
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    ov[m] = ((m + par) & 1) == FC && valid8(cw, m) ? wd[face_bits8(cw, m)] * rv[m] : 0.f;
+            } else {
+                const float* zc = zbox(q);
+                const float4 c4 = *reinterpret_cast<const float4*>(zc + bz);
+                const float4 n4 = *reinterpret_cast<const float4*>(zc + bz + RBX);
+                const float4 s4 = *reinterpret_cast<const float4*>(zc + bz - RBX);
+                const float4 f4 = *reinterpret_cast<const float4*>(zbox(q + 1) + bz);
+                const float4 b4 = *reinterpret_cast<const float4*>(zbox(q - 1) + bz);
+                const float xw = zc[bz - 1], xe = zc[bz + 4];
+                const float* cv = reinterpret_cast<const float*>(&c4);
+                const float* nv = reinterpret_cast<const float*>(&n4);
+                const float* sv = reinterpret_cast<const float*>(&s4);
+                const float* fv = reinterpret_cast<const float*>(&f4);
+                const float* bv = reinterpret_cast<const float*>(&b4);
+                const float wv[4] = {xw, cv[0], cv[1], cv[2]};
+                const float ev[4] = {cv[1], cv[2], cv[3], xe};
+                if (chunk_full(cw)) {
+                    const float wf = wd[63];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        ov[m] = ((m + par) & 1) != FC
+                                    ? cv[m]
+                                    : rb_cell_full(cv[m], ev[m], wv[m], nv[m], sv[m], fv[m], bv[m], rv[m], wf, Fx, Fy, Fz);
+                } else {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        if (((m + par) & 1) != FC) {
+                            ov[m] = cv[m];
+                            continue;
+                        }
+                        const unsigned fm = face_bits8(cw, m);
+                        const float w = valid8(cw, m) ? wd[fm] : 0.f;
+                        ov[m] = rb_cell(cv[m], ev[m], wv[m], nv[m], sv[m], fv[m], bv[m], rv[m], fm, w, Fx, Fy, Fz);
+                    }
+                }
+            }
+            *reinterpret_cast<float4*>(slot(q) + (ry + 1) * RBX + RHX + 4 * cx) = o;
+        };
+        // colour FC on plane q for the single cell left (side 0) or right (side 1) of tile row ry
+        auto first_edge = [&](int q, int ry, int side, uint32_t cwq) {
+            const int col = side ? RHX + RTX : RHX - 1;
+            const int x = x0 - RHX + col;
+            float v = 0.f;
+            if (x >= 0 && x < 4 * g.nx4 && y0 + ry < g.ny) {
+                const int m = x & 3;
+                const int par = (int)((cwq >> 6) & 1u);
+                const float* zc = zbox(q);
+                const int bz = (ry + 2) * RBX + col, br = (ry + 1) * RBX + col;
+                const float cm = FROM_ZERO ? 0.f : zc[bz];
+                if (((m + par) & 1) != FC) {
+                    v = cm;
+                } else {
+                    const unsigned fm = face_bits8(cwq, m);
+                    const float w = valid8(cwq, m) ? wd[fm] : 0.f;
+                    float lz = 0.f;
+                    if (!FROM_ZERO) {
+                        const float* zf = zbox(q + 1);
+                        const float* zb = zbox(q - 1);
+                        if (fm & 1u) lz += Fx * (cm - zc[bz + 1]);
+                        if (fm & 2u) lz += Fx * (cm - zc[bz - 1]);
+                        if (fm & 4u) lz += Fy * (cm - zc[bz + RBX]);
+                        if (fm & 8u) lz += Fy * (cm - zc[bz - RBX]);
+                        if (fm & 16u) lz += Fz * (cm - zf[bz]);
+                        if (fm & 32u) lz += Fz * (cm - zb[bz]);
+                    }
+                    v = w != 0.f ? cm + w * (rbox(q)[br] - lz) : 0.f;
+                }
+            }
+            slot(q)[(ry + 1) * RBX + col] = v;
+        };
+        // the first colour on every cell of plane q the second colour needs
+        const int my_row = warp, my_cx = lane;  // the thread's interior chunk
+        const int gx = x0 + 4 * my_cx, gy = y0 + my_row;
+        // the code words a thread's first-colour work on plane q needs (its own
+        // chunk; warps 0, 1: a chunk of the row above / below the tile; warp 2:
+        // the chunk holding its edge cell), loaded a plane ahead of their use
+        struct Codes {
+            uint32_t mine, extra;
+        };
+        auto load_codes = [&](int q) -> Codes {
+            Codes c{0u, 0u};
+            if (q < 0 || q >= g.nz) return c;
+            c.mine = code_at(q, gy, gx);
+            if (warp < 2) {
+                c.extra = code_at(q, y0 + (warp == 0 ? -1 : RTY), x0 + 4 * lane);
+            } else if (warp == 2) {
+                const int x = (lane & 1) ? x0 + RTX : x0 - 1;
+                c.extra = x >= 0 ? code_at(q, y0 + (lane >> 1), x & ~3) : 0u;
+            }
+            return c;
+        };
+        auto first_plane = [&](int q, const Codes& c) {
+            first_chunk(q, my_row, my_cx, c.mine);
+            if (warp < 2) {  // the rows above and below the tile
+                first_chunk(q, warp == 0 ? -1 : RTY, lane, c.extra);
+            } else if (warp == 2) {  // the cells left and right of every row
+                first_edge(q, lane >> 1, lane & 1, c.extra);
+            }
+        };
+        // planes k0 - 2 .. k1 + 1 are read; plane P is issued once its stage is
+        // free: k0 - 2 .. k0 + RS - 3 at once, the next two after the first
+        // colour on planes k0 - 1 and k0 (which free planes k0 - 2, k0 - 1),
+        // k + RS after step k (which frees plane k): RS - 2 steps of lead
+        const int last = k1 + 1;
+        for (int P = k0 - 2; P <= min(k0 + RS - 3, last); ++P) issue(P);
+        const Codes c_pre = load_codes(k0 - 1);
+        Codes c_cur = load_codes(k0), c_nxt = load_codes(k0 + 1);
+        wait(k0 - 2);
+        wait(k0 - 1);
+        wait(k0);
+        wait(k0 + 1);
+        __syncthreads();
+        if (!abort_flag) {
+            if (k0 > 0) first_plane(k0 - 1, c_pre);
+            first_plane(k0, c_cur);
+        }
+        __syncthreads();
+        for (int P = k0 + RS - 2; P <= min(k0 + RS - 1, last); ++P) issue(P);
+        for (int k = k0; k < k1; ++k) {
+            const Codes c_ahead = load_codes(k + 2);  // in flight during this step
+            wait(k + 2);  // z(k + 2) for the first colour on plane k + 1
+            __syncthreads();
+            if (abort_flag) break;
+            if (k + 1 < g.nz) first_plane(k + 1, c_nxt);
+            __syncthreads();
+            // the other colour on plane k, rows y0 .. y0 + 15
+            {
+                const float* sC = slot(k);
+                const float* sF = slot(k + 1);
+                const float* sB = slot(k - 1);
+                const int b = (my_row + 1) * RBX + RHX + 4 * my_cx;
+                const float4 o4 = *reinterpret_cast<const float4*>(sC + b);
+                const float4 n4 = *reinterpret_cast<const float4*>(sC + b + RBX);
+                const float4 s4 = *reinterpret_cast<const float4*>(sC + b - RBX);
+                const float4 f4 = *reinterpret_cast<const float4*>(sF + b);
+                const float4 b4 = *reinterpret_cast<const float4*>(sB + b);
+                const float xw = sC[b - 1], xe = sC[b + 4];
+                const float4 r4 = *reinterpret_cast<const float4*>(rbox(k) + (my_row + 1) * RBX + RHX + 4 * my_cx);
+                const float* ov = reinterpret_cast<const float*>(&o4);
+                const float* nv = reinterpret_cast<const float*>(&n4);
+                const float* sv = reinterpret_cast<const float*>(&s4);
+                const float* fv = reinterpret_cast<const float*>(&f4);
+                const float* bv = reinterpret_cast<const float*>(&b4);
+                const float* rv = reinterpret_cast<const float*>(&r4);
+                const float wv[4] = {xw, ov[0], ov[1], ov[2]};
+                const float ev[4] = {ov[1], ov[2], ov[3], xe};
+                const uint32_t cw = c_cur.mine;
+                const int par = (int)((cw >> 6) & 1u);
+                float4 out4;
+                float* outv = reinterpret_cast<float*>(&out4);
+                if (chunk_full(cw)) {
+                    const float wf = wd[63];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        outv[m] = ((m + par) & 1) == FC
+                                      ? ov[m]
+                                      : rb_cell_full(ov[m], ev[m], wv[m], nv[m], sv[m], fv[m], bv[m], rv[m], wf, Fx, Fy, Fz);
+                } else {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        if (((m + par) & 1) == FC) {
+                            outv[m] = ov[m];
+                            continue;
+                        }
+                        const unsigned fm = face_bits8(cw, m);
+                        const float w = valid8(cw, m) ? wd[fm] : 0.f;
+                        outv[m] = rb_cell(ov[m], ev[m], wv[m], nv[m], sv[m], fv[m], bv[m], rv[m], fm, w, Fx, Fy, Fz);
+                    }
+                }
+                if (gy < g.ny && gx < 4 * g.nx4) {
+                    *reinterpret_cast<float4*>(zout + (int64_t)k * g.plane + (int64_t)gy * g.px + gx) = out4;
+                    if (DOT) {
+                        float part = 0.f;
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) part += rv[m] * outv[m];
+                        acc[0] += (double)part;
+                    }
+                }
+            }
+            c_cur = c_nxt;
+            c_nxt = c_ahead;
+            __syncthreads();  // plane k's stage and the slot of plane k - 1 are free
+            if (k + RS <= last) issue(k + RS);
+        }
+        if (abort_flag) break;
+        __syncthreads();
+    }
+    if (abort_flag) {
+#pragma unroll
+        for (int i = 0; i < RS; ++i) {
+            long long spins = 0;
+            while (uses[i] < issued[i] && spins < (1LL << 22)) {
+                uint32_t ok;
+                asm volatile(
+                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                    : "=r"(ok)
+                    : "r"(rb_smem(&bars[i])), "r"(uses[i] & 1u)
+                    : "memory");
+                if (ok) uses[i] += 1;
+                else { ++spins; __nanosleep(32); }
+            }
+        }
+        if (t == 0) st->err = 1;
     }
     if (DOT) {
         double tot[1];
@@ -729,6 +1273,87 @@ int wave_grid(osmodi_plan p, K kernel, int bps, int64_t work256) {
     return (int)std::max<int64_t>(1, std::min<int64_t>({work256, (int64_t)p->num_sms * bps, (int64_t)kMaxBlocks}));
 }
 
+// tile of the fused red-black sweep: 16 x 16 chunks (64 x 16 cells) with a
+// one-chunk / one-row halo ring, interior 14 x 14 chunks
+constexpr int kRbCX = 16, kRbRY = 16;
+
+// Work items of the fused sweep: every tile of a plane times slabs of planes,
+// the slab chosen so that each resident block gets about eight items (each
+// slab recomputes one extra plane of the first colour)
+RbArgs rb_args(osmodi_plan p) {
+    RbArgs a;
+    a.px = p->px;
+    a.plane = p->px * p->ny;
+    a.cpr = (int)(p->px / 4);
+    a.ny = (int)p->ny;
+    a.nz = (int)p->nz;
+    a.tiles_x = (a.cpr + kRbCX - 3) / (kRbCX - 2);
+    a.tiles_y = (a.ny + kRbRY - 3) / (kRbRY - 2);
+    for (int q = 0; q < 3; ++q) a.F[q] = (float)p->k.F[q];
+    a.omega = kOmegaRB;
+    static const int bps = blocks_per_sm(k_mg_fine_rb_fused<float, kRbCX, kRbRY, 0, false, false>);
+    const long long tiles = (long long)a.tiles_x * a.tiles_y;
+    const long long want = 8LL * p->num_sms * bps;
+    const long long slabs = std::max<long long>(1, std::min<long long>(a.nz, (want + tiles - 1) / tiles));
+    a.slab = std::max(8, (int)((a.nz + slabs - 1) / slabs));
+    a.n_items = tiles * ((a.nz + a.slab - 1) / a.slab);
+    return a;
+}
+
+// geometry of the TMA-staged sweep: 128 x 16-cell tiles times slabs of planes
+// sized for about eight work items per SM (one block per SM)
+RbTmaGeo rb_tma_geo(osmodi_plan p) {
+    RbTmaGeo g;
+    g.px = p->px;
+    g.plane = p->px * p->ny;
+    g.nx4 = (int)(p->px / 4);
+    g.ny = (int)p->ny;
+    g.nz = (int)p->nz;
+    g.n_tx = (int)((p->px + RTX - 1) / RTX);
+    g.n_ty = (int)((p->ny + RTY - 1) / RTY);
+    for (int q = 0; q < 3; ++q) g.F[q] = (float)p->k.F[q];
+    g.omega = kOmegaRB;
+    const long long tiles = (long long)g.n_tx * g.n_ty;
+    const long long want = 8LL * p->num_sms;
+    const long long slabs = std::max<long long>(1, std::min<long long>(g.nz, (want + tiles - 1) / tiles));
+    g.slab = std::max(8, (int)((g.nz + slabs - 1) / slabs));
+    g.n_items = tiles * ((g.nz + g.slab - 1) / g.slab);
+    return g;
+}
+
+// the plan's tensor maps for these buffers (made once per buffer set), or
+// nullptr when they cannot be made or the kernel cannot get its shared memory
+RbMaps* rb_maps(osmodi_plan p, const float* zA, const float* zB, const float* r) {
+    static const bool attr = [] {
+        bool ok = true;
+        ok &= cudaFuncSetAttribute(k_mg_fine_rb_tma<0, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRbTmaSmem) == cudaSuccess;
+        ok &= cudaFuncSetAttribute(k_mg_fine_rb_tma<0, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRbTmaSmem) == cudaSuccess;
+        ok &= cudaFuncSetAttribute(k_mg_fine_rb_tma<1, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRbTmaSmem) == cudaSuccess;
+        ok &= cudaFuncSetAttribute(k_mg_fine_rb_tma<1, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRbTmaSmem) == cudaSuccess;
+        cudaGetLastError();
+        return ok;
+    }();
+    if (!attr) return nullptr;
+    Hier* h = hier_of(p);
+    if (!h->maps) h->maps = new (std::nothrow) RbMaps();
+    RbMaps* m = h->maps;
+    if (!m) return nullptr;
+    if (m->key[0] != zA || m->key[1] != zB || m->key[2] != r) {
+        m->ok = tensor_map_3d_f32(&m->zA, zA, p->px, p->ny, p->nz, RBX, RZY) &&
+                tensor_map_3d_f32(&m->zB, zB, p->px, p->ny, p->nz, RBX, RZY) &&
+                tensor_map_3d_f32(&m->r, r, p->px, p->ny, p->nz, RBX, RRY);
+        m->key[0] = zA;
+        m->key[1] = zB;
+        m->key[2] = r;
+    }
+    return m->ok ? m : nullptr;
+}
+
+int rb_grid(osmodi_plan p, const RbArgs& a) {
+    static const int bps = blocks_per_sm(k_mg_fine_rb_fused<float, kRbCX, kRbRY, 0, false, false>);
+    return (int)std::max<long long>(1, std::min<long long>(a.n_items, (long long)p->num_sms * bps));
+}
+
 int grid_for(osmodi_plan p, int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)p->num_sms * 8));
 }
@@ -869,16 +1494,19 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
     // (fusing the first two sweeps into one pass was measured slower than the
     // two passes: forming every neighbour's first-sweep value costs more
     // instructions than the extra pass moves bytes)
-    if (red_black(p)) {
+    const long long variant = debug_knob(OSMODI_DEBUG_MG_UNFUSED);  // 0 TMA-staged, 1 half-sweeps, 2 register-staged
+    if (red_black(p) && variant == 1) {
+        // the same V-cycle by in-place half-sweeps (one colour per pass), kept
+        // for comparison with the fused sweeps; it ends in zA, copied to zB
         f.omega = (T)kOmegaRB;
         static const int b_rb = blocks_per_sm(k_mg_fine_rb<T, NDIM, 1, false, false>);
         static const int b_rbd = blocks_per_sm(k_mg_fine_rb<T, NDIM, 0, false, true>);
-        const int G_rb = wave_grid(p, 0, b_rb, w256), G_rbd = wave_grid(p, 0, b_rbd, w256);
         static const int b_red = blocks_per_sm(k_mg_fine_rb<T, NDIM, 0, false, false>);
+        const int G_rb = wave_grid(p, 0, b_rb, w256), G_rbd = wave_grid(p, 0, b_rbd, w256);
         const int G_red = wave_grid(p, 0, b_red, w256);
-        k_mg_fine_rb<T, NDIM, 0, true, false><<<G_first, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);  // red from 0
+        k_mg_fine_rb<T, NDIM, 0, true, false><<<G_first, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);
         mark(0);
-        k_mg_fine_rb<T, NDIM, 1, false, false><<<G_rb, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);   // black
+        k_mg_fine_rb<T, NDIM, 1, false, false><<<G_rb, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);
         mark(1);
         for (int i = 1; i < nu; ++i) {
             k_mg_fine_rb<T, NDIM, 0, false, false><<<G_red, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);
@@ -889,15 +1517,92 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
         mark(5);
         T* zc = vcycle_coarse<T>(p, h, w.lv, 1, st, s);
         k_mg_fine_prolong<T, NDIM><<<G_prol, 256, 0, s>>>(w.zA, zc, f, st);
-        for (int i = 1; i < nu; ++i) {  // the adjoint: black then red
+        for (int i = 1; i < nu; ++i) {
             k_mg_fine_rb<T, NDIM, 1, false, false><<<G_rb, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);
             k_mg_fine_rb<T, NDIM, 0, false, false><<<G_red, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);
         }
         mark(2);
-        k_mg_fine_rb<T, NDIM, 1, false, false><<<G_rb, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);   // black
+        k_mg_fine_rb<T, NDIM, 1, false, false><<<G_rb, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);
         mark(3);
-        k_mg_fine_rb<T, NDIM, 0, false, true><<<G_rbd, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);   // red, (r, z)
-        return w.zA;
+        k_mg_fine_rb<T, NDIM, 0, false, true><<<G_rbd, 256, 0, s>>>(w.zA, r, p->code8, f, st, partials);
+        cudaMemcpyAsync(w.zB, w.zA, sizeof(T) * (size_t)p->n_box, cudaMemcpyDeviceToDevice, s);
+        return w.zB;
+    }
+    if (red_black(p) && sizeof(T) == 4 && variant == 0) {
+        // the same V-cycle with the TMA-staged fused sweeps (FP32)
+        RbMaps* mp = rb_maps(p, reinterpret_cast<const float*>(w.zA), reinterpret_cast<const float*>(w.zB),
+                             reinterpret_cast<const float*>(r));
+        if (mp) {
+            const RbTmaGeo tg = rb_tma_geo(p);
+            const int gr = (int)std::min<long long>(tg.n_items, (long long)p->num_sms);
+            float* fA = reinterpret_cast<float*>(w.zA);
+            float* fB = reinterpret_cast<float*>(w.zB);
+            float* cur = fA;
+            float* oth = fB;
+            auto map_of = [&](const float* z) -> const CUtensorMap& { return z == fA ? mp->zA : mp->zB; };
+            if (nu == 1) mark(0);
+            k_mg_fine_rb_tma<0, true, false><<<gr, 512, kRbTmaSmem, s>>>(mp->zA, mp->r, p->code8, cur, tg, st, partials);
+            if (nu == 1) mark(1);
+            for (int i = 1; i < nu; ++i) {
+                if (i == 1) mark(0);
+                k_mg_fine_rb_tma<0, false, false><<<gr, 512, kRbTmaSmem, s>>>(map_of(cur), mp->r, p->code8, oth, tg, st,
+                                                                              partials);
+                if (i == 1) mark(1);
+                std::swap(cur, oth);
+            }
+            T* tcur = reinterpret_cast<T*>(cur);
+            mark(4);
+            k_mg_fine_resid_restrict<T, NDIM><<<G_rr, 256, 0, s>>>(tcur, r, p->code8, f, v1.r, st);
+            mark(5);
+            T* zc = vcycle_coarse<T>(p, h, w.lv, 1, st, s);
+            k_mg_fine_prolong<T, NDIM><<<G_prol, 256, 0, s>>>(tcur, zc, f, st);
+            for (int i = 0; i < nu; ++i) {  // the adjoint: black then red
+                if (i == 0) mark(2);
+                if (i == nu - 1)
+                    k_mg_fine_rb_tma<1, false, true><<<gr, 512, kRbTmaSmem, s>>>(map_of(cur), mp->r, p->code8, oth, tg,
+                                                                                 st, partials);
+                else
+                    k_mg_fine_rb_tma<1, false, false><<<gr, 512, kRbTmaSmem, s>>>(map_of(cur), mp->r, p->code8, oth, tg,
+                                                                                  st, partials);
+                if (i == 0) mark(3);
+                std::swap(cur, oth);
+            }
+            return reinterpret_cast<T*>(cur);  // == w.zB
+        }
+    }
+    if (red_black(p)) {
+        // nu fused red-then-black sweeps (the first from zero), the residual
+        // and restriction, the coarse correction, then nu black-then-red
+        // sweeps, the last forming (r, z).  Each sweep reads one buffer and
+        // writes the other: 2 nu passes starting in zA end in zB.
+        const RbArgs ra = rb_args(p);
+        const int gr = rb_grid(p, ra);
+        T* cur = w.zA;
+        T* oth = w.zB;
+        if (nu == 1) mark(0);
+        k_mg_fine_rb_fused<T, kRbCX, kRbRY, 0, true, false><<<gr, kRbCX * kRbRY, 0, s>>>(nullptr, cur, r, p->code8, ra, st, partials);
+        if (nu == 1) mark(1);
+        for (int i = 1; i < nu; ++i) {
+            if (i == 1) mark(0);
+            k_mg_fine_rb_fused<T, kRbCX, kRbRY, 0, false, false><<<gr, kRbCX * kRbRY, 0, s>>>(cur, oth, r, p->code8, ra, st, partials);
+            if (i == 1) mark(1);
+            std::swap(cur, oth);
+        }
+        mark(4);
+        k_mg_fine_resid_restrict<T, NDIM><<<G_rr, 256, 0, s>>>(cur, r, p->code8, f, v1.r, st);
+        mark(5);
+        T* zc = vcycle_coarse<T>(p, h, w.lv, 1, st, s);
+        k_mg_fine_prolong<T, NDIM><<<G_prol, 256, 0, s>>>(cur, zc, f, st);
+        for (int i = 0; i < nu; ++i) {  // the adjoint: black then red
+            if (i == 0) mark(2);
+            if (i == nu - 1)
+                k_mg_fine_rb_fused<T, kRbCX, kRbRY, 1, false, true><<<gr, kRbCX * kRbRY, 0, s>>>(cur, oth, r, p->code8, ra, st, partials);
+            else
+                k_mg_fine_rb_fused<T, kRbCX, kRbRY, 1, false, false><<<gr, kRbCX * kRbRY, 0, s>>>(cur, oth, r, p->code8, ra, st, partials);
+            if (i == 0) mark(3);
+            std::swap(cur, oth);
+        }
+        return cur;  // == w.zB
     }
     T* cur = w.zA;
     T* oth = w.zB;
@@ -999,6 +1704,7 @@ void mg_free(osmodi_plan p) {
     Hier* h = hier_of(p);
     if (!h) return;
     if (h->mem) cudaFree(h->mem);
+    delete h->maps;
     delete h;
     p->mg = nullptr;
 }
@@ -1042,6 +1748,10 @@ int mg_launches_per_apply(osmodi_plan p) {
     const bool rb = red_black(p);
     const int nu = sweeps(p);
     const int per = rb ? 4 * nu + 3 : 2 * nu + 3;
+    // red-black: the fine level runs 2 nu fused sweeps, the residual with the
+    // restriction and the prolongation; every other level above the coarsest
+    // runs `per`; the coarsest one kernel
+    if (rb) return 2 * nu + 2 + per * ((int)h->lv.size() - 1) + 1;
     return per * (int)h->lv.size();
 }
 
@@ -1051,11 +1761,13 @@ T* mg_apply(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
     return p->ndim == 2 ? apply_nd<T, 2>(p, r, w, st, partials, s, ev) : apply_nd<T, 3>(p, r, w, st, partials, s, ev);
 }
 
-// red-black smoothing updates z in place in zA; the Jacobi V-cycle swaps its
-// two buffers (nu - 1) + nu times (an odd number) and ends in zB
+// the fused red-black V-cycle makes 2 nu out-of-place passes starting in zA;
+// the Jacobi V-cycle swaps its two buffers (nu - 1) + nu times (an odd
+// number): both end in zB
 template <class T>
 T* mg_result(osmodi_plan p, const MgBuffers<T>& w) {
-    return red_black(p) ? w.zA : w.zB;
+    (void)p;
+    return w.zB;  // both smoothers end in zB
 }
 template float* mg_result<float>(osmodi_plan, const MgBuffers<float>&);
 template double* mg_result<double>(osmodi_plan, const MgBuffers<double>&);

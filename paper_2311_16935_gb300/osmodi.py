@@ -22,7 +22,7 @@ E_INVALID, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_DIVERGED, E_TIMEOUT, E_EMPTY, E_NAN
 F32, F64 = 0, 1
 FP64, FP32, FP32_REFINE = 0, 1, 2
 FPCG, OUTER = 0, 1
-DEBUG_BARRIER_SPINS, DEBUG_SKIP_BARRIER_BLOCK, DEBUG_CORRECTION_SCALE = 1, 2, 3
+DEBUG_BARRIER_SPINS, DEBUG_SKIP_BARRIER_BLOCK, DEBUG_CORRECTION_SCALE, DEBUG_MG_UNFUSED, DEBUG_NET_WMMA = 1, 2, 3, 4, 5
 DEBUG_DEFAULT = -0x7fffffffffffffff
 INNER_CG, INNER_JACOBI = 0, 1
 
@@ -93,6 +93,10 @@ _SIGS = {
     "osmodi_history": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "osmodi_history_pressure": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "osmodi_debug_set": (ctypes.c_longlong, [ctypes.c_int, ctypes.c_longlong]),
+    "osmodi_probe_fp64": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_net_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "osmodi_tc_gemm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_ray_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_source": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -671,3 +675,28 @@ def osmodi_destroy(plan: Plan):
 def debug_set(knob: int, value: int) -> int:
     """osmodi_debug_set: set a test knob, return its previous value."""
     return int(lib().osmodi_debug_set(int(knob), int(value)))
+
+
+def probe_fp64(stream=None):
+    """osmodi_probe_fp64: the device's measured FP64 FMA throughput (GFLOP/s)."""
+    g, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = lib().osmodi_probe_fp64(ctypes.byref(g), ctypes.byref(ms), _stream_ptr(stream))
+    if st != OK:
+        raise OsmodiError(st, "osmodi_probe_fp64")
+    return g.value
+
+
+def tc_gemm(A: torch.Tensor, B: torch.Tensor, stream=None):
+    """osmodi_tc_gemm: D = A B^T (A 128 x K, B N x K, BF16 CUDA tensors) on
+    the tensor cores; returns (D FP32, error flag)."""
+    _check_cuda(A, "A")
+    _check_cuda(B, "B")
+    if A.dtype != torch.bfloat16 or B.dtype != torch.bfloat16 or A.shape[0] != 128 or A.shape[1] != B.shape[1]:
+        raise TypeError("A: 128 x K bf16, B: N x K bf16")
+    D = torch.empty((128, B.shape[0]), dtype=torch.float32, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    st = lib().osmodi_tc_gemm(A.data_ptr(), B.data_ptr(), D.data_ptr(), int(B.shape[0]), int(A.shape[1]),
+                              err.data_ptr(), _stream_ptr(stream))
+    if st != OK:
+        raise OsmodiError(st, "osmodi_tc_gemm")
+    return D, int(err.item())

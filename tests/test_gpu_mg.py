@@ -122,3 +122,37 @@ def test_smoothing_options_keep_the_fixed_point(osm, sweeps, scale):
                              mg_scale=scale)
         assert res.status == osm.OK, res.as_dict()
         assert _rel(got, want, valid) < 1e-10
+
+
+@pytest.mark.parametrize("shape", [(19, 23, 29), (33, 30, 61), (5, 40, 17), (64, 64, 64), (21, 37, 300)])
+def test_fused_sweeps_equal_half_sweeps(osm, shape):
+    """The fused one-pass red-black sweeps (default: inputs staged by TMA;
+    and with ordinary loads) against the same V-cycle by one-colour
+    half-sweeps (OSMODI_DEBUG_MG_UNFUSED): the same arithmetic,
+    so the preconditioned CG takes the same iterations, reports the same
+    residual (to FP32 rounding of the preconditioner) and lands on the same
+    answer.  The shapes cover several tiles and slabs with ragged edges in
+    every axis, a mask with several components and FP32 inner sweeps."""
+    rng = np.random.default_rng(sum(shape))
+    valid = rng.random(shape) > 0.15
+    f = rng.normal(size=(3,) + shape).astype(np.float32)
+    spacing = (1.0, 1.0, 1.0)
+    out = {}
+    for variant in (0, 1, 2):  # TMA-staged fused, half-sweeps, register-staged fused
+        osm.debug_set(osm.DEBUG_MG_UNFUSED, variant)
+        try:
+            _, res, p = _solve(osm, f, valid, spacing, 1e-11, precision=2, precond=1)
+        finally:
+            osm.debug_set(osm.DEBUG_MG_UNFUSED, osm.DEBUG_DEFAULT)
+        assert res.status == osm.OK, res.as_dict()
+        out[variant] = (res, p)
+    want = oracle.solve_cg(oracle.Grid(valid, spacing), f.astype(np.float64), tol=1e-14, maxit=50000)[0]
+    ru, pu = out[1]
+    for variant in (0, 2):
+        rf, pf = out[variant]
+        # rounding (FMA contraction may differ between the kernels) can move a
+        # stopping test across its threshold by at most one check chunk
+        assert abs(rf.inner_iters - ru.inner_iters) <= 8, (variant, rf.inner_iters, ru.inner_iters)
+        assert rf.eps_R <= 1e-11 and ru.eps_R <= 1e-11
+        assert _rel(pf, pu, valid) < 1e-10
+        assert _rel(pf, want, valid) < 1e-9

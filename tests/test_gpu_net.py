@@ -60,8 +60,15 @@ def _rel(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-30))
 
 
-def test_forward_matches_reference(osm):
-    n = 16
+@pytest.mark.parametrize("n", [16, 24])
+def test_forward_matches_reference(osm, n):
+    """The forward pass (tcgen05 tensor cores) element by element against the
+    FP64 reference fed the same BF16 weights and input and storing every
+    activation in BF16 as the GPU does: max |GPU - reference| <= 1e-2 of the
+    output's largest magnitude.  Rounding the FP32-accumulated sums to BF16
+    can land on the other side of a BF16 rounding boundary than the FP64
+    sum; such flips are one BF16 ulp (2^-8 relative) of one activation and
+    stay far below the bound after the remaining layers."""
     valid, f, target = _problem(n, 1)
     params, d = _params(2)
     net = osm.Net((n, n, n), train=False)
@@ -72,19 +79,62 @@ def test_forward_matches_reference(osm):
     net.forward(g, m, 1.0, p)
     got = net.get_output()
     x, s = onet.features(f.astype(np.float64), valid, 1.0)
-    want, _ = onet.forward(_oracle_params(d), bf16_round(x))
-    assert _rel(got, want) < 3e-2
+    want, _ = onet.forward(_oracle_params(d), bf16_round(x), store=bf16_round)
+    scale = float(np.abs(want).max())
+    assert float(np.abs(got - want).max()) <= 1e-2 * scale
+    assert _rel(got, want) < 1e-2
     np.testing.assert_allclose(p.cpu().numpy()[valid], got[valid] * s, rtol=1e-5, atol=1e-6 * s)
     net.close()
+
+
+def test_tcgen05_and_wmma_paths_agree(osm):
+    """Forward output and every parameter gradient of the tcgen05 path
+    against the warp-level wmma path (OSMODI_DEBUG_NET_WMMA) on the same
+    inputs: the same BF16 products summed in FP32 in another order."""
+    n = 32
+    valid, f, target = _problem(n, 5)
+    params, d = _params(6)
+    g = torch.from_numpy(f).cuda()
+    m = torch.from_numpy(valid.astype(np.uint8)).cuda()
+    tgt = torch.from_numpy(target).cuda()
+    outs = {}
+    for wmma in (0, 1):
+        osm.debug_set(osm.DEBUG_NET_WMMA, wmma)
+        try:
+            net = osm.Net((n, n, n), train=True)
+            net.set_params(params)
+            loss = net.backward(g, m, 1.0, tgt)
+            outs[wmma] = (net.get_output(), net.get_grads(), loss)
+            net.close()
+        finally:
+            osm.debug_set(osm.DEBUG_NET_WMMA, osm.DEBUG_DEFAULT)
+    (o0, g0, l0), (o1, g1, l1) = outs[0], outs[1]
+    assert float(np.abs(o0 - o1).max()) <= 1e-2 * float(np.abs(o1).max())
+    assert l0 == pytest.approx(l1, rel=1e-2)
+    from paper_2311_16935_gb300 import seednet
+
+    d0, d1 = seednet.unpack(g0), seednet.unpack(g1)
+    scale = max(float(np.abs(v).max()) for v in d1.values())
+    for k in d1:
+        a, b = np.ravel(d0[k]).astype(np.float64), np.ravel(d1[k]).astype(np.float64)
+        if k == "out.b":  # exactly 0 (the loss ignores constants): compare absolutely
+            assert abs(a[0]) <= 1e-5 * scale and abs(b[0]) <= 1e-5 * scale
+            continue
+        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+        assert _rel(a, b) < 5e-2 and cos > 0.998, (k, _rel(a, b), cos)
 
 
 def test_parameter_gradients_match_reference(osm):
     """Parameter gradients against the FP64 reference fed the same BF16-stored
     activations and operands.  The remaining differences are FP32-vs-FP64
-    accumulation flipping individual BF16 roundings; their relative effect
-    grows with depth (fewer voxels per coarse tensor), so the bound is 2e-2
-    at full and half resolution and 8e-2 below, with every gradient tensor
-    pointing the same way (cosine >= 0.997)."""
+    accumulation flipping individual BF16 roundings (one BF16 ulp, 2^-8
+    relative, of an activation whose sum lies within ~1e-6 of a rounding
+    boundary; a flip can also flip a ReLU).  A weight gradient sums such
+    errors over the voxels of its level, so its relative error grows as the
+    level shrinks: on this 32^3 net the levels below half resolution hold 8^3
+    and 4^3 voxels.  Bounds: 2e-2 (the survey's figure) at full and half
+    resolution, 5e-2 at the two coarse levels (measured worst 3.5e-2, the
+    4^3 bottleneck), every tensor pointing the same way (cosine >= 0.999)."""
     n = 32
     valid, f, target = _problem(n, 3)
     params, d = _params(4)
@@ -116,8 +166,9 @@ def test_parameter_gradients_match_reference(osm):
         a, b = np.ravel(gd[k]).astype(np.float64), np.ravel(ref[k])
         cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
         worst[k] = (_rel(a, b), cos)
+    print("gradient rel. error, cosine by tensor:", sorted(worst.items(), key=lambda kv: -kv[1][0]))
     bad = {k: v for k, v in worst.items()
-           if v[0] > (2e-2 if level.get(k.split(".")[0], 2) <= 1 else 8e-2) or v[1] < 0.997}
+           if v[0] > (2e-2 if level.get(k.split(".")[0], 2) <= 1 else 5e-2) or v[1] < 0.999}
     assert not bad, sorted(worst.items(), key=lambda kv: -kv[1][0])
     net.close()
 
@@ -141,3 +192,29 @@ def test_training_reduces_loss_and_seed_helps(osm):
         saved.append(r_zero.inner_iters - r_seed.inner_iters)
     assert np.mean(dists) < 0.9, dists
     assert np.mean(saved) > 0, saved
+
+
+@pytest.mark.parametrize("n", [64, 128, 256])
+def test_forward_paths_agree_at_width(osm, n):
+    """At the widths where the tensor-core kernels change tiling (rows of 64,
+    one 128-voxel segment, two segments per row) the forward pass on tcgen05
+    equals the wmma path's to BF16 rounding of the stored activations."""
+    from paper_2311_16935_gb300 import seednet
+
+    prob = seednet.blob_problem(n, 77)
+    params = seednet.init_params(3)
+    outs = []
+    for wmma in (0, 1):
+        osm.debug_set(osm.DEBUG_NET_WMMA, wmma)
+        try:
+            net = osm.Net((n, n, n), train=False)
+            net.set_params(params)
+            p = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+            net.forward(prob.grad, None, 1.0, p)
+            outs.append(net.get_output())
+            net.close()
+        finally:
+            osm.debug_set(osm.DEBUG_NET_WMMA, osm.DEBUG_DEFAULT)
+    a, b = outs
+    assert np.isfinite(a).all()
+    assert float(np.abs(a - b).max()) <= 1e-2 * float(np.abs(b).max())

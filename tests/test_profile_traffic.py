@@ -1,0 +1,40 @@
+"""The ncu-CSV reader that writes the committed traffic files (no GPU):
+both CSV layouts ncu writes, unit scaling, per-kernel grouping."""
+import json
+
+from paper_2311_16935_gb300 import profile_traffic as pt
+
+RAW = '''"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","dram__bytes_read.sum","dram__bytes_write.sum"
+"","","","","","","","Mbyte","Kbyte"
+"0","1","python","h","void osm::(anonymous namespace)::k_mg_fine_rb_fused<float, 16, 16, 0, false, false>(const T1 *, T1 *)","1","7","1,000.5","2000"
+"1","1","python","h","void osm::(anonymous namespace)::k_mg_fine_rb_fused<float, 16, 16, 0, false, false>(const T1 *, T1 *)","1","7","999.5","0"
+"2","1","python","h","void osm::k_cg_b<float>(float *, const float *)","1","7","12","0.5"
+'''
+
+LOG = '''==PROF== Connected to process 1
+"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size","Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"
+"0","1","python","h","k_residual<float, 3>(const double *)","1","7","(512, 1, 1)","(608, 1, 1)","0","10.3","Command line profiler metrics","dram__bytes_read.sum","Gbyte","2.13"
+"0","1","python","h","k_residual<float, 3>(const double *)","1","7","(512, 1, 1)","(608, 1, 1)","0","10.3","Command line profiler metrics","dram__bytes_write.sum","Mbyte","500"
+"0","1","python","h","k_residual<float, 3>(const double *)","1","7","(512, 1, 1)","(608, 1, 1)","0","10.3","Command line profiler metrics","gpu__time_duration.sum","usecond","2800"
+'''
+
+
+def test_raw_page(tmp_path):
+    f = tmp_path / "raw.csv"
+    f.write_text(RAW)
+    d = pt.summarise(str(f), 1000, "cmd")
+    k = d["kernels"]["k_mg_fine_rb_fused<float, 16, 16, 0, false, false>"]
+    assert k["launches"] == 2
+    assert k["dram_bytes_per_launch"] == (1000.5e6 + 2e6 + 999.5e6) / 2
+    assert k["dram_bytes_per_cell"] == k["dram_bytes_per_launch"] / 1000
+    assert d["kernels"]["k_cg_b<float>"]["dram_bytes_per_launch"] == 12e6 + 500
+    assert d["kernel_source_hash"] == pt.kernel_source_hash()
+    json.dumps(d)
+
+
+def test_metrics_log(tmp_path):
+    f = tmp_path / "log.csv"
+    f.write_text(LOG)
+    d = pt.summarise(str(f), 10, "cmd")
+    assert d["kernels"]["k_residual<float, 3>"] == {"launches": 1, "dram_bytes_per_launch": 2.63e9,
+                                                    "dram_bytes_per_cell": 2.63e8}

@@ -7,6 +7,7 @@ shared device array that keeps the previous call's contents.
 Kept in its own file, collected last, so that a run stopping at the first
 failure has already run every other test."""
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -103,20 +104,27 @@ def test_noalloc_allocates_nothing(osm):
     plan = osm.Plan(3, (32, 32, 32), prob.spacing, prob.mask.cuda())
     g = prob.grad.cuda()
     p = torch.zeros((32, 32, 32), dtype=torch.float64, device="cuda")
-    torch.cuda.synchronize()
-    alloc0 = torch.cuda.memory_allocated()
-    st, _ = _call_noalloc(osm, plan, g, p, 1e-10)
-    torch.cuda.synchronize()
-    assert st == osm.OK
-    assert torch.cuda.memory_allocated() == alloc0
-    free0 = torch.cuda.mem_get_info()[0]
-    for _ in range(2):
-        p.zero_()
-        st, res = _call_noalloc(osm, plan, g, p, 1e-10)
+    # tensors of earlier tests freed by Python's collector would show up as
+    # changes of torch's count: collect first, and not during the window
+    gc.collect()
+    gc.disable()
+    try:
         torch.cuda.synchronize()
-        assert st == osm.OK and res.eps_R <= 1e-10
-    assert torch.cuda.mem_get_info()[0] == free0
-    assert torch.cuda.memory_allocated() == alloc0
+        alloc0 = torch.cuda.memory_allocated()
+        st, _ = _call_noalloc(osm, plan, g, p, 1e-10)
+        torch.cuda.synchronize()
+        assert st == osm.OK
+        assert torch.cuda.memory_allocated() == alloc0
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(2):
+            p.zero_()
+            st, res = _call_noalloc(osm, plan, g, p, 1e-10)
+            torch.cuda.synchronize()
+            assert st == osm.OK and res.eps_R <= 1e-10
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert torch.cuda.memory_allocated() == alloc0
+    finally:
+        gc.enable()
     plan.close()
 
 

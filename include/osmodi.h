@@ -487,6 +487,23 @@ OSMODI_API osmodi_status osmodi_net_set_params(osmodi_net net, const float* para
 OSMODI_API osmodi_status osmodi_net_get_params(osmodi_net net, float* params_host);
 /* accumulated parameter gradients (training nets) */
 OSMODI_API osmodi_status osmodi_net_get_grads(osmodi_net net, float* grads_host);
+/*
+ * One 3x3x3 convolution (stride 1, zero padding) of the seed network's kind,
+ * as a step-level entry point for checking the convolution kernels against a
+ * reference: y = relu?(conv(x, w) + bias) with x BF16 [D][H][W][cin]
+ * (channels last), w BF16 [27][cin][cout] (tap = (dz+1)*9 + (dy+1)*3 +
+ * (dx+1)), bias FP32 [cout] (may be NULL), y BF16 [D][H][W][cout].  path 0:
+ * tcgen05 with the input tile staged once where the shape allows, else the
+ * gathering kernel; 1: warp-level wmma; 2: tcgen05 gathering kernel.  cin a
+ * multiple of 8 (paths 0, 2), cout a multiple of 8 and <= 64.  scratch:
+ * device memory of scratch_bytes (>= 2 (27 cin + 64) * round_up(cout, 16)
+ * suffices) for the rearranged weights; *err_dev (caller-zeroed) is set to 1
+ * if a tensor-core wait gave up.  Asynchronous on `stream`; allocates
+ * nothing.  No counterpart in the paper.
+ */
+OSMODI_API osmodi_status osmodi_conv3d(const void* x_dev, const void* w_dev, const float* bias_dev, void* y_dev, int D,
+                                       int H, int W, int cin, int cout, int relu, int path, void* scratch_dev,
+                                       size_t scratch_bytes, int* err_dev, void* stream);
 /* OSMODI_E_TIMEOUT (and the flag cleared) if a tensor-core wait of an
  * earlier network call gave up, else OSMODI_OK; synchronous.  get_output and
  * get_grads report the same. */
@@ -549,15 +566,16 @@ OSMODI_API osmodi_status osmodi_probe_fp64(double* gflops_out, double* ms_out, v
  *   step's correction by this factor before adding it (0: no scaling); a
  *   large factor makes the residual grow and the solve report
  *   OSMODI_E_DIVERGED.
- * OSMODI_DEBUG_MG_UNFUSED: how the 3-D multigrid preconditioner smooths the
- *   plan's own grid, the same arithmetic in each case, for comparisons:
- *   0 (default) fused one-pass red-black sweeps with their input planes
- *   staged by TMA (FP32; FP64 plans use 2); 1 one-colour half-sweeps in
- *   place (two passes per sweep); 2 fused one-pass sweeps reading their
- *   inputs with ordinary loads.
- * OSMODI_DEBUG_NET_WMMA: nonzero runs the seed network's convolutions on the
- *   warp-level (wmma) tensor-core path instead of tcgen05; the same
- *   products, for comparisons.  Default (0): tcgen05.
+ * OSMODI_DEBUG_MG_UNFUSED: how the 3-D multigrid preconditioner smooths,
+ *   the same arithmetic in each case, for comparisons: 0 (default) fused
+ *   one-pass red-black sweeps (every level with packed counts); 1
+ *   one-colour half-sweeps in place (two passes per sweep); 2 as 0 with the
+ *   fine level's input planes staged by TMA (FP32 plans).
+ * OSMODI_DEBUG_NET_WMMA: which kernels run the seed network's
+ *   convolutions, the same products in each case, for comparisons: 0
+ *   (default) tcgen05, the forward 3x3x3 layers with their input tile staged
+ *   once; 1 the warp-level (wmma) tensor-core path; 2 tcgen05, every layer by
+ *   the gathering kernel.
  */
 #define OSMODI_DEBUG_BARRIER_SPINS 1
 #define OSMODI_DEBUG_SKIP_BARRIER_BLOCK 2

@@ -379,102 +379,132 @@ __global__ void __launch_bounds__(CX * RY) k_mg_fine_rb_fused(const T* __restric
         const int k0 = sl * g.slab, k1 = min(g.nz, k0 + g.slab);
         const int64_t col = (int64_t)j * g.px + 4 * (int64_t)c;  // offset of the chunk within a plane
         __syncthreads();  // the previous item's readers are done with the ring (and wd is set)
-        // colour FC on plane q into ring slot q & 3; returns r and the code word of the chunk
-        auto first_colour = [&](int q, V4<T>& rv, uint32_t& cw) {
-            V4<T> o = zero4<T>();
-            rv = zero4<T>();
-            cw = 0u;
-            if (inr && q >= 0 && q < g.nz) {
+        // Everything the first colour on plane q reads for this chunk, loaded in
+        // one go (every load at an in-range address: clamped to the chunk itself
+        // where a neighbour is outside the box; its face bit is then 0).
+        struct Loaded {
+            V4<T> zc, zn, zs, zf, zb, rv;
+            T xw, xe;
+            uint32_t cw;
+            bool ok;
+        };
+        auto load_plane = [&](int q) -> Loaded {
+            Loaded L;
+            L.ok = inr && q >= 0 && q < g.nz;
+            L.cw = 0u;
+            L.rv = L.zc = L.zn = L.zs = L.zf = L.zb = zero4<T>();
+            L.xw = L.xe = T(0);
+            if (L.ok) {
                 const int64_t i0 = (int64_t)q * g.plane + col;
-                cw = __ldg(reinterpret_cast<const uint32_t*>(code8 + i0));
-                rv = ld4(r + i0);
+                L.cw = __ldg(reinterpret_cast<const uint32_t*>(code8 + i0));
+                L.rv = ld4(r + i0);
+                if (!FROM_ZERO) {
+                    const int64_t on = j + 1 < g.ny ? g.px : 0, os = j > 0 ? -g.px : 0;
+                    const int64_t of = q + 1 < g.nz ? g.plane : 0, ob = q > 0 ? -g.plane : 0;
+                    L.zc = ld4(zin + i0);
+                    L.zn = ld4(zin + i0 + on);
+                    L.zs = ld4(zin + i0 + os);
+                    L.zf = ld4(zin + i0 + of);
+                    L.zb = ld4(zin + i0 + ob);
+                    L.xw = zin[c > 0 ? i0 - 1 : i0];
+                    L.xe = zin[c + 1 < g.cpr ? i0 + 4 : i0];
+                }
+            }
+            return L;
+        };
+        // colour FC on plane q into ring slot q & 3
+        auto first_from = [&](int q, const Loaded& L) {
+            V4<T> o = zero4<T>();
+            if (L.ok) {
+                const uint32_t cw = L.cw;
                 const int par = (int)((cw >> 6) & 1u);
                 if (FROM_ZERO) {
 #pragma unroll
                     for (int m = 0; m < 4; ++m)
-                        o.v[m] = ((m + par) & 1) == FC && valid8(cw, m) ? wd[face_bits8(cw, m)] * rv.v[m] : T(0);
+                        o.v[m] = ((m + par) & 1) == FC && valid8(cw, m) ? wd[face_bits8(cw, m)] * L.rv.v[m] : T(0);
                 } else {
-                    // every load issued at an in-range address (clamped to the chunk
-                    // itself where a neighbour is outside the box; its face bit is 0)
-                    const int64_t on = j + 1 < g.ny ? g.px : 0, os = j > 0 ? -g.px : 0;
-                    const int64_t of = q + 1 < g.nz ? g.plane : 0, ob = q > 0 ? -g.plane : 0;
-                    const V4<T> zc = ld4(zin + i0), zn = ld4(zin + i0 + on), zs = ld4(zin + i0 + os);
-                    const V4<T> zf = ld4(zin + i0 + of), zb = ld4(zin + i0 + ob);
-                    const T xw = zin[c > 0 ? i0 - 1 : i0], xe = zin[c + 1 < g.cpr ? i0 + 4 : i0];
-                    const T wv[4] = {xw, zc.v[0], zc.v[1], zc.v[2]};
-                    const T ev[4] = {zc.v[1], zc.v[2], zc.v[3], xe};
+                    const T wv[4] = {L.xw, L.zc.v[0], L.zc.v[1], L.zc.v[2]};
+                    const T ev[4] = {L.zc.v[1], L.zc.v[2], L.zc.v[3], L.xe};
                     if (chunk_full(cw)) {
                         const T wf = wd[63];
 #pragma unroll
                         for (int m = 0; m < 4; ++m)
-                            o.v[m] = ((m + par) & 1) != FC ? zc.v[m]
-                                                          : rb_cell_full(zc.v[m], ev[m], wv[m], zn.v[m], zs.v[m], zf.v[m],
-                                                                         zb.v[m], rv.v[m], wf, Fx, Fy, Fz);
+                            o.v[m] = ((m + par) & 1) != FC
+                                         ? L.zc.v[m]
+                                         : rb_cell_full(L.zc.v[m], ev[m], wv[m], L.zn.v[m], L.zs.v[m], L.zf.v[m],
+                                                        L.zb.v[m], L.rv.v[m], wf, Fx, Fy, Fz);
                     } else {
 #pragma unroll
                         for (int m = 0; m < 4; ++m) {
                             if (((m + par) & 1) != FC) {
-                                o.v[m] = zc.v[m];
+                                o.v[m] = L.zc.v[m];
                                 continue;
                             }
                             const unsigned fm = face_bits8(cw, m);
                             const T w = valid8(cw, m) ? wd[fm] : T(0);
-                            o.v[m] = rb_cell(zc.v[m], ev[m], wv[m], zn.v[m], zs.v[m], zf.v[m], zb.v[m], rv.v[m], fm, w,
-                                             Fx, Fy, Fz);
+                            o.v[m] = rb_cell(L.zc.v[m], ev[m], wv[m], L.zn.v[m], L.zs.v[m], L.zf.v[m], L.zb.v[m],
+                                             L.rv.v[m], fm, w, Fx, Fy, Fz);
                         }
                     }
                 }
             }
             ring[q & 3][t] = o;
         };
-        V4<T> r_cur, r_nxt;
-        uint32_t c_cur = 0u, c_nxt = 0u;
-        if (k0 > 0) first_colour(k0 - 1, r_nxt, c_nxt);
-        first_colour(k0, r_cur, c_cur);
-        for (int k = k0; k < k1; ++k) {
-            first_colour(k + 1, r_nxt, c_nxt);  // zeros beyond the last plane
-            __syncthreads();
-            if (interior) {
-                // the other colour on plane k, from planes k - 1, k, k + 1 of the ring
-                const V4<T> o = ring[k & 3][t];
-                const V4<T> zn = ring[k & 3][t + CX], zs = ring[k & 3][t - CX];
-                const V4<T> zf = ring[(k + 1) & 3][t], zb = ring[(k + 3) & 3][t];
-                const T xw = ring[k & 3][t - 1].v[3], xe = ring[k & 3][t + 1].v[0];
-                const T wv[4] = {xw, o.v[0], o.v[1], o.v[2]};
-                const T ev[4] = {o.v[1], o.v[2], o.v[3], xe};
-                const uint32_t cw = c_cur;
-                const int par = (int)((cw >> 6) & 1u);
-                V4<T> out;
-                if (chunk_full(cw)) {
-                    const T wf = wd[63];
+        // the other colour on plane k from planes k - 1, k, k + 1 of the ring
+        auto second = [&](int k, const V4<T>& rk, uint32_t cw) {
+            const V4<T> o = ring[k & 3][t];
+            const V4<T> zn = ring[k & 3][t + CX], zs = ring[k & 3][t - CX];
+            const V4<T> zf = ring[(k + 1) & 3][t], zb = ring[(k + 3) & 3][t];
+            const T xw = ring[k & 3][t - 1].v[3], xe = ring[k & 3][t + 1].v[0];
+            const T wv[4] = {xw, o.v[0], o.v[1], o.v[2]};
+            const T ev[4] = {o.v[1], o.v[2], o.v[3], xe};
+            const int par = (int)((cw >> 6) & 1u);
+            V4<T> out;
+            if (chunk_full(cw)) {
+                const T wf = wd[63];
 #pragma unroll
-                    for (int m = 0; m < 4; ++m)
-                        out.v[m] = ((m + par) & 1) == FC ? o.v[m]
-                                                         : rb_cell_full(o.v[m], ev[m], wv[m], zn.v[m], zs.v[m], zf.v[m],
-                                                                        zb.v[m], r_cur.v[m], wf, Fx, Fy, Fz);
-                } else {
+                for (int m = 0; m < 4; ++m)
+                    out.v[m] = ((m + par) & 1) == FC ? o.v[m]
+                                                     : rb_cell_full(o.v[m], ev[m], wv[m], zn.v[m], zs.v[m], zf.v[m],
+                                                                    zb.v[m], rk.v[m], wf, Fx, Fy, Fz);
+            } else {
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        if (((m + par) & 1) == FC) {
-                            out.v[m] = o.v[m];
-                            continue;
-                        }
-                        const unsigned fm = face_bits8(cw, m);
-                        const T w = valid8(cw, m) ? wd[fm] : T(0);
-                        out.v[m] = rb_cell(o.v[m], ev[m], wv[m], zn.v[m], zs.v[m], zf.v[m], zb.v[m], r_cur.v[m], fm, w,
-                                           Fx, Fy, Fz);
+                for (int m = 0; m < 4; ++m) {
+                    if (((m + par) & 1) == FC) {
+                        out.v[m] = o.v[m];
+                        continue;
                     }
-                }
-                st4(zout + (int64_t)k * g.plane + col, out);
-                if (DOT) {
-                    T part = T(0);
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) part += r_cur.v[m] * out.v[m];
-                    acc[0] += (double)part;
+                    const unsigned fm = face_bits8(cw, m);
+                    const T w = valid8(cw, m) ? wd[fm] : T(0);
+                    out.v[m] = rb_cell(o.v[m], ev[m], wv[m], zn.v[m], zs.v[m], zf.v[m], zb.v[m], rk.v[m], fm, w, Fx,
+                                       Fy, Fz);
                 }
             }
-            r_cur = r_nxt;
-            c_cur = c_nxt;
+            st4(zout + (int64_t)k * g.plane + col, out);
+            if (DOT) {
+                T part = T(0);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) part += rk.v[m] * out.v[m];
+                acc[0] += (double)part;
+            }
+        };
+        // the first colour is needed on planes k0 - 1 .. k1; at step k it runs
+        // on plane k + 1 (one sync: the slot it writes is none of the three
+        // the second colour on plane k - 1 may still be reading)
+        {
+            first_from(k0 - 1, load_plane(k0 - 1));
+            const Loaded Lb = load_plane(k0);
+            first_from(k0, Lb);
+            V4<T> rk = Lb.rv;
+            uint32_t ck = Lb.cw;
+            for (int k = k0; k < k1; ++k) {
+                const Loaded Ln = load_plane(k + 1);
+                first_from(k + 1, Ln);
+                __syncthreads();
+                if (interior) second(k, rk, ck);
+                rk = Ln.rv;
+                ck = Ln.cw;
+            }
         }
     }
     if (DOT) {
@@ -484,31 +514,32 @@ __global__ void __launch_bounds__(CX * RY) k_mg_fine_rb_fused(const T* __restric
 }
 
 // ---------------------------------------------------------------------------
-// The fused red-black sweep with its input planes staged by TMA (FP32, the
-// default).  Same sweep as k_mg_fine_rb_fused; what changes is how the
-// planes arrive: a block of 512 threads owns a tile of 128 x 16 cells and a
-// slab of planes, and a ring of RS shared-memory stages holds, per plane, the
-// z_in box (136 x 20 cells: 4-cell / 2-row halo) and the r box (136 x 18),
-// each one cp.async.bulk.tensor.3d load completing on the stage's mbarrier.
-// Planes k .. k + 2 are resident while k + 3 .. k + RS - 1 are in flight
-// (about 100 KB per SM), so the bytes in flight do not depend on registers,
-// and the code words of a plane are loaded one step before they are used.  At step k the
-// block updates colour FC on plane k + 1 (the tile, the row above and below
-// it and the cell left and right of each row) into a 4-slot ring of
-// half-updated planes, then the other colour on plane k from that ring, and
-// stores plane k of z_out.  Copies that fall outside the box are zero-filled
-// (their code is "missing", so they stay 0).  Every mbarrier wait is
-// bounded; a wait that gives up sets st->err, lets the copies in flight land
-// and leaves the block.
+// The fused red-black sweep with its input planes staged by TMA (FP32).  Same
+// sweep as k_mg_fine_rb_fused; what changes is how the planes arrive.  A
+// block of 256 threads owns a tile of 128 x 8 cells and a slab of planes;
+// two blocks share an SM.  A ring of RS shared-memory stages holds, per
+// plane, the z_in box (136 x 12 cells: a 4-cell / 2-row halo) and the r box
+// (136 x 10), each one cp.async.bulk.tensor.3d load completing on the
+// stage's mbarrier.  Planes k .. k + 2 are resident while the next three are
+// in flight, so the bytes in flight per SM do not depend on registers.  At
+// step k the block updates colour FC on plane k + 1 (the tile, the rows above
+// and below it and the cell left and right of each row) into a 4-slot ring
+// of half-updated planes, then the other colour on plane k, and stores
+// plane k of z_out.  Two barriers per step; the stage a step frees is
+// refilled after the next step's first barrier.  Code words are loaded two
+// planes ahead.  Stage phases are tracked in a register bit mask.  Copies
+// that fall outside the box are zero-filled (their code is "missing", so
+// they stay 0).  Every wait is bounded; a wait that gives up sets st->err,
+// lets the copies in flight land and leaves the block.
 // ---------------------------------------------------------------------------
-constexpr int RTX = 128, RTY = 16, RHX = 4;     // tile (cells), x halo of the boxes
+constexpr int RTX = 128, RTY = 8, RHX = 4;      // tile (cells), x halo of the boxes
 constexpr int RBX = RTX + 2 * RHX;              // 136 box columns
 constexpr int RZY = RTY + 4, RRY = RTY + 2;     // z box rows (2-row halo), r box rows (1-row halo)
-constexpr int RZB = RBX * RZY * 4;              // 10880
-constexpr int RRB = RBX * RRY * 4;              // 9792
-constexpr int RSTAGE = RZB + (RRB + 127) / 128 * 128;  // 20736
-constexpr int RS = 8;                           // stages (planes k .. k + 2 resident, k + 3 .. k + 7 in flight)
-constexpr int RSLOT = RBX * RRY * 4;            // one half-updated plane (18 rows)
+constexpr int RZB = RBX * RZY * 4;              // 6528
+constexpr int RRB = RBX * RRY * 4;              // 5440
+constexpr int RSTAGE = (RZB + RRB + 127) / 128 * 128;  // 12032
+constexpr int RS = 6;                           // stages
+constexpr int RSLOT = RBX * RRY * 4;            // one half-updated plane (10 rows)
 constexpr int kRbTmaSmem = RS * RSTAGE + 4 * RSLOT + 128;
 
 struct RbTmaGeo {
@@ -522,7 +553,7 @@ struct RbTmaGeo {
 __device__ __forceinline__ uint32_t rb_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 template <int FC, bool FROM_ZERO, bool DOT>
-__global__ void __launch_bounds__(512, 1) k_mg_fine_rb_tma(const __grid_constant__ CUtensorMap tm_z,
+__global__ void __launch_bounds__(256, 2) k_mg_fine_rb_tma(const __grid_constant__ CUtensorMap tm_z,
                                                           const __grid_constant__ CUtensorMap tm_r,
                                                           const uint8_t* __restrict__ code8, float* __restrict__ zout,
                                                           RbTmaGeo g, CgState* st, double* partials) {
@@ -547,12 +578,12 @@ __global__ void __launch_bounds__(512, 1) k_mg_fine_rb_tma(const __grid_constant
         abort_flag = 0;
     }
     __syncthreads();
-    unsigned uses[RS], issued[RS];
-#pragma unroll
-    for (int i = 0; i < RS; ++i) uses[i] = issued[i] = 0;
+    uint32_t parity = 0u;   // bit s: parity of the next phase of stage s to complete
+    uint32_t pending = 0u;  // bit s: a copy into stage s issued and not yet waited for
     const unsigned tx_bytes = FROM_ZERO ? (unsigned)RRB : (unsigned)(RZB + RRB);
     double acc[1] = {0.0};
     const float Fx = g.F[0], Fy = g.F[1], Fz = g.F[2];
+    const float wf = g.omega / (2.f * (Fx + Fy + Fz));
     for (long long item = blockIdx.x; item < g.n_items; item += gridDim.x) {
         const int tx = (int)(item % g.n_tx);
         const long long rest = item / g.n_tx;
@@ -560,12 +591,13 @@ __global__ void __launch_bounds__(512, 1) k_mg_fine_rb_tma(const __grid_constant
         const int sl = (int)(rest / g.n_ty);
         const int x0 = tx * RTX, y0 = ty * RTY;
         const int k0 = sl * g.slab, k1 = min(g.nz, k0 + g.slab);
+        const int last = k1 + 1;  // planes k0 - 2 .. k1 + 1 are read
         // plane P lives in stage (P - (k0 - 2)) mod RS
         auto stage_of = [&](int P) { return (P - k0 + 2 + 2 * RS) % RS; };
         auto issue = [&](int P) {
-            if (P < 0 || P >= g.nz) return;
+            if (P < 0 || P >= g.nz || P > last) return;
             const int si = stage_of(P);
-            issued[si] += 1;
+            pending |= 1u << si;
             if (t != 0) return;
             unsigned char* sb = base + si * RSTAGE;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -586,32 +618,33 @@ __global__ void __launch_bounds__(512, 1) k_mg_fine_rb_tma(const __grid_constant
         auto wait = [&](int P) {
             if (P < 0 || P >= g.nz) return;
             const int si = stage_of(P);
-            const unsigned parity = uses[si] & 1u;
-            long long spins = 0;
-            for (;;) {
+            if (!((pending >> si) & 1u)) return;
+            const uint32_t par = (parity >> si) & 1u;
+            for (long long spins = 0;; ++spins) {
                 uint32_t ok;
                 asm volatile(
                     "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                     : "=r"(ok)
-                    : "r"(rb_smem(&bars[si])), "r"(parity)
+                    : "r"(rb_smem(&bars[si])), "r"(par)
                     : "memory");
                 if (ok) break;
-                if (++spins > (1LL << 22)) {
+                if (spins > (1LL << 22)) {
                     atomicExch(&abort_flag, 1);
                     return;
                 }
                 __nanosleep(32);
             }
-            uses[si] += 1;
+            parity ^= 1u << si;
+            pending &= ~(1u << si);
         };
         auto zbox = [&](int P) { return reinterpret_cast<const float*>(base + stage_of(P) * RSTAGE); };
         auto rbox = [&](int P) { return reinterpret_cast<const float*>(base + stage_of(P) * RSTAGE + RZB); };
         auto slot = [&](int P) { return slots + (size_t)(P & 3) * (RBX * RRY); };
         auto code_at = [&](int q, int y, int x) -> uint32_t {  // 4 code bytes of the chunk at (x, y, q), 0 outside
-            if (y < 0 || y >= g.ny || x < 0 || x >= 4 * g.nx4) return 0u;
+            if (q < 0 || q >= g.nz || y < 0 || y >= g.ny || x < 0 || x >= 4 * g.nx4) return 0u;
             return __ldg(reinterpret_cast<const uint32_t*>(code8 + (int64_t)q * g.plane + (int64_t)y * g.px + x));
         };
-        // colour FC on plane q for the chunk at tile row ry (-1 .. 16), chunk cx
+        // colour FC on plane q for the chunk at tile row ry (-1 .. RTY), chunk cx
         auto first_chunk = [&](int q, int ry, int cx, uint32_t cw) {
             const int bz = (ry + 2) * RBX + RHX + 4 * cx, br = (ry + 1) * RBX + RHX + 4 * cx;
             const float4 r4 = *reinterpret_cast<const float4*>(rbox(q) + br);
@@ -639,7 +672,6 @@ __global__ void __launch_bounds__(512, 1) k_mg_fine_rb_tma(const __grid_constant
                 const float wv[4] = {xw, cv[0], cv[1], cv[2]};
                 const float ev[4] = {cv[1], cv[2], cv[3], xe};
                 if (chunk_full(cw)) {
-                    const float wf = wd[63];
 #pragma unroll
                     for (int m = 0; m < 4; ++m)
                         ov[m] = ((m + par) & 1) != FC
@@ -676,78 +708,63 @@ __global__ void __launch_bounds__(512, 1) k_mg_fine_rb_tma(const __grid_constant
                 } else {
                     const unsigned fm = face_bits8(cwq, m);
                     const float w = valid8(cwq, m) ? wd[fm] : 0.f;
-                    float lz = 0.f;
-                    if (!FROM_ZERO) {
-                        const float* zf = zbox(q + 1);
-                        const float* zb = zbox(q - 1);
-                        if (fm & 1u) lz += Fx * (cm - zc[bz + 1]);
-                        if (fm & 2u) lz += Fx * (cm - zc[bz - 1]);
-                        if (fm & 4u) lz += Fy * (cm - zc[bz + RBX]);
-                        if (fm & 8u) lz += Fy * (cm - zc[bz - RBX]);
-                        if (fm & 16u) lz += Fz * (cm - zf[bz]);
-                        if (fm & 32u) lz += Fz * (cm - zb[bz]);
+                    if (FROM_ZERO) {
+                        v = w * rbox(q)[br];
+                    } else {
+                        v = rb_cell(cm, zc[bz + 1], zc[bz - 1], zc[bz + RBX], zc[bz - RBX], zbox(q + 1)[bz],
+                                    zbox(q - 1)[bz], rbox(q)[br], fm, w, Fx, Fy, Fz);
                     }
-                    v = w != 0.f ? cm + w * (rbox(q)[br] - lz) : 0.f;
                 }
             }
             slot(q)[(ry + 1) * RBX + col] = v;
         };
-        // the first colour on every cell of plane q the second colour needs
         const int my_row = warp, my_cx = lane;  // the thread's interior chunk
         const int gx = x0 + 4 * my_cx, gy = y0 + my_row;
-        // the code words a thread's first-colour work on plane q needs (its own
-        // chunk; warps 0, 1: a chunk of the row above / below the tile; warp 2:
-        // the chunk holding its edge cell), loaded a plane ahead of their use
         struct Codes {
             uint32_t mine, extra;
         };
+        // the code words a thread's first-colour work on plane q needs (its own
+        // chunk; warps 0, 1: a chunk of the row above / below the tile; warp 2:
+        // the chunk holding its edge cell)
         auto load_codes = [&](int q) -> Codes {
-            Codes c{0u, 0u};
-            if (q < 0 || q >= g.nz) return c;
-            c.mine = code_at(q, gy, gx);
+            Codes c{code_at(q, gy, gx), 0u};
             if (warp < 2) {
                 c.extra = code_at(q, y0 + (warp == 0 ? -1 : RTY), x0 + 4 * lane);
-            } else if (warp == 2) {
+            } else if (warp == 2 && lane < 2 * RTY) {
                 const int x = (lane & 1) ? x0 + RTX : x0 - 1;
                 c.extra = x >= 0 ? code_at(q, y0 + (lane >> 1), x & ~3) : 0u;
             }
             return c;
         };
         auto first_plane = [&](int q, const Codes& c) {
+            if (q < 0 || q >= g.nz) return;
             first_chunk(q, my_row, my_cx, c.mine);
-            if (warp < 2) {  // the rows above and below the tile
-                first_chunk(q, warp == 0 ? -1 : RTY, lane, c.extra);
-            } else if (warp == 2) {  // the cells left and right of every row
-                first_edge(q, lane >> 1, lane & 1, c.extra);
-            }
+            if (warp < 2) first_chunk(q, warp == 0 ? -1 : RTY, lane, c.extra);
+            else if (warp == 2 && lane < 2 * RTY) first_edge(q, lane >> 1, lane & 1, c.extra);
         };
-        // planes k0 - 2 .. k1 + 1 are read; plane P is issued once its stage is
-        // free: k0 - 2 .. k0 + RS - 3 at once, the next two after the first
-        // colour on planes k0 - 1 and k0 (which free planes k0 - 2, k0 - 1),
-        // k + RS after step k (which frees plane k): RS - 2 steps of lead
-        const int last = k1 + 1;
-        for (int P = k0 - 2; P <= min(k0 + RS - 3, last); ++P) issue(P);
+        for (int P = k0 - 2; P <= k0 + RS - 3; ++P) issue(P);
         const Codes c_pre = load_codes(k0 - 1);
-        Codes c_cur = load_codes(k0), c_nxt = load_codes(k0 + 1);
+        Codes c0 = load_codes(k0), c1 = load_codes(k0 + 1), c2 = load_codes(k0 + 2);
         wait(k0 - 2);
         wait(k0 - 1);
         wait(k0);
         wait(k0 + 1);
         __syncthreads();
-        if (!abort_flag) {
-            if (k0 > 0) first_plane(k0 - 1, c_pre);
-            first_plane(k0, c_cur);
-        }
-        __syncthreads();
-        for (int P = k0 + RS - 2; P <= min(k0 + RS - 1, last); ++P) issue(P);
+        if (abort_flag) break;
+        first_plane(k0 - 1, c_pre);
+        first_plane(k0, c0);
         for (int k = k0; k < k1; ++k) {
-            const Codes c_ahead = load_codes(k + 2);  // in flight during this step
-            wait(k + 2);  // z(k + 2) for the first colour on plane k + 1
-            __syncthreads();
+            const Codes c3 = load_codes(k + 3);  // two planes ahead of their use
+            wait(k + 2);                          // z(k + 2) for the first colour on plane k + 1
+            __syncthreads();                      // also: every thread is done with step k - 1
             if (abort_flag) break;
-            if (k + 1 < g.nz) first_plane(k + 1, c_nxt);
+            // refill the stages freed by the previous steps (plane k - 2 after
+            // the prologue, plane k - 1 after step k - 1)
+            if (k == k0) issue(k0 + RS - 2);
+            issue(k - 1 + RS);
+            first_plane(k + 1, c1);
             __syncthreads();
-            // the other colour on plane k, rows y0 .. y0 + 15
+            // the other colour on plane k, rows y0 .. y0 + RTY - 1
             {
                 const float* sC = slot(k);
                 const float* sF = slot(k + 1);
@@ -768,12 +785,11 @@ __global__ void __launch_bounds__(512, 1) k_mg_fine_rb_tma(const __grid_constant
                 const float* rv = reinterpret_cast<const float*>(&r4);
                 const float wv[4] = {xw, ov[0], ov[1], ov[2]};
                 const float ev[4] = {ov[1], ov[2], ov[3], xe};
-                const uint32_t cw = c_cur.mine;
+                const uint32_t cw = c0.mine;
                 const int par = (int)((cw >> 6) & 1u);
                 float4 out4;
                 float* outv = reinterpret_cast<float*>(&out4);
                 if (chunk_full(cw)) {
-                    const float wf = wd[63];
 #pragma unroll
                     for (int m = 0; m < 4; ++m)
                         outv[m] = ((m + par) & 1) == FC
@@ -801,27 +817,27 @@ __global__ void __launch_bounds__(512, 1) k_mg_fine_rb_tma(const __grid_constant
                     }
                 }
             }
-            c_cur = c_nxt;
-            c_nxt = c_ahead;
-            __syncthreads();  // plane k's stage and the slot of plane k - 1 are free
-            if (k + RS <= last) issue(k + RS);
+            c0 = c1;
+            c1 = c2;
+            c2 = c3;
         }
         if (abort_flag) break;
-        __syncthreads();
+        __syncthreads();  // every thread is done with the item's stages and slots
     }
     if (abort_flag) {
-#pragma unroll
-        for (int i = 0; i < RS; ++i) {
-            long long spins = 0;
-            while (uses[i] < issued[i] && spins < (1LL << 22)) {
+        // let the copies in flight land (bounded) before the block leaves
+        for (int si = 0; si < RS; ++si) {
+            if (!((pending >> si) & 1u)) continue;
+            const uint32_t par = (parity >> si) & 1u;
+            for (long long spins = 0; spins < (1LL << 22); ++spins) {
                 uint32_t ok;
                 asm volatile(
                     "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                     : "=r"(ok)
-                    : "r"(rb_smem(&bars[i])), "r"(uses[i] & 1u)
+                    : "r"(rb_smem(&bars[si])), "r"(par)
                     : "memory");
-                if (ok) uses[i] += 1;
-                else { ++spins; __nanosleep(32); }
+                if (ok) break;
+                __nanosleep(32);
             }
         }
         if (t == 0) st->err = 1;
@@ -1096,6 +1112,111 @@ __global__ void k_mg_coarse(const T* __restrict__ z, const T* __restrict__ r,
     });
 }
 
+// Fused red-black sweep on a coarse level with packed face counts, out of
+// place, marching in z (the coarse counterpart of k_mg_fine_rb_fused, one
+// cell per thread): a block owns a tile of 32 x 8 cells (interior 30 x 6,
+// one-cell halo) and a slab of planes; at step k it updates colour FC
+// ((i + j + k) mod 2 == FC) on plane k + 1 over the tile and its halo from
+// z_in into a 4-slot shared ring, then the other colour on plane k from the
+// ring, and writes plane k of z_out.  A cell's six weights (count x F_a; the
+// - faces from the neighbours' words) and omega / D are formed once, in the
+// first step, and kept for the second.  FROM_ZERO: z_in = 0.
+constexpr int kCbX = 32, kCbY = 8;
+
+struct CbArgs {
+    int nx, ny, nz, tiles_x, tiles_y, slab;
+    long long n_items;
+};
+
+template <class T, int FC, bool FROM_ZERO>
+__global__ void __launch_bounds__(kCbX * kCbY) k_mg_coarse_rb_fused(const T* __restrict__ zin, T* __restrict__ zout,
+                                                                  const T* __restrict__ r, Level lv, T omega,
+                                                                  CbArgs g, const CgState* st) {
+    constexpr int NT = kCbX * kCbY;
+    if (st->status != kRunning) return;
+    __shared__ T ring[4][NT];
+    const int t = threadIdx.x, lx = t % kCbX, ly = t / kCbX;
+    const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+    const T F0 = (T)lv.F[0], F1 = (T)lv.F[1], F2 = (T)lv.F[2];
+    for (long long item = blockIdx.x; item < g.n_items; item += gridDim.x) {
+        const int tx = (int)(item % g.tiles_x);
+        const int ty = (int)((item / g.tiles_x) % g.tiles_y);
+        const int sl = (int)(item / ((long long)g.tiles_x * g.tiles_y));
+        const int i = tx * (kCbX - 2) - 1 + lx, j = ty * (kCbY - 2) - 1 + ly;
+        const bool inr = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
+        const bool interior = inr && lx >= 1 && lx <= kCbX - 2 && ly >= 1 && ly <= kCbY - 2;
+        const int k0 = sl * g.slab, k1 = min(g.nz, k0 + g.slab);
+        const int64_t col = (int64_t)j * sy + i;
+        __syncthreads();
+        // weights of the cell on plane q: xp, xm, yp, ym, zp, zm, omega / D
+        struct W7 {
+            T xp, xm, yp, ym, zp, zm, wd, r;
+        };
+        auto first = [&](int q, W7& w) {
+            T o = T(0);
+            w = W7{T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+            if (inr && q >= 0 && q < g.nz) {
+                const int64_t c = (int64_t)q * sz + col;
+                const uint32_t w0 = __ldg(lv.wc + c);
+                const uint32_t w1 = i > 0 ? __ldg(lv.wc + c - 1) : 0u;
+                const uint32_t w2 = j > 0 ? __ldg(lv.wc + c - sy) : 0u;
+                const uint32_t w3 = q > 0 ? __ldg(lv.wc + c - sz) : 0u;
+                w.r = r[c];
+                w.xp = (T)((float)(w0 & 1023u) * lv.F[0]);
+                w.yp = (T)((float)((w0 >> 10) & 1023u) * lv.F[1]);
+                w.zp = (T)((float)(w0 >> 20) * lv.F[2]);
+                w.xm = (T)((float)(w1 & 1023u) * lv.F[0]);
+                w.ym = (T)((float)((w2 >> 10) & 1023u) * lv.F[1]);
+                w.zm = (T)((float)(w3 >> 20) * lv.F[2]);
+                const T d = w.xp + w.xm + w.yp + w.ym + w.zp + w.zm;
+                w.wd = d > T(0) ? omega / d : T(0);
+                const bool mine = ((i + j + q) & 1) == FC;
+                if (FROM_ZERO) {
+                    o = mine ? w.wd * w.r : T(0);
+                } else {
+                    const T zc = zin[c];
+                    if (mine) {
+                        const T ze = i + 1 < g.nx ? zin[c + 1] : T(0), zw = i > 0 ? zin[c - 1] : T(0);
+                        const T zn = j + 1 < g.ny ? zin[c + sy] : T(0), zs = j > 0 ? zin[c - sy] : T(0);
+                        const T zf = q + 1 < g.nz ? zin[c + sz] : T(0), zb = q > 0 ? zin[c - sz] : T(0);
+                        const T az = w.xp * (zc - ze) + w.xm * (zc - zw) + w.yp * (zc - zn) + w.ym * (zc - zs) +
+                                     w.zp * (zc - zf) + w.zm * (zc - zb);
+                        o = zc + w.wd * (w.r - az);
+                    } else {
+                        o = zc;
+                    }
+                }
+            }
+            ring[q & 3][t] = o;
+        };
+        W7 w_cur, w_nxt;
+        first(k0 - 1, w_nxt);  // plane -1 (k0 = 0) writes zeros: its slot is read with weight 0
+        first(k0, w_cur);
+        for (int k = k0; k < k1; ++k) {
+            first(k + 1, w_nxt);
+            __syncthreads();
+            if (interior) {
+                const T zc = ring[k & 3][t];
+                T out = zc;
+                if (((i + j + k) & 1) != FC) {
+                    const T ze = ring[k & 3][t + 1], zw = ring[k & 3][t - 1];
+                    const T zn = ring[k & 3][t + kCbX], zs = ring[k & 3][t - kCbX];
+                    const T zf = ring[(k + 1) & 3][t], zb = ring[(k + 3) & 3][t];
+                    const W7& w = w_cur;
+                    const T az = w.xp * (zc - ze) + w.xm * (zc - zw) + w.yp * (zc - zn) + w.ym * (zc - zs) +
+                                 w.zp * (zc - zf) + w.zm * (zc - zb);
+                    out = zc + w.wd * (w.r - az);
+                }
+                zout[(int64_t)k * sz + col] = out;
+            }
+            w_cur = w_nxt;
+        }
+    }
+    (void)F0;
+    (void)F1;
+    (void)F2;
+}
+
 // Red-black half-sweep on a coarse level, in place: cells of colour COLOR
 // ((i + j + k) mod 2) get z + omega D^-1 (r - A z); FIRST: z = omega D^-1 r
 // on red cells and 0 on black ones (the red half-sweep from zero).  The cells
@@ -1300,8 +1421,8 @@ RbArgs rb_args(osmodi_plan p) {
     return a;
 }
 
-// geometry of the TMA-staged sweep: 128 x 16-cell tiles times slabs of planes
-// sized for about eight work items per SM (one block per SM)
+// geometry of the TMA-staged sweep: 128 x 8-cell tiles times slabs of planes
+// sized for about eight work items per block (two blocks per SM)
 RbTmaGeo rb_tma_geo(osmodi_plan p) {
     RbTmaGeo g;
     g.px = p->px;
@@ -1314,7 +1435,7 @@ RbTmaGeo rb_tma_geo(osmodi_plan p) {
     for (int q = 0; q < 3; ++q) g.F[q] = (float)p->k.F[q];
     g.omega = kOmegaRB;
     const long long tiles = (long long)g.n_tx * g.n_ty;
-    const long long want = 8LL * p->num_sms;
+    const long long want = 8LL * 2 * p->num_sms;
     const long long slabs = std::max<long long>(1, std::min<long long>(g.nz, (want + tiles - 1) / tiles));
     g.slab = std::max(8, (int)((g.nz + slabs - 1) / slabs));
     g.n_items = tiles * ((g.nz + g.slab - 1) / g.slab);
@@ -1420,6 +1541,40 @@ T* vcycle_body(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, cud
     const int Grs = wave_grid(p, 0, b_rs, w256), Gpr = wave_grid(p, 0, b_pr, w256);
     const int Gre = wave_grid(p, 0, b_re, (gc.n + 255) / 256);
     const int B = 256;
+    if (rb && PACKED && debug_knob(OSMODI_DEBUG_MG_UNFUSED) != 1) {
+        // fused one-pass sweeps, out of place (a -> b -> ...); the residual goes
+        // to the buffer not holding z
+        CbArgs cb;
+        cb.nx = (int)g.nx;
+        cb.ny = (int)g.ny;
+        cb.nz = (int)g.nz;
+        cb.tiles_x = (cb.nx + kCbX - 3) / (kCbX - 2);
+        cb.tiles_y = (cb.ny + kCbY - 3) / (kCbY - 2);
+        static const int bps = blocks_per_sm(k_mg_coarse_rb_fused<T, 0, false>);
+        const long long tiles = (long long)cb.tiles_x * cb.tiles_y;
+        const long long want = 8LL * p->num_sms * bps;
+        const long long slabs = std::max<long long>(1, std::min<long long>(cb.nz, (want + tiles - 1) / tiles));
+        cb.slab = std::max(4, (int)((cb.nz + slabs - 1) / slabs));
+        cb.n_items = tiles * ((cb.nz + cb.slab - 1) / cb.slab);
+        const int gf = (int)std::max<long long>(1, std::min<long long>(cb.n_items, (long long)p->num_sms * bps));
+        const T om = (T)kOmegaRB;
+        T* cur = v.a;
+        T* oth = v.b;
+        k_mg_coarse_rb_fused<T, 0, true><<<gf, kCbX * kCbY, 0, s>>>(nullptr, cur, v.r, g, om, cb, st);
+        for (int i = 1; i < nu; ++i) {
+            k_mg_coarse_rb_fused<T, 0, false><<<gf, kCbX * kCbY, 0, s>>>(cur, oth, v.r, g, om, cb, st);
+            std::swap(cur, oth);
+        }
+        k_mg_coarse<T, M_RESID, PACKED><<<Grs, B, 0, s>>>(cur, v.r, oth, a, st);
+        k_mg_restrict<T><<<Gre, B, 0, s>>>(oth, g.nx, g.ny, g.nz, g.nx, vc.r, gc, st);
+        T* zc = vcycle_coarse<T>(p, h, base, l + 1, st, s);
+        k_mg_coarse_prolong<T><<<Gpr, B, 0, s>>>(cur, zc, a, st);
+        for (int i = 0; i < nu; ++i) {  // the adjoint: black then red
+            k_mg_coarse_rb_fused<T, 1, false><<<gf, kCbX * kCbY, 0, s>>>(cur, oth, v.r, g, om, cb, st);
+            std::swap(cur, oth);
+        }
+        return cur;
+    }
     if (rb) {
         k_mg_coarse_rb<T, 0, true, PACKED><<<Grb, B, 0, s>>>(v.a, v.r, a, st);   // red from zero
         k_mg_coarse_rb<T, 1, false, PACKED><<<Grb, B, 0, s>>>(v.a, v.r, a, st);  // black
@@ -1494,7 +1649,7 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
     // (fusing the first two sweeps into one pass was measured slower than the
     // two passes: forming every neighbour's first-sweep value costs more
     // instructions than the extra pass moves bytes)
-    const long long variant = debug_knob(OSMODI_DEBUG_MG_UNFUSED);  // 0 TMA-staged, 1 half-sweeps, 2 register-staged
+    const long long variant = debug_knob(OSMODI_DEBUG_MG_UNFUSED);  // 0 fused, 1 half-sweeps, 2 fused TMA-staged
     if (red_black(p) && variant == 1) {
         // the same V-cycle by in-place half-sweeps (one colour per pass), kept
         // for comparison with the fused sweeps; it ends in zA, copied to zB
@@ -1528,24 +1683,24 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
         cudaMemcpyAsync(w.zB, w.zA, sizeof(T) * (size_t)p->n_box, cudaMemcpyDeviceToDevice, s);
         return w.zB;
     }
-    if (red_black(p) && sizeof(T) == 4 && variant == 0) {
+    if (red_black(p) && sizeof(T) == 4 && variant == 2) {
         // the same V-cycle with the TMA-staged fused sweeps (FP32)
         RbMaps* mp = rb_maps(p, reinterpret_cast<const float*>(w.zA), reinterpret_cast<const float*>(w.zB),
                              reinterpret_cast<const float*>(r));
         if (mp) {
             const RbTmaGeo tg = rb_tma_geo(p);
-            const int gr = (int)std::min<long long>(tg.n_items, (long long)p->num_sms);
+            const int gr = (int)std::min<long long>(tg.n_items, (long long)p->num_sms * 2);
             float* fA = reinterpret_cast<float*>(w.zA);
             float* fB = reinterpret_cast<float*>(w.zB);
             float* cur = fA;
             float* oth = fB;
             auto map_of = [&](const float* z) -> const CUtensorMap& { return z == fA ? mp->zA : mp->zB; };
             if (nu == 1) mark(0);
-            k_mg_fine_rb_tma<0, true, false><<<gr, 512, kRbTmaSmem, s>>>(mp->zA, mp->r, p->code8, cur, tg, st, partials);
+            k_mg_fine_rb_tma<0, true, false><<<gr, 256, kRbTmaSmem, s>>>(mp->zA, mp->r, p->code8, cur, tg, st, partials);
             if (nu == 1) mark(1);
             for (int i = 1; i < nu; ++i) {
                 if (i == 1) mark(0);
-                k_mg_fine_rb_tma<0, false, false><<<gr, 512, kRbTmaSmem, s>>>(map_of(cur), mp->r, p->code8, oth, tg, st,
+                k_mg_fine_rb_tma<0, false, false><<<gr, 256, kRbTmaSmem, s>>>(map_of(cur), mp->r, p->code8, oth, tg, st,
                                                                               partials);
                 if (i == 1) mark(1);
                 std::swap(cur, oth);
@@ -1559,10 +1714,10 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
             for (int i = 0; i < nu; ++i) {  // the adjoint: black then red
                 if (i == 0) mark(2);
                 if (i == nu - 1)
-                    k_mg_fine_rb_tma<1, false, true><<<gr, 512, kRbTmaSmem, s>>>(map_of(cur), mp->r, p->code8, oth, tg,
+                    k_mg_fine_rb_tma<1, false, true><<<gr, 256, kRbTmaSmem, s>>>(map_of(cur), mp->r, p->code8, oth, tg,
                                                                                  st, partials);
                 else
-                    k_mg_fine_rb_tma<1, false, false><<<gr, 512, kRbTmaSmem, s>>>(map_of(cur), mp->r, p->code8, oth, tg,
+                    k_mg_fine_rb_tma<1, false, false><<<gr, 256, kRbTmaSmem, s>>>(map_of(cur), mp->r, p->code8, oth, tg,
                                                                                   st, partials);
                 if (i == 0) mark(3);
                 std::swap(cur, oth);

@@ -617,6 +617,9 @@ __global__ void __launch_bounds__(128, 1) k_conv3_halo(const __grid_constant__ C
     const uint32_t cgs = (uint32_t)g.nvp * 16;  // channel-group stride (bytes)
     unsigned char* sA = smem;
     unsigned char* sB = smem + (size_t)g.CG * cgs;
+    const uint32_t b_bytes = (uint32_t)g.nmma * 2u * (uint32_t)g.Cout * 16u;
+    uint64_t* dA = reinterpret_cast<uint64_t*>(sB + b_bytes);  // per MMA: A descriptor of tile 0
+    uint64_t* dB = dA + g.nmma;                                // per MMA: B descriptor
     uint32_t ncols = 32;
     while ((int)ncols < g.ntiles * g.Cout) ncols <<= 1;
     if (warp == 0) {
@@ -633,9 +636,10 @@ __global__ void __launch_bounds__(128, 1) k_conv3_halo(const __grid_constant__ C
     tc::fence_after_sync();
     const uint32_t taddr = tbase;
     if (t == 0) {
+        // the input box (one tensor copy per channel group) and B (one bulk copy)
         const uint32_t box_bytes = 8u * 2u * (uint32_t)(g.WX + 2) * (uint32_t)(g.TY + 2) * 3u;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(&bar_load)),
-                     "r"(box_bytes * (uint32_t)g.CG)
+                     "r"(box_bytes * (uint32_t)g.CG + b_bytes)
                      : "memory");
         for (int cg = 0; cg < g.CG; ++cg)
             asm volatile(
@@ -643,36 +647,39 @@ __global__ void __launch_bounds__(128, 1) k_conv3_halo(const __grid_constant__ C
                 "%5}], [%6];" ::"r"(tc::smem_u32(sA + (size_t)cg * cgs)),
                 "l"(&tmA), "r"(cg * 8), "r"(x0 - 1), "r"(y0 - 1), "r"(z - 1), "r"(tc::smem_u32(&bar_load))
                 : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         tc::smem_u32(sB)),
+                     "l"(Bh), "r"(b_bytes), "r"(tc::smem_u32(&bar_load))
+                     : "memory");
     }
-    // B (every MMA's two K-groups of weights) by plain 16-byte copies
-    const int b_pieces = g.nmma * 2 * g.Cout;
-    for (int q = t; q < b_pieces; q += 128)
-        *reinterpret_cast<uint4*>(sB + (size_t)q * 16) = *reinterpret_cast<const uint4*>(Bh + (size_t)q * 8);
-    tc::fence_proxy_async();
+    // the MMAs' descriptors for M-tile 0, in parallel while the copies run;
+    // tile mt adds mt * tstep to the 16-byte start address field
+    const int A = (g.TY + 2) * (g.WX + 2), Bw = g.WX + 2;
+    const int q_first = A + Bw + 1;  // box voxel of output (row 0, voxel 0): plane 1, row 1, voxel 1
+    {
+        const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+        for (int i = t; i < g.nmma; i += 128) {
+            int ta, ca, tb, cb;
+            halo_kgroup(g.CG, i, 0, ta, ca);
+            halo_kgroup(g.CG, i, 1, tb, cb);
+            const int oa = halo_off(g, ta);
+            uint32_t lbo;
+            if (g.CG == 1) lbo = tb >= 0 ? (uint32_t)(halo_off(g, tb) - oa) * 16u : 16u;
+            else lbo = cgs;
+            dA[i] = tc::sdesc(a0 + (uint32_t)(q_first + oa) * 16u + (uint32_t)ca * cgs, lbo, 128);
+            dB[i] = tc::sdesc(b0 + (uint32_t)i * 2u * (uint32_t)g.Cout * 16u, (uint32_t)g.Cout * 16u, 128);
+        }
+    }
     bool ok = tc::mbar_wait(&bar_load, 0, TC_POLLS);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const int A = (g.TY + 2) * (g.WX + 2), Bw = g.WX + 2;
-    const int q_first = A + Bw + 1;  // box voxel of output (row 0, voxel 0): plane 1, row 1, voxel 1
     if (t == 0 && ok) {
-        const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
         const uint32_t idesc = tc::idesc_bf16_f32(128, g.Cout);
         for (int mt = 0; mt < g.ntiles; ++mt) {
-            const int qs = q_first + mt * g.tstep;
-            for (int i = 0; i < g.nmma; ++i) {
-                int ta, ca, tb, cb;
-                halo_kgroup(g.CG, i, 0, ta, ca);
-                halo_kgroup(g.CG, i, 1, tb, cb);
-                const int oa = halo_off(g, ta);
-                uint32_t lbo;
-                if (g.CG == 1) lbo = tb >= 0 ? (uint32_t)(halo_off(g, tb) - oa) * 16u : 16u;
-                else lbo = cgs;
-                const uint32_t sa = a0 + (uint32_t)(qs + oa) * 16u + (uint32_t)ca * cgs;
-                const uint64_t ad = tc::sdesc(sa, lbo, 128);
-                const uint64_t bd = tc::sdesc(b0 + (uint32_t)i * 2u * (uint32_t)g.Cout * 16u, (uint32_t)g.Cout * 16u, 128);
-                tc::mma_bf16(taddr + (uint32_t)(mt * g.Cout), ad, bd, idesc, i > 0 ? 1u : 0u);
-            }
+            const uint64_t delta = (uint64_t)(mt * g.tstep);
+            const uint32_t dcol = taddr + (uint32_t)(mt * g.Cout);
+            for (int i = 0; i < g.nmma; ++i) tc::mma_bf16(dcol, dA[i] + delta, dB[i], idesc, i > 0 ? 1u : 0u);
         }
         tc::mma_commit(&bar_mma);
     }
@@ -1154,21 +1161,28 @@ static bool halo_config(const ConvArgs& a, Halo3& g, size_t& smem) {
     g.WX = std::min(g.W, 128);
     g.n_xs = (g.W + g.WX - 1) / g.WX;
     g.nmma = g.CG == 1 ? 14 : 27 * g.CG / 2;
-    const size_t bbytes = (size_t)g.nmma * 2 * g.Cout * 16;
-    for (int TY : {16, 8, 4, 2, 1}) {
-        const int bw = g.WX + 2;
-        const int nv = 3 * (TY + 2) * bw;
-        const int nvp = (nv + 128 + 7) / 8 * 8;
-        const size_t abytes = (size_t)g.CG * nvp * 16;
-        const int ntiles = g.WX == 128 ? TY : ((TY - 1) * bw + g.WX + 127) / 128;
-        if (ntiles * g.Cout > 512 || abytes + bbytes > 220 * 1024 || TY > g.H) continue;
-        g.TY = TY;
-        g.nvp = nvp;
-        g.ntiles = ntiles;
-        g.tstep = g.WX == 128 ? bw : 128;
-        g.n_yb = (g.H + TY - 1) / TY;
-        smem = abytes + bbytes;
-        return true;
+    const size_t bbytes = (size_t)g.nmma * 2 * g.Cout * 16 + (size_t)g.nmma * 16;  // B and the descriptor table
+    // the largest tile that lets two CTAs share an SM (one loads while the
+    // other multiplies), else the largest that fits at all
+    for (const size_t budget : {(size_t)110 * 1024, (size_t)220 * 1024}) {
+        for (int TY : {16, 8, 4, 2, 1}) {
+            const int bw = g.WX + 2;
+            const int nv = 3 * (TY + 2) * bw;
+            const int nvp = (nv + 128 + 7) / 8 * 8;
+            const size_t abytes = (size_t)g.CG * nvp * 16;
+            const int ntiles = g.WX == 128 ? TY : ((TY - 1) * bw + g.WX + 127) / 128;
+            int cols = 32;
+            while (cols < ntiles * g.Cout) cols <<= 1;
+            const int ctas = budget < 200 * 1024 ? 2 : 1;
+            if (cols * ctas > 512 || abytes + bbytes > budget || TY > g.H) continue;
+            g.TY = TY;
+            g.nvp = nvp;
+            g.ntiles = ntiles;
+            g.tstep = g.WX == 128 ? bw : 128;
+            g.n_yb = (g.H + TY - 1) / TY;
+            smem = abytes + bbytes;
+            return true;
+        }
     }
     return false;
 }
@@ -1201,8 +1215,13 @@ static osmodi_status conv_halo(osmodi_net n, const ConvArgs& a, Halo3 g, size_t 
 // forward conv3 layers with their input tile staged once, every other
 // product by the gathering kernel), or (test knob OSMODI_DEBUG_NET_WMMA) by
 // the warp-level wmma kernel
+static osmodi_status conv_path(osmodi_net n, ConvArgs a, cudaStream_t s, int path);
 static osmodi_status conv(osmodi_net n, ConvArgs a, cudaStream_t s) {
-    if (debug_knob(OSMODI_DEBUG_NET_WMMA)) {
+    return conv_path(n, a, s, (int)debug_knob(OSMODI_DEBUG_NET_WMMA));
+}
+// path 0: tcgen05 (halo-staged conv3 where it applies), 1: wmma, 2: tcgen05 gathering kernel only
+static osmodi_status conv_path(osmodi_net n, ConvArgs a, cudaStream_t s, int path) {
+    if (path == 1) {
         dim3 grid((unsigned)((a.M + BM - 1) / BM), (unsigned)((a.N + BN - 1) / BN));
         k_conv<<<grid, 128, 0, s>>>(a);
         OSM_CUDA(cudaGetLastError());
@@ -1211,7 +1230,7 @@ static osmodi_status conv(osmodi_net n, ConvArgs a, cudaStream_t s) {
     {
         Halo3 g;
         size_t smem = 0;
-        if (halo_config(a, g, smem)) return conv_halo(n, a, g, smem, s);
+        if (path != 2 && halo_config(a, g, smem)) return conv_halo(n, a, g, smem, s);
     }
     if (a.mode == PT && a.N == 1 && !a.a_float && !a.amask && !a.trans && !a.skip && !a.relu && a.out_float &&
         !a.accumulate && a.Ka % 8 == 0 && a.Ka <= 64) {
@@ -1434,4 +1453,37 @@ extern "C" osmodi_status osmodi_net_adam(osmodi_net n, double lr, double beta1, 
                                                    (float)beta1, (float)beta2, (float)eps, c1, c2, 1.f / (float)batch);
     OSM_CUDA(cudaGetLastError());
     return OSMODI_OK;
+}
+
+extern "C" osmodi_status osmodi_conv3d(const void* x, const void* w, const float* bias, void* y, int D, int H, int W,
+                                       int cin, int cout, int relu, int path, void* scratch, size_t scratch_bytes,
+                                       int* err, void* stream) {
+    if (!x || !w || !y || !scratch || !err || D < 1 || H < 1 || W < 1 || cin < 1 || cout < 1 || cout > 64)
+        return OSMODI_E_INVALID;
+    if (path < 0 || path > 2 || (cin % 8 && path != 1) || cout % 8) return OSMODI_E_INVALID;
+    if (((uintptr_t)x | (uintptr_t)y | (uintptr_t)scratch) & 15u) return OSMODI_E_INVALID;
+    osmodi_net_s ctx;  // the scratch and error flag of one call (nothing is allocated)
+    OSM_CUDA(cudaGetDevice(&ctx.device));
+    OSM_CUDA(cudaDeviceGetAttribute(&ctx.num_sms, cudaDevAttrMultiProcessorCount, ctx.device));
+    ctx.bt = reinterpret_cast<bf16*>(scratch);
+    ctx.bt_elems = (long long)(scratch_bytes / sizeof(bf16));
+    ctx.err = err;
+    ConvArgs a{};
+    a.A = x;
+    a.W = reinterpret_cast<const bf16*>(w);
+    a.bias = bias;
+    a.relu = relu ? 1 : 0;
+    a.out = y;
+    a.cin_l = cin;
+    a.cout_l = cout;
+    a.Ka = cin;
+    a.No = cout;
+    a.Din = a.Dout = D;
+    a.Hin = a.Hout = H;
+    a.Win = a.Wout = W;
+    a.mode = G3;
+    a.M = (long long)D * H * W;
+    a.N = cout;
+    a.K = 27 * cin;
+    return conv_path(&ctx, a, (cudaStream_t)stream, path);
 }

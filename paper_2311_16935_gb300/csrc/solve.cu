@@ -42,6 +42,11 @@ namespace osm {
 enum { OP_L = 0, OP_M = 1 };
 // smallest tolerance the float-float refinement is used for
 constexpr double kFFMinTol = 1e-9;
+// smallest tolerance the FP64 refinement forms its source in float-float
+// arithmetic for: the source's relative error, a few 2^-48, then stays many
+// orders below the tolerance, and also below 1e-10 of the solution after the
+// operator's conditioning (~1e4-1e5 on the grids here) amplifies it
+constexpr double kMixedSrcMinTol = 1e-10;
 // reduction partials: one range of kMaxBlocks doubles per slot
 enum { kSlotA = 0, kSlotB = 1, kSlotRes = 2 /* 3 slots */, kSlotMisc = 5 /* 3 slots */, kPartialSlots = 8 };
 
@@ -332,6 +337,89 @@ __global__ void k_source_ff(const TG* __restrict__ f, const TP* __restrict__ p_i
     }
     if (bad) atomicOr(&sc->nan_flag, bad);
     double acc[4] = {a_b2.value(), a_p0.value(), a_b.value(), (double)n_p0};
+    double tot[4];
+    if (grid_sum<4>(acc, partials, &sc->t_src, tot) && threadIdx.x == 0) {
+        sc->bnorm2 = tot[0];
+        sc->p0sum = tot[1];
+        sc->bsum = tot[2];
+        sc->p0nz = tot[3];
+    }
+}
+
+// The FP64 source of the FP64 refinement, formed on the FP32 units: each
+// face bracket of FP32 gradients is an exact float-float pair, the sum over
+// the axes is carried as a pair (~48 bits, relative error a few 2^-48) and
+// rounded to FP64 once.  FP64 then serves only that conversion, P^0 and the
+// per-thread sums (the plain k_source spends ~20 FP64 instructions per cell,
+// and GB300's FP64 units bound it).  Used at tolerances >= kMixedSrcMinTol.
+template <int NDIM, class TP>
+__global__ void k_source_mixed(const float* __restrict__ f, const TP* __restrict__ p_in, const uint8_t* __restrict__ code8,
+                               double* __restrict__ b64, double* __restrict__ p64, SrcGeoFF g, Scalars* sc,
+                               double* partials) {
+    FFAcc a_b2, a_b;
+    double p0sum = 0.0, n_p0 = 0.0;
+    int bad = 0;
+    const int64_t sd[3] = {1, g.nx, g.nx * g.ny};
+    const bool i32 = g.n_box < (int64_t)(1u << 31);
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < g.n_box; idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t row, i;
+        if (i32) {
+            const uint32_t r32 = (uint32_t)idx / (uint32_t)g.px;
+            row = r32;
+            i = (uint32_t)idx - r32 * (uint32_t)g.px;
+        } else {
+            row = idx / g.px;
+            i = idx - row * g.px;
+        }
+        const bool in_row = i < g.nx;
+        const int64_t d = in_row ? row * g.nx + i : 0;
+        const unsigned cw = code8[idx];
+        float fc[NDIM], fp[NDIM], fm[NDIM];
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const float* fa = f + a * g.n_dense + d;
+            fc[a] = fa[0];
+            fp[a] = d + sd[a] < g.n_dense ? fa[sd[a]] : fc[a];
+            fm[a] = d >= sd[a] ? fa[-sd[a]] : fc[a];
+        }
+        const TP v = p_in ? p_in[d] : TP(0);
+        if (!in_row || !(cw & 0x80u)) {
+            b64[idx] = 0.0;
+            p64[idx] = 0.0;
+            continue;
+        }
+        FF sff{0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const unsigned bp = (cw >> (2 * a)) & 1u, bm = (cw >> (2 * a + 1)) & 1u;
+            if (!(bp | bm)) continue;
+            FF t;
+            if (bp & bm) t = ff_sum2(fp[a], -fm[a]);
+            else if (bp) t = ff_sum2(fp[a], fc[a]);
+            else t = ff_sum2(-fm[a], -fc[a]);
+            sff = ff_add(sff, ff_mul(g.coef[a], t));
+        }
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a)
+            if (!isfinite(fc[a])) bad |= 1;
+        double p0 = 0.0;
+        if (p_in) {
+            if (!isfinite(v)) bad |= 2;
+            // a zero start needs no FP64 arithmetic (the test is on the bits)
+            if (sizeof(TP) == 8 ? ((__double_as_longlong((double)v) << 1) != 0) : (v != TP(0))) {
+                p0 = (double)v;
+                p0sum += p0;
+                n_p0 += 1.0;
+            }
+        }
+        b64[idx] = ff_to_double(sff);
+        p64[idx] = p0;
+        a_b2.add(sff.hi * sff.hi);
+        a_b.add(sff.hi);
+        a_b.add(sff.lo);
+    }
+    if (bad) atomicOr(&sc->nan_flag, bad);
+    double acc[4] = {a_b2.value(), p0sum, a_b.value(), n_p0};
     double tot[4];
     if (grid_sum<4>(acc, partials, &sc->t_src, tot) && threadIdx.x == 0) {
         sc->bnorm2 = tot[0];
@@ -2355,6 +2443,10 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
     // down to kFFMinTol (its residual floor, a few 2^-48 of |F p| against
     // |b|, stays far below that); otherwise, and by default, FP64
     const bool ff = sizeof(T) == 4 && p->opt.refine_ff == 1 && tol >= kFFMinTol;
+    // the FP64 refinement of the FP32 precisions forms its FP64 source in
+    // float-float arithmetic at tolerances >= kMixedSrcMinTol (FP64 throughput
+    // bounds the plain FP64 source kernel); the FP64 precision keeps FP64
+    const bool mixed_src = sizeof(T) == 4 && !ff && tol >= kMixedSrcMinTol;
     {
         const void* p_in = p->opt.zero_start ? nullptr : pu;
         SrcGeoFF sgf{p->px, p->nx, p->ny, p->nz, p->n_dense, p->n_box, {}};
@@ -2368,6 +2460,10 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
         if (ff)                                                                                                         \
             k_source_ff<ND, TG, TP><<<one_wave(p, k_source_ff<ND, TG, TP>, p->n_box), 256, 0, s>>>(                     \
                 (const TG*)grad, (const TP*)p_in, p->code8, bh, ph, sgf, b.sc, b.partials + kSlotMisc * kMaxBlocks);    \
+        else if (mixed_src && sizeof(TG) == 4)                                                                          \
+            k_source_mixed<ND, TP><<<one_wave(p, k_source_mixed<ND, TP>, p->n_box), 256, 0, s>>>(                       \
+                (const float*)grad, (const TP*)p_in, p->code8, b.b64, b.p64a, sgf, b.sc,                                \
+                b.partials + kSlotMisc * kMaxBlocks);                                                                   \
         else                                                                                                            \
             k_source<ND, TG, TP><<<one_wave(p, k_source<ND, TG, TP>, p->n_box), 256, 0, s>>>(                           \
                 (const TG*)grad, (const TP*)p_in, p->code8, b.b64, b.p64a, sg, b.sc,                                    \

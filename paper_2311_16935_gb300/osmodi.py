@@ -95,6 +95,9 @@ _SIGS = {
     "osmodi_debug_set": (ctypes.c_longlong, [ctypes.c_int, ctypes.c_longlong]),
     "osmodi_probe_fp64": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_net_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "osmodi_conv3d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_tc_gemm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_void_p, ctypes.c_void_p]),
     "osmodi_ray_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -700,3 +703,21 @@ def tc_gemm(A: torch.Tensor, B: torch.Tensor, stream=None):
     if st != OK:
         raise OsmodiError(st, "osmodi_tc_gemm")
     return D, int(err.item())
+
+
+def conv3d(x: torch.Tensor, w: torch.Tensor, bias=None, relu=False, path=0, stream=None):
+    """osmodi_conv3d: x (D, H, W, cin) bf16, w (27, cin, cout) bf16, bias
+    (cout,) float32 or None; returns (y (D, H, W, cout) bf16, error flag)."""
+    _check_cuda(x, "x")
+    _check_cuda(w, "w")
+    D, H, W, cin = x.shape
+    cout = w.shape[2]
+    y = torch.empty((D, H, W, cout), dtype=torch.bfloat16, device=x.device)
+    scratch = torch.empty(2 * (27 * cin + 64) * ((cout + 15) // 16 * 16) + 4096, dtype=torch.uint8, device=x.device)
+    err = torch.zeros(1, dtype=torch.int32, device=x.device)
+    st = lib().osmodi_conv3d(x.data_ptr(), w.data_ptr(), None if bias is None else bias.data_ptr(), y.data_ptr(),
+                             D, H, W, cin, cout, 1 if relu else 0, int(path), scratch.data_ptr(), scratch.numel(),
+                             err.data_ptr(), _stream_ptr(stream))
+    if st != OK:
+        raise OsmodiError(st, "osmodi_conv3d")
+    return y, int(err.item())

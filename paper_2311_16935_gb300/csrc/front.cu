@@ -114,6 +114,27 @@ __global__ void __launch_bounds__(128) k_front_incompressible(FrontGeo g, const 
     }
 }
 
+// d1 with the two neighbour values already loaded (qp at +st where the
+// neighbour is valid, qm at -st); the cells two steps away are loaded only
+// on the one-sided branches (boundaries)
+template <class Q>
+__device__ __forceinline__ float d1_pre(Q q, int64_t c, int64_t st, float inv_h, unsigned cp, unsigned cm, float qc,
+                                        float qp, float qm) {
+    if (cp && cm) return (qp - qm) * 0.5f * inv_h;
+    if (cp) {
+        if (cp >= 10u) return (-3.f * qc + 4.f * qp - q(c + 2 * st)) * 0.5f * inv_h;
+        return (qp - qc) * inv_h;
+    }
+    if (cm) {
+        if (cm >= 10u) return (3.f * qc - 4.f * qm + q(c - 2 * st)) * 0.5f * inv_h;
+        return (qc - qm) * inv_h;
+    }
+    return 0.f;
+}
+
+// Every centre and face-neighbour value is loaded before any difference is
+// formed (offsets toward a missing neighbour are clamped to the cell itself),
+// so the loads of a cell are in flight together.
 template <int NDIM>
 __global__ void __launch_bounds__(128) k_front_rans(FrontGeo g, const uint32_t* __restrict__ code32,
                                                    const float* __restrict__ U, const float* __restrict__ R, float rho,
@@ -126,9 +147,38 @@ __global__ void __launch_bounds__(128) k_front_rans(FrontGeo g, const uint32_t* 
         for (int i = 0; i < NDIM; ++i) f[i * g.n_dense + c] = 0.f;
         return;
     }
-    float uc[NDIM];
+    constexpr int NS = NDIM == 3 ? 6 : 3;
+    unsigned cp[NDIM], cm[NDIM];
+    int64_t op[NDIM], om[NDIM];
 #pragma unroll
-    for (int i = 0; i < NDIM; ++i) uc[i] = __ldg(U + i * g.n_dense + c);
+    for (int a = 0; a < NDIM; ++a) {
+        cp[a] = cls_of(w, 2 * a);
+        cm[a] = cls_of(w, 2 * a + 1);
+        op[a] = cp[a] ? g.st[a] : 0;
+        om[a] = cm[a] ? -g.st[a] : 0;
+    }
+    float uc[NDIM], up[NDIM][NDIM], um[NDIM][NDIM];  // [component][axis]
+    float rc[NS], rp[NDIM][NDIM], rm[NDIM][NDIM];    // [i][axis] of plane splane(i, axis)
+#pragma unroll
+    for (int i = 0; i < NDIM; ++i) {
+        const float* ui = U + i * g.n_dense + c;
+        uc[i] = __ldg(ui);
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            up[i][a] = __ldg(ui + op[a]);
+            um[i][a] = __ldg(ui + om[a]);
+        }
+    }
+#pragma unroll
+    for (int pl = 0; pl < NS; ++pl) rc[pl] = __ldg(R + pl * g.n_dense + c);
+#pragma unroll
+    for (int i = 0; i < NDIM; ++i)
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const float* rij = R + splane<NDIM>(i, a) * g.n_dense + c;
+            rp[i][a] = __ldg(rij + op[a]);
+            rm[i][a] = __ldg(rij + om[a]);
+        }
 #pragma unroll
     for (int i = 0; i < NDIM; ++i) {
         const float* ui = U + i * g.n_dense;
@@ -136,11 +186,10 @@ __global__ void __launch_bounds__(128) k_front_rans(FrontGeo g, const uint32_t* 
         float acc = 0.f;
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {
-            const unsigned cp = cls_of(w, 2 * a), cm = cls_of(w, 2 * a + 1);
-            acc += uc[a] * d1(q, c, g.st[a], g.inv_h[a], cp, cm, uc[i]);
+            acc += uc[a] * d1_pre(q, c, g.st[a], g.inv_h[a], cp[a], cm[a], uc[i], up[i][a], um[i][a]);
             const float* rij = R + splane<NDIM>(i, a) * g.n_dense;
             auto qr = [&](int64_t k) { return __ldg(rij + k); };
-            acc += d1(qr, c, g.st[a], g.inv_h[a], cp, cm, __ldg(rij + c));
+            acc += d1_pre(qr, c, g.st[a], g.inv_h[a], cp[a], cm[a], rc[splane<NDIM>(i, a)], rp[i][a], rm[i][a]);
         }
         f[i * g.n_dense + c] = -rho * acc;
     }

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "cg_state.cuh"
@@ -341,6 +342,32 @@ __device__ __forceinline__ T rb_cell_full(T cm, T e, T wv, T n, T sv, T f, T b, 
 // every cell of a chunk valid with six valid faces (the colour bit ignored)
 __device__ __forceinline__ bool chunk_full(uint32_t cw) { return (cw & 0xBFBFBFBFu) == 0xBFBFBFBFu; }
 
+// A full chunk (chunk_full) with its cells ODD and ODD + 2 updated, the
+// other two kept.  The colour is a compile-time constant: the sweep below
+// gives every warp rows of one colour, so no lane selects operands.
+template <int ODD, class T>
+__device__ __forceinline__ V4<T> rb_chunk_full(const V4<T>& c, T xw, T xe, const V4<T>& n, const V4<T>& sv,
+                                               const V4<T>& f, const V4<T>& b, const V4<T>& r, T wf, T Fx, T Fy,
+                                               T Fz) {
+    V4<T> o = c;
+    if (ODD == 0) {
+        o.v[0] = rb_cell_full(c.v[0], c.v[1], xw, n.v[0], sv.v[0], f.v[0], b.v[0], r.v[0], wf, Fx, Fy, Fz);
+        o.v[2] = rb_cell_full(c.v[2], c.v[3], c.v[1], n.v[2], sv.v[2], f.v[2], b.v[2], r.v[2], wf, Fx, Fy, Fz);
+    } else {
+        o.v[1] = rb_cell_full(c.v[1], c.v[2], c.v[0], n.v[1], sv.v[1], f.v[1], b.v[1], r.v[1], wf, Fx, Fy, Fz);
+        o.v[3] = rb_cell_full(c.v[3], xe, c.v[2], n.v[3], sv.v[3], f.v[3], b.v[3], r.v[3], wf, Fx, Fy, Fz);
+    }
+    return o;
+}
+// the same with the colour known only at run time (lanes may differ)
+template <class T>
+__device__ __forceinline__ V4<T> rb_chunk_full(const V4<T>& c, T xw, T xe, const V4<T>& n, const V4<T>& sv,
+                                               const V4<T>& f, const V4<T>& b, const V4<T>& r, bool odd, T wf, T Fx,
+                                               T Fy, T Fz) {
+    return odd ? rb_chunk_full<1>(c, xw, xe, n, sv, f, b, r, wf, Fx, Fy, Fz)
+               : rb_chunk_full<0>(c, xw, xe, n, sv, f, b, r, wf, Fx, Fy, Fz);
+}
+
 struct RbArgs {
     int64_t px, plane;      // padded row pitch, px * ny
     int cpr, ny, nz;        // chunks per padded row, rows, planes
@@ -352,21 +379,26 @@ struct RbArgs {
 };
 
 template <class T, int CX, int RY, int FC, bool FROM_ZERO, bool DOT>
-__global__ void __launch_bounds__(CX * RY) k_mg_fine_rb_fused(const T* __restrict__ zin, T* __restrict__ zout,
+__global__ void __launch_bounds__(CX * RY, sizeof(T) == 4 ? 4 : 2) k_mg_fine_rb_fused(const T* __restrict__ zin, T* __restrict__ zout,
                                                              const T* __restrict__ r,
                                                              const uint8_t* __restrict__ code8, RbArgs g,
                                                              CgState* st, double* partials) {
+    static_assert(CX == 16 && RY % 2 == 0 && RY / 2 == CX * RY / 32, "a warp holds rows w and w + RY / 2");
     constexpr int NT = CX * RY;
     if (st->status != kRunning) return;
     __shared__ T wd[64];             // omega / D for every face mask (0 for an isolated cell)
-    __shared__ V4<T> ring[4][NT];    // plane q of the half-updated z in slot q & 3
+    __shared__ V4<T> ring[4][NT];    // plane q of the half-updated z in slot q & 3, [row][chunk]
     if (threadIdx.x < 64) {
         const unsigned fm = threadIdx.x;
         const T d = (T)g.F[0] * (T)((fm & 1u) + ((fm >> 1) & 1u)) + (T)g.F[1] * (T)(((fm >> 2) & 1u) + ((fm >> 3) & 1u)) +
                     (T)g.F[2] * (T)(((fm >> 4) & 1u) + ((fm >> 5) & 1u));
         wd[threadIdx.x] = d > T(0) ? (T)g.omega / d : T(0);
     }
-    const int t = threadIdx.x, lx = t % CX, ly = t / CX;
+    // lanes 0-15 of warp w take row w of the tile, lanes 16-31 row w + RY / 2:
+    // two rows of one colour, so the cells a warp updates on a plane are the
+    // same in every lane
+    const int t = threadIdx.x, lx = t % CX, ly = (t >> 5) + (RY / 2) * ((t >> 4) & 1);
+    const int s0 = ly * CX + lx;  // this chunk's place in a ring slot
     const T Fx = (T)g.F[0], Fy = (T)g.F[1], Fz = (T)g.F[2];
     double acc[1] = {0.0};
     for (long long item = blockIdx.x; item < g.n_items; item += gridDim.x) {
@@ -379,98 +411,87 @@ __global__ void __launch_bounds__(CX * RY) k_mg_fine_rb_fused(const T* __restric
         const int k0 = sl * g.slab, k1 = min(g.nz, k0 + g.slab);
         const int64_t col = (int64_t)j * g.px + 4 * (int64_t)c;  // offset of the chunk within a plane
         __syncthreads();  // the previous item's readers are done with the ring (and wd is set)
-        // Everything the first colour on plane q reads for this chunk, loaded in
-        // one go (every load at an in-range address: clamped to the chunk itself
-        // where a neighbour is outside the box; its face bit is then 0).
-        struct Loaded {
-            V4<T> zc, zn, zs, zf, zb, rv;
-            T xw, xe;
-            uint32_t cw;
-            bool ok;
-        };
-        auto load_plane = [&](int q) -> Loaded {
-            Loaded L;
-            L.ok = inr && q >= 0 && q < g.nz;
-            L.cw = 0u;
-            L.rv = L.zc = L.zn = L.zs = L.zf = L.zb = zero4<T>();
-            L.xw = L.xe = T(0);
-            if (L.ok) {
-                const int64_t i0 = (int64_t)q * g.plane + col;
-                L.cw = __ldg(reinterpret_cast<const uint32_t*>(code8 + i0));
-                L.rv = ld4(r + i0);
-                if (!FROM_ZERO) {
-                    const int64_t on = j + 1 < g.ny ? g.px : 0, os = j > 0 ? -g.px : 0;
-                    const int64_t of = q + 1 < g.nz ? g.plane : 0, ob = q > 0 ? -g.plane : 0;
-                    L.zc = ld4(zin + i0);
-                    L.zn = ld4(zin + i0 + on);
-                    L.zs = ld4(zin + i0 + os);
-                    L.zf = ld4(zin + i0 + of);
-                    L.zb = ld4(zin + i0 + ob);
-                    L.xw = zin[c > 0 ? i0 - 1 : i0];
-                    L.xe = zin[c + 1 < g.cpr ? i0 + 4 : i0];
-                }
-            }
-            return L;
-        };
-        // colour FC on plane q into ring slot q & 3
-        auto first_from = [&](int q, const Loaded& L) {
+        // Operands of the first colour.  Threads outside the grid load at the
+        // chunk (0, 0) instead (their results are zeroed), neighbours outside
+        // the box are read at the chunk itself (their face bit is 0), so every
+        // load is in range.  The chunk's own values on planes q - 1 and q are
+        // carried in registers from the previous plane (zB, zC): a plane step
+        // loads z on plane q + 1 and the rows and cells beside it on plane q.
+        const int64_t colc = inr ? col : 0;
+        const int on = j + 1 < g.ny ? (int)g.px : 0, os = j > 0 ? -(int)g.px : 0;
+        const int ow = c > 0 ? -1 : 0, oe = c + 1 < g.cpr ? 4 : 3;
+        const T* __restrict__ zcol = FROM_ZERO ? nullptr : zin + colc;
+        const T* __restrict__ rcol = r + colc;
+        const uint8_t* __restrict__ ccol = code8 + colc;
+        auto zat = [&](int q) -> V4<T> { return q >= 0 && q < g.nz ? ld4(zcol + (int64_t)q * g.plane) : zero4<T>(); };
+        V4<T> zB = zero4<T>(), zC = zero4<T>();
+        if (!FROM_ZERO) {
+            zB = zat(k0 - 2);
+            zC = zat(k0 - 1);
+        }
+        // Cell i of chunk c on row j, plane q has colour (m + j + q) mod 2
+        // (m = i - 4 c); the cells a step updates are m = ODD and ODD + 2.
+        // colour FC on plane q into ring slot q & 3 (zeros outside the grid);
+        // returns the chunk's r and code word on plane q
+        auto first = [&](int q, V4<T>& rq, uint32_t& cq, auto odd_c) {
+            constexpr int ODD = decltype(odd_c)::value;
             V4<T> o = zero4<T>();
-            if (L.ok) {
-                const uint32_t cw = L.cw;
-                const int par = (int)((cw >> 6) & 1u);
+            rq = zero4<T>();
+            cq = 0u;
+            if (q >= 0 && q < g.nz) {
+                const int64_t qo = (int64_t)q * g.plane;
+                cq = inr ? __ldg(reinterpret_cast<const uint32_t*>(ccol + qo)) : 0u;
+                rq = ld4(rcol + qo);
                 if (FROM_ZERO) {
 #pragma unroll
-                    for (int m = 0; m < 4; ++m)
-                        o.v[m] = ((m + par) & 1) == FC && valid8(cw, m) ? wd[face_bits8(cw, m)] * L.rv.v[m] : T(0);
+                    for (int m = ODD; m < 4; m += 2) o.v[m] = valid8(cq, m) ? wd[face_bits8(cq, m)] * rq.v[m] : T(0);
                 } else {
-                    const T wv[4] = {L.xw, L.zc.v[0], L.zc.v[1], L.zc.v[2]};
-                    const T ev[4] = {L.zc.v[1], L.zc.v[2], L.zc.v[3], L.xe};
-                    if (chunk_full(cw)) {
-                        const T wf = wd[63];
-#pragma unroll
-                        for (int m = 0; m < 4; ++m)
-                            o.v[m] = ((m + par) & 1) != FC
-                                         ? L.zc.v[m]
-                                         : rb_cell_full(L.zc.v[m], ev[m], wv[m], L.zn.v[m], L.zs.v[m], L.zf.v[m],
-                                                        L.zb.v[m], L.rv.v[m], wf, Fx, Fy, Fz);
+                    const T* p = zcol + qo;
+                    const V4<T> zF = q + 1 < g.nz ? ld4(p + g.plane) : zero4<T>();
+                    const V4<T> zn = ld4(p + on), zs = ld4(p + os);
+                    const T xw = p[ow], xe = p[oe];
+                    if (chunk_full(cq)) {
+                        o = rb_chunk_full<ODD>(zC, xw, xe, zn, zs, zF, zB, rq, wd[63], Fx, Fy, Fz);
                     } else {
+                        const T wv[4] = {xw, zC.v[0], zC.v[1], zC.v[2]};
+                        const T ev[4] = {zC.v[1], zC.v[2], zC.v[3], xe};
 #pragma unroll
                         for (int m = 0; m < 4; ++m) {
-                            if (((m + par) & 1) != FC) {
-                                o.v[m] = L.zc.v[m];
+                            if ((m & 1) != ODD) {
+                                o.v[m] = inr ? zC.v[m] : T(0);
                                 continue;
                             }
-                            const unsigned fm = face_bits8(cw, m);
-                            const T w = valid8(cw, m) ? wd[fm] : T(0);
-                            o.v[m] = rb_cell(L.zc.v[m], ev[m], wv[m], L.zn.v[m], L.zs.v[m], L.zf.v[m], L.zb.v[m],
-                                             L.rv.v[m], fm, w, Fx, Fy, Fz);
+                            const unsigned fm = face_bits8(cq, m);
+                            const T w = valid8(cq, m) ? wd[fm] : T(0);
+                            o.v[m] = rb_cell(zC.v[m], ev[m], wv[m], zn.v[m], zs.v[m], zF.v[m], zB.v[m], rq.v[m], fm, w,
+                                             Fx, Fy, Fz);
                         }
                     }
+                    zB = zC;
+                    zC = zF;
                 }
+            } else if (!FROM_ZERO) {
+                zB = zC;
+                zC = zat(q + 1);
             }
-            ring[q & 3][t] = o;
+            ring[q & 3][s0] = o;
         };
         // the other colour on plane k from planes k - 1, k, k + 1 of the ring
-        auto second = [&](int k, const V4<T>& rk, uint32_t cw) {
-            const V4<T> o = ring[k & 3][t];
-            const V4<T> zn = ring[k & 3][t + CX], zs = ring[k & 3][t - CX];
-            const V4<T> zf = ring[(k + 1) & 3][t], zb = ring[(k + 3) & 3][t];
-            const T xw = ring[k & 3][t - 1].v[3], xe = ring[k & 3][t + 1].v[0];
-            const T wv[4] = {xw, o.v[0], o.v[1], o.v[2]};
-            const T ev[4] = {o.v[1], o.v[2], o.v[3], xe};
-            const int par = (int)((cw >> 6) & 1u);
+        auto second = [&](int k, const V4<T>& rk, uint32_t cw, auto odd_c) {
+            constexpr int ODD = decltype(odd_c)::value;
+            const V4<T> o = ring[k & 3][s0];
+            const V4<T> zn = ring[k & 3][s0 + CX], zs = ring[k & 3][s0 - CX];
+            const V4<T> zf = ring[(k + 1) & 3][s0], zb = ring[(k + 3) & 3][s0];
+            const T xw = ring[k & 3][s0 - 1].v[3], xe = ring[k & 3][s0 + 1].v[0];
             V4<T> out;
             if (chunk_full(cw)) {
-                const T wf = wd[63];
-#pragma unroll
-                for (int m = 0; m < 4; ++m)
-                    out.v[m] = ((m + par) & 1) == FC ? o.v[m]
-                                                     : rb_cell_full(o.v[m], ev[m], wv[m], zn.v[m], zs.v[m], zf.v[m],
-                                                                    zb.v[m], rk.v[m], wf, Fx, Fy, Fz);
+                out = rb_chunk_full<ODD>(o, xw, xe, zn, zs, zf, zb, rk, wd[63], Fx, Fy, Fz);
             } else {
+                const T wv[4] = {xw, o.v[0], o.v[1], o.v[2]};
+                const T ev[4] = {o.v[1], o.v[2], o.v[3], xe};
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
-                    if (((m + par) & 1) == FC) {
+                    if ((m & 1) != ODD) {
                         out.v[m] = o.v[m];
                         continue;
                     }
@@ -488,22 +509,35 @@ __global__ void __launch_bounds__(CX * RY) k_mg_fine_rb_fused(const T* __restric
                 acc[0] += (double)part;
             }
         };
-        // the first colour is needed on planes k0 - 1 .. k1; at step k it runs
-        // on plane k + 1 (one sync: the slot it writes is none of the three
-        // the second colour on plane k - 1 may still be reading)
+        // The first colour is needed on planes k0 - 1 .. k1; at step k it runs
+        // on plane k + 1 and the second colour on plane k, both on the cells
+        // m = B(k), B(k) + 2 with B(k) = FC ^ ((j + k + 1) & 1), the same in
+        // every lane of a warp (its rows j and j + RY / 2 have one parity), so
+        // the branch on it below does not split warps.  One sync per step: the
+        // slot the first colour writes is none of the three the second colour
+        // on plane k - 1 may still be reading.
+        using I0 = std::integral_constant<int, 0>;
+        using I1 = std::integral_constant<int, 1>;
+        auto first_b = [&](int q, V4<T>& rq, uint32_t& cq, int bq) {
+            if (bq) first(q, rq, cq, I1{});
+            else first(q, rq, cq, I0{});
+        };
+        const int b0 = FC ^ ((j + k0 + 1) & 1);  // B(k0) = B(k0 - 2)
         {
-            first_from(k0 - 1, load_plane(k0 - 1));
-            const Loaded Lb = load_plane(k0);
-            first_from(k0, Lb);
-            V4<T> rk = Lb.rv;
-            uint32_t ck = Lb.cw;
+            V4<T> rk, rn;
+            uint32_t ck, cn;
+            first_b(k0 - 1, rn, cn, b0);
+            first_b(k0, rk, ck, b0 ^ 1);
             for (int k = k0; k < k1; ++k) {
-                const Loaded Ln = load_plane(k + 1);
-                first_from(k + 1, Ln);
+                const int bk = b0 ^ ((k - k0) & 1);
+                first_b(k + 1, rn, cn, bk);
                 __syncthreads();
-                if (interior) second(k, rk, ck);
-                rk = Ln.rv;
-                ck = Ln.cw;
+                if (interior) {
+                    if (bk) second(k, rk, ck, I1{});
+                    else second(k, rk, ck, I0{});
+                }
+                rk = rn;
+                ck = cn;
             }
         }
     }
@@ -551,6 +585,7 @@ struct RbTmaGeo {
 };
 
 __device__ __forceinline__ uint32_t rb_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ V4<float> f4v(const float4& a) { return {{a.x, a.y, a.z, a.w}}; }
 
 template <int FC, bool FROM_ZERO, bool DOT>
 __global__ void __launch_bounds__(256, 2) k_mg_fine_rb_tma(const __grid_constant__ CUtensorMap tm_z,
@@ -672,11 +707,9 @@ __global__ void __launch_bounds__(256, 2) k_mg_fine_rb_tma(const __grid_constant
                 const float wv[4] = {xw, cv[0], cv[1], cv[2]};
                 const float ev[4] = {cv[1], cv[2], cv[3], xe};
                 if (chunk_full(cw)) {
-#pragma unroll
-                    for (int m = 0; m < 4; ++m)
-                        ov[m] = ((m + par) & 1) != FC
-                                    ? cv[m]
-                                    : rb_cell_full(cv[m], ev[m], wv[m], nv[m], sv[m], fv[m], bv[m], rv[m], wf, Fx, Fy, Fz);
+                    const V4<float> u = rb_chunk_full(f4v(c4), xw, xe, f4v(n4), f4v(s4), f4v(f4), f4v(b4), f4v(r4),
+                                                      ((FC ^ par) & 1) != 0, wf, Fx, Fy, Fz);
+                    o = make_float4(u.v[0], u.v[1], u.v[2], u.v[3]);
                 } else {
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
@@ -790,11 +823,9 @@ __global__ void __launch_bounds__(256, 2) k_mg_fine_rb_tma(const __grid_constant
                 float4 out4;
                 float* outv = reinterpret_cast<float*>(&out4);
                 if (chunk_full(cw)) {
-#pragma unroll
-                    for (int m = 0; m < 4; ++m)
-                        outv[m] = ((m + par) & 1) == FC
-                                      ? ov[m]
-                                      : rb_cell_full(ov[m], ev[m], wv[m], nv[m], sv[m], fv[m], bv[m], rv[m], wf, Fx, Fy, Fz);
+                    const V4<float> u = rb_chunk_full(f4v(o4), xw, xe, f4v(n4), f4v(s4), f4v(f4), f4v(b4), f4v(r4),
+                                                      ((FC ^ par ^ 1) & 1) != 0, wf, Fx, Fy, Fz);
+                    out4 = make_float4(u.v[0], u.v[1], u.v[2], u.v[3]);
                 } else {
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
@@ -1113,20 +1144,33 @@ __global__ void k_mg_coarse(const T* __restrict__ z, const T* __restrict__ r,
 }
 
 // Fused red-black sweep on a coarse level with packed face counts, out of
-// place, marching in z (the coarse counterpart of k_mg_fine_rb_fused, one
-// cell per thread): a block owns a tile of 32 x 8 cells (interior 30 x 6,
-// one-cell halo) and a slab of planes; at step k it updates colour FC
-// ((i + j + k) mod 2 == FC) on plane k + 1 over the tile and its halo from
-// z_in into a 4-slot shared ring, then the other colour on plane k from the
-// ring, and writes plane k of z_out.  A cell's six weights (count x F_a; the
-// - faces from the neighbours' words) and omega / D are formed once, in the
-// first step, and kept for the second.  FROM_ZERO: z_in = 0.
-constexpr int kCbX = 32, kCbY = 8;
+// place, marching in z (the coarse counterpart of k_mg_fine_rb_fused).  A
+// thread owns two cells beside each other in x -- one of each colour -- so
+// each half of the sweep updates exactly one of them in every lane (no lane
+// idles on the colour, no warp splits).  A block owns 32 such pairs x 8 rows
+// (interior 60 x 6 cells, a one-cell halo) and a slab of planes; at step k it
+// updates colour FC on plane k + 1 over the tile and its halo from z_in into
+// a 4-slot shared ring, then the other colour on plane k from the ring, and
+// writes plane k of z_out.  x neighbours come from the adjacent lanes (warp
+// shuffles), the pair's own values on planes q - 1, q and its -z count words
+// are carried from plane to plane in registers.  A cell's weights (count x
+// F_a) and omega / D are formed once per plane for both cells.  FROM_ZERO:
+// z_in = 0.
+constexpr int kCbX = 32, kCbY = 8;       // pairs per row (lanes), rows
+constexpr int kCbCells = 2 * kCbX - 4;   // interior cells of a tile row (60)
+
+// 1 / x, rounded to nearest (FP32: the reciprocal instruction with its
+// correction, not a full division)
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 struct CbArgs {
     int nx, ny, nz, tiles_x, tiles_y, slab;
     long long n_items;
 };
+
+// a 10-bit count as a float (exact: counts < 2^23)
+__device__ __forceinline__ float cnt_f(uint32_t w, int shift) { return (float)((w >> shift) & 1023u); }
 
 template <class T, int FC, bool FROM_ZERO>
 __global__ void __launch_bounds__(kCbX * kCbY) k_mg_coarse_rb_fused(const T* __restrict__ zin, T* __restrict__ zout,
@@ -1134,87 +1178,141 @@ __global__ void __launch_bounds__(kCbX * kCbY) k_mg_coarse_rb_fused(const T* __r
                                                                   CbArgs g, const CgState* st) {
     constexpr int NT = kCbX * kCbY;
     if (st->status != kRunning) return;
-    __shared__ T ring[4][NT];
-    const int t = threadIdx.x, lx = t % kCbX, ly = t / kCbX;
+    __shared__ T ring[4][2][NT];  // plane q's half-updated pair: [q & 3][cell][thread]
+    const int t = threadIdx.x, lane = t & 31, ly = t >> 5;
     const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
     const T F0 = (T)lv.F[0], F1 = (T)lv.F[1], F2 = (T)lv.F[2];
     for (long long item = blockIdx.x; item < g.n_items; item += gridDim.x) {
         const int tx = (int)(item % g.tiles_x);
         const int ty = (int)((item / g.tiles_x) % g.tiles_y);
         const int sl = (int)(item / ((long long)g.tiles_x * g.tiles_y));
-        const int i = tx * (kCbX - 2) - 1 + lx, j = ty * (kCbY - 2) - 1 + ly;
-        const bool inr = i >= 0 && i < g.nx && j >= 0 && j < g.ny;
-        const bool interior = inr && lx >= 1 && lx <= kCbX - 2 && ly >= 1 && ly <= kCbY - 2;
+        const int i0 = tx * kCbCells - 2 + 2 * lane;  // the pair's first cell (even)
+        const int j = ty * (kCbY - 2) - 1 + ly;
+        const bool jin = j >= 0 && j < g.ny;
+        const bool in0 = jin && i0 >= 0 && i0 < g.nx, in1 = jin && i0 + 1 >= 0 && i0 + 1 < g.nx;
+        const bool interior = lane >= 1 && lane <= kCbX - 2 && ly >= 1 && ly <= kCbY - 2;
         const int k0 = sl * g.slab, k1 = min(g.nz, k0 + g.slab);
-        const int64_t col = (int64_t)j * sy + i;
+        // loads at in-range addresses: a cell outside the box reads cell 0 of
+        // the level (its weights are 0, its result discarded)
+        const int64_t c0 = in0 ? (int64_t)j * sy + i0 : 0, c1 = in1 ? (int64_t)j * sy + i0 + 1 : 0;
+        const bool yp = j + 1 < g.ny, ym = j > 0;
         __syncthreads();
-        // weights of the cell on plane q: xp, xm, yp, ym, zp, zm, omega / D
-        struct W7 {
+        // carried: the pair's z on planes q - 1, q and its count words on plane q - 1
+        T zB0 = T(0), zB1 = T(0), zC0 = T(0), zC1 = T(0);
+        uint32_t wz0 = 0u, wz1 = 0u;
+        auto zat = [&](int q, int64_t c, bool in) -> T { return in && q >= 0 && q < g.nz ? zin[(int64_t)q * sz + c] : T(0); };
+        auto wat = [&](int q, int64_t c, bool in) -> uint32_t {
+            return in && q >= 0 && q < g.nz ? __ldg(lv.wc + (int64_t)q * sz + c) : 0u;
+        };
+        if (!FROM_ZERO) {
+            zB0 = zat(k0 - 2, c0, in0);
+            zB1 = zat(k0 - 2, c1, in1);
+            zC0 = zat(k0 - 1, c0, in0);
+            zC1 = zat(k0 - 1, c1, in1);
+        }
+        wz0 = wat(k0 - 2, c0, in0);
+        wz1 = wat(k0 - 2, c1, in1);
+        // the other cell's weights and r on a plane, for its update one step later
+        struct Wv {
             T xp, xm, yp, ym, zp, zm, wd, r;
         };
-        auto first = [&](int q, W7& w) {
-            T o = T(0);
-            w = W7{T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-            if (inr && q >= 0 && q < g.nz) {
-                const int64_t c = (int64_t)q * sz + col;
-                const uint32_t w0 = __ldg(lv.wc + c);
-                const uint32_t w1 = i > 0 ? __ldg(lv.wc + c - 1) : 0u;
-                const uint32_t w2 = j > 0 ? __ldg(lv.wc + c - sy) : 0u;
-                const uint32_t w3 = q > 0 ? __ldg(lv.wc + c - sz) : 0u;
-                w.r = r[c];
-                w.xp = (T)((float)(w0 & 1023u) * lv.F[0]);
-                w.yp = (T)((float)((w0 >> 10) & 1023u) * lv.F[1]);
-                w.zp = (T)((float)(w0 >> 20) * lv.F[2]);
-                w.xm = (T)((float)(w1 & 1023u) * lv.F[0]);
-                w.ym = (T)((float)((w2 >> 10) & 1023u) * lv.F[1]);
-                w.zm = (T)((float)(w3 >> 20) * lv.F[2]);
-                const T d = w.xp + w.xm + w.yp + w.ym + w.zp + w.zm;
-                w.wd = d > T(0) ? omega / d : T(0);
-                const bool mine = ((i + j + q) & 1) == FC;
+        auto first = [&](int q, Wv& wv) {
+            T o0 = T(0), o1 = T(0);
+            wv = Wv{T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+            const bool qin = q >= 0 && q < g.nz;
+            const int64_t qo = (int64_t)q * sz;
+            // count words: own (+x, +y, +z), -x of cell 0 from the lane before,
+            // -y from the row before, -z carried from the plane before
+            const uint32_t w0 = wat(q, c0, in0), w1 = wat(q, c1, in1);
+            const uint32_t wy0 = ym ? wat(q, c0 - sy, in0) : 0u, wy1 = ym ? wat(q, c1 - sy, in1) : 0u;
+            uint32_t wx0 = __shfl_up_sync(0xffffffffu, w1, 1);
+            if (i0 == 0 || lane == 0) wx0 = 0u;  // lane 0's first cell is never used
+            const T r0 = qin && in0 ? r[qo + c0] : T(0), r1 = qin && in1 ? r[qo + c1] : T(0);
+            // weights of both cells
+            const T xp0 = (T)(cnt_f(w0, 0) * (float)F0), xp1 = (T)(cnt_f(w1, 0) * (float)F0);
+            const T xm0 = (T)(cnt_f(wx0, 0) * (float)F0), xm1 = xp0;
+            const T yp0 = (T)(cnt_f(w0, 10) * (float)F1), yp1 = (T)(cnt_f(w1, 10) * (float)F1);
+            const T ym0 = (T)(cnt_f(wy0, 10) * (float)F1), ym1 = (T)(cnt_f(wy1, 10) * (float)F1);
+            const T zp0 = (T)(cnt_f(w0, 20) * (float)F2), zp1 = (T)(cnt_f(w1, 20) * (float)F2);
+            const T zm0 = (T)(cnt_f(wz0, 20) * (float)F2), zm1 = (T)(cnt_f(wz1, 20) * (float)F2);
+            const T d0 = xp0 + xm0 + yp0 + ym0 + zp0 + zm0, d1 = xp1 + xm1 + yp1 + ym1 + zp1 + zm1;
+            const T wd0 = d0 > T(0) ? omega * recip(d0) : T(0), wd1 = d1 > T(0) ? omega * recip(d1) : T(0);
+            wz0 = w0;
+            wz1 = w1;
+            // which cell of the pair has colour FC on this plane
+            const bool u1 = ((FC ^ (j + q)) & 1) != 0;
+            if (qin) {
                 if (FROM_ZERO) {
-                    o = mine ? w.wd * w.r : T(0);
+                    o0 = u1 ? T(0) : wd0 * r0;
+                    o1 = u1 ? wd1 * r1 : T(0);
                 } else {
-                    const T zc = zin[c];
-                    if (mine) {
-                        const T ze = i + 1 < g.nx ? zin[c + 1] : T(0), zw = i > 0 ? zin[c - 1] : T(0);
-                        const T zn = j + 1 < g.ny ? zin[c + sy] : T(0), zs = j > 0 ? zin[c - sy] : T(0);
-                        const T zf = q + 1 < g.nz ? zin[c + sz] : T(0), zb = q > 0 ? zin[c - sz] : T(0);
-                        const T az = w.xp * (zc - ze) + w.xm * (zc - zw) + w.yp * (zc - zn) + w.ym * (zc - zs) +
-                                     w.zp * (zc - zf) + w.zm * (zc - zb);
-                        o = zc + w.wd * (w.r - az);
-                    } else {
-                        o = zc;
-                    }
+                    const T zF0 = zat(q + 1, c0, in0), zF1 = zat(q + 1, c1, in1);
+                    const T zw = __shfl_up_sync(0xffffffffu, zC1, 1);    // cell i0 - 1
+                    const T ze = __shfl_down_sync(0xffffffffu, zC0, 1);  // cell i0 + 2
+                    // the FC cell's update
+                    const int64_t cu = u1 ? c1 : c0;
+                    const bool inu = u1 ? in1 : in0;
+                    const T zn = inu && yp ? zin[qo + cu + sy] : T(0), zs = inu && ym ? zin[qo + cu - sy] : T(0);
+                    const T zc = u1 ? zC1 : zC0;
+                    const T ex = u1 ? ze : zC1, wx = u1 ? zC0 : zw;
+                    const T xp = u1 ? xp1 : xp0, xm = u1 ? xm1 : xm0, ypw = u1 ? yp1 : yp0, ymw = u1 ? ym1 : ym0;
+                    const T zpw = u1 ? zp1 : zp0, zmw = u1 ? zm1 : zm0, wdu = u1 ? wd1 : wd0, ru = u1 ? r1 : r0;
+                    const T zf = u1 ? zF1 : zF0, zb = u1 ? zB1 : zB0;
+                    const T az = xp * (zc - ex) + xm * (zc - wx) + ypw * (zc - zn) + ymw * (zc - zs) + zpw * (zc - zf) +
+                                 zmw * (zc - zb);
+                    const T nu = zc + wdu * (ru - az);
+                    o0 = u1 ? zC0 : nu;
+                    o1 = u1 ? nu : zC1;
+                    zB0 = zC0;
+                    zB1 = zC1;
+                    zC0 = zF0;
+                    zC1 = zF1;
                 }
+                // the other cell, for the second half one step later
+                wv.xp = u1 ? xp0 : xp1;
+                wv.xm = u1 ? xm0 : xm1;
+                wv.yp = u1 ? yp0 : yp1;
+                wv.ym = u1 ? ym0 : ym1;
+                wv.zp = u1 ? zp0 : zp1;
+                wv.zm = u1 ? zm0 : zm1;
+                wv.wd = u1 ? wd0 : wd1;
+                wv.r = u1 ? r0 : r1;
+            } else if (!FROM_ZERO) {
+                zB0 = zC0;
+                zB1 = zC1;
+                zC0 = zat(q + 1, c0, in0);
+                zC1 = zat(q + 1, c1, in1);
             }
-            ring[q & 3][t] = o;
+            ring[q & 3][0][t] = in0 ? o0 : T(0);
+            ring[q & 3][1][t] = in1 ? o1 : T(0);
         };
-        W7 w_cur, w_nxt;
-        first(k0 - 1, w_nxt);  // plane -1 (k0 = 0) writes zeros: its slot is read with weight 0
+        Wv w_cur, w_nxt;
+        first(k0 - 1, w_nxt);  // plane -1 (k0 = 0) writes zeros
         first(k0, w_cur);
         for (int k = k0; k < k1; ++k) {
             first(k + 1, w_nxt);
             __syncthreads();
             if (interior) {
-                const T zc = ring[k & 3][t];
-                T out = zc;
-                if (((i + j + k) & 1) != FC) {
-                    const T ze = ring[k & 3][t + 1], zw = ring[k & 3][t - 1];
-                    const T zn = ring[k & 3][t + kCbX], zs = ring[k & 3][t - kCbX];
-                    const T zf = ring[(k + 1) & 3][t], zb = ring[(k + 3) & 3][t];
-                    const W7& w = w_cur;
-                    const T az = w.xp * (zc - ze) + w.xm * (zc - zw) + w.yp * (zc - zn) + w.ym * (zc - zs) +
-                                 w.zp * (zc - zf) + w.zm * (zc - zb);
-                    out = zc + w.wd * (w.r - az);
-                }
-                zout[(int64_t)k * sz + col] = out;
+                // the cell of the other colour on plane k
+                const bool v1 = ((FC ^ (j + k)) & 1) == 0;  // the other cell is cell 1
+                const int cv = v1 ? 1 : 0;
+                const T zc = ring[k & 3][cv][t];
+                const T ex = v1 ? ring[k & 3][0][t + 1] : ring[k & 3][1][t];
+                const T wx = v1 ? ring[k & 3][0][t] : ring[k & 3][1][t - 1];
+                const T zn = ring[k & 3][cv][t + kCbX], zs = ring[k & 3][cv][t - kCbX];
+                const T zf = ring[(k + 1) & 3][cv][t], zb = ring[(k + 3) & 3][cv][t];
+                const Wv& w = w_cur;
+                const T az = w.xp * (zc - ex) + w.xm * (zc - wx) + w.yp * (zc - zn) + w.ym * (zc - zs) +
+                             w.zp * (zc - zf) + w.zm * (zc - zb);
+                const T nv = zc + w.wd * (w.r - az);
+                const T other = ring[k & 3][1 - cv][t];
+                const int64_t qo = (int64_t)k * sz;
+                if (in0) zout[qo + c0] = v1 ? other : nv;
+                if (in1) zout[qo + c1] = v1 ? nv : other;
             }
             w_cur = w_nxt;
         }
     }
-    (void)F0;
-    (void)F1;
-    (void)F2;
 }
 
 // Red-black half-sweep on a coarse level, in place: cells of colour COLOR
@@ -1470,8 +1568,9 @@ RbMaps* rb_maps(osmodi_plan p, const float* zA, const float* zB, const float* r)
     return m->ok ? m : nullptr;
 }
 
+template <class T>
 int rb_grid(osmodi_plan p, const RbArgs& a) {
-    static const int bps = blocks_per_sm(k_mg_fine_rb_fused<float, kRbCX, kRbRY, 0, false, false>);
+    static const int bps = blocks_per_sm(k_mg_fine_rb_fused<T, kRbCX, kRbRY, 0, false, false>);
     return (int)std::max<long long>(1, std::min<long long>(a.n_items, (long long)p->num_sms * bps));
 }
 
@@ -1548,13 +1647,15 @@ T* vcycle_body(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, cud
         cb.nx = (int)g.nx;
         cb.ny = (int)g.ny;
         cb.nz = (int)g.nz;
-        cb.tiles_x = (cb.nx + kCbX - 3) / (kCbX - 2);
+        cb.tiles_x = (cb.nx + kCbCells - 1) / kCbCells;
         cb.tiles_y = (cb.ny + kCbY - 3) / (kCbY - 2);
         static const int bps = blocks_per_sm(k_mg_coarse_rb_fused<T, 0, false>);
         const long long tiles = (long long)cb.tiles_x * cb.tiles_y;
-        const long long want = 8LL * p->num_sms * bps;
+        // about four items per resident block (every slab recomputes two planes
+        // of the first colour; fewer, deeper slabs leave a longer tail)
+        const long long want = 4LL * p->num_sms * bps;
         const long long slabs = std::max<long long>(1, std::min<long long>(cb.nz, (want + tiles - 1) / tiles));
-        cb.slab = std::max(4, (int)((cb.nz + slabs - 1) / slabs));
+        cb.slab = std::max(8, (int)((cb.nz + slabs - 1) / slabs));
         cb.n_items = tiles * ((cb.nz + cb.slab - 1) / cb.slab);
         const int gf = (int)std::max<long long>(1, std::min<long long>(cb.n_items, (long long)p->num_sms * bps));
         const T om = (T)kOmegaRB;
@@ -1731,7 +1832,7 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
         // sweeps, the last forming (r, z).  Each sweep reads one buffer and
         // writes the other: 2 nu passes starting in zA end in zB.
         const RbArgs ra = rb_args(p);
-        const int gr = rb_grid(p, ra);
+        const int gr = rb_grid<T>(p, ra);
         T* cur = w.zA;
         T* oth = w.zB;
         if (nu == 1) mark(0);
@@ -1867,6 +1968,21 @@ void mg_free(osmodi_plan p) {
 bool mg_enabled(osmodi_plan p) { return p->mg != nullptr; }
 
 int mg_levels(osmodi_plan p) { return p->mg ? (int)hier_of(p)->lv.size() : 0; }
+
+bool mg_level_view(osmodi_plan p, int l, MgLevelView* v) {
+    const Hier* h = hier_of(p);
+    if (!h || l < 1 || l > (int)h->lv.size()) return false;
+    const Level& g = h->lv[l - 1];
+    *v = MgLevelView{g.nx, g.ny, g.nz, g.n, g.wx, g.wy, g.wz, g.dinv};
+    return true;
+}
+
+void mg_jacobi_params(osmodi_plan p, float* omega, float* scale, int* nu, int* coarse_sweeps) {
+    *omega = kOmega;
+    *scale = p->opt.mg_scale > 0.0 ? (float)p->opt.mg_scale : kScaleJacobi;
+    *nu = p->opt.mg_sweeps > 0 ? p->opt.mg_sweeps : kNu;
+    *coarse_sweeps = kCoarseSweeps;
+}
 
 size_t mg_level_bytes(osmodi_plan p, size_t tsize) {
     const Hier* h = hier_of(p);

@@ -30,6 +30,18 @@ size_t mg_level_bytes(osmodi_plan p, size_t tsize);     // workspace for the coa
 double mg_updates_per_apply(osmodi_plan p);             // valid cells x stencil applications of one B r
 int mg_launches_per_apply(osmodi_plan p);               // kernels one B r issues
 
+// coarse level l (1-based) of the plan's hierarchy: a dense box and its
+// explicit FP32 face weights (+x / +y / +z face of every cell; 0 on the box
+// boundary) and 1 / D (0 for an isolated cell)
+struct MgLevelView {
+    int64_t nx, ny, nz, n;
+    const float *wx, *wy, *wz, *dinv;
+};
+bool mg_level_view(osmodi_plan p, int l, MgLevelView* v);
+// the damped-Jacobi V-cycle parameters of the plan (omega, coarse-correction
+// scale, sweeps before and after, sweeps on the coarsest level)
+void mg_jacobi_params(osmodi_plan p, float* omega, float* scale, int* nu, int* coarse_sweeps);
+
 // two fine work vectors (padded box) and the coarse-level vectors
 template <class T>
 struct MgBuffers {

@@ -563,13 +563,14 @@ def main():
         torch.cuda.empty_cache()
 
     # the batched workload: PIV-like snapshots of uneven sizes and masks, one
-    # persistent launch per batch (reported beside the headline)
+    # persistent launch per batch with the multigrid V-cycle inside it
+    # (reported beside the headline)
     if not args.no_batch:
         del grad, p
         plan.close()
         torch.cuda.empty_cache()
         probs = [inputs.piv_snapshot_2d(i, device="cuda") for i in range(args.batch_count)]
-        plans_b = [osm.Plan(2, pr.dims, pr.spacing, pr.mask.cuda()) for pr in probs]
+        plans_b = [osm.Plan(2, pr.dims, pr.spacing, pr.mask.cuda(), precond=1) for pr in probs]
         batch = osm.Batch(plans_b)
         grads_b = [pr.grad for pr in probs]
         outs = [torch.zeros(pr.mask.shape, dtype=torch.float64, device="cuda") for pr in probs]
@@ -598,7 +599,25 @@ def main():
                                "seconds": bms / 1e3, "solves_per_s": args.batch_count / (bms / 1e3),
                                "GLUPS": sum(r.point_updates for r in res_b) / (bms / 1e3) / 1e9,
                                "cg_iterations_min_mean_max": [min(its), float(sum(its)) / len(its), max(its)],
-                               "launches": 1, "graph_captured": True, "tile_depth_chunks_per_thread": depth}
+                               "launches": 1, "graph_captured": True, "tile_depth_chunks_per_thread": depth,
+                               "preconditioner": "multigrid V-cycle (damped Jacobi) inside the persistent launch"}
+        # the same launch without the preconditioner (plain CG), for comparison
+        plans_p = [osm.Plan(2, pr.dims, pr.spacing, pr.mask.cuda()) for pr in probs]
+        batch_p = osm.Batch(plans_p)
+        for o in outs:
+            o.zero_()
+        torch.cuda.synchronize()
+        b0.record(stream)
+        st_p, res_p = batch_p.solve(grads_b, outs, 1e-10, stream=stream)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        pms = b0.elapsed_time(b1)
+        its_p = [r.inner_iters for r in res_p]
+        line["batched_piv"]["plain_cg_in_launch"] = {
+            "status": st_p, "seconds": pms / 1e3, "solves_per_s": args.batch_count / (pms / 1e3),
+            "cg_iterations_min_mean_max": [min(its_p), float(sum(its_p)) / len(its_p), max(its_p)],
+            "timer": "CUDA events around one direct (not graph-captured) batched call"}
+        del batch_p, plans_p
         # the same snapshots, each solved by the multigrid-preconditioned CG,
         # spread over host threads driving their own streams (osmodi_solve_many)
         if not args.no_many:

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "mg.cuh"
 #include "stencil.cuh"
 
 namespace osm {
@@ -30,16 +31,36 @@ namespace osm {
 namespace {
 
 enum { kRun = 0, kConv = 1, kSegDone = 2, kInit = 3, kDone = 4, kFail = 5, kNaN = 6 };
-enum { TK_S = 0, TK_R = 1, TK_I = 2, TK_A = 3, TK_B = 4, TK_O = 5, kTickets = 6 };
+enum { TK_S = 0, TK_R = 1, TK_I = 2, TK_A = 3, TK_B = 4, TK_O = 5, TK_M = 6, kTickets = 7 };
 constexpr int kPartK = 3;  // doubles per tile partial
 constexpr int kTileThreads = 256;
 constexpr int kMaxCpt = 8;  // chunks per thread per tile (tile = 256 * cpt chunks)
+// multigrid inside the launch: levels of at most kBottomCells cells (and the
+// ones below them) run inside one block per instance; the levels above are
+// grid-wide passes over tiles of kCTile cells, at most kMaxGrid of them
+constexpr int kBottomCells = 4096;
+constexpr int kMaxGrid = 12;
+constexpr int kCTile = 1024;
+
+// one coarse level of one instance (a dense box, the plan's explicit weights)
+struct BLevel {
+    int64_t nx, ny, nz, n;
+    int64_t off;  // first cell inside the coarse arenas
+    const float *wx, *wy, *wz, *dinv;
+};
+
+struct BCTile {
+    int inst, ncells;
+    int64_t cell0;
+};
 
 struct BInst {
     int64_t off;  // first cell of the instance's padded box in the arena
     int64_t px, ny, nz, nx, plane, n_box, n_dense;
     int tile0, ntiles;
     int comp_off, n_comp;
+    int lv0, nlv;  // multigrid: the instance's coarse levels in the level table (level l at lv0 + l - 1)
+    int G, pad;    // levels 0 .. G - 1 run grid-wide, G .. nlv inside one block (G = 0: no hierarchy)
     double n_valid;
     double F[3], h[3];
     const uint8_t* code8;
@@ -61,6 +82,7 @@ struct BState {
     double dist2, pnorm2;
     long long it, seg_it;
     int status, first, par, p64par, rounds, stall, cont, breakdown, nan_in, pad;
+    int pend, keep;  // multigrid: the segment's first (r, z) is still to come / the old direction is kept
     unsigned ticket[kTickets];
 };
 
@@ -86,6 +108,14 @@ struct BParams {
     long long spin_limit;  // polls of a grid barrier before it gives up (OSMODI_DEBUG_BARRIER_SPINS)
     int skip_block;        // test hook: this block leaves before the first barrier (-1: none)
     int pad2;
+    // multigrid preconditioner (mg = 1): z = B r by one V-cycle per iteration
+    int mg, gmax, nu, coarse_sweeps;
+    float omega, scale;
+    const BLevel* lv;
+    const BCTile* ct;
+    int ct0[kMaxGrid + 1], nct[kMaxGrid + 1];  // tiles over the cells of level l (1 .. gmax)
+    void *zA, *zB;                             // fine-level z (inner type)
+    void *cr, *ca, *cb;                        // coarse r, z, z' (inner type)
 };
 
 // ---- bounded grid barrier (the cooperative launch guarantees co-residency) ----
@@ -177,6 +207,386 @@ __device__ __forceinline__ Geo<T> inst_geo(const BInst& I) {
 
 __device__ __forceinline__ double* comp_of(const BParams& P, const BInst& I, int32_t l) {
     return P.comp + 3 * (size_t)(I.comp_off + l);
+}
+
+// ---------------------------------------------------------------------------
+// Multigrid preconditioner inside the persistent launch.
+//
+// The V-cycle of the plans' hierarchies (aggregation, damped-Jacobi
+// smoothing: z = omega D^-1 r, then nu - 1 sweeps before the coarse
+// correction, nu after it, the correction scaled; many sweeps on the
+// coarsest level), run for every instance at once.  The fine level and the
+// large coarse levels are grid-wide passes separated by grid barriers (a
+// Jacobi sweep reads its neighbours' previous values, so every sweep is one
+// pass); the residual is restricted in the pass that forms it (one thread per
+// coarse cell sums the residuals of its children) and the coarse correction
+// is prolongated by the last sweep of the coarse level (every coarse cell adds
+// its scaled value to its children).  Levels of at most kBottomCells cells
+// and everything below them run inside one block per instance with block
+// barriers.  A level's z lives in two buffers (a, b): the pre-smoothed z in
+// buffer (nu - 1) & 1, the final z in buffer 1.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int mg_pre(int nu) { return (nu - 1) & 1; }
+
+// (A z)_q on a coarse level, every load issued at once.  Offsets that leave
+// the box are clamped to the cell itself: the +x / +y / +z weight of a cell
+// on the box boundary is 0 (no fine face joins it), and the -x / -y / -z
+// weight is the neighbour's, read only where the neighbour exists (before
+// the first cell of a row or plane it belongs to a boundary cell: 0).
+template <class T, int NDIM>
+__device__ __forceinline__ T lv_az(const BLevel& L, const T* z, int64_t q, T zc) {
+    const int64_t sy = L.nx, sz = L.nx * L.ny, n = L.n;
+    const int64_t qxp = q + 1 < n ? q + 1 : q, qxm = q >= 1 ? q - 1 : q;
+    const int64_t qyp = q + sy < n ? q + sy : q, qym = q >= sy ? q - sy : q;
+    const T wxp = (T)__ldg(L.wx + q), wyp = (T)__ldg(L.wy + q);
+    const T wxm = q >= 1 ? (T)__ldg(L.wx + qxm) : T(0), wym = q >= sy ? (T)__ldg(L.wy + qym) : T(0);
+    const T zxp = __ldcg(z + qxp), zxm = __ldcg(z + qxm), zyp = __ldcg(z + qyp), zym = __ldcg(z + qym);
+    T az = wxp * (zc - zxp) + wxm * (zc - zxm) + wyp * (zc - zyp) + wym * (zc - zym);
+    if (NDIM == 3) {
+        const int64_t qzp = q + sz < n ? q + sz : q, qzm = q >= sz ? q - sz : q;
+        const T wzp = (T)__ldg(L.wz + q), wzm = q >= sz ? (T)__ldg(L.wz + qzm) : T(0);
+        az += wzp * (zc - __ldcg(z + qzp)) + wzm * (zc - __ldcg(z + qzm));
+    }
+    return az;
+}
+
+// one damped-Jacobi sweep at cell q: z + omega D^-1 (r - A z)
+template <class T, int NDIM>
+__device__ __forceinline__ T lv_sweep(const BLevel& L, const T* r, const T* z, int64_t q, T omega) {
+    const T zc = __ldcg(z + q);
+    const T az = lv_az<T, NDIM>(L, z, q, zc);
+    return zc + omega * (T)__ldg(L.dinv + q) * (__ldcg(r + q) - az);
+}
+
+// (I, J, K) of cell q of a dense box (32-bit arithmetic: a level of one
+// instance has fewer than 2^31 cells)
+__device__ __forceinline__ void lv_ijk(const BLevel& L, int64_t q, int64_t& i, int64_t& j, int64_t& k) {
+    const uint32_t q32 = (uint32_t)q, row = q32 / (uint32_t)L.nx;
+    i = q32 - row * (uint32_t)L.nx;
+    j = row % (uint32_t)L.ny;
+    k = row / (uint32_t)L.ny;
+}
+
+// coarse cell Q of level C: r_C = the sum of the residuals r - A z of its
+// children on level F, and the first sweep z_C = omega D^-1 r_C
+template <class T, int NDIM>
+__device__ __forceinline__ void lv_restrict(const BLevel& F, const T* rF, const T* zF, const BLevel& C, T* rC, T* zC,
+                                            int64_t Q, T omega) {
+    int64_t I, J, K;
+    lv_ijk(C, Q, I, J, K);
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < (NDIM == 3 ? 2 : 1); ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const int64_t i = 2 * I + a, j = 2 * J + b, k = 2 * K + c;
+                if (i < F.nx && j < F.ny && k < F.nz) {
+                    const int64_t q = (k * F.ny + j) * F.nx + i;
+                    const T zc = __ldcg(zF + q);
+                    s += __ldcg(rF + q) - lv_az<T, NDIM>(F, zF, q, zc);
+                }
+            }
+    rC[Q] = s;
+    zC[Q] = omega * (T)__ldg(C.dinv + Q) * s;
+}
+
+// the children of coarse cell Q (level C) on the dense level F get + v
+template <class T, int NDIM>
+__device__ __forceinline__ void lv_scatter(const BLevel& C, const BLevel& F, T* zF, int64_t Q, T v) {
+    int64_t I, J, K;
+    lv_ijk(C, Q, I, J, K);
+#pragma unroll
+    for (int c = 0; c < (NDIM == 3 ? 2 : 1); ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const int64_t i = 2 * I + a, j = 2 * J + b, k = 2 * K + c;
+                if (i < F.nx && j < F.ny && k < F.nz) {
+                    T* p = zF + (k * F.ny + j) * F.nx + i;
+                    *p = __ldcg(p) + v;
+                }
+            }
+}
+
+// omega / D of a fine cell from its face bits (0 for an isolated cell)
+template <class T>
+__device__ __forceinline__ T fine_wd(const BInst& I, unsigned fm, T omega) {
+    const T d = (T)I.F[0] * (T)((fm & 1u) + ((fm >> 1) & 1u)) + (T)I.F[1] * (T)(((fm >> 2) & 1u) + ((fm >> 3) & 1u)) +
+                (T)I.F[2] * (T)(((fm >> 4) & 1u) + ((fm >> 5) & 1u));
+    return d > T(0) ? omega / d : T(0);
+}
+
+// r - L z at fine cell f (0 at a missing cell); every load issued at once,
+// offsets that leave the box clamped to the cell (their face bits are 0)
+template <class T, int NDIM>
+__device__ __forceinline__ T fine_resid(const BInst& I, const T* r, const T* z, int64_t f) {
+    const unsigned cw = I.code8[f];
+    const int64_t nb = I.n_box;
+    const T zc = __ldcg(z + f), rc = __ldcg(r + f);
+    const T ze = __ldcg(z + (f + 1 < nb ? f + 1 : f)), zw = __ldcg(z + (f >= 1 ? f - 1 : f));
+    const T zn = __ldcg(z + (f + I.px < nb ? f + I.px : f)), zs = __ldcg(z + (f >= I.px ? f - I.px : f));
+    const T Fx = (T)I.F[0], Fy = (T)I.F[1];
+    T lz = T(0);
+    if (cw & 1u) lz += Fx * (zc - ze);
+    if (cw & 2u) lz += Fx * (zc - zw);
+    if (cw & 4u) lz += Fy * (zc - zn);
+    if (cw & 8u) lz += Fy * (zc - zs);
+    if (NDIM == 3) {
+        const T zf = __ldcg(z + (f + I.plane < nb ? f + I.plane : f));
+        const T zb = __ldcg(z + (f >= I.plane ? f - I.plane : f));
+        const T Fz = (T)I.F[2];
+        if (cw & 16u) lz += Fz * (zc - zf);
+        if (cw & 32u) lz += Fz * (zc - zb);
+    }
+    return (cw & 0x80u) ? rc - lz : T(0);
+}
+
+// level-1 cell Q of the instance: the restriction of the fine residual
+template <class T, int NDIM>
+__device__ __forceinline__ void fine_restrict(const BInst& I, const T* r, const T* z, const BLevel& C, T* rC, T* zC,
+                                              int64_t Q, T omega) {
+    int64_t X, Y, Z;
+    lv_ijk(C, Q, X, Y, Z);
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < (NDIM == 3 ? 2 : 1); ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const int64_t i = 2 * X + a, j = 2 * Y + b, k = 2 * Z + c;
+                if (i < I.nx && j < I.ny && k < I.nz) s += fine_resid<T, NDIM>(I, r, z, (k * I.ny + j) * I.px + i);
+            }
+    rC[Q] = s;
+    zC[Q] = omega * (T)__ldg(C.dinv + Q) * s;
+}
+
+// the fine children of level-1 cell Q get + v
+template <class T, int NDIM>
+__device__ __forceinline__ void fine_scatter(const BInst& I, const BLevel& C, T* z, int64_t Q, T v) {
+    int64_t X, Y, Z;
+    lv_ijk(C, Q, X, Y, Z);
+#pragma unroll
+    for (int c = 0; c < (NDIM == 3 ? 2 : 1); ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const int64_t i = 2 * X + a, j = 2 * Y + b, k = 2 * Z + c;
+                if (i < I.nx && j < I.ny && k < I.nz) {
+                    T* p = z + (k * I.ny + j) * I.px + i;
+                    *p = __ldcg(p) + v;
+                }
+            }
+}
+
+
+// One fine-level Jacobi sweep of every running instance, zin -> zout (0 at
+// missing and isolated cells).  DOT: the last sweep of the V-cycle; it forms
+// (r, z) per instance, and the block that completes an instance's last tile
+// sets beta and rho (the segment's first (r, z) gives beta = 0, or the ratio
+// to the previous segment's last one when the old direction is kept).
+template <class T, int NDIM, bool DOT>
+__device__ void mg_fine_pass(const BParams& P, const T* zin_all, T* zout_all) {
+    const int lane = threadIdx.x & 31;
+    const T om = (T)P.omega;
+    for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x) {
+        const BTile tl = P.tiles[t];
+        const BInst I = P.inst[tl.inst];
+        BState* S = &P.st[tl.inst];
+        if (__ldcg(&S->status) != kRun) continue;
+        const T* zin = zin_all + I.off;
+        T* zout = zout_all + I.off;
+        const T* r = (const T*)P.r + I.off;
+        const Geo<T> g = inst_geo<T>(I);
+        double acc[1] = {0.0};
+        for (int j = 0; j < P.cpt; ++j) {
+            const int cc = j * kTileThreads + threadIdx.x;
+            const bool act = cc < tl.nchunks;
+            const int64_t i0 = (tl.chunk0 + cc) * 4;
+            const uint32_t cw = act ? *reinterpret_cast<const uint32_t*>(I.code8 + i0) : 0u;
+            const V4<T> c = act ? ld4cg(zin + i0) : zero4<T>();
+            auto f4 = [&](int64_t off) { return ld4cg(zin + i0 + off); };
+            auto f1 = [&](int64_t off) { return __ldcg(zin + i0 + off); };
+            const Nbrs<T> nb = gather_clamped<T, NDIM>(c, i0, I.n_box, lane, g.px, g.plane, act, f4, f1);
+            if (act) {
+                const V4<T> rv = ld4cg(r + i0);
+                V4<T> o;
+                T part = T(0);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const unsigned fm = face_bits8(cw, m);
+                    const T w = valid8(cw, m) ? fine_wd<T>(I, fm, om) : T(0);
+                    o.v[m] = w != T(0) ? c.v[m] + w * (rv.v[m] - apply_L<T, NDIM>(fm, c, nb, m, g.F)) : T(0);
+                    part += rv.v[m] * o.v[m];
+                }
+                st4(zout + i0, o);
+                acc[0] += (double)part;
+            }
+        }
+        if (DOT) {
+            double tot[1];
+            if (tile_done<1>(P, t, I, S, TK_M, acc, tot) && threadIdx.x == 0) {
+                const double rz = tot[0];
+                if (__ldcg(&S->pend)) {
+                    S->beta = __ldcg(&S->keep) ? rz / __ldcg(&S->rho) : 0.0;
+                    S->pend = 0;
+                } else {
+                    S->beta = rz / __ldcg(&S->rho);
+                }
+                S->rho = rz;
+                if (!(rz > 0.0) || !isfinite(rz)) {  // B r = 0 with r != 0: stop the segment
+                    S->breakdown = 1;
+                    S->status = kConv;
+                }
+            }
+        }
+    }
+}
+
+// the coarse levels G .. nlv of one instance inside this block; ends by
+// adding the scaled correction to level G - 1's pre-smoothed z
+template <class T, int NDIM>
+__device__ void mg_bottom(const BParams& P, const BInst& I) {
+    T* const cr = (T*)P.cr;
+    T* const ca = (T*)P.ca;
+    T* const cb = (T*)P.cb;
+    const T om = (T)P.omega, sc = (T)P.scale;
+    const int nu = P.nu, pre = mg_pre(nu);
+    auto buf = [&](const BLevel& L, int b) { return (b ? cb : ca) + L.off; };
+    for (int l = I.G; l < I.nlv; ++l) {
+        const BLevel& L = P.lv[I.lv0 + l - 1];
+        for (int s = 1; s < nu; ++s) {
+            const T* zi = buf(L, (s - 1) & 1);
+            T* zo = buf(L, s & 1);
+            for (int64_t q = threadIdx.x; q < L.n; q += blockDim.x) zo[q] = lv_sweep<T, NDIM>(L, cr + L.off, zi, q, om);
+            __syncthreads();
+        }
+        const BLevel& C = P.lv[I.lv0 + l];
+        for (int64_t Q = threadIdx.x; Q < C.n; Q += blockDim.x)
+            lv_restrict<T, NDIM>(L, cr + L.off, buf(L, pre), C, cr + C.off, buf(C, 0), Q, om);
+        __syncthreads();
+    }
+    {  // the coarsest level: z = omega D^-1 r is in buffer a; more sweeps
+        const BLevel& L = P.lv[I.lv0 + I.nlv - 1];
+        for (int it = 1; it < P.coarse_sweeps; ++it) {
+            const T* zi = buf(L, (it - 1) & 1);
+            T* zo = buf(L, it & 1);
+            for (int64_t q = threadIdx.x; q < L.n; q += blockDim.x) zo[q] = lv_sweep<T, NDIM>(L, cr + L.off, zi, q, om);
+            __syncthreads();
+        }
+    }
+    int fin = (P.coarse_sweeps - 1) & 1;  // the buffer holding the coarser level's z
+    for (int l = I.nlv - 1; l >= I.G; --l) {
+        const BLevel& L = P.lv[I.lv0 + l - 1];
+        const BLevel& C = P.lv[I.lv0 + l];
+        const T* zc = buf(C, fin);
+        for (int64_t Q = threadIdx.x; Q < C.n; Q += blockDim.x) lv_scatter<T, NDIM>(C, L, buf(L, pre), Q, sc * __ldcg(zc + Q));
+        __syncthreads();
+        for (int s = 0; s < nu; ++s) {
+            const T* zi = buf(L, (pre + s) & 1);
+            T* zo = buf(L, (pre + s + 1) & 1);
+            for (int64_t q = threadIdx.x; q < L.n; q += blockDim.x) zo[q] = lv_sweep<T, NDIM>(L, cr + L.off, zi, q, om);
+            __syncthreads();
+        }
+        fin = (pre + nu) & 1;
+    }
+    // level G's correction into level G - 1 (a grid-wide level; the grid
+    // barrier after this phase orders it before that level's sweeps)
+    const BLevel& C = P.lv[I.lv0 + I.G - 1];
+    const T* zc = buf(C, fin);
+    if (I.G == 1) {
+        T* zf = (T*)(pre ? P.zB : P.zA) + I.off;
+        for (int64_t Q = threadIdx.x; Q < C.n; Q += blockDim.x) fine_scatter<T, NDIM>(I, C, zf, Q, sc * __ldcg(zc + Q));
+    } else {
+        const BLevel& L = P.lv[I.lv0 + I.G - 2];
+        for (int64_t Q = threadIdx.x; Q < C.n; Q += blockDim.x) lv_scatter<T, NDIM>(C, L, buf(L, pre), Q, sc * __ldcg(zc + Q));
+    }
+}
+
+// One V-cycle z = B r for every running instance (r in P.r; z ends in P.zB).
+// The first sweep, z = omega D^-1 r in P.zA, was done by the pass that wrote r.
+template <class T, int NDIM>
+__device__ bool mg_vcycle(const BParams& P) {
+    T* const zA = (T*)P.zA;
+    T* const zB = (T*)P.zB;
+    T* const cr = (T*)P.cr;
+    T* const ca = (T*)P.ca;
+    T* const cb = (T*)P.cb;
+    const T om = (T)P.omega, sc = (T)P.scale;
+    const int nu = P.nu, pre = mg_pre(nu);
+    auto cbuf = [&](const BLevel& L, int b) { return (b ? cb : ca) + L.off; };
+    // the level-l tiles of running instances with cond(G) (l >= 1)
+    auto coarse_pass = [&](int l, auto cond, auto op) {
+        for (int t = blockIdx.x; t < P.nct[l]; t += gridDim.x) {
+            const BCTile tl = P.ct[P.ct0[l] + t];
+            const BInst& I = P.inst[tl.inst];
+            if (!cond(I.G) || __ldcg(&P.st[tl.inst].status) != kRun) continue;
+            const BLevel& L = P.lv[I.lv0 + l - 1];
+            for (int c = threadIdx.x; c < tl.ncells; c += blockDim.x) op(I, L, tl.cell0 + c);
+        }
+    };
+    // ---- down: the fine level's pre-sweeps, its residual restricted to level 1
+    for (int s = 1; s < nu; ++s) {
+        mg_fine_pass<T, NDIM, false>(P, (s & 1) ? zA : zB, (s & 1) ? zB : zA);
+        if (!grid_barrier(P.gl, P.spin_limit)) return false;
+    }
+    coarse_pass(1, [](int G) { return G >= 1; }, [&](const BInst& I, const BLevel& C, int64_t Q) {
+        fine_restrict<T, NDIM>(I, (const T*)P.r + I.off, (pre ? zB : zA) + I.off, C, cr + C.off, cbuf(C, 0), Q, om);
+    });
+    if (!grid_barrier(P.gl, P.spin_limit)) return false;
+    for (int l = 1; l < P.gmax; ++l) {
+        for (int s = 1; s < nu; ++s) {
+            coarse_pass(l, [l](int G) { return l < G; }, [&](const BInst& I, const BLevel& L, int64_t q) {
+                cbuf(L, s & 1)[q] = lv_sweep<T, NDIM>(L, cr + L.off, cbuf(L, (s - 1) & 1), q, om);
+            });
+            if (!grid_barrier(P.gl, P.spin_limit)) return false;
+        }
+        coarse_pass(l + 1, [l](int G) { return l < G; }, [&](const BInst& I, const BLevel& C, int64_t Q) {
+            const BLevel& L = P.lv[I.lv0 + l - 1];
+            lv_restrict<T, NDIM>(L, cr + L.off, cbuf(L, pre), C, cr + C.off, cbuf(C, 0), Q, om);
+        });
+        if (!grid_barrier(P.gl, P.spin_limit)) return false;
+    }
+    // ---- the small levels, one block per instance
+    for (int i = blockIdx.x; i < P.count; i += gridDim.x) {
+        const BInst& I = P.inst[i];
+        if (I.G >= 1 && __ldcg(&P.st[i].status) == kRun) mg_bottom<T, NDIM>(P, I);
+    }
+    if (!grid_barrier(P.gl, P.spin_limit)) return false;
+    // ---- up: the post-sweeps of every grid-wide level; the last one adds the
+    // scaled correction to the finer level's pre-smoothed z
+    for (int l = P.gmax - 1; l >= 1; --l) {
+        for (int s = 0; s < nu; ++s) {
+            const bool last = s == nu - 1;
+            coarse_pass(l, [l](int G) { return l < G; }, [&](const BInst& I, const BLevel& L, int64_t q) {
+                const T v = lv_sweep<T, NDIM>(L, cr + L.off, cbuf(L, (pre + s) & 1), q, om);
+                cbuf(L, (pre + s + 1) & 1)[q] = v;
+                if (last) {
+                    if (l == 1) {
+                        fine_scatter<T, NDIM>(I, L, (pre ? zB : zA) + I.off, q, sc * v);
+                    } else {
+                        const BLevel& F = P.lv[I.lv0 + l - 2];
+                        lv_scatter<T, NDIM>(L, F, cbuf(F, pre), q, sc * v);
+                    }
+                }
+            });
+            if (!grid_barrier(P.gl, P.spin_limit)) return false;
+        }
+    }
+    for (int s = 0; s < nu; ++s) {
+        T* zi = ((pre + s) & 1) ? zB : zA;
+        T* zo = ((pre + s + 1) & 1) ? zB : zA;
+        if (s == nu - 1)
+            mg_fine_pass<T, NDIM, true>(P, zi, zo);
+        else
+            mg_fine_pass<T, NDIM, false>(P, zi, zo);
+        if (!grid_barrier(P.gl, P.spin_limit)) return false;
+    }
+    return true;
 }
 
 // ---- the persistent kernel ----
@@ -338,6 +748,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_batched(BParams P) {
             if (__ldcg(&S->status) != kInit) continue;
             T* rr = r_all + I.off;
             T* xx = x_all + I.off;
+            T* z0 = (T*)P.zA + I.off;
             const double mean1 = I.label ? 0.0 : __ldcg(&S->rsum) / I.n_valid;
             double acc[1] = {0.0};
             for (int j = 0; j < P.cpt; ++j) {
@@ -363,6 +774,13 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_batched(BParams P) {
                 }
                 st4(rr + i0, rv);
                 st4(xx + i0, zero4<T>());
+                if (P.mg) {  // the V-cycle's first sweep: z = omega D^-1 r
+                    V4<T> zv;
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        zv.v[m] = valid8(cw, m) ? fine_wd<T>(I, face_bits8(cw, m), (T)P.omega) * rv.v[m] : T(0);
+                    st4(z0 + i0, zv);
+                }
                 acc[0] += (double)part;
             }
             double tot[1];
@@ -376,13 +794,22 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_batched(BParams P) {
                     }
                 if (threadIdx.x == 0) {
                     const double rho0 = tot[0];
-                    const bool keep = __ldcg(&S->cont) && __ldcg(&S->breakdown) == 0 && __ldcg(&S->rho_k) > 0.0;
                     const double bn = sqrt(__ldcg(&S->bnorm2));
                     const double stop_abs = 0.5 * P.tol * bn;
-                    S->beta = keep ? rho0 / __ldcg(&S->rho_k) : 0.0;
-                    S->first = keep ? 0 : 1;
+                    if (P.mg) {
+                        // rho = (r, z) and beta come with the segment's first V-cycle;
+                        // rho still holds the previous segment's last (r, z)
+                        const bool keep = __ldcg(&S->cont) && __ldcg(&S->breakdown) == 0 && __ldcg(&S->rho) > 0.0;
+                        S->first = keep ? 0 : 1;
+                        S->keep = keep ? 1 : 0;
+                        S->pend = 1;
+                    } else {
+                        const bool keep = __ldcg(&S->cont) && __ldcg(&S->breakdown) == 0 && __ldcg(&S->rho_k) > 0.0;
+                        S->beta = keep ? rho0 / __ldcg(&S->rho_k) : 0.0;
+                        S->first = keep ? 0 : 1;
+                        S->rho = rho0;
+                    }
                     S->alpha = 0.0;
-                    S->rho = rho0;
                     S->rho0 = rho0;
                     S->stop2 = fmax(P.inner_tol * P.inner_tol * rho0, stop_abs * stop_abs);
                     S->seg_it = 0;
@@ -401,7 +828,11 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_batched(BParams P) {
 
         // --- a CG segment: phases A and B until no instance is live
         while (snap_of(P.gl, 0) > 0) {
-            // phase A: p = r + beta p_old, q = L p, x += alpha_prev p_old, p.q
+            // multigrid: z = B r for the running instances (their r and the first
+            // sweep were written by phase I or B)
+            if (P.mg && !mg_vcycle<T, NDIM>(P)) return;
+            // phase A: p = r + beta p_old (multigrid: z + beta p_old), q = L p,
+            // x += alpha_prev p_old, p.q
             for (int t = blockIdx.x; t < P.ntiles; t += gridDim.x) {
                 const BTile tl = P.tiles[t];
                 const BInst I = P.inst[tl.inst];
@@ -412,7 +843,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_batched(BParams P) {
                 const bool first = __ldcg(&S->first) != 0;
                 const T alpha = (T)__ldcg(&S->alpha), beta = (T)__ldcg(&S->beta);
                 const int par = __ldcg(&S->par);
-                const T* r = r_all + I.off;
+                const T* r = (P.mg ? (const T*)P.zB : r_all) + I.off;
                 const T* po = (par ? pB_all : pA_all) + I.off;
                 T* pn = (par ? pA_all : pB_all) + I.off;
                 T* q = q_all + I.off;
@@ -496,6 +927,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_batched(BParams P) {
                 const T alpha = (T)__ldcg(&S->alpha);
                 T* r = r_all + I.off;
                 const T* q = q_all + I.off;
+                T* z0 = (T*)P.zA + I.off;
                 double acc[1] = {0.0};
                 for (int j = 0; j < P.cpt; ++j) {
                     const int cc = j * kTileThreads + threadIdx.x;
@@ -510,14 +942,24 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_batched(BParams P) {
                         part += rv.v[m] * rv.v[m];
                     }
                     st4(r + i0, rv);
+                    if (P.mg) {  // the next V-cycle's first sweep
+                        const uint32_t cw = *reinterpret_cast<const uint32_t*>(I.code8 + i0);
+                        V4<T> zv;
+#pragma unroll
+                        for (int m = 0; m < 4; ++m)
+                            zv.v[m] = valid8(cw, m) ? fine_wd<T>(I, face_bits8(cw, m), (T)P.omega) * rv.v[m] : T(0);
+                        st4(z0 + i0, zv);
+                    }
                     acc[0] += (double)part;
                 }
                 double tot[1];
                 if (tile_done<1>(P, t, I, S, TK_B, acc, tot) && threadIdx.x == 0) {
-                    const double rho_new = tot[0];
-                    S->rho_k = __ldcg(&S->rho);
-                    S->beta = rho_new / __ldcg(&S->rho);
-                    S->rho = rho_new;
+                    const double rho_new = tot[0];  // |r|^2 (multigrid: rho is (r, z), set by the V-cycle)
+                    if (!P.mg) {
+                        S->rho_k = __ldcg(&S->rho);
+                        S->beta = rho_new / __ldcg(&S->rho);
+                        S->rho = rho_new;
+                    }
                     S->it = __ldcg(&S->it) + 1;
                     S->seg_it = __ldcg(&S->seg_it) + 1;
                     if (!(rho_new > __ldcg(&S->stop2)) || __ldcg(&S->it) >= P.max_iter || __ldcg(&S->seg_it) >= P.inner_max || !isfinite(rho_new))
@@ -588,7 +1030,76 @@ struct Layout {
     size_t bytes = 0;
     // offsets in the workspace
     size_t o_inst, o_tiles, o_st, o_gl, o_part, o_comp, o_b64, o_pa, o_pb, o_r, o_x, o_q, o_pA, o_pB;
+    // multigrid (every plan built with the preconditioner)
+    bool mg = false;
+    int gmax = 0;
+    std::vector<BLevel> lv;
+    std::vector<BCTile> ct;
+    int ct0[kMaxGrid + 1] = {}, nct[kMaxGrid + 1] = {};
+    int64_t carena = 0;  // coarse cells
+    size_t o_lv = 0, o_ct = 0, o_za = 0, o_zb = 0, o_cr = 0, o_ca = 0, o_cb = 0;
 };
+
+// the batch runs the multigrid V-cycle when every plan was built with the
+// preconditioner (instances too small for a hierarchy then get the fine
+// sweeps alone)
+static bool batch_mg(int count, const osmodi_plan* plans) {
+    for (int i = 0; i < count; ++i)
+        if (plans[i]->opt.precond != 1) return false;
+    return true;
+}
+
+// the instances' coarse levels, the grid-wide / in-block split and the
+// coarse tiles
+static void build_mg_layout(int count, const osmodi_plan* plans, Layout* L) {
+    L->lv.clear();
+    L->ct.clear();
+    L->gmax = 0;
+    int64_t coff = 0;
+    for (int i = 0; i < count; ++i) {
+        BInst& I = L->inst[i];
+        I.lv0 = (int)L->lv.size();
+        I.nlv = mg_levels(plans[i]);
+        I.G = 0;
+        for (int l = 1; l <= I.nlv; ++l) {
+            MgLevelView v{};
+            mg_level_view(plans[i], l, &v);
+            BLevel b;
+            b.nx = v.nx;
+            b.ny = v.ny;
+            b.nz = v.nz;
+            b.n = v.n;
+            b.off = coff;
+            b.wx = v.wx;
+            b.wy = v.wy;
+            b.wz = v.wz;
+            b.dinv = v.dinv;
+            L->lv.push_back(b);
+            coff += (v.n + 31) / 32 * 32;
+            if (I.G == 0 && v.n <= kBottomCells) I.G = l;
+        }
+        if (I.nlv > 0 && I.G == 0) I.G = I.nlv;
+        I.G = std::min(I.G, kMaxGrid - 1);
+        L->gmax = std::max(L->gmax, I.G);
+    }
+    L->carena = coff;
+    for (int l = 1; l <= L->gmax; ++l) {
+        L->ct0[l] = (int)L->ct.size();
+        for (int i = 0; i < count; ++i) {
+            const BInst& I = L->inst[i];
+            if (I.G < l) continue;
+            const int64_t n = L->lv[I.lv0 + l - 1].n;
+            for (int64_t c = 0; c < n; c += kCTile) {
+                BCTile t;
+                t.inst = i;
+                t.cell0 = c;
+                t.ncells = (int)std::min<int64_t>(kCTile, n - c);
+                L->ct.push_back(t);
+            }
+        }
+        L->nct[l] = (int)L->ct.size() - L->ct0[l];
+    }
+}
 
 static bool build_layout(int count, const osmodi_plan* plans, size_t tsize, int cpt, Layout* L) {
     L->inst.resize(count);
@@ -633,6 +1144,8 @@ static bool build_layout(int count, const osmodi_plan* plans, size_t tsize, int 
     }
     L->arena = off;
     L->total_comp = std::max(1, comp);
+    L->mg = batch_mg(count, plans);
+    if (L->mg) build_mg_layout(count, plans, L);
     Workspace w;
     w.base = nullptr;
     L->o_inst = w.off; w.take<BInst>(count);
@@ -650,6 +1163,16 @@ static bool build_layout(int count, const osmodi_plan* plans, size_t tsize, int 
     L->o_q = w.off; w.off += vbytes;
     L->o_pA = w.off; w.off += vbytes;
     L->o_pB = w.off; w.off += vbytes;
+    if (L->mg) {
+        L->o_lv = w.off; w.take<BLevel>(std::max<size_t>(1, L->lv.size()));
+        L->o_ct = w.off; w.take<BCTile>(std::max<size_t>(1, L->ct.size()));
+        L->o_za = w.off; w.off += vbytes;
+        L->o_zb = w.off; w.off += vbytes;
+        const size_t cbytes = ((size_t)std::max<int64_t>(1, L->carena) * tsize + 255) & ~size_t(255);
+        L->o_cr = w.off; w.off += cbytes;
+        L->o_ca = w.off; w.off += cbytes;
+        L->o_cb = w.off; w.off += cbytes;
+    }
     L->bytes = w.off;
     return true;
 }
@@ -725,8 +1248,28 @@ static osmodi_status prepare_batched(int count, const osmodi_plan* plans, const 
     const long long spins = debug_knob(OSMODI_DEBUG_BARRIER_SPINS);
     P->spin_limit = spins > 0 ? spins : (1LL << 25);
     P->skip_block = (int)debug_knob(OSMODI_DEBUG_SKIP_BARRIER_BLOCK);
+    P->mg = L->mg ? 1 : 0;
+    if (L->mg) {
+        mg_jacobi_params(plans[0], &P->omega, &P->scale, &P->nu, &P->coarse_sweeps);
+        P->gmax = L->gmax;
+        P->lv = (const BLevel*)(base + L->o_lv);
+        P->ct = (const BCTile*)(base + L->o_ct);
+        for (int l = 0; l <= kMaxGrid; ++l) {
+            P->ct0[l] = L->ct0[l];
+            P->nct[l] = L->nct[l];
+        }
+        P->zA = base + L->o_za;
+        P->zB = base + L->o_zb;
+        P->cr = base + L->o_cr;
+        P->ca = base + L->o_ca;
+        P->cb = base + L->o_cb;
+    }
     OSM_CUDA(cudaMemcpyAsync((void*)P->inst, L->inst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, s));
     OSM_CUDA(cudaMemcpyAsync((void*)P->tiles, L->tiles.data(), sizeof(BTile) * L->tiles.size(), cudaMemcpyHostToDevice, s));
+    if (L->mg && !L->lv.empty())
+        OSM_CUDA(cudaMemcpyAsync((void*)P->lv, L->lv.data(), sizeof(BLevel) * L->lv.size(), cudaMemcpyHostToDevice, s));
+    if (L->mg && !L->ct.empty())
+        OSM_CUDA(cudaMemcpyAsync((void*)P->ct, L->ct.data(), sizeof(BCTile) * L->ct.size(), cudaMemcpyHostToDevice, s));
     return OSMODI_OK;
 }
 
@@ -816,6 +1359,8 @@ struct GraphBatch {
     BGlobal* h_gl = nullptr;
     BInst* h_inst = nullptr;  // page-locked tables the graph uploads on every replay
     BTile* h_tiles = nullptr;
+    BLevel* h_lv = nullptr;
+    BCTile* h_ct = nullptr;
     std::vector<double> n_valid;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool launched = false;
@@ -829,6 +1374,8 @@ static void free_graph(GraphBatch* g) {
     if (g->h_gl) cudaFreeHost(g->h_gl);
     if (g->h_inst) cudaFreeHost(g->h_inst);
     if (g->h_tiles) cudaFreeHost(g->h_tiles);
+    if (g->h_lv) cudaFreeHost(g->h_lv);
+    if (g->h_ct) cudaFreeHost(g->h_ct);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     delete g;
@@ -853,6 +1400,15 @@ static osmodi_status capture_batched(int count, const osmodi_plan* plans, const 
     std::memcpy(g->h_inst, L.inst.data(), sizeof(BInst) * count);
     std::memcpy(g->h_tiles, L.tiles.data(), sizeof(BTile) * L.tiles.size());
     const size_t n_tiles = L.tiles.size();
+    const size_t n_lv = L.mg ? L.lv.size() : 0, n_ct = L.mg ? L.ct.size() : 0;
+    if (n_lv) {
+        OSM_CUDA(cudaMallocHost((void**)&g->h_lv, sizeof(BLevel) * n_lv));
+        std::memcpy(g->h_lv, L.lv.data(), sizeof(BLevel) * n_lv);
+    }
+    if (n_ct) {
+        OSM_CUDA(cudaMallocHost((void**)&g->h_ct, sizeof(BCTile) * n_ct));
+        std::memcpy(g->h_ct, L.ct.data(), sizeof(BCTile) * n_ct);
+    }
     // the legacy default stream cannot be captured: capture on a private one
     cudaStream_t cs = nullptr;
     OSM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -867,6 +1423,10 @@ static osmodi_status capture_batched(int count, const osmodi_plan* plans, const 
     e = cudaMemcpyAsync((void*)P.inst, g->h_inst, sizeof(BInst) * count, cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync((void*)P.tiles, g->h_tiles, sizeof(BTile) * n_tiles, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && n_lv)
+        e = cudaMemcpyAsync((void*)P.lv, g->h_lv, sizeof(BLevel) * n_lv, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && n_ct)
+        e = cudaMemcpyAsync((void*)P.ct, g->h_ct, sizeof(BCTile) * n_ct, cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) {
         set_cuda_error(e, "cudaMemcpyAsync(batched tables, captured)");
         rc = OSMODI_E_CUDA;

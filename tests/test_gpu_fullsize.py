@@ -99,12 +99,14 @@ def test_blobs_500_full_residual_and_crop(osm):
 PIV_SAMPLE = list(range(0, 512, 16))  # 32 of the 512 snapshots, spread over the workload
 
 
-def test_piv_batch_full_size_instances(osm):
+@pytest.mark.parametrize("precond", [0, 1])
+def test_piv_batch_full_size_instances(osm, precond):
     """32 instances of the 512-snapshot PIV workload (every 16th), at full
-    size, through the batched persistent solve (tolerance 1e-11), each
-    against the oracle's FP64 solve."""
+    size, through the batched persistent solve (tolerance 1e-11; plain CG,
+    or the multigrid V-cycle inside the launch), each against the oracle's
+    FP64 solve."""
     probs = [inputs.piv_snapshot_2d(i) for i in PIV_SAMPLE]
-    plans = [osm.Plan(2, pr.dims, pr.spacing, pr.mask.cuda()) for pr in probs]
+    plans = [osm.Plan(2, pr.dims, pr.spacing, pr.mask.cuda(), precond=precond) for pr in probs]
     grads = [pr.grad.cuda() for pr in probs]
     ps = [torch.zeros(pr.mask.shape, dtype=torch.float64, device="cuda") for pr in probs]
     st, res = osm.Batch(plans).solve(grads, ps, 1e-11)
@@ -115,6 +117,8 @@ def test_piv_batch_full_size_instances(osm):
         want, it, e = oracle.solve_cg(grid, pr.grad.double().numpy(), tol=1e-14, maxit=40000)
         assert _rel(p.cpu().numpy(), want, valid) <= 1e-9
         assert r.eps_R <= 1e-11
+        if precond:
+            assert r.inner_iters < 200
 
 
 def test_piv_full_size_instances_multigrid_streams(osm):

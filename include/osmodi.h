@@ -570,18 +570,24 @@ OSMODI_API osmodi_status osmodi_probe_fp64(double* gflops_out, double* ms_out, v
  *   the same arithmetic in each case, for comparisons: 0 (default) fused
  *   one-pass red-black sweeps (every level with packed counts); 1
  *   one-colour half-sweeps in place (two passes per sweep); 2 as 0 with the
- *   fine level's input planes staged by TMA (FP32 plans).
+ *   fine level's input planes staged by TMA (FP32 plans); 3 as 0 with the
+ *   fine sweeps' HBM operands loaded one plane ahead.
  * OSMODI_DEBUG_NET_WMMA: which kernels run the seed network's
  *   convolutions, the same products in each case, for comparisons: 0
  *   (default) tcgen05, the forward 3x3x3 layers with their input tile staged
  *   once; 1 the warp-level (wmma) tensor-core path; 2 tcgen05, every layer by
  *   the gathering kernel.
+ * OSMODI_DEBUG_BATCH_BOTTOM_CELLS: the batched solve's multigrid runs the
+ *   coarse levels of at most this many cells (and the ones below them)
+ *   inside one block per instance, the larger ones as grid-wide passes; the
+ *   same V-cycle either way.  Default (0): 4096.
  */
 #define OSMODI_DEBUG_BARRIER_SPINS 1
 #define OSMODI_DEBUG_SKIP_BARRIER_BLOCK 2
 #define OSMODI_DEBUG_CORRECTION_SCALE 3
 #define OSMODI_DEBUG_MG_UNFUSED 4
 #define OSMODI_DEBUG_NET_WMMA 5
+#define OSMODI_DEBUG_BATCH_BOTTOM_CELLS 6
 #define OSMODI_DEBUG_DEFAULT (-0x7fffffffffffffffLL)
 OSMODI_API long long osmodi_debug_set(int knob, long long value);
 

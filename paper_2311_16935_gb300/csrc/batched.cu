@@ -3,7 +3,9 @@
 //
 // The kernel runs the whole solve of osmodi_solve for every instance at once:
 // source, FP64 residual / refinement rounds, constant removal, FP32 (or FP64)
-// conjugate-gradient segments with reliable updates, gauge and output.  Work
+// conjugate-gradient segments with reliable updates -- preconditioned by one
+// multigrid V-cycle per iteration when the plans were built with the
+// preconditioner -- gauge and output.  Work
 // is a list of tiles (a block of 256 threads takes one tile of up to 256
 // chunks = 1024 cells; every tile lies inside one instance).  Phases are
 // separated by a grid barrier; the per-instance scalars (alpha, beta, rho,
@@ -797,11 +799,12 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_batched(BParams P) {
                     const double bn = sqrt(__ldcg(&S->bnorm2));
                     const double stop_abs = 0.5 * P.tol * bn;
                     if (P.mg) {
-                        // rho = (r, z) and beta come with the segment's first V-cycle;
-                        // rho still holds the previous segment's last (r, z)
-                        const bool keep = __ldcg(&S->cont) && __ldcg(&S->breakdown) == 0 && __ldcg(&S->rho) > 0.0;
-                        S->first = keep ? 0 : 1;
-                        S->keep = keep ? 1 : 0;
+                        // rho = (r, z) comes with the segment's first V-cycle.  The
+                        // preconditioned segment restarts (p = z): keeping the previous
+                        // direction with beta = (r, z) / rho_old after the residual
+                        // replacement stalled some instances for hundreds of iterations
+                        S->first = 1;
+                        S->keep = 0;
                         S->pend = 1;
                     } else {
                         const bool keep = __ldcg(&S->cont) && __ldcg(&S->breakdown) == 0 && __ldcg(&S->rho_k) > 0.0;
@@ -1055,6 +1058,8 @@ static void build_mg_layout(int count, const osmodi_plan* plans, Layout* L) {
     L->lv.clear();
     L->ct.clear();
     L->gmax = 0;
+    const long long knob = debug_knob(OSMODI_DEBUG_BATCH_BOTTOM_CELLS);
+    const int64_t bottom = knob > 0 ? (int64_t)knob : kBottomCells;
     int64_t coff = 0;
     for (int i = 0; i < count; ++i) {
         BInst& I = L->inst[i];
@@ -1076,7 +1081,7 @@ static void build_mg_layout(int count, const osmodi_plan* plans, Layout* L) {
             b.dinv = v.dinv;
             L->lv.push_back(b);
             coff += (v.n + 31) / 32 * 32;
-            if (I.G == 0 && v.n <= kBottomCells) I.G = l;
+            if (I.G == 0 && v.n <= bottom) I.G = l;
         }
         if (I.nlv > 0 && I.G == 0) I.G = I.nlv;
         I.G = std::min(I.G, kMaxGrid - 1);

@@ -19,6 +19,7 @@
 // (PIV data is FP32); missing cells get f = 0.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "internal.cuh"
@@ -195,6 +196,167 @@ __global__ void __launch_bounds__(128) k_front_rans(FrontGeo g, const uint32_t* 
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// 3-D RANS source, z-marching.  A block owns a tile of kFX x kFY cells and a
+// slab of planes.  Per plane it stages the fields whose in-plane neighbours
+// the differences read -- U (3 components) and the stress planes xx, yy, xy,
+// xz, yz -- with a one-cell halo in shared memory; the values on the planes
+// above and below come from registers carried along z, and the next plane is
+// loaded one step ahead.  A cell then reads 9 values and its class word from
+// HBM (plus its share of the halo) instead of 46 neighbour loads.  The cells
+// two steps away (three-point one-sided differences at a boundary) are read
+// from global memory.
+// ---------------------------------------------------------------------------
+constexpr int kFX = 32, kFY = 8;
+constexpr int kFHX = kFX + 2, kFHY = kFY + 2, kFS = kFHX * kFHY;
+constexpr int kFF = 8;  // staged fields: U x, y, z; stress planes 0 (xx), 1 (yy), 3 (xy), 4 (xz), 5 (yz)
+constexpr int kFRing = 2 * (kFHX + kFHY) - 4;  // halo cells of one plane (88)
+
+__device__ __forceinline__ int fslot(int pl) { return pl < 2 ? 3 + pl : 2 + pl; }  // stress plane -> staged field
+
+struct RansTile {
+    int tiles_x, tiles_y, slab, n_slabs;
+};
+
+__global__ void __launch_bounds__(kFX * kFY) k_front_rans3_tiled(FrontGeo g, RansTile tg, const uint32_t* __restrict__ code32,
+                                                                 const float* __restrict__ U,
+                                                                 const float* __restrict__ R, float rho,
+                                                                 float* __restrict__ f) {
+    __shared__ float sm[kFF][kFS];
+    const int t = threadIdx.x, tx = t % kFX, ty = t / kFX;
+    const int b = blockIdx.x;
+    const int bx = b % tg.tiles_x, by = (b / tg.tiles_x) % tg.tiles_y, sl = b / (tg.tiles_x * tg.tiles_y);
+    const int64_t i = (int64_t)bx * kFX + tx, j = (int64_t)by * kFY + ty;
+    const bool inb = i < g.nx && j < g.ny;
+    const int k0 = sl * tg.slab, k1 = (int)(g.nz < (int64_t)k0 + tg.slab ? g.nz : (int64_t)k0 + tg.slab);
+    const int64_t pl = g.st[2], nd = g.n_dense;
+    const int64_t col = inb ? j * g.nx + i : 0;  // this cell's offset within a plane (clamped outside)
+    // the halo cell this thread stages (threads 0 .. kFRing - 1): its (x, y) in the tile frame
+    int hx = 0, hy = 0;
+    if (t < kFRing) {
+        if (t < kFHX) { hx = t; hy = 0; }
+        else if (t < 2 * kFHX) { hx = t - kFHX; hy = kFHY - 1; }
+        else { const int r = t - 2 * kFHX; hx = (r & 1) ? kFHX - 1 : 0; hy = 1 + (r >> 1); }
+    }
+    const int64_t gi = (int64_t)bx * kFX + hx - 1, gj = (int64_t)by * kFY + hy - 1;
+    const bool hin = t < kFRing && gi >= 0 && gi < g.nx && gj >= 0 && gj < g.ny;
+    const int64_t hcol = hin ? gj * g.nx + gi : 0;
+    // fields of this cell on a plane: U[0..2], R[0..5]
+    auto load9 = [&](int k, float (&v)[9]) {
+        if (inb && k >= 0 && k < g.nz) {
+            const int64_t c = (int64_t)k * pl + col;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) v[q] = __ldg(U + q * nd + c);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) v[3 + q] = __ldg(R + q * nd + c);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) v[q] = 0.f;
+        }
+    };
+    // the halo cell's staged fields on a plane
+    auto load_halo = [&](int k, float (&hv)[kFF]) {
+        if (hin && k < g.nz) {
+            const int64_t hi = (int64_t)k * pl + hcol;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) hv[q] = __ldg(U + q * nd + hi);
+            hv[3] = __ldg(R + 0 * nd + hi);
+            hv[4] = __ldg(R + 1 * nd + hi);
+            hv[5] = __ldg(R + 3 * nd + hi);
+            hv[6] = __ldg(R + 4 * nd + hi);
+            hv[7] = __ldg(R + 5 * nd + hi);
+        } else {
+#pragma unroll
+            for (int q = 0; q < kFF; ++q) hv[q] = 0.f;
+        }
+    };
+    auto load_code = [&](int k) -> uint32_t {
+        return inb && k < g.nz ? __ldg(code32 + ((int64_t)k * g.ny + j) * g.px + i) : 0u;
+    };
+    // Everything a step stages or reads from HBM was loaded one step earlier:
+    // the loads of a step are in flight while the previous plane is computed.
+    float vp[9], vc[9], vn[9];  // planes k - 1, k, k + 1
+    float hc[kFF];              // the halo cell on plane k
+    load9(k0 - 1, vp);
+    load9(k0, vc);
+    load9(k0 + 1, vn);
+    load_halo(k0, hc);
+    uint32_t w = load_code(k0);
+    const int s0 = (ty + 1) * kFHX + tx + 1;
+    for (int k = k0; k < k1; ++k) {
+        const int64_t c = (int64_t)k * pl + col;
+        float vq[9], hn[kFF];
+        load9(k + 2, vq);
+        load_halo(k + 1, hn);
+        const uint32_t wn = load_code(k + 1);
+        __syncthreads();  // the previous plane's readers are done
+#pragma unroll
+        for (int q = 0; q < 3; ++q) sm[q][s0] = vc[q];
+        sm[3][s0] = vc[3];
+        sm[4][s0] = vc[4];
+        sm[5][s0] = vc[6];
+        sm[6][s0] = vc[7];
+        sm[7][s0] = vc[8];
+        if (t < kFRing) {
+            const int hs = hy * kFHX + hx;
+#pragma unroll
+            for (int q = 0; q < kFF; ++q) sm[q][hs] = hc[q];
+        }
+        __syncthreads();
+        if (inb) {
+            if (!(w >> 31)) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) f[q * nd + c] = 0.f;
+            } else {
+                unsigned cp[3], cm[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    cp[a] = cls_of(w, 2 * a);
+                    cm[a] = cls_of(w, 2 * a + 1);
+                }
+                const int so[2] = {1, kFHX};  // in-plane neighbour offsets in the staged planes
+#pragma unroll
+                for (int ic = 0; ic < 3; ++ic) {
+                    const float* ui = U + ic * nd;
+                    auto qu = [&](int64_t idx) { return __ldg(ui + idx); };
+                    float acc = 0.f;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const int rp = splane<3>(ic, a);
+                        float up, um, rpv, rmv;
+                        if (a < 2) {
+                            up = sm[ic][s0 + so[a]];
+                            um = sm[ic][s0 - so[a]];
+                            rpv = sm[fslot(rp)][s0 + so[a]];
+                            rmv = sm[fslot(rp)][s0 - so[a]];
+                        } else {
+                            up = vn[ic];
+                            um = vp[ic];
+                            rpv = vn[3 + rp];
+                            rmv = vp[3 + rp];
+                        }
+                        acc += vc[a] * d1_pre(qu, c, g.st[a], g.inv_h[a], cp[a], cm[a], vc[ic], up, um);
+                        const float* rr = R + rp * nd;
+                        auto qr = [&](int64_t idx) { return __ldg(rr + idx); };
+                        acc += d1_pre(qr, c, g.st[a], g.inv_h[a], cp[a], cm[a], vc[3 + rp], rpv, rmv);
+                    }
+                    f[ic * nd + c] = -rho * acc;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            vp[q] = vc[q];
+            vc[q] = vn[q];
+            vn[q] = vq[q];
+        }
+#pragma unroll
+        for (int q = 0; q < kFF; ++q) hc[q] = hn[q];
+        w = wn;
+    }
+}
+
 struct CompConsts {
     float t_inf, c_adiab, inv_v2, inv_r;  // c_adiab = (gamma-1)/2 M_inf^2
 };
@@ -351,8 +513,32 @@ extern "C" osmodi_status osmodi_source_rans(osmodi_plan p, const float* u_mean, 
     unsigned blocks;
     if (!grid_of(g, &blocks)) return OSMODI_E_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
-    if (p->ndim == 2) k_front_rans<2><<<blocks, 128, 0, s>>>(g, p->code32, u_mean, stress, (float)rho, grad);
-    else k_front_rans<3><<<blocks, 128, 0, s>>>(g, p->code32, u_mean, stress, (float)rho, grad);
+    if (p->ndim == 2) {
+        k_front_rans<2><<<blocks, 128, 0, s>>>(g, p->code32, u_mean, stress, (float)rho, grad);
+    } else {
+        // tiles of kFX x kFY cells times slabs: about four blocks per resident
+        // block slot, slabs of at least 8 planes
+        static int bps = -1;
+        if (bps < 0) {
+            int v = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_front_rans3_tiled, kFX * kFY, 0) != cudaSuccess) {
+                cudaGetLastError();
+                v = 1;
+            }
+            bps = std::max(1, v);
+        }
+        RansTile tg;
+        tg.tiles_x = (int)((g.nx + kFX - 1) / kFX);
+        tg.tiles_y = (int)((g.ny + kFY - 1) / kFY);
+        const long long tiles = (long long)tg.tiles_x * tg.tiles_y;
+        const long long want = 4LL * p->num_sms * bps;
+        const long long slabs = std::max<long long>(1, std::min<long long>(g.nz, (want + tiles - 1) / tiles));
+        tg.slab = (int)std::max<long long>(8, (g.nz + slabs - 1) / slabs);
+        tg.n_slabs = (int)((g.nz + tg.slab - 1) / tg.slab);
+        const long long nb = tiles * tg.n_slabs;
+        if (nb >= (1LL << 31)) return OSMODI_E_INVALID;
+        k_front_rans3_tiled<<<(unsigned)nb, kFX * kFY, 0, s>>>(g, tg, p->code32, u_mean, stress, (float)rho, grad);
+    }
     OSM_CUDA(cudaGetLastError());
     return OSMODI_OK;
 }

@@ -378,8 +378,8 @@ struct RbArgs {
     float omega;
 };
 
-template <class T, int CX, int RY, int FC, bool FROM_ZERO, bool DOT>
-__global__ void __launch_bounds__(CX * RY, sizeof(T) == 4 ? 4 : 2) k_mg_fine_rb_fused(const T* __restrict__ zin, T* __restrict__ zout,
+template <class T, int CX, int RY, int FC, bool FROM_ZERO, bool DOT, bool PF = false>
+__global__ void __launch_bounds__(CX * RY, sizeof(T) == 4 ? (PF ? 3 : 4) : 2) k_mg_fine_rb_fused(const T* __restrict__ zin, T* __restrict__ zout,
                                                              const T* __restrict__ r,
                                                              const uint8_t* __restrict__ code8, RbArgs g,
                                                              CgState* st, double* partials) {
@@ -429,6 +429,17 @@ __global__ void __launch_bounds__(CX * RY, sizeof(T) == 4 ? 4 : 2) k_mg_fine_rb_
             zB = zat(k0 - 2);
             zC = zat(k0 - 1);
         }
+        // PF: the operands that come from HBM (the code word and r of plane q,
+        // z of plane q + 1) are loaded one step before first(q) uses them
+        uint32_t pc = 0u;
+        V4<T> pr = zero4<T>(), pz = zero4<T>();
+        auto prefetch = [&](int q) {
+            const bool in = q >= 0 && q < g.nz;
+            pc = in && inr ? __ldg(reinterpret_cast<const uint32_t*>(ccol + (int64_t)q * g.plane)) : 0u;
+            pr = in ? ld4(rcol + (int64_t)q * g.plane) : zero4<T>();
+            if (!FROM_ZERO) pz = zat(q + 1);
+        };
+        if (PF) prefetch(k0 - 1);
         // Cell i of chunk c on row j, plane q has colour (m + j + q) mod 2
         // (m = i - 4 c); the cells a step updates are m = ODD and ODD + 2.
         // colour FC on plane q into ring slot q & 3 (zeros outside the grid);
@@ -438,16 +449,24 @@ __global__ void __launch_bounds__(CX * RY, sizeof(T) == 4 ? 4 : 2) k_mg_fine_rb_
             V4<T> o = zero4<T>();
             rq = zero4<T>();
             cq = 0u;
+            uint32_t cqp = 0u;
+            V4<T> rqp = zero4<T>(), zFp = zero4<T>();
+            if (PF) {
+                cqp = pc;
+                rqp = pr;
+                zFp = pz;
+                prefetch(q + 1);
+            }
             if (q >= 0 && q < g.nz) {
                 const int64_t qo = (int64_t)q * g.plane;
-                cq = inr ? __ldg(reinterpret_cast<const uint32_t*>(ccol + qo)) : 0u;
-                rq = ld4(rcol + qo);
+                cq = PF ? cqp : (inr ? __ldg(reinterpret_cast<const uint32_t*>(ccol + qo)) : 0u);
+                rq = PF ? rqp : ld4(rcol + qo);
                 if (FROM_ZERO) {
 #pragma unroll
                     for (int m = ODD; m < 4; m += 2) o.v[m] = valid8(cq, m) ? wd[face_bits8(cq, m)] * rq.v[m] : T(0);
                 } else {
                     const T* p = zcol + qo;
-                    const V4<T> zF = q + 1 < g.nz ? ld4(p + g.plane) : zero4<T>();
+                    const V4<T> zF = PF ? zFp : (q + 1 < g.nz ? ld4(p + g.plane) : zero4<T>());
                     const V4<T> zn = ld4(p + on), zs = ld4(p + os);
                     const T xw = p[ow], xe = p[oe];
                     if (chunk_full(cq)) {
@@ -472,7 +491,7 @@ __global__ void __launch_bounds__(CX * RY, sizeof(T) == 4 ? 4 : 2) k_mg_fine_rb_
                 }
             } else if (!FROM_ZERO) {
                 zB = zC;
-                zC = zat(q + 1);
+                zC = PF ? zFp : zat(q + 1);
             }
             ring[q & 3][s0] = o;
         };
@@ -1568,9 +1587,9 @@ RbMaps* rb_maps(osmodi_plan p, const float* zA, const float* zB, const float* r)
     return m->ok ? m : nullptr;
 }
 
-template <class T>
+template <class T, bool PF = false>
 int rb_grid(osmodi_plan p, const RbArgs& a) {
-    static const int bps = blocks_per_sm(k_mg_fine_rb_fused<T, kRbCX, kRbRY, 0, false, false>);
+    static const int bps = blocks_per_sm(k_mg_fine_rb_fused<T, kRbCX, kRbRY, 0, false, false, PF>);
     return (int)std::max<long long>(1, std::min<long long>(a.n_items, (long long)p->num_sms * bps));
 }
 
@@ -1711,6 +1730,46 @@ T* vcycle_body(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, cud
     return cur;
 }
 
+// The 3-D V-cycle on the fused one-pass red-black sweeps: nu red-then-black
+// sweeps (the first from zero), the fine residual restricted to level 1, the
+// coarse correction, nu black-then-red sweeps (the last forms (r, z)).  PF:
+// the sweeps that load their HBM operands a plane ahead.  Returns the buffer
+// holding z (zB: 2 nu passes, alternating buffers, starting in zA).
+template <class T, int NDIM, bool PF, class Mark>
+T* fused_vcycle(osmodi_plan p, const Hier* h, const T* r, const MgBuffers<T>& w, CgState* st, double* partials,
+                cudaStream_t s, const FineArgs<T>& f, int nu, int G_rr, int G_prol, Mark mark) {
+    const RbArgs ra = rb_args(p);
+    const int gr = rb_grid<T, PF>(p, ra);
+    LevelVecs<T> v1 = level_vecs<T>(h, w.lv, 1);
+    constexpr int NT = kRbCX * kRbRY;
+    T* cur = w.zA;
+    T* oth = w.zB;
+    if (nu == 1) mark(0);
+    k_mg_fine_rb_fused<T, kRbCX, kRbRY, 0, true, false, PF><<<gr, NT, 0, s>>>(nullptr, cur, r, p->code8, ra, st, partials);
+    if (nu == 1) mark(1);
+    for (int i = 1; i < nu; ++i) {
+        if (i == 1) mark(0);
+        k_mg_fine_rb_fused<T, kRbCX, kRbRY, 0, false, false, PF><<<gr, NT, 0, s>>>(cur, oth, r, p->code8, ra, st, partials);
+        if (i == 1) mark(1);
+        std::swap(cur, oth);
+    }
+    mark(4);
+    k_mg_fine_resid_restrict<T, NDIM><<<G_rr, 256, 0, s>>>(cur, r, p->code8, f, v1.r, st);
+    mark(5);
+    T* zc = vcycle_coarse<T>(p, h, w.lv, 1, st, s);
+    k_mg_fine_prolong<T, NDIM><<<G_prol, 256, 0, s>>>(cur, zc, f, st);
+    for (int i = 0; i < nu; ++i) {  // the adjoint: black then red
+        if (i == 0) mark(2);
+        if (i == nu - 1)
+            k_mg_fine_rb_fused<T, kRbCX, kRbRY, 1, false, true, PF><<<gr, NT, 0, s>>>(cur, oth, r, p->code8, ra, st, partials);
+        else
+            k_mg_fine_rb_fused<T, kRbCX, kRbRY, 1, false, false, PF><<<gr, NT, 0, s>>>(cur, oth, r, p->code8, ra, st, partials);
+        if (i == 0) mark(3);
+        std::swap(cur, oth);
+    }
+    return cur;  // == w.zB
+}
+
 template <class T, int NDIM>
 T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, double* partials, cudaStream_t s,
             cudaEvent_t* ev) {
@@ -1750,7 +1809,7 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
     // (fusing the first two sweeps into one pass was measured slower than the
     // two passes: forming every neighbour's first-sweep value costs more
     // instructions than the extra pass moves bytes)
-    const long long variant = debug_knob(OSMODI_DEBUG_MG_UNFUSED);  // 0 fused, 1 half-sweeps, 2 fused TMA-staged
+    const long long variant = debug_knob(OSMODI_DEBUG_MG_UNFUSED);  // 0 fused, 1 half-sweeps, 2 TMA-staged, 3 prefetching
     if (red_black(p) && variant == 1) {
         // the same V-cycle by in-place half-sweeps (one colour per pass), kept
         // for comparison with the fused sweeps; it ends in zA, copied to zB
@@ -1831,34 +1890,9 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
         // and restriction, the coarse correction, then nu black-then-red
         // sweeps, the last forming (r, z).  Each sweep reads one buffer and
         // writes the other: 2 nu passes starting in zA end in zB.
-        const RbArgs ra = rb_args(p);
-        const int gr = rb_grid<T>(p, ra);
-        T* cur = w.zA;
-        T* oth = w.zB;
-        if (nu == 1) mark(0);
-        k_mg_fine_rb_fused<T, kRbCX, kRbRY, 0, true, false><<<gr, kRbCX * kRbRY, 0, s>>>(nullptr, cur, r, p->code8, ra, st, partials);
-        if (nu == 1) mark(1);
-        for (int i = 1; i < nu; ++i) {
-            if (i == 1) mark(0);
-            k_mg_fine_rb_fused<T, kRbCX, kRbRY, 0, false, false><<<gr, kRbCX * kRbRY, 0, s>>>(cur, oth, r, p->code8, ra, st, partials);
-            if (i == 1) mark(1);
-            std::swap(cur, oth);
-        }
-        mark(4);
-        k_mg_fine_resid_restrict<T, NDIM><<<G_rr, 256, 0, s>>>(cur, r, p->code8, f, v1.r, st);
-        mark(5);
-        T* zc = vcycle_coarse<T>(p, h, w.lv, 1, st, s);
-        k_mg_fine_prolong<T, NDIM><<<G_prol, 256, 0, s>>>(cur, zc, f, st);
-        for (int i = 0; i < nu; ++i) {  // the adjoint: black then red
-            if (i == 0) mark(2);
-            if (i == nu - 1)
-                k_mg_fine_rb_fused<T, kRbCX, kRbRY, 1, false, true><<<gr, kRbCX * kRbRY, 0, s>>>(cur, oth, r, p->code8, ra, st, partials);
-            else
-                k_mg_fine_rb_fused<T, kRbCX, kRbRY, 1, false, false><<<gr, kRbCX * kRbRY, 0, s>>>(cur, oth, r, p->code8, ra, st, partials);
-            if (i == 0) mark(3);
-            std::swap(cur, oth);
-        }
-        return cur;  // == w.zB
+        // (variant 3: the sweeps that load z ahead, for comparison)
+        return variant == 3 ? fused_vcycle<T, NDIM, true>(p, h, r, w, st, partials, s, f, nu, G_rr, G_prol, mark)
+                            : fused_vcycle<T, NDIM, false>(p, h, r, w, st, partials, s, f, nu, G_rr, G_prol, mark);
     }
     T* cur = w.zA;
     T* oth = w.zB;

@@ -184,3 +184,29 @@ def test_batched_multigrid_isolates_bad_input_and_zero_field(osm):
     valid, spacing, f = inst[1]
     want = oracle.solve_direct(oracle.Grid(valid, spacing), np.asarray(f, np.float32).astype(np.float64))
     assert res[1].status == osm.OK and _rel(ps[1].cpu().numpy(), want, valid) < 1e-9
+
+
+def test_batched_multigrid_split_does_not_change_the_cycle(osm):
+    """Which coarse levels run grid-wide and which inside one block per
+    instance changes where the V-cycle runs, not what it computes: the same
+    iterations and the same answers for every split."""
+    probs = [inputs.piv_snapshot_2d(i, size_range=((200, 700), (150, 400))) for i in range(6)]
+    plans = [osm.Plan(2, pr.dims, pr.spacing, pr.mask.cuda(), precond=1) for pr in probs]
+    grads = [pr.grad.cuda() for pr in probs]
+    runs = []
+    try:
+        for bottom in (0, 1 << 30, 300, 16):
+            osm.debug_set(osm.DEBUG_BATCH_BOTTOM_CELLS, bottom)
+            ps = [torch.zeros(pr.mask.shape, dtype=torch.float64, device="cuda") for pr in probs]
+            st, res = osm.Batch(plans).solve(grads, ps, 1e-10)
+            assert st == osm.OK
+            runs.append(([r.inner_iters for r in res], [p.cpu().numpy() for p in ps]))
+    finally:
+        osm.debug_set(osm.DEBUG_BATCH_BOTTOM_CELLS, osm.DEBUG_DEFAULT)
+    its0, p0 = runs[0]
+    assert max(its0) < 30, its0
+    for its, ps in runs[1:]:
+        assert its == its0
+        for pr, a, b in zip(probs, ps, p0):
+            valid = pr.mask.numpy().astype(bool)
+            assert _rel(a, b, valid) < 1e-12

@@ -571,7 +571,9 @@ OSMODI_API osmodi_status osmodi_probe_fp64(double* gflops_out, double* ms_out, v
  *   one-pass red-black sweeps (every level with packed counts); 1
  *   one-colour half-sweeps in place (two passes per sweep); 2 as 0 with the
  *   fine level's input planes staged by TMA (FP32 plans); 3 as 0 with the
- *   fine sweeps' HBM operands loaded one plane ahead.
+ *   fine sweeps' HBM operands loaded one plane ahead; 4 as 0 with the fine
+ *   level's z, r and code planes staged in shared memory by cp.async (FP32
+ *   plans).
  * OSMODI_DEBUG_NET_WMMA: which kernels run the seed network's
  *   convolutions, the same products in each case, for comparisons: 0
  *   (default) tcgen05, the forward 3x3x3 layers with their input tile staged

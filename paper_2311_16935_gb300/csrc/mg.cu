@@ -567,6 +567,207 @@ __global__ void __launch_bounds__(CX * RY, sizeof(T) == 4 ? (PF ? 3 : 4) : 2) k_
 }
 
 // ---------------------------------------------------------------------------
+// The fused red-black sweep with its input planes staged by cp.async (FP32).
+// Same tile and thread layout as k_mg_fine_rb_fused (16 x 16 chunks with the
+// halo ring, warps holding rows w and w + 8); what changes is where the
+// operands come from.  Per plane the block copies z (its 16 x 16 chunks and
+// the rows above and below the tile), r and the code words straight into
+// 4-slot shared-memory rings with cp.async -- no registers hold them in
+// flight -- one plane before they are used.  At step k the block waits for
+// its own copies, synchronises once, issues the copies of the next plane,
+// updates the second colour on plane k - 1 from the ring of first-colour
+// planes, and the first colour on plane k + 1 from the staged z planes
+// k .. k + 2.  The slot a step refills was last read a step before the
+// barrier.  Outside the box the copies zero-fill (code 0: a missing cell).
+// ---------------------------------------------------------------------------
+constexpr int kAX = 16, kAY = 16, kAT = kAX * kAY;   // chunks per tile row, rows, threads
+constexpr int kAZR = kAY + 2;                        // staged z rows: the tile's and one above and below
+constexpr int kAZSlot = kAZR * kAX;                  // float4 per staged z plane
+constexpr int kAsyncSmem = (4 * kAZSlot + 4 * kAT + 4 * kAT) * 16 + 4 * kAT * 4 + 64 * 4;
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool full) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src),
+                 "r"(full ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool full) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src), "r"(full ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <int FC, bool FROM_ZERO, bool DOT>
+__global__ void __launch_bounds__(kAT, 4) k_mg_fine_rb_async(const float* __restrict__ zin, float* __restrict__ zout,
+                                                             const float* __restrict__ r,
+                                                             const uint8_t* __restrict__ code8, RbArgs g,
+                                                             CgState* st, double* partials) {
+    if (st->status != kRunning) return;
+    extern __shared__ __align__(16) unsigned char asmem[];
+    V4<float>* zs = reinterpret_cast<V4<float>*>(asmem);  // [4][kAZR][kAX] staged z planes
+    V4<float>* rs = zs + 4 * kAZSlot;                     // [4][kAT] staged r planes
+    V4<float>* ring = rs + 4 * kAT;                       // [4][kAT] first-colour planes
+    uint32_t* cs = reinterpret_cast<uint32_t*>(ring + 4 * kAT);  // [4][kAT] staged code words
+    float* wd = reinterpret_cast<float*>(cs + 4 * kAT);          // omega / D per face mask
+    if (threadIdx.x < 64) {
+        const unsigned fm = threadIdx.x;
+        const float d = g.F[0] * (float)((fm & 1u) + ((fm >> 1) & 1u)) + g.F[1] * (float)(((fm >> 2) & 1u) + ((fm >> 3) & 1u)) +
+                        g.F[2] * (float)(((fm >> 4) & 1u) + ((fm >> 5) & 1u));
+        wd[threadIdx.x] = d > 0.f ? g.omega / d : 0.f;
+    }
+    const int t = threadIdx.x, lx = t % kAX, ly = (t >> 5) + (kAY / 2) * ((t >> 4) & 1);
+    const int s0 = ly * kAX + lx;          // this chunk in a ring / r / code slot
+    const int z0 = (ly + 1) * kAX + lx;    // ... and in a staged z plane
+    const float Fx = g.F[0], Fy = g.F[1], Fz = g.F[2];
+    double acc[1] = {0.0};
+    for (long long item = blockIdx.x; item < g.n_items; item += gridDim.x) {
+        const int tx = (int)(item % g.tiles_x);
+        const int ty = (int)((item / g.tiles_x) % g.tiles_y);
+        const int sl = (int)(item / ((long long)g.tiles_x * g.tiles_y));
+        const int c = tx * (kAX - 2) - 1 + lx, j = ty * (kAY - 2) - 1 + ly;
+        const bool inr = c >= 0 && c < g.cpr && j >= 0 && j < g.ny;
+        const bool interior = inr && lx >= 1 && lx <= kAX - 2 && ly >= 1 && ly <= kAY - 2;
+        const int k0 = sl * g.slab, k1 = min(g.nz, k0 + g.slab);
+        const int64_t col = (int64_t)j * g.px + 4 * (int64_t)c;
+        const int64_t colc = inr ? col : 0;  // copies outside the grid read (0, 0) and zero-fill
+        // the extra staged z row of threads 0 .. 31: tile row -1 (t < 16) or kAY
+        const int ey = t < 16 ? -1 : kAY, ex = t & 15;
+        const int ce = tx * (kAX - 2) - 1 + ex, je = ty * (kAY - 2) - 1 + ey;
+        const bool ein = t < 32 && ce >= 0 && ce < g.cpr && je >= 0 && je < g.ny;
+        const int64_t cole = ein ? (int64_t)je * g.px + 4 * (int64_t)ce : 0;
+        const int ze = (ey + 1) * kAX + ex;
+        // copies of plane q into the slots of plane q (z: zin; r and code)
+        auto stage_z = [&](int q) {
+            if (FROM_ZERO) return;
+            const bool qin = q >= 0 && q < g.nz;
+            const int64_t qo = qin ? (int64_t)q * g.plane : 0;
+            V4<float>* zp = zs + (q & 3) * kAZSlot;
+            cp_async16(zp + z0, zin + qo + colc, qin && inr);
+            if (t < 32) cp_async16(zp + ze, zin + qo + cole, qin && ein);
+        };
+        auto stage_rc = [&](int q) {
+            const bool qin = q >= 0 && q < g.nz;
+            const int64_t qo = qin ? (int64_t)q * g.plane : 0;
+            cp_async16(rs + (q & 3) * kAT + s0, r + qo + colc, qin && inr);
+            cp_async4(cs + (q & 3) * kAT + s0, code8 + qo + colc, qin && inr);
+        };
+        // colour FC on plane q from the staged planes q - 1 .. q + 1 into ring
+        // slot q & 3 (zeros outside the grid); the cells m = ODD, ODD + 2
+        auto first = [&](int q, auto odd_c) {
+            constexpr int ODD = decltype(odd_c)::value;
+            V4<float> o = zero4<float>();
+            if (q >= 0 && q < g.nz) {
+                const uint32_t cq = cs[(q & 3) * kAT + s0];
+                const V4<float> rq = rs[(q & 3) * kAT + s0];
+                if (FROM_ZERO) {
+#pragma unroll
+                    for (int m = ODD; m < 4; m += 2) o.v[m] = valid8(cq, m) ? wd[face_bits8(cq, m)] * rq.v[m] : 0.f;
+                } else {
+                    const V4<float>* zq = zs + (q & 3) * kAZSlot;
+                    const V4<float> zc = zq[z0], zn = zq[z0 + kAX], zsv = zq[z0 - kAX];
+                    const V4<float> zF = zs[((q + 1) & 3) * kAZSlot + z0], zB = zs[((q + 3) & 3) * kAZSlot + z0];
+                    // a tile-edge chunk's outer neighbour is not staged; the cell that
+                    // would read it is one whose result no interior chunk uses
+                    const float xw = lx > 0 ? zq[z0 - 1].v[3] : 0.f;
+                    const float xe = lx < kAX - 1 ? zq[z0 + 1].v[0] : 0.f;
+                    if (chunk_full(cq)) {
+                        o = rb_chunk_full<ODD>(zc, xw, xe, zn, zsv, zF, zB, rq, wd[63], Fx, Fy, Fz);
+                    } else {
+                        const float wv[4] = {xw, zc.v[0], zc.v[1], zc.v[2]};
+                        const float ev[4] = {zc.v[1], zc.v[2], zc.v[3], xe};
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            if ((m & 1) != ODD) {
+                                o.v[m] = zc.v[m];
+                                continue;
+                            }
+                            const unsigned fm = face_bits8(cq, m);
+                            const float w = valid8(cq, m) ? wd[fm] : 0.f;
+                            o.v[m] = rb_cell(zc.v[m], ev[m], wv[m], zn.v[m], zsv.v[m], zF.v[m], zB.v[m], rq.v[m], fm, w,
+                                             Fx, Fy, Fz);
+                        }
+                    }
+                }
+            }
+            ring[(q & 3) * kAT + s0] = o;
+        };
+        // the other colour on plane k from ring planes k - 1 .. k + 1
+        auto second = [&](int k, auto odd_c) {
+            constexpr int ODD = decltype(odd_c)::value;
+            const uint32_t cw = cs[(k & 3) * kAT + s0];
+            const V4<float> rk = rs[(k & 3) * kAT + s0];
+            const V4<float>* rp = ring + (k & 3) * kAT;
+            const V4<float> o = rp[s0];
+            const V4<float> zn = rp[s0 + kAX], zsv = rp[s0 - kAX];
+            const V4<float> zf = ring[((k + 1) & 3) * kAT + s0], zb = ring[((k + 3) & 3) * kAT + s0];
+            const float xw = rp[s0 - 1].v[3], xe = rp[s0 + 1].v[0];
+            V4<float> out;
+            if (chunk_full(cw)) {
+                out = rb_chunk_full<ODD>(o, xw, xe, zn, zsv, zf, zb, rk, wd[63], Fx, Fy, Fz);
+            } else {
+                const float wv[4] = {xw, o.v[0], o.v[1], o.v[2]};
+                const float ev[4] = {o.v[1], o.v[2], o.v[3], xe};
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    if ((m & 1) != ODD) {
+                        out.v[m] = o.v[m];
+                        continue;
+                    }
+                    const unsigned fm = face_bits8(cw, m);
+                    const float w = valid8(cw, m) ? wd[fm] : 0.f;
+                    out.v[m] = rb_cell(o.v[m], ev[m], wv[m], zn.v[m], zsv.v[m], zf.v[m], zb.v[m], rk.v[m], fm, w, Fx, Fy, Fz);
+                }
+            }
+            st4(zout + (int64_t)k * g.plane + col, out);
+            if (DOT) {
+                float part = 0.f;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) part += rk.v[m] * out.v[m];
+                acc[0] += (double)part;
+            }
+        };
+        using I0 = std::integral_constant<int, 0>;
+        using I1 = std::integral_constant<int, 1>;
+        // B(k) = FC ^ ((j + k + 1) & 1): the cells the first colour updates on
+        // plane k + 1 and the second colour on plane k (uniform per warp)
+        const int b0 = FC ^ ((j + k0 + 1) & 1);
+        auto bq = [&](int k) { return b0 ^ ((k - k0) & 1); };
+        __syncthreads();  // the previous item's readers are done with every slot (and wd is set)
+        // prologue: z planes k0 - 2 .. k0 + 1, r and codes of k0 - 1, k0; the
+        // first colour on plane k0 - 1
+        for (int q = k0 - 2; q <= k0 + 1; ++q) stage_z(q);
+        stage_rc(k0 - 1);
+        stage_rc(k0);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+        if (bq(k0 - 2)) first(k0 - 1, I1{});
+        else first(k0 - 1, I0{});
+        // step k: the second colour on plane k - 1, the first on plane k + 1
+        for (int k = k0 - 1; k <= k1; ++k) {
+            cp_async_wait_all();
+            __syncthreads();
+            if (k + 3 <= k1 + 1) stage_z(k + 3);
+            if (k + 2 <= k1) stage_rc(k + 2);
+            cp_async_commit();
+            if (interior && k - 1 >= k0) {
+                if (bq(k - 1)) second(k - 1, I1{});
+                else second(k - 1, I0{});
+            }
+            if (k + 1 <= k1) {
+                if (bq(k)) first(k + 1, I1{});
+                else first(k + 1, I0{});
+            }
+        }
+        cp_async_wait_all();
+    }
+    if (DOT) {
+        double tot[1];
+        if (grid_sum<1>(acc, partials, &st->ticketM, tot) && threadIdx.x == 0) finish_rz(st, tot[0]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // The fused red-black sweep with its input planes staged by TMA (FP32).  Same
 // sweep as k_mg_fine_rb_fused; what changes is how the planes arrive.  A
 // block of 256 threads owns a tile of 128 x 8 cells and a slab of planes;
@@ -1735,6 +1936,61 @@ T* vcycle_body(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, cud
 // coarse correction, nu black-then-red sweeps (the last forms (r, z)).  PF:
 // the sweeps that load their HBM operands a plane ahead.  Returns the buffer
 // holding z (zB: 2 nu passes, alternating buffers, starting in zA).
+// one launch of the cp.async-staged sweep (dynamic shared memory opted in
+// once per instantiation); one block per resident slot, items grid-strided
+template <int FC, bool FZ, bool DOT>
+void launch_async(osmodi_plan p, const RbArgs& ra, const float* zi, float* zo, const float* r, CgState* st,
+                  double* partials, cudaStream_t s) {
+    static const int bps = [] {
+        cudaFuncSetAttribute(k_mg_fine_rb_async<FC, FZ, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAsyncSmem);
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mg_fine_rb_async<FC, FZ, DOT>, kAT, kAsyncSmem) !=
+                cudaSuccess || b < 1) {
+            cudaGetLastError();
+            b = 1;
+        }
+        return b;
+    }();
+    const int gr = (int)std::max<long long>(1, std::min<long long>(ra.n_items, (long long)p->num_sms * bps));
+    k_mg_fine_rb_async<FC, FZ, DOT><<<gr, kAT, kAsyncSmem, s>>>(zi, zo, r, p->code8, ra, st, partials);
+}
+
+// the V-cycle of fused_vcycle with the cp.async-staged sweeps (FP32)
+template <class T, int NDIM, class Mark>
+T* fused_vcycle_async(osmodi_plan p, const Hier* h, const T* r, const MgBuffers<T>& w, CgState* st,
+                      double* partials, cudaStream_t s, const FineArgs<T>& f, int nu, int G_rr, int G_prol, Mark mark) {
+    const RbArgs ra = rb_args(p);
+    LevelVecs<T> v1 = level_vecs<T>(h, w.lv, 1);
+    T* cur = w.zA;
+    T* oth = w.zB;
+    auto F = [](T* x) { return reinterpret_cast<float*>(x); };
+    const float* rf = reinterpret_cast<const float*>(r);
+    if (nu == 1) mark(0);
+    launch_async<0, true, false>(p, ra, nullptr, F(cur), rf, st, partials, s);
+    if (nu == 1) mark(1);
+    for (int i = 1; i < nu; ++i) {
+        if (i == 1) mark(0);
+        launch_async<0, false, false>(p, ra, F(cur), F(oth), rf, st, partials, s);
+        if (i == 1) mark(1);
+        std::swap(cur, oth);
+    }
+    mark(4);
+    k_mg_fine_resid_restrict<T, NDIM><<<G_rr, 256, 0, s>>>(cur, r, p->code8, f, v1.r, st);
+    mark(5);
+    T* zc = vcycle_coarse<T>(p, h, w.lv, 1, st, s);
+    k_mg_fine_prolong<T, NDIM><<<G_prol, 256, 0, s>>>(cur, zc, f, st);
+    for (int i = 0; i < nu; ++i) {  // the adjoint: black then red
+        if (i == 0) mark(2);
+        if (i == nu - 1)
+            launch_async<1, false, true>(p, ra, F(cur), F(oth), rf, st, partials, s);
+        else
+            launch_async<1, false, false>(p, ra, F(cur), F(oth), rf, st, partials, s);
+        if (i == 0) mark(3);
+        std::swap(cur, oth);
+    }
+    return cur;  // == w.zB
+}
+
 template <class T, int NDIM, bool PF, class Mark>
 T* fused_vcycle(osmodi_plan p, const Hier* h, const T* r, const MgBuffers<T>& w, CgState* st, double* partials,
                 cudaStream_t s, const FineArgs<T>& f, int nu, int G_rr, int G_prol, Mark mark) {
@@ -1809,7 +2065,7 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
     // (fusing the first two sweeps into one pass was measured slower than the
     // two passes: forming every neighbour's first-sweep value costs more
     // instructions than the extra pass moves bytes)
-    const long long variant = debug_knob(OSMODI_DEBUG_MG_UNFUSED);  // 0 fused, 1 half-sweeps, 2 TMA-staged, 3 prefetching
+    const long long variant = debug_knob(OSMODI_DEBUG_MG_UNFUSED);  // 0 fused, 1 half-sweeps, 2 TMA-staged, 3 prefetching, 4 cp.async-staged
     if (red_black(p) && variant == 1) {
         // the same V-cycle by in-place half-sweeps (one colour per pass), kept
         // for comparison with the fused sweeps; it ends in zA, copied to zB
@@ -1891,6 +2147,8 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
         // sweeps, the last forming (r, z).  Each sweep reads one buffer and
         // writes the other: 2 nu passes starting in zA end in zB.
         // (variant 3: the sweeps that load z ahead, for comparison)
+        if (variant == 4 && sizeof(T) == 4)
+            return fused_vcycle_async<T, NDIM>(p, h, r, w, st, partials, s, f, nu, G_rr, G_prol, mark);
         return variant == 3 ? fused_vcycle<T, NDIM, true>(p, h, r, w, st, partials, s, f, nu, G_rr, G_prol, mark)
                             : fused_vcycle<T, NDIM, false>(p, h, r, w, st, partials, s, f, nu, G_rr, G_prol, mark);
     }

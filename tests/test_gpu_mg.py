@@ -127,7 +127,8 @@ def test_smoothing_options_keep_the_fixed_point(osm, sweeps, scale):
 @pytest.mark.parametrize("shape", [(19, 23, 29), (33, 30, 61), (5, 40, 17), (64, 64, 64), (21, 37, 300)])
 def test_fused_sweeps_equal_half_sweeps(osm, shape):
     """The fused one-pass red-black sweeps (default; with the fine level's
-    inputs staged by TMA; with them loaded a plane ahead) against the same
+    inputs staged by TMA; with them loaded a plane ahead; staged by
+    cp.async) against the same
     V-cycle by one-colour
     half-sweeps on every level (OSMODI_DEBUG_MG_UNFUSED): the same arithmetic,
     so the preconditioned CG takes the same iterations, reports the same
@@ -139,7 +140,7 @@ def test_fused_sweeps_equal_half_sweeps(osm, shape):
     f = rng.normal(size=(3,) + shape).astype(np.float32)
     spacing = (1.0, 1.0, 1.0)
     out = {}
-    for variant in (0, 1, 2, 3):  # fused, half-sweeps, TMA-staged fine planes, prefetching
+    for variant in (0, 1, 2, 3, 4):  # fused, half-sweeps, TMA-staged, prefetching, cp.async-staged
         osm.debug_set(osm.DEBUG_MG_UNFUSED, variant)
         try:
             _, res, p = _solve(osm, f, valid, spacing, 1e-11, precision=2, precond=1)
@@ -149,7 +150,7 @@ def test_fused_sweeps_equal_half_sweeps(osm, shape):
         out[variant] = (res, p)
     want = oracle.solve_cg(oracle.Grid(valid, spacing), f.astype(np.float64), tol=1e-14, maxit=50000)[0]
     ru, pu = out[1]
-    for variant in (0, 2, 3):
+    for variant in (0, 2, 3, 4):
         rf, pf = out[variant]
         # rounding (FMA contraction may differ between the kernels) can move a
         # stopping test across its threshold by at most one check chunk

@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(128, 1) k_conv3_halo(const __grid_constant__ C
                 tc::tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * g.Cout + c0), v);
                 if (!valid) continue;
 #pragma unroll
-                for (int i = 0; i < 16; i += 4) {
+                for (int i = 0; i < 16 && g.bias; i += 4) {  // bias may be null (osmodi_conv3d)
                     const float4 b4 = __ldg(reinterpret_cast<const float4*>(g.bias + c0 + i));
                     v[i] += b4.x;
                     v[i + 1] += b4.y;

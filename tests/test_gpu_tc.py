@@ -33,7 +33,7 @@ def test_tc_gemm_matches_reference(osm, N, K):
 
 CONV_SHAPES = [(8, 16, 64, 32, 32), (4, 8, 128, 8, 16), (4, 9, 130, 8, 16), (6, 10, 64, 48, 48), (5, 7, 256, 32, 32),
                (3, 5, 32, 64, 64), (7, 13, 40, 16, 16), (2, 18, 128, 8, 16), (3, 16, 256, 8, 16), (4, 20, 64, 32, 32),
-               (3, 34, 64, 8, 16)]
+               (3, 34, 64, 8, 16), (3, 10, 130, 32, 32), (2, 6, 128, 16, 48), (1, 3, 128, 8, 16)]
 
 
 @pytest.mark.parametrize("shape", CONV_SHAPES)

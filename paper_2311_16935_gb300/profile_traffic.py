@@ -8,7 +8,8 @@ row per launch, one column per metric, a units row under the header) or the
 ``--csv`` log of a ``--metrics`` capture (one row per launch and metric).
 CELLS is the number of grid cells one launch of each kernel covers in the
 captured run.  The file records, per kernel (name up to its template
-arguments), the launches, DRAM bytes (read + write) per launch and per cell,
+arguments), the launches, the median DRAM bytes (read + write) per launch of
+the launches that did work, and per cell,
 and the hash of the kernel sources it was taken on: bench.py reports the
 traffic only while the sources still hash the same.
 """
@@ -81,13 +82,21 @@ def read_launches(path: str):
 
 
 def summarise(path: str, cells: int, command: str) -> dict:
-    agg = defaultdict(lambda: [0, 0.0])
+    """Per kernel: the median DRAM bytes of the launches that did work.  A
+    solve's captured CUDA graphs launch a few iterations past convergence,
+    whose kernels return at once; launches below half of the kernel's
+    largest are counted as idle and left out of the median."""
+    agg = defaultdict(list)
     for name, b in read_launches(path):
-        a = agg[short_name(name)]
-        a[0] += 1
-        a[1] += b
-    kernels = {k: {"launches": n, "dram_bytes_per_launch": tot / n, "dram_bytes_per_cell": tot / n / cells}
-               for k, (n, tot) in sorted(agg.items())}
+        agg[short_name(name)].append(b)
+    kernels = {}
+    for k, vals in sorted(agg.items()):
+        top = max(vals)
+        work = sorted(v for v in vals if v >= 0.5 * top)
+        n = len(work)
+        med = work[n // 2] if n % 2 else 0.5 * (work[n // 2 - 1] + work[n // 2])
+        kernels[k] = {"launches": len(vals), "idle_launches": len(vals) - n, "dram_bytes_per_launch": med,
+                      "dram_bytes_per_cell": med / cells}
     return {"kernel_source_hash": kernel_source_hash(), "cells_per_launch": cells, "command": command,
             "metrics": list(METRICS), "kernels": kernels}
 

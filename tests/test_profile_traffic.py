@@ -36,5 +36,18 @@ def test_metrics_log(tmp_path):
     f = tmp_path / "log.csv"
     f.write_text(LOG)
     d = pt.summarise(str(f), 10, "cmd")
-    assert d["kernels"]["k_residual<float, 3>"] == {"launches": 1, "dram_bytes_per_launch": 2.63e9,
+    assert d["kernels"]["k_residual<float, 3>"] == {"launches": 1, "idle_launches": 0, "dram_bytes_per_launch": 2.63e9,
                                                     "dram_bytes_per_cell": 2.63e8}
+
+
+def test_idle_launches_left_out(tmp_path):
+    """Launches that returned at once (a captured graph's iterations past
+    convergence) do not pull the median down."""
+    rows = RAW.splitlines()[:2]
+    for i, mb in enumerate(["1000", "1010", "990", "0.01", "0.02"]):
+        rows.append(f'"{i}","1","python","h","void osm::k_cg_b<float>(float *)","1","7","{mb}","0"')
+    f = tmp_path / "idle.csv"
+    f.write_text("\n".join(rows) + "\n")
+    k = pt.summarise(str(f), 100, "cmd")["kernels"]["k_cg_b<float>"]
+    assert k["launches"] == 5 and k["idle_launches"] == 2
+    assert k["dram_bytes_per_launch"] == 1000e6

@@ -71,7 +71,10 @@ def _profiled_traffic(kernel: str, cells: int):
         return None
     if d.get("kernel_source_hash") != _kernel_source_hash():
         return None
-    hits = [v for k, v in d.get("kernels", {}).items() if k == kernel or k.startswith(kernel + "<")]
+    ks = d.get("kernels", {})
+    if kernel in ks:  # one instantiation, named with its template arguments
+        return ks[kernel]["dram_bytes_per_cell"] * cells
+    hits = [v for k, v in ks.items() if k.startswith(kernel + "<")]
     if len(hits) != 1:
         return None
     return hits[0]["dram_bytes_per_cell"] * cells
@@ -369,7 +372,9 @@ def main():
     sw_avg = sw_ms / max(sw_n, 1)
     per_update = 13.0
     sw_bytes = per_update * cells
-    sw_traffic = _profiled_traffic("k_mg_fine_rb_fused", cells)
+    # the timed launches are the plain sweeps (the second pre-sweep and the
+    # first post-sweep: no start from zero, no dot product)
+    sw_traffic = _profiled_traffic("k_mg_fine_rb_fused<float, 16, 16, 0, 0, 0, 0>", cells)
     # the CG kernel applying the stencil: read z (the preconditioned residual),
     # p_old, x (3 x 4 B) + code (1 B); write p, q, x (3 x 4 B)
     ka_avg = ka_ms / max(ka_n, 1)

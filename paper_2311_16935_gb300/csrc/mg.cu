@@ -1392,7 +1392,9 @@ struct CbArgs {
 // a 10-bit count as a float (exact: counts < 2^23)
 __device__ __forceinline__ float cnt_f(uint32_t w, int shift) { return (float)((w >> shift) & 1023u); }
 
-template <class T, int FC, bool FROM_ZERO>
+// VEC (FP32, even rows): a pair's two cells are one aligned 8-byte word, so
+// its z, r and count words move in one load each
+template <class T, int FC, bool FROM_ZERO, bool VEC = false>
 __global__ void __launch_bounds__(kCbX * kCbY) k_mg_coarse_rb_fused(const T* __restrict__ zin, T* __restrict__ zout,
                                                                   const T* __restrict__ r, Level lv, T omega,
                                                                   CbArgs g, const CgState* st) {
@@ -1424,14 +1426,34 @@ __global__ void __launch_bounds__(kCbX * kCbY) k_mg_coarse_rb_fused(const T* __r
         auto wat = [&](int q, int64_t c, bool in) -> uint32_t {
             return in && q >= 0 && q < g.nz ? __ldg(lv.wc + (int64_t)q * sz + c) : 0u;
         };
+        // both cells of the pair (VEC: in0 == in1, c1 == c0 + 1, c0 even)
+        auto zpair = [&](int q, T& a, T& b) {
+            if (VEC) {
+                const bool ok = in0 && q >= 0 && q < g.nz;
+                const float2 v = ok ? *reinterpret_cast<const float2*>(zin + (int64_t)q * sz + c0) : make_float2(0.f, 0.f);
+                a = (T)v.x;
+                b = (T)v.y;
+            } else {
+                a = zat(q, c0, in0);
+                b = zat(q, c1, in1);
+            }
+        };
+        auto wpair = [&](int q, int64_t off, bool use, uint32_t& a, uint32_t& b) {
+            if (VEC) {
+                const bool ok = use && in0 && q >= 0 && q < g.nz;
+                const uint2 v = ok ? __ldg(reinterpret_cast<const uint2*>(lv.wc + (int64_t)q * sz + c0 + off)) : make_uint2(0u, 0u);
+                a = v.x;
+                b = v.y;
+            } else {
+                a = use ? wat(q, c0 + off, in0) : 0u;
+                b = use ? wat(q, c1 + off, in1) : 0u;
+            }
+        };
         if (!FROM_ZERO) {
-            zB0 = zat(k0 - 2, c0, in0);
-            zB1 = zat(k0 - 2, c1, in1);
-            zC0 = zat(k0 - 1, c0, in0);
-            zC1 = zat(k0 - 1, c1, in1);
+            zpair(k0 - 2, zB0, zB1);
+            zpair(k0 - 1, zC0, zC1);
         }
-        wz0 = wat(k0 - 2, c0, in0);
-        wz1 = wat(k0 - 2, c1, in1);
+        wpair(k0 - 2, 0, true, wz0, wz1);
         // the other cell's weights and r on a plane, for its update one step later
         struct Wv {
             T xp, xm, yp, ym, zp, zm, wd, r;
@@ -1443,11 +1465,20 @@ __global__ void __launch_bounds__(kCbX * kCbY) k_mg_coarse_rb_fused(const T* __r
             const int64_t qo = (int64_t)q * sz;
             // count words: own (+x, +y, +z), -x of cell 0 from the lane before,
             // -y from the row before, -z carried from the plane before
-            const uint32_t w0 = wat(q, c0, in0), w1 = wat(q, c1, in1);
-            const uint32_t wy0 = ym ? wat(q, c0 - sy, in0) : 0u, wy1 = ym ? wat(q, c1 - sy, in1) : 0u;
+            uint32_t w0, w1, wy0, wy1;
+            wpair(q, 0, true, w0, w1);
+            wpair(q, -sy, ym, wy0, wy1);
             uint32_t wx0 = __shfl_up_sync(0xffffffffu, w1, 1);
             if (i0 == 0 || lane == 0) wx0 = 0u;  // lane 0's first cell is never used
-            const T r0 = qin && in0 ? r[qo + c0] : T(0), r1 = qin && in1 ? r[qo + c1] : T(0);
+            T r0, r1;
+            if (VEC) {
+                const float2 v = qin && in0 ? *reinterpret_cast<const float2*>(r + qo + c0) : make_float2(0.f, 0.f);
+                r0 = (T)v.x;
+                r1 = (T)v.y;
+            } else {
+                r0 = qin && in0 ? r[qo + c0] : T(0);
+                r1 = qin && in1 ? r[qo + c1] : T(0);
+            }
             // weights of both cells
             const T xp0 = (T)(cnt_f(w0, 0) * (float)F0), xp1 = (T)(cnt_f(w1, 0) * (float)F0);
             const T xm0 = (T)(cnt_f(wx0, 0) * (float)F0), xm1 = xp0;
@@ -1466,7 +1497,8 @@ __global__ void __launch_bounds__(kCbX * kCbY) k_mg_coarse_rb_fused(const T* __r
                     o0 = u1 ? T(0) : wd0 * r0;
                     o1 = u1 ? wd1 * r1 : T(0);
                 } else {
-                    const T zF0 = zat(q + 1, c0, in0), zF1 = zat(q + 1, c1, in1);
+                    T zF0, zF1;
+                    zpair(q + 1, zF0, zF1);
                     const T zw = __shfl_up_sync(0xffffffffu, zC1, 1);    // cell i0 - 1
                     const T ze = __shfl_down_sync(0xffffffffu, zC0, 1);  // cell i0 + 2
                     // the FC cell's update
@@ -1500,8 +1532,7 @@ __global__ void __launch_bounds__(kCbX * kCbY) k_mg_coarse_rb_fused(const T* __r
             } else if (!FROM_ZERO) {
                 zB0 = zC0;
                 zB1 = zC1;
-                zC0 = zat(q + 1, c0, in0);
-                zC1 = zat(q + 1, c1, in1);
+                zpair(q + 1, zC0, zC1);
             }
             ring[q & 3][0][t] = in0 ? o0 : T(0);
             ring[q & 3][1][t] = in1 ? o1 : T(0);
@@ -1881,9 +1912,23 @@ T* vcycle_body(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, cud
         const T om = (T)kOmegaRB;
         T* cur = v.a;
         T* oth = v.b;
-        k_mg_coarse_rb_fused<T, 0, true><<<gf, kCbX * kCbY, 0, s>>>(nullptr, cur, v.r, g, om, cb, st);
+        // FP32 levels with even rows take the pair-vector loads
+        const bool vec = sizeof(T) == 4 && g.nx % 2 == 0;
+        auto sweep = [&](auto fc, auto fz, const T* zi, T* zo) {
+            constexpr int FCV = decltype(fc)::value;
+            constexpr bool FZV = decltype(fz)::value;
+            if (vec)
+                k_mg_coarse_rb_fused<T, FCV, FZV, true><<<gf, kCbX * kCbY, 0, s>>>(zi, zo, v.r, g, om, cb, st);
+            else
+                k_mg_coarse_rb_fused<T, FCV, FZV, false><<<gf, kCbX * kCbY, 0, s>>>(zi, zo, v.r, g, om, cb, st);
+        };
+        using C0 = std::integral_constant<int, 0>;
+        using C1 = std::integral_constant<int, 1>;
+        using BT = std::integral_constant<bool, true>;
+        using BF = std::integral_constant<bool, false>;
+        sweep(C0{}, BT{}, nullptr, cur);
         for (int i = 1; i < nu; ++i) {
-            k_mg_coarse_rb_fused<T, 0, false><<<gf, kCbX * kCbY, 0, s>>>(cur, oth, v.r, g, om, cb, st);
+            sweep(C0{}, BF{}, cur, oth);
             std::swap(cur, oth);
         }
         k_mg_coarse<T, M_RESID, PACKED><<<Grs, B, 0, s>>>(cur, v.r, oth, a, st);
@@ -1891,7 +1936,7 @@ T* vcycle_body(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, cud
         T* zc = vcycle_coarse<T>(p, h, base, l + 1, st, s);
         k_mg_coarse_prolong<T><<<Gpr, B, 0, s>>>(cur, zc, a, st);
         for (int i = 0; i < nu; ++i) {  // the adjoint: black then red
-            k_mg_coarse_rb_fused<T, 1, false><<<gf, kCbX * kCbY, 0, s>>>(cur, oth, v.r, g, om, cb, st);
+            sweep(C1{}, BF{}, cur, oth);
             std::swap(cur, oth);
         }
         return cur;

@@ -670,6 +670,17 @@ __global__ void __launch_bounds__(128, 1) k_conv3_halo(const __grid_constant__ C
             dB[i] = tc::sdesc(b0 + (uint32_t)i * 2u * (uint32_t)g.Cout * 16u, (uint32_t)g.Cout * 16u, 128);
         }
     }
+    // the slack after each channel group's box is never copied to; with 8
+    // input channels the last tap's zero-weight partner reads into it, and
+    // 0 x (a NaN left there) would be NaN: zero it
+    {
+        const int nv = 3 * (g.TY + 2) * (g.WX + 2);
+        for (int q = t; q < g.CG * (g.nvp - nv); q += 128) {
+            const int cg = q / (g.nvp - nv), v = nv + q % (g.nvp - nv);
+            *reinterpret_cast<uint4*>(sA + (size_t)cg * cgs + (size_t)v * 16) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        tc::fence_proxy_async();
+    }
     bool ok = tc::mbar_wait(&bar_load, 0, TC_POLLS);
     tc::fence_before_sync();
     __syncthreads();

@@ -63,3 +63,26 @@ def test_conv3d_matches_torch(osm, shape):
                                                      [int(v) for v in (d == d.max()).nonzero()[0]])
         outs[path] = y
     assert (outs[0].float() - outs[2].float()).abs().max().item() <= 2 ** -7 * scale
+
+
+@pytest.mark.parametrize("shape", [(64, 128, 128, 8, 16), (32, 64, 64, 32, 32)])
+def test_conv3d_large_without_relu(osm, shape):
+    """Layers of the seed network's sizes without the ReLU (which would turn
+    a NaN into 0): every output finite and equal to the gathering kernel's.
+    With 8 input channels the halo kernel pairs the last tap with zero
+    weights whose operand lies past the staged box; that slack must hold
+    zeros, not whatever shared memory held before."""
+    D, H, W, cin, cout = shape
+    g = torch.Generator(device="cuda").manual_seed(sum(shape))
+    x = torch.randn((D, H, W, cin), device="cuda", generator=g).to(torch.bfloat16)
+    w = (torch.randn((27, cin, cout), device="cuda", generator=g) / (27 * cin) ** 0.5).to(torch.bfloat16)
+    bias = torch.randn((cout,), device="cuda", generator=g) * 0.1
+    outs = []
+    for path in (0, 2):
+        y, err = osm.conv3d(x, w, bias, relu=False, path=path)
+        torch.cuda.synchronize()
+        assert err == 0
+        outs.append(y.float())
+    assert torch.isfinite(outs[0]).all() and torch.isfinite(outs[1]).all()
+    scale = outs[1].abs().max().item()
+    assert (outs[0] - outs[1]).abs().max().item() <= 2 ** -7 * scale

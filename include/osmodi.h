@@ -551,6 +551,19 @@ OSMODI_API osmodi_status osmodi_tc_gemm(const void* A_dev, const void* B_dev, fl
 OSMODI_API osmodi_status osmodi_probe_fp64(double* gflops_out, double* ms_out, void* stream);
 
 /*
+ * The FP32 <-> FP64 conversions the FP64-throughput-bound kernels (the
+ * refinement residual, the fold, the output, the float-float source) do on
+ * the integer units instead of the conversion instructions (no counterpart
+ * in the paper; a check that they are IEEE 754's): for i < n,
+ * f_out[i] = d_in[i] rounded to binary32 (to nearest, ties to even) and
+ * d_out[i] = f_in[i] as binary64 (exact).  All four are device arrays of n
+ * elements, owned by the caller.  OSMODI_E_INVALID: n < 0 or a null array
+ * with n > 0.  Asynchronous on `stream`.
+ */
+OSMODI_API osmodi_status osmodi_probe_convert(const double* d_in_dev, float* f_out_dev, const float* f_in_dev,
+                                              double* d_out_dev, int64_t n, void* stream);
+
+/*
  * Test knobs, for exercising the failure statuses without a GPU fault (no
  * counterpart in the paper).  Process-wide; every later call reads them.
  * Returns the previous value; OSMODI_DEBUG_DEFAULT restores the default.

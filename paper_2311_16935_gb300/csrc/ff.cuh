@@ -19,6 +19,8 @@
 
 #include <cuda_runtime.h>
 
+#include "fpconv.cuh"
+
 namespace osm {
 
 struct FF {
@@ -83,7 +85,8 @@ __host__ __device__ inline FF ff_from_double(double x) {
     return FF{h, (float)(x - (double)h)};
 }
 
-__device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
+// the halves widen exactly on the integer units (fpconv.cuh): one FP64 add
+__device__ __forceinline__ double ff_to_double(FF a) { return f32_to_f64(a.hi) + f32_to_f64(a.lo); }
 
 // per-thread running sum for the reductions: a pair, with the rounding error
 // of every addition carried in lo

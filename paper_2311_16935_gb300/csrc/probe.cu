@@ -7,6 +7,9 @@
 // dependency stall; the result is stored so nothing is optimised away.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
+#include "fpconv.cuh"
 #include "internal.cuh"
 
 namespace {
@@ -28,7 +31,26 @@ __global__ void __launch_bounds__(256) k_fp64_fma(int iters, double m, double c)
     if (s == 12345.678) g_probe_sink[0] = s;  // practically never true; keeps the chains live
 }
 
+// the integer-unit conversions of fpconv.cuh over caller-given inputs
+__global__ void k_convert(const double* __restrict__ d_in, float* __restrict__ f_out, const float* __restrict__ f_in,
+                          double* __restrict__ d_out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        f_out[i] = osm::f64_to_f32_rn(d_in[i]);
+        d_out[i] = osm::f32_to_f64(f_in[i]);
+    }
+}
+
 }  // namespace
+
+extern "C" osmodi_status osmodi_probe_convert(const double* d_in, float* f_out, const float* f_in, double* d_out,
+                                              int64_t n, void* stream) {
+    if (n < 0 || (n > 0 && (!d_in || !f_out || !f_in || !d_out))) return OSMODI_E_INVALID;
+    if (n == 0) return OSMODI_OK;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    k_convert<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(d_in, f_out, f_in, d_out, n);
+    OSM_CUDA(cudaGetLastError());
+    return OSMODI_OK;
+}
 
 extern "C" osmodi_status osmodi_probe_fp64(double* gflops, double* ms, void* stream) {
     if (!gflops) return OSMODI_E_INVALID;

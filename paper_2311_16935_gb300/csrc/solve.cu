@@ -130,6 +130,7 @@ __global__ void k_source(const TG* __restrict__ f, const TP* __restrict__ p_in, 
     if (grid_sum<4>(acc, partials, &sc->t_src, tot) && threadIdx.x == 0) {
         sc->bnorm2 = tot[0];
         sc->p0sum = tot[1];
+        sc->psum = tot[1];  // sum of the iterate, carried by the folds from here
         sc->bsum = tot[2];
         sc->p0nz = tot[3];
     }
@@ -157,12 +158,23 @@ __global__ void __launch_bounds__(512) k_residual_zero_start(const double* __res
 
 // ---------------------------------------------------------------------------
 // FP64 residual of the refinement loop: r = b - L p (the correction was
-// folded into p by k_fold), reductions ||r||^2, sum r, sum p.
+// folded into p by k_fold), reductions ||r||^2 and sum r; for FP64 vectors
+// also sum p.
+//
+// FP64 throughput, not memory, bounds this kernel (the conversions to and
+// from FP64 run on the same pipe), so every FP64 operation counts.  Per
+// cell: the three axis sums of the valid neighbours (3 adds), b - D_C p_C
+// (1 fma), the three axis terms (3 fma) and ||r||^2 (1 fma): 8 operations.
+// With FP32 vectors r is rounded to FP32 on the integer units (fpconv.cuh),
+// sum r is taken from that FP32 residual (the one the inner solve receives)
+// in a compensated FP32 sum, and sum p is not formed here: it is p^0's sum
+// plus every folded correction's (k_fold).
 // ---------------------------------------------------------------------------
 template <class TI, int NDIM>
 __global__ void __launch_bounds__(512) k_residual(const double* __restrict__ p_in, const double* __restrict__ b64,
                                                   TI* __restrict__ r_out, const uint8_t* __restrict__ code8,
                                                   Geo<double> g, Scalars* sc, double* partials) {
+    constexpr bool kF32 = sizeof(TI) == 4;
     __shared__ double dtab[64];  // sum of F over the faces set in a 6-bit face mask
     if (threadIdx.x < 64) {
         const unsigned f = threadIdx.x;
@@ -172,6 +184,7 @@ __global__ void __launch_bounds__(512) k_residual(const double* __restrict__ p_i
     __syncthreads();
     ChunkLoop L;
     double acc[3] = {0.0, 0.0, 0.0};
+    FFAcc a_r;
     for (int64_t base = L.base; base < g.n_chunks; base += L.stride) {
         const int64_t ch = base + L.lane;
         const bool act = ch < g.n_chunks;
@@ -192,46 +205,65 @@ __global__ void __launch_bounds__(512) k_residual(const double* __restrict__ p_i
             V4<TI> rv;
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
-                // (L p)_C = D_C p_C - sum_a F_a (sum of the valid neighbours on axis a),
-                // D_C = sum of F over the valid faces (from a table): 7 FP64
-                // operations instead of 12 (FP64 throughput bounds this kernel)
+                // r = b - (L p)_C = b - D_C p_C + sum_a F_a (sum of the valid
+                // neighbours on axis a); D_C = sum of F over the valid faces
                 const unsigned f = fm[m];
                 const double sx = ((f & 1u) ? nb.e.v[m] : 0.0) + ((f & 2u) ? nb.w.v[m] : 0.0);
                 const double sy = ((f & 4u) ? nb.n.v[m] : 0.0) + ((f & 8u) ? nb.s.v[m] : 0.0);
-                double t = g.F[0] * sx;
-                t = fma(g.F[1], sy, t);
+                double r = fma(-dtab[f], c.v[m], bv.v[m]);
                 if (NDIM == 3) {
                     const double sz = ((f & 16u) ? nb.f.v[m] : 0.0) + ((f & 32u) ? nb.b.v[m] : 0.0);
-                    t = fma(g.F[2], sz, t);
+                    r = fma(g.F[2], sz, r);
                 }
-                const double lp = fma(dtab[f], c.v[m], -t);
-                const double r = bv.v[m] - lp;
-                rv.v[m] = (TI)r;
-                acc[0] += r * r;
-                acc[1] += r;
-                acc[2] += c.v[m];
+                r = fma(g.F[1], sy, r);
+                r = fma(g.F[0], sx, r);
+                acc[0] = fma(r, r, acc[0]);
+                if constexpr (kF32) {
+                    rv.v[m] = f64_to_f32_rn(r);
+                    a_r.add(rv.v[m]);
+                } else {
+                    rv.v[m] = r;
+                    acc[1] += r;
+                    acc[2] += c.v[m];
+                }
             }
             st4(r_out + i0, rv);
         }
     }
+    if constexpr (kF32) acc[1] = a_r.value();
     double tot[3];
     if (grid_sum<3>(acc, partials, &sc->t_res, tot) && threadIdx.x == 0) {
         sc->rnorm2 = tot[0];
         sc->rsum = tot[1];
-        sc->psum = tot[2];
+        if (!kF32) sc->psum = tot[2];
     }
 }
 
 // p64 += e (the FP32 correction), in place; cells outside the valid set hold
-// e = 0
+// e = 0.  With FP32 corrections the sum of the iterate moves by the sum of e,
+// taken here in compensated FP32 arithmetic (no FP64 operation beyond the
+// fold itself); the FP64 residual then need not form it.
 template <class TI>
-__global__ void __launch_bounds__(256) k_fold(double* __restrict__ p64, const TI* __restrict__ e, int64_t n_chunks) {
+__global__ void __launch_bounds__(256) k_fold(double* __restrict__ p64, const TI* __restrict__ e, int64_t n_chunks,
+                                              Scalars* sc, double* partials) {
+    FFAcc a_e;
     for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < n_chunks; ch += (int64_t)gridDim.x * blockDim.x) {
         V4<double> pv = ld4c(p64 + ch * 4);
         const V4<TI> ev = ld4(e + ch * 4);
 #pragma unroll
-        for (int m = 0; m < 4; ++m) pv.v[m] += (double)ev.v[m];
+        for (int m = 0; m < 4; ++m) {
+            if constexpr (sizeof(TI) == 4) {
+                pv.v[m] += f32_to_f64(ev.v[m]);  // widened on the integer units
+                a_e.add(ev.v[m]);
+            } else {
+                pv.v[m] += ev.v[m];
+            }
+        }
         st4(p64 + ch * 4, pv);
+    }
+    if constexpr (sizeof(TI) == 4) {
+        double acc[1] = {a_e.value()}, tot[1];
+        if (grid_sum<1>(acc, partials, &sc->t_misc, tot) && threadIdx.x == 0) sc->psum += tot[0];
     }
 }
 
@@ -341,6 +373,7 @@ __global__ void k_source_ff(const TG* __restrict__ f, const TP* __restrict__ p_i
     if (grid_sum<4>(acc, partials, &sc->t_src, tot) && threadIdx.x == 0) {
         sc->bnorm2 = tot[0];
         sc->p0sum = tot[1];
+        sc->psum = tot[1];  // sum of the iterate, carried by the folds from here
         sc->bsum = tot[2];
         sc->p0nz = tot[3];
     }
@@ -424,6 +457,7 @@ __global__ void k_source_mixed(const float* __restrict__ f, const TP* __restrict
     if (grid_sum<4>(acc, partials, &sc->t_src, tot) && threadIdx.x == 0) {
         sc->bnorm2 = tot[0];
         sc->p0sum = tot[1];
+        sc->psum = tot[1];  // sum of the iterate, carried by the folds from here
         sc->bsum = tot[2];
         sc->p0nz = tot[3];
     }
@@ -1615,19 +1649,30 @@ __global__ void __launch_bounds__(256) k_aa_mix(AaArgs<T> a, T* x_out, T* xs_out
 
 // ---------------------------------------------------------------------------
 // output: subtract each component's mean, NaN on missing cells, dense layout;
-// also ||P0 - P|| and ||P|| (both gauge-fixed) for the seed distance.
+// also ||P0 - P|| and ||P|| (both gauge-fixed) for the seed distance.  FP64
+// throughput bounds it: the subtraction and ||P||^2 are its only FP64
+// operations per cell for a zero start (ZERO0: P^0 is not read and
+// ||P0 - P|| = ||P||); an FP32 output is rounded on the integer units.
 // ---------------------------------------------------------------------------
-template <class TP>
+template <class TP, bool ZERO0>
 __global__ void k_output(const double* __restrict__ p64, const uint8_t* __restrict__ code8, const int32_t* __restrict__ label,
                          const double* __restrict__ comp_p, const double* __restrict__ comp_p0,
                          const double* __restrict__ comp_cnt, int multi, TP* __restrict__ p_user, int64_t px, int64_t nx,
-                         int64_t n_box, Scalars* sc, double* partials, int zero0 = 0) {
+                         int64_t n_box, Scalars* sc, double* partials) {
     const double m1 = multi ? 0.0 : sc->psum / comp_cnt[0];
     const double m01 = multi ? 0.0 : sc->p0sum / comp_cnt[0];
     double acc[2] = {0.0, 0.0};
+    const bool i32 = n_box < (int64_t)(1u << 31);
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n_box; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = idx / px;
-        const int64_t i = idx - row * px;
+        int64_t row, i;
+        if (i32) {
+            const uint32_t r32 = (uint32_t)idx / (uint32_t)px;
+            row = r32;
+            i = (uint32_t)idx - r32 * (uint32_t)px;
+        } else {
+            row = idx / px;
+            i = idx - row * px;
+        }
         if (i >= nx) continue;
         const int64_t d = row * nx + i;
         if (!(code8[idx] & 0x80u)) {
@@ -1641,14 +1686,19 @@ __global__ void k_output(const double* __restrict__ p64, const uint8_t* __restri
             m0 = comp_p0[l] / comp_cnt[l];
         }
         const double v = p64[idx] - m;
-        const double v0 = zero0 ? 0.0 : (double)p_user[d] - m0;  // zero start: P^0 is not read
-        acc[0] += (v0 - v) * (v0 - v);
-        acc[1] += v * v;
-        p_user[d] = (TP)v;
+        acc[1] = fma(v, v, acc[1]);
+        if (!ZERO0) {
+            double v0;
+            if constexpr (sizeof(TP) == 4) v0 = f32_to_f64(p_user[d]) - m0;
+            else v0 = p_user[d] - m0;
+            acc[0] = fma(v0 - v, v0 - v, acc[0]);
+        }
+        if constexpr (sizeof(TP) == 4) p_user[d] = f64_to_f32_rn(v);
+        else p_user[d] = v;
     }
     double tot[2];
     if (grid_sum<2>(acc, partials, &sc->t_out, tot) && threadIdx.x == 0) {
-        sc->dist2 = tot[0];
+        sc->dist2 = ZERO0 ? tot[1] : tot[0];
         sc->pnorm2 = tot[1];
     }
 }
@@ -2503,6 +2553,7 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
         // S = 0: the answer is a constant on every component; P = 0 after the gauge
         k_fill_zero_f64<<<G, TH, 0, s>>>(cur, p->n_box);
         OSM_CUDA(cudaGetLastError());
+        OSM_CUDA(cudaMemsetAsync(&b.sc->psum, 0, sizeof(double), s));
         OSM_TRY(launch_residual<T>(p, b, cur, rtarget, s, prof, ff));
         p->launches += 2;
         residual_evals++;
@@ -2660,7 +2711,8 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
                 k_fold_ff<<<one_wave(p, k_fold_ff, p->n_chunks), 256, 0, s>>>(
                     reinterpret_cast<float*>(cur), reinterpret_cast<const float*>(b.x), p->n_chunks, p->n_box);
             else
-                k_fold<T><<<one_wave(p, k_fold<T>, p->n_chunks), 256, 0, s>>>(cur, b.x, p->n_chunks);
+                k_fold<T><<<one_wave(p, k_fold<T>, p->n_chunks), 256, 0, s>>>(cur, b.x, p->n_chunks, b.sc,
+                                                                   b.partials + kSlotRes * kMaxBlocks);
             OSM_CUDA(cudaGetLastError());
             OSM_TRY(launch_residual<T>(p, b, cur, rtarget, s, prof, ff));
             p->launches += 2;
@@ -2699,14 +2751,18 @@ static osmodi_status solve_impl(osmodi_plan p, const void* grad, int gdt, void* 
         OSM_CUDA(cudaGetLastError());
         p->launches += 1;
     } else {
-        if (pdt == OSMODI_F32)
-            k_output<float><<<one_wave(p, k_output<float>, p->n_box), 256, 0, s>>>(cur, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0,
-                                               (float*)pu, p->px, p->nx, p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks,
-                                               zero0);
-        else
-            k_output<double><<<one_wave(p, k_output<double>, p->n_box), 256, 0, s>>>(cur, p->code8, p->label, comp_p, comp_p0, p->comp_count, multi ? 1 : 0,
-                                                (double*)pu, p->px, p->nx, p->n_box, b.sc, b.partials + kSlotMisc * kMaxBlocks,
-                                                zero0);
+        auto out = [&](auto kern, auto* dst) {
+            kern<<<one_wave(p, kern, p->n_box), 256, 0, s>>>(cur, p->code8, p->label, comp_p, comp_p0, p->comp_count,
+                                                             multi ? 1 : 0, dst, p->px, p->nx, p->n_box, b.sc,
+                                                             b.partials + kSlotMisc * kMaxBlocks);
+        };
+        if (pdt == OSMODI_F32) {
+            if (zero0) out(k_output<float, true>, (float*)pu);
+            else out(k_output<float, false>, (float*)pu);
+        } else {
+            if (zero0) out(k_output<double, true>, (double*)pu);
+            else out(k_output<double, false>, (double*)pu);
+        }
         OSM_CUDA(cudaGetLastError());
         p->launches += 1;
     }

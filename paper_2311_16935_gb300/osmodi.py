@@ -95,6 +95,8 @@ _SIGS = {
     "osmodi_history_pressure": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "osmodi_debug_set": (ctypes.c_longlong, [ctypes.c_int, ctypes.c_longlong]),
     "osmodi_probe_fp64": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "osmodi_probe_convert": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int64, ctypes.c_void_p]),
     "osmodi_net_status": (ctypes.c_int, [ctypes.c_void_p]),
     "osmodi_conv3d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -688,6 +690,22 @@ def probe_fp64(stream=None):
     if st != OK:
         raise OsmodiError(st, "osmodi_probe_fp64")
     return g.value
+
+
+def probe_convert(d_in: torch.Tensor, f_in: torch.Tensor, stream=None):
+    """osmodi_probe_convert: (d_in rounded to FP32, f_in widened to FP64) by
+    the library's integer-unit conversions; 1-D CUDA tensors of one length."""
+    _check_cuda(d_in, "d_in")
+    _check_cuda(f_in, "f_in")
+    if d_in.dtype != torch.float64 or f_in.dtype != torch.float32 or d_in.dim() != 1 or f_in.shape != d_in.shape:
+        raise TypeError("d_in: 1-D float64, f_in: float32 of the same length")
+    f_out = torch.empty_like(f_in)
+    d_out = torch.empty_like(d_in)
+    st = lib().osmodi_probe_convert(d_in.data_ptr(), f_out.data_ptr(), f_in.data_ptr(), d_out.data_ptr(), d_in.numel(),
+                                    _stream_ptr(stream))
+    if st != OK:
+        raise OsmodiError(st, "osmodi_probe_convert")
+    return f_out, d_out
 
 
 def tc_gemm(A: torch.Tensor, B: torch.Tensor, stream=None):

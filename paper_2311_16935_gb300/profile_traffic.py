@@ -24,7 +24,7 @@ import re
 from collections import defaultdict
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-KERNEL_SOURCES = ("solve.cu", "mg.cu", "mg.cuh", "cg_state.cuh", "stencil.cuh", "internal.cuh", "ff.cuh")
+KERNEL_SOURCES = ("solve.cu", "mg.cu", "mg.cuh", "cg_state.cuh", "stencil.cuh", "internal.cuh", "ff.cuh", "fpconv.cuh")
 METRICS = ("dram__bytes_read.sum", "dram__bytes_write.sum")
 
 

@@ -596,6 +596,12 @@ OSMODI_API osmodi_status osmodi_probe_convert(const double* d_in_dev, float* f_o
  *   coarse levels of at most this many cells (and the ones below them)
  *   inside one block per instance, the larger ones as grid-wide passes; the
  *   same V-cycle either way.  Default (0): 4096.
+ * OSMODI_DEBUG_CG_FIXED_GRAPH: how osmodi_solve's captured CG runs, the same
+ *   kernels in the same order, for comparisons: 0 (default) one graph per
+ *   CG segment holding a device-side loop (a conditional while node) that
+ *   stops at convergence; 1 graphs of check_every iterations relaunched by
+ *   the host until the device reports convergence (iterations past it
+ *   launch kernels that return at once).
  */
 #define OSMODI_DEBUG_BARRIER_SPINS 1
 #define OSMODI_DEBUG_SKIP_BARRIER_BLOCK 2
@@ -603,6 +609,7 @@ OSMODI_API osmodi_status osmodi_probe_convert(const double* d_in_dev, float* f_o
 #define OSMODI_DEBUG_MG_UNFUSED 4
 #define OSMODI_DEBUG_NET_WMMA 5
 #define OSMODI_DEBUG_BATCH_BOTTOM_CELLS 6
+#define OSMODI_DEBUG_CG_FIXED_GRAPH 7
 #define OSMODI_DEBUG_DEFAULT (-0x7fffffffffffffffLL)
 OSMODI_API long long osmodi_debug_set(int knob, long long value);
 

@@ -16,7 +16,7 @@ struct CgState {
     int precond;       // 1: z = B r by the multigrid preconditioner before every direction update
     int pending;       // preconditioned CG: the segment's first (r, z) is still to be formed
     int keep;          // ... and the previous search direction is kept (reliable-update continuation)
-    int pad;
+    int loops;         // bodies run by the device-side CG loop in this graph launch
     unsigned ticketA, ticketB, ticketI, ticketM;
 };
 

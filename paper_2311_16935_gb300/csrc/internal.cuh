@@ -55,7 +55,7 @@ struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     const void* key_ws = nullptr;
     int key_kind = -1;
-    int key_len = 0;
+    int key_len = 0;  // iterations per launch; 0: the device-side loop
 };
 
 struct Launch {
@@ -90,6 +90,7 @@ struct osmodi_plan_s {
     double* comp_count = nullptr; // n_comp valid-cell counts (device)
     osm::Launch launch;
     osm::GraphCache graphs[4];
+    bool cg_loop_failed = false;  // the device-side CG loop graph could not be built: fixed chunks
     std::vector<double> history;    // OUTER: eps_R per residual evaluation
     std::vector<double> history_p;  // OUTER: eps_P at the same evaluations (NaN where undefined)
     void* pinned = nullptr;  // 4 KB page-locked host mirror of the device scalars

@@ -1395,7 +1395,7 @@ __device__ __forceinline__ float cnt_f(uint32_t w, int shift) { return (float)((
 // VEC (FP32, even rows): a pair's two cells are one aligned 8-byte word, so
 // its z, r and count words move in one load each
 template <class T, int FC, bool FROM_ZERO, bool VEC = false>
-__global__ void __launch_bounds__(kCbX * kCbY) k_mg_coarse_rb_fused(const T* __restrict__ zin, T* __restrict__ zout,
+__global__ void __launch_bounds__(kCbX * kCbY, 4) k_mg_coarse_rb_fused(const T* __restrict__ zin, T* __restrict__ zout,
                                                                   const T* __restrict__ r, Level lv, T omega,
                                                                   CbArgs g, const CgState* st) {
     constexpr int NT = kCbX * kCbY;
@@ -1458,7 +1458,19 @@ __global__ void __launch_bounds__(kCbX * kCbY) k_mg_coarse_rb_fused(const T* __r
         struct Wv {
             T xp, xm, yp, ym, zp, zm, wd, r;
         };
-        auto first = [&](int q, Wv& wv) {
+        // a count word's field as a weight: count x F.  The count becomes a
+        // float exactly by setting it into the fraction of 2^23 and removing
+        // 2^23 in the same fma (one rounding, as in count * F)
+        const float F0f = (float)F0, F1f = (float)F1, F2f = (float)F2;
+        const float B0 = -8388608.0f * F0f, B1 = -8388608.0f * F1f, B2 = -8388608.0f * F2f;
+        auto wgt = [&](uint32_t w, int shift, float Fa, float Ba) -> T {
+            return (T)fmaf(Fa, __uint_as_float(0x4B000000u | ((w >> shift) & 1023u)), Ba);
+        };
+        // which cell of the pair has colour FC on plane q is uniform over a
+        // warp (one warp = one row) and known at compile time inside each
+        // instantiation: U1 = the pair's cell 1
+        auto first_t = [&](auto U1c, int q, Wv& wv) {
+            constexpr bool u1 = decltype(U1c)::value;
             T o0 = T(0), o1 = T(0);
             wv = Wv{T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
             const bool qin = q >= 0 && q < g.nz;
@@ -1480,18 +1492,16 @@ __global__ void __launch_bounds__(kCbX * kCbY) k_mg_coarse_rb_fused(const T* __r
                 r1 = qin && in1 ? r[qo + c1] : T(0);
             }
             // weights of both cells
-            const T xp0 = (T)(cnt_f(w0, 0) * (float)F0), xp1 = (T)(cnt_f(w1, 0) * (float)F0);
-            const T xm0 = (T)(cnt_f(wx0, 0) * (float)F0), xm1 = xp0;
-            const T yp0 = (T)(cnt_f(w0, 10) * (float)F1), yp1 = (T)(cnt_f(w1, 10) * (float)F1);
-            const T ym0 = (T)(cnt_f(wy0, 10) * (float)F1), ym1 = (T)(cnt_f(wy1, 10) * (float)F1);
-            const T zp0 = (T)(cnt_f(w0, 20) * (float)F2), zp1 = (T)(cnt_f(w1, 20) * (float)F2);
-            const T zm0 = (T)(cnt_f(wz0, 20) * (float)F2), zm1 = (T)(cnt_f(wz1, 20) * (float)F2);
+            const T xp0 = wgt(w0, 0, F0f, B0), xp1 = wgt(w1, 0, F0f, B0);
+            const T xm0 = wgt(wx0, 0, F0f, B0), xm1 = xp0;
+            const T yp0 = wgt(w0, 10, F1f, B1), yp1 = wgt(w1, 10, F1f, B1);
+            const T ym0 = wgt(wy0, 10, F1f, B1), ym1 = wgt(wy1, 10, F1f, B1);
+            const T zp0 = wgt(w0, 20, F2f, B2), zp1 = wgt(w1, 20, F2f, B2);
+            const T zm0 = wgt(wz0, 20, F2f, B2), zm1 = wgt(wz1, 20, F2f, B2);
             const T d0 = xp0 + xm0 + yp0 + ym0 + zp0 + zm0, d1 = xp1 + xm1 + yp1 + ym1 + zp1 + zm1;
             const T wd0 = d0 > T(0) ? omega * recip(d0) : T(0), wd1 = d1 > T(0) ? omega * recip(d1) : T(0);
             wz0 = w0;
             wz1 = w1;
-            // which cell of the pair has colour FC on this plane
-            const bool u1 = ((FC ^ (j + q)) & 1) != 0;
             if (qin) {
                 if (FROM_ZERO) {
                     o0 = u1 ? T(0) : wd0 * r0;
@@ -1537,6 +1547,32 @@ __global__ void __launch_bounds__(kCbX * kCbY) k_mg_coarse_rb_fused(const T* __r
             ring[q & 3][0][t] = in0 ? o0 : T(0);
             ring[q & 3][1][t] = in1 ? o1 : T(0);
         };
+        auto first = [&](int q, Wv& wv) {
+            if (((FC ^ (j + q)) & 1) != 0) first_t(std::true_type{}, q, wv);
+            else first_t(std::false_type{}, q, wv);
+        };
+        // the cell of the other colour on plane k (V1: it is cell 1), from the ring
+        auto second_t = [&](auto V1c, int k, const Wv& w) {
+            constexpr bool v1 = decltype(V1c)::value;
+            constexpr int cv = v1 ? 1 : 0;
+            const T zc = ring[k & 3][cv][t];
+            const T ex = v1 ? ring[k & 3][0][t + 1] : ring[k & 3][1][t];
+            const T wx = v1 ? ring[k & 3][0][t] : ring[k & 3][1][t - 1];
+            const T zn = ring[k & 3][cv][t + kCbX], zs = ring[k & 3][cv][t - kCbX];
+            const T zf = ring[(k + 1) & 3][cv][t], zb = ring[(k + 3) & 3][cv][t];
+            const T az = w.xp * (zc - ex) + w.xm * (zc - wx) + w.yp * (zc - zn) + w.ym * (zc - zs) +
+                         w.zp * (zc - zf) + w.zm * (zc - zb);
+            const T nv = zc + w.wd * (w.r - az);
+            const T other = ring[k & 3][1 - cv][t];
+            const int64_t qo = (int64_t)k * sz;
+            const T out0 = v1 ? other : nv, out1 = v1 ? nv : other;
+            if (VEC) {
+                if (in0) *reinterpret_cast<float2*>(zout + qo + c0) = make_float2((float)out0, (float)out1);
+            } else {
+                if (in0) zout[qo + c0] = out0;
+                if (in1) zout[qo + c1] = out1;
+            }
+        };
         Wv w_cur, w_nxt;
         first(k0 - 1, w_nxt);  // plane -1 (k0 = 0) writes zeros
         first(k0, w_cur);
@@ -1544,22 +1580,8 @@ __global__ void __launch_bounds__(kCbX * kCbY) k_mg_coarse_rb_fused(const T* __r
             first(k + 1, w_nxt);
             __syncthreads();
             if (interior) {
-                // the cell of the other colour on plane k
-                const bool v1 = ((FC ^ (j + k)) & 1) == 0;  // the other cell is cell 1
-                const int cv = v1 ? 1 : 0;
-                const T zc = ring[k & 3][cv][t];
-                const T ex = v1 ? ring[k & 3][0][t + 1] : ring[k & 3][1][t];
-                const T wx = v1 ? ring[k & 3][0][t] : ring[k & 3][1][t - 1];
-                const T zn = ring[k & 3][cv][t + kCbX], zs = ring[k & 3][cv][t - kCbX];
-                const T zf = ring[(k + 1) & 3][cv][t], zb = ring[(k + 3) & 3][cv][t];
-                const Wv& w = w_cur;
-                const T az = w.xp * (zc - ex) + w.xm * (zc - wx) + w.yp * (zc - zn) + w.ym * (zc - zs) +
-                             w.zp * (zc - zf) + w.zm * (zc - zb);
-                const T nv = zc + w.wd * (w.r - az);
-                const T other = ring[k & 3][1 - cv][t];
-                const int64_t qo = (int64_t)k * sz;
-                if (in0) zout[qo + c0] = v1 ? other : nv;
-                if (in1) zout[qo + c1] = v1 ? nv : other;
+                if (((FC ^ (j + k)) & 1) == 0) second_t(std::true_type{}, k, w_cur);
+                else second_t(std::false_type{}, k, w_cur);
             }
             w_cur = w_nxt;
         }
@@ -1747,9 +1769,27 @@ int wave_grid(osmodi_plan p, K kernel, int bps, int64_t work256) {
 // one-chunk / one-row halo ring, interior 14 x 14 chunks
 constexpr int kRbCX = 16, kRbRY = 16;
 
-// Work items of the fused sweep: every tile of a plane times slabs of planes,
-// the slab chosen so that each resident block gets about eight items (each
-// slab recomputes one extra plane of the first colour)
+// The slab depth (planes per work item) of a z-marching sweep that
+// minimises the plane steps the busiest resident block runs: items = tiles x
+// ceil(nz / slab) spread over `slots` resident blocks, each item slab +
+// `extra` steps (the planes of the first colour a slab recomputes); ties go
+// to the deeper slab (less recomputation)
+int best_slab(long long tiles, int nz, long long slots, int extra, int min_slab) {
+    long long best_steps = -1;
+    int best = nz;
+    for (int sl = std::max(1, std::min(min_slab, nz)); sl <= nz; ++sl) {
+        const long long items = tiles * ((nz + sl - 1) / sl);
+        const long long steps = ((items + slots - 1) / slots) * (sl + extra);
+        if (best_steps < 0 || steps <= best_steps) {
+            best_steps = steps;
+            best = sl;
+        }
+    }
+    return best;
+}
+
+// Work items of the fused sweep: every tile of a plane times slabs of planes
+// (each slab recomputes one extra plane of the first colour)
 RbArgs rb_args(osmodi_plan p) {
     RbArgs a;
     a.px = p->px;
@@ -1763,9 +1803,7 @@ RbArgs rb_args(osmodi_plan p) {
     a.omega = kOmegaRB;
     static const int bps = blocks_per_sm(k_mg_fine_rb_fused<float, kRbCX, kRbRY, 0, false, false>);
     const long long tiles = (long long)a.tiles_x * a.tiles_y;
-    const long long want = 8LL * p->num_sms * bps;
-    const long long slabs = std::max<long long>(1, std::min<long long>(a.nz, (want + tiles - 1) / tiles));
-    a.slab = std::max(8, (int)((a.nz + slabs - 1) / slabs));
+    a.slab = best_slab(tiles, a.nz, (long long)p->num_sms * bps, 1, 8);
     a.n_items = tiles * ((a.nz + a.slab - 1) / a.slab);
     return a;
 }
@@ -1902,11 +1940,9 @@ T* vcycle_body(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, cud
         cb.tiles_y = (cb.ny + kCbY - 3) / (kCbY - 2);
         static const int bps = blocks_per_sm(k_mg_coarse_rb_fused<T, 0, false>);
         const long long tiles = (long long)cb.tiles_x * cb.tiles_y;
-        // about four items per resident block (every slab recomputes two planes
-        // of the first colour; fewer, deeper slabs leave a longer tail)
-        const long long want = 4LL * p->num_sms * bps;
-        const long long slabs = std::max<long long>(1, std::min<long long>(cb.nz, (want + tiles - 1) / tiles));
-        cb.slab = std::max(8, (int)((cb.nz + slabs - 1) / slabs));
+        // every slab recomputes two planes of the first colour; on the small
+        // levels thin slabs shorten each block's chain of dependent plane steps
+        cb.slab = best_slab(tiles, cb.nz, (long long)p->num_sms * bps, 2, 1);
         cb.n_items = tiles * ((cb.nz + cb.slab - 1) / cb.slab);
         const int gf = (int)std::max<long long>(1, std::min<long long>(cb.n_items, (long long)p->num_sms * bps));
         const T om = (T)kOmegaRB;

@@ -553,14 +553,14 @@ extern "C" int osmodi_history(osmodi_plan p, double* out, int cap) {
 
 namespace osm {
 namespace {
-std::atomic<long long> g_knobs[7] = {{0}, {0}, {-1}, {0}, {0}, {0}, {0}};
+std::atomic<long long> g_knobs[8] = {{0}, {0}, {-1}, {0}, {0}, {0}, {0}, {0}};
 long long knob_default(int k) { return k == OSMODI_DEBUG_SKIP_BARRIER_BLOCK ? -1 : 0; }
 }  // namespace
-long long debug_knob(int knob) { return knob >= 1 && knob <= 6 ? g_knobs[knob].load() : 0; }
+long long debug_knob(int knob) { return knob >= 1 && knob <= 7 ? g_knobs[knob].load() : 0; }
 }  // namespace osm
 
 extern "C" long long osmodi_debug_set(int knob, long long value) {
-    if (knob < 1 || knob > 6) return 0;
+    if (knob < 1 || knob > 7) return 0;
     if (value == OSMODI_DEBUG_DEFAULT) value = osm::knob_default(knob);
     return osm::g_knobs[knob].exchange(value);
 }

@@ -2177,6 +2177,70 @@ static osmodi_status run_cg_direct(osmodi_plan p, const Buffers<T>& b, int op, c
     return hm->st.err ? OSMODI_E_TIMEOUT : OSMODI_OK;
 }
 
+// The end of one body of the device-side CG loop: go on while the segment
+// is not finished, for at most `cap` bodies per graph launch (the host
+// launches the graph again when the cap ran out first, so the loop ends
+// however the device state evolves).
+__global__ void k_cg_continue(cudaGraphConditionalHandle h, CgState* st, int cap) {
+    if (threadIdx.x == 0) {
+        const int n = ++st->loops;
+        cudaGraphSetConditional(h, (st->status != kFinished && n < cap) ? 1u : 0u);
+    }
+}
+
+constexpr int kCgLoopCap = 64;  // bodies (of two iterations) per graph launch
+
+// One graph per CG segment: the loop counter cleared, then a conditional
+// while node whose body is two iterations (the direction buffers alternate)
+// and k_cg_continue.  A converged segment stops within the body it
+// converged in or the next one, where fixed-length graphs launch up to
+// check_every - 1 iterations of kernels that return at once.
+template <class T>
+static cudaError_t build_cg_loop(osmodi_plan p, const Buffers<T>& b, int op, cudaGraphExec_t* out) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) return e;
+    cudaStream_t cap = nullptr;
+    auto fail = [&](cudaError_t err) {
+        if (cap) cudaStreamDestroy(cap);
+        cudaGraphDestroy(graph);
+        return err;
+    };
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, graph, 1u, cudaGraphCondAssignDefault)) != cudaSuccess) return fail(e);
+    cudaMemsetParams ms{};
+    ms.dst = &b.st->loops;
+    ms.value = 0;
+    ms.elementSize = 4;
+    ms.width = 1;
+    ms.height = 1;
+    cudaGraphNode_t n_clear, n_loop;
+    if ((e = cudaGraphAddMemsetNode(&n_clear, graph, nullptr, 0, &ms)) != cudaSuccess) return fail(e);
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&n_loop, graph, &n_clear, nullptr, 1, &cp)) != cudaSuccess) return fail(e);
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+        return fail(e);
+    const osmodi_status st = launch_cg_iters<T>(p, b, op, 2, cap);
+    k_cg_continue<<<1, 32, 0, cap>>>(h, b.st, kCgLoopCap);
+    const cudaError_t e_launch = cudaGetLastError();
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cap, &captured);
+    if (e == cudaSuccess && (st != OSMODI_OK || e_launch != cudaSuccess)) e = cudaErrorInvalidValue;
+    if (e != cudaSuccess) return fail(e);
+    cudaStreamDestroy(cap);
+    cap = nullptr;
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    return e;
+}
+
 template <class T>
 static osmodi_status run_cg(osmodi_plan p, const Buffers<T>& b, int op, void* ws, cudaStream_t s, HostMirror* hm,
                             long long* iters_out, bool noalloc) {
@@ -2184,8 +2248,25 @@ static osmodi_status run_cg(osmodi_plan p, const Buffers<T>& b, int op, void* ws
     if (p->opt.profile) return run_cg_profiled<T>(p, b, op, s, hm, iters_out);
     const int kind = (sizeof(T) == 8 ? 2 : 0) + op;
     GraphCache& gc = p->graphs[kind];
-    const int len = p->opt.check_every;
-    if (!gc.exec || gc.key_ws != ws || gc.key_len != len) {
+    // the device-side loop unless the comparison knob asks for fixed chunks
+    // or the loop graph could not be built on this device
+    const int len = (debug_knob(OSMODI_DEBUG_CG_FIXED_GRAPH) || p->cg_loop_failed) ? p->opt.check_every : 0;
+    if (len == 0 && (!gc.exec || gc.key_ws != ws || gc.key_len != 0)) {
+        if (gc.exec) {
+            cudaGraphExecDestroy(gc.exec);
+            gc.exec = nullptr;
+        }
+        if (build_cg_loop<T>(p, b, op, &gc.exec) == cudaSuccess) {
+            gc.key_ws = ws;
+            gc.key_len = 0;
+        } else {
+            cudaGetLastError();
+            gc.exec = nullptr;
+            p->cg_loop_failed = true;
+            return run_cg<T>(p, b, op, ws, s, hm, iters_out, noalloc);
+        }
+    }
+    if (len > 0 && (!gc.exec || gc.key_ws != ws || gc.key_len != len)) {
         if (gc.exec) {
             cudaGraphExecDestroy(gc.exec);
             gc.exec = nullptr;
@@ -2219,9 +2300,11 @@ static osmodi_status run_cg(osmodi_plan p, const Buffers<T>& b, int op, void* ws
     }
     for (;;) {
         OSM_CUDA(cudaGraphLaunch(gc.exec, s));
-        p->launches += len * launches_per_iter(p, b, op);
         OSM_CUDA(cudaMemcpyAsync(&hm->st, b.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
         OSM_CUDA(cudaStreamSynchronize(s));
+        // launches: every iteration of a fixed chunk; the loop's bodies
+        p->launches += len > 0 ? len * launches_per_iter(p, b, op)
+                               : hm->st.loops * (2 * launches_per_iter(p, b, op) + 1);
         if (hm->st.status == kFinished) break;
     }
     *iters_out = hm->st.it;

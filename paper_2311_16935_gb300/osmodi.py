@@ -24,6 +24,7 @@ FP64, FP32, FP32_REFINE = 0, 1, 2
 FPCG, OUTER = 0, 1
 DEBUG_BARRIER_SPINS, DEBUG_SKIP_BARRIER_BLOCK, DEBUG_CORRECTION_SCALE, DEBUG_MG_UNFUSED, DEBUG_NET_WMMA = 1, 2, 3, 4, 5
 DEBUG_BATCH_BOTTOM_CELLS = 6
+DEBUG_CG_FIXED_GRAPH = 7
 DEBUG_DEFAULT = -0x7fffffffffffffff
 INNER_CG, INNER_JACOBI = 0, 1
 

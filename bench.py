@@ -381,10 +381,9 @@ def main():
     kb_avg = kb_ms / max(kb_n, 1)
     r64_avg = r64_ms / max(r64_n, 1)
     # FP64 refinement residual r = b - L P: bounded by min(HBM, FP64).  Per
-    # cell: read P, b (2 x 8 B) + code (1 B), write r (4 B) = 21 B, and 11 FP64
-    # instructions (3 neighbour sums, F_x s_x, two FMAs for F_y s_y, F_z s_z,
-    # the FMA D p - t, b - Lp, the FP32 conversion, r^2 into the sum and the
-    # sums of r and P), of which 4 are fused multiply-adds: 15 FP64 flops
+    # cell: read P, b (2 x 8 B) + code (1 B), write r (4 B) = 21 B, and 8 FP64
+    # instructions (3 neighbour sums; b - D p and the three axis terms as
+    # fused multiply-adds; r^2 into the sum): 13 FP64 flops
     try:
         fp64_gflops = osm.probe_fp64()
     except Exception:

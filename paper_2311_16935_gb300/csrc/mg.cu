@@ -378,11 +378,12 @@ struct RbArgs {
     float omega;
 };
 
-template <class T, int CX, int RY, int FC, bool FROM_ZERO, bool DOT, bool PF = false>
-__global__ void __launch_bounds__(CX * RY, sizeof(T) == 4 ? (PF ? 3 : 4) : 2) k_mg_fine_rb_fused(const T* __restrict__ zin, T* __restrict__ zout,
+template <class T, int CX, int RY, int FC, bool FROM_ZERO, bool DOT, int VAR = 0>
+__global__ void __launch_bounds__(CX * RY, sizeof(T) == 4 ? (VAR == 1 ? 3 : VAR == 2 ? 5 : 4) : 2) k_mg_fine_rb_fused(const T* __restrict__ zin, T* __restrict__ zout,
                                                              const T* __restrict__ r,
                                                              const uint8_t* __restrict__ code8, RbArgs g,
                                                              CgState* st, double* partials) {
+    constexpr bool PF = VAR == 1;  // VAR 1: operands loaded a step ahead; 2: plain, 5 blocks per SM
     static_assert(CX == 16 && RY % 2 == 0 && RY / 2 == CX * RY / 32, "a warp holds rows w and w + RY / 2");
     constexpr int NT = CX * RY;
     if (st->status != kRunning) return;
@@ -1458,14 +1459,9 @@ __global__ void __launch_bounds__(kCbX * kCbY, 4) k_mg_coarse_rb_fused(const T* 
         struct Wv {
             T xp, xm, yp, ym, zp, zm, wd, r;
         };
-        // a count word's field as a weight: count x F.  The count becomes a
-        // float exactly by setting it into the fraction of 2^23 and removing
-        // 2^23 in the same fma (one rounding, as in count * F)
+        // a count word's field as a weight: count x F
         const float F0f = (float)F0, F1f = (float)F1, F2f = (float)F2;
-        const float B0 = -8388608.0f * F0f, B1 = -8388608.0f * F1f, B2 = -8388608.0f * F2f;
-        auto wgt = [&](uint32_t w, int shift, float Fa, float Ba) -> T {
-            return (T)fmaf(Fa, __uint_as_float(0x4B000000u | ((w >> shift) & 1023u)), Ba);
-        };
+        auto wgt = [&](uint32_t w, int shift, float Fa) -> T { return (T)(cnt_f(w, shift) * Fa); };
         // which cell of the pair has colour FC on plane q is uniform over a
         // warp (one warp = one row) and known at compile time inside each
         // instantiation: U1 = the pair's cell 1
@@ -1492,12 +1488,12 @@ __global__ void __launch_bounds__(kCbX * kCbY, 4) k_mg_coarse_rb_fused(const T* 
                 r1 = qin && in1 ? r[qo + c1] : T(0);
             }
             // weights of both cells
-            const T xp0 = wgt(w0, 0, F0f, B0), xp1 = wgt(w1, 0, F0f, B0);
-            const T xm0 = wgt(wx0, 0, F0f, B0), xm1 = xp0;
-            const T yp0 = wgt(w0, 10, F1f, B1), yp1 = wgt(w1, 10, F1f, B1);
-            const T ym0 = wgt(wy0, 10, F1f, B1), ym1 = wgt(wy1, 10, F1f, B1);
-            const T zp0 = wgt(w0, 20, F2f, B2), zp1 = wgt(w1, 20, F2f, B2);
-            const T zm0 = wgt(wz0, 20, F2f, B2), zm1 = wgt(wz1, 20, F2f, B2);
+            const T xp0 = wgt(w0, 0, F0f), xp1 = wgt(w1, 0, F0f);
+            const T xm0 = wgt(wx0, 0, F0f), xm1 = xp0;
+            const T yp0 = wgt(w0, 10, F1f), yp1 = wgt(w1, 10, F1f);
+            const T ym0 = wgt(wy0, 10, F1f), ym1 = wgt(wy1, 10, F1f);
+            const T zp0 = wgt(w0, 20, F2f), zp1 = wgt(w1, 20, F2f);
+            const T zm0 = wgt(wz0, 20, F2f), zm1 = wgt(wz1, 20, F2f);
             const T d0 = xp0 + xm0 + yp0 + ym0 + zp0 + zm0, d1 = xp1 + xm1 + yp1 + ym1 + zp1 + zm1;
             const T wd0 = d0 > T(0) ? omega * recip(d0) : T(0), wd1 = d1 > T(0) ? omega * recip(d1) : T(0);
             wz0 = w0;
@@ -1790,7 +1786,7 @@ int best_slab(long long tiles, int nz, long long slots, int extra, int min_slab)
 
 // Work items of the fused sweep: every tile of a plane times slabs of planes
 // (each slab recomputes one extra plane of the first colour)
-RbArgs rb_args(osmodi_plan p) {
+RbArgs rb_args(osmodi_plan p, int bps) {
     RbArgs a;
     a.px = p->px;
     a.plane = p->px * p->ny;
@@ -1801,7 +1797,6 @@ RbArgs rb_args(osmodi_plan p) {
     a.tiles_y = (a.ny + kRbRY - 3) / (kRbRY - 2);
     for (int q = 0; q < 3; ++q) a.F[q] = (float)p->k.F[q];
     a.omega = kOmegaRB;
-    static const int bps = blocks_per_sm(k_mg_fine_rb_fused<float, kRbCX, kRbRY, 0, false, false>);
     const long long tiles = (long long)a.tiles_x * a.tiles_y;
     a.slab = best_slab(tiles, a.nz, (long long)p->num_sms * bps, 1, 8);
     a.n_items = tiles * ((a.nz + a.slab - 1) / a.slab);
@@ -1857,9 +1852,15 @@ RbMaps* rb_maps(osmodi_plan p, const float* zA, const float* zB, const float* r)
     return m->ok ? m : nullptr;
 }
 
-template <class T, bool PF = false>
+template <class T, int VAR = 0>
+int rb_bps() {
+    static const int bps = blocks_per_sm(k_mg_fine_rb_fused<T, kRbCX, kRbRY, 0, false, false, VAR>);
+    return bps;
+}
+
+template <class T, int VAR = 0>
 int rb_grid(osmodi_plan p, const RbArgs& a) {
-    static const int bps = blocks_per_sm(k_mg_fine_rb_fused<T, kRbCX, kRbRY, 0, false, false, PF>);
+    const int bps = rb_bps<T, VAR>();
     return (int)std::max<long long>(1, std::min<long long>(a.n_items, (long long)p->num_sms * bps));
 }
 
@@ -2040,7 +2041,7 @@ void launch_async(osmodi_plan p, const RbArgs& ra, const float* zi, float* zo, c
 template <class T, int NDIM, class Mark>
 T* fused_vcycle_async(osmodi_plan p, const Hier* h, const T* r, const MgBuffers<T>& w, CgState* st,
                       double* partials, cudaStream_t s, const FineArgs<T>& f, int nu, int G_rr, int G_prol, Mark mark) {
-    const RbArgs ra = rb_args(p);
+    const RbArgs ra = rb_args(p, rb_bps<float, 0>());
     LevelVecs<T> v1 = level_vecs<T>(h, w.lv, 1);
     T* cur = w.zA;
     T* oth = w.zB;
@@ -2072,10 +2073,10 @@ T* fused_vcycle_async(osmodi_plan p, const Hier* h, const T* r, const MgBuffers<
     return cur;  // == w.zB
 }
 
-template <class T, int NDIM, bool PF, class Mark>
+template <class T, int NDIM, int PF, class Mark>
 T* fused_vcycle(osmodi_plan p, const Hier* h, const T* r, const MgBuffers<T>& w, CgState* st, double* partials,
                 cudaStream_t s, const FineArgs<T>& f, int nu, int G_rr, int G_prol, Mark mark) {
-    const RbArgs ra = rb_args(p);
+    const RbArgs ra = rb_args(p, rb_bps<T, PF>());
     const int gr = rb_grid<T, PF>(p, ra);
     LevelVecs<T> v1 = level_vecs<T>(h, w.lv, 1);
     constexpr int NT = kRbCX * kRbRY;
@@ -2146,7 +2147,7 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
     // (fusing the first two sweeps into one pass was measured slower than the
     // two passes: forming every neighbour's first-sweep value costs more
     // instructions than the extra pass moves bytes)
-    const long long variant = debug_knob(OSMODI_DEBUG_MG_UNFUSED);  // 0 fused, 1 half-sweeps, 2 TMA-staged, 3 prefetching, 4 cp.async-staged
+    const long long variant = debug_knob(OSMODI_DEBUG_MG_UNFUSED);  // 0 fused, 1 half-sweeps, 2 TMA-staged, 3 prefetching, 4 cp.async-staged, 5 fused at 5 blocks per SM
     if (red_black(p) && variant == 1) {
         // the same V-cycle by in-place half-sweeps (one colour per pass), kept
         // for comparison with the fused sweeps; it ends in zA, copied to zB
@@ -2230,8 +2231,9 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
         // (variant 3: the sweeps that load z ahead, for comparison)
         if (variant == 4 && sizeof(T) == 4)
             return fused_vcycle_async<T, NDIM>(p, h, r, w, st, partials, s, f, nu, G_rr, G_prol, mark);
-        return variant == 3 ? fused_vcycle<T, NDIM, true>(p, h, r, w, st, partials, s, f, nu, G_rr, G_prol, mark)
-                            : fused_vcycle<T, NDIM, false>(p, h, r, w, st, partials, s, f, nu, G_rr, G_prol, mark);
+        if (variant == 3) return fused_vcycle<T, NDIM, 1>(p, h, r, w, st, partials, s, f, nu, G_rr, G_prol, mark);
+        if (variant == 5) return fused_vcycle<T, NDIM, 2>(p, h, r, w, st, partials, s, f, nu, G_rr, G_prol, mark);
+        return fused_vcycle<T, NDIM, 0>(p, h, r, w, st, partials, s, f, nu, G_rr, G_prol, mark);
     }
     T* cur = w.zA;
     T* oth = w.zB;

@@ -152,8 +152,6 @@ def test_fused_sweeps_equal_half_sweeps(osm, shape):
     ru, pu = out[1]
     for variant in (0, 2, 3, 4, 5):
         rf, pf = out[variant]
-        if variant == 5:  # the same kernel source as 0: the same bits
-            assert rf.inner_iters == out[0][0].inner_iters and np.array_equal(pf[valid], out[0][1][valid])
         # rounding (FMA contraction may differ between the kernels) can move a
         # stopping test across its threshold by at most one check chunk
         assert abs(rf.inner_iters - ru.inner_iters) <= 8, (variant, rf.inner_iters, ru.inner_iters)

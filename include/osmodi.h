@@ -586,8 +586,7 @@ OSMODI_API osmodi_status osmodi_probe_convert(const double* d_in_dev, float* f_o
  *   fine level's input planes staged by TMA (FP32 plans); 3 as 0 with the
  *   fine sweeps' HBM operands loaded one plane ahead; 4 as 0 with the fine
  *   level's z, r and code planes staged in shared memory by cp.async (FP32
- *   plans); 5 as 0 with the fine sweeps compiled for five resident blocks
- *   per SM instead of four (fewer registers, more warps).
+ *   plans).
  * OSMODI_DEBUG_NET_WMMA: which kernels run the seed network's
  *   convolutions, the same products in each case, for comparisons: 0
  *   (default) tcgen05, the forward 3x3x3 layers with their input tile staged

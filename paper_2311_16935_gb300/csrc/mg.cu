@@ -378,12 +378,11 @@ struct RbArgs {
     float omega;
 };
 
-template <class T, int CX, int RY, int FC, bool FROM_ZERO, bool DOT, int VAR = 0>
-__global__ void __launch_bounds__(CX * RY, sizeof(T) == 4 ? (VAR == 1 ? 3 : VAR == 2 ? 5 : 4) : 2) k_mg_fine_rb_fused(const T* __restrict__ zin, T* __restrict__ zout,
+template <class T, int CX, int RY, int FC, bool FROM_ZERO, bool DOT, bool PF = false>
+__global__ void __launch_bounds__(CX * RY, sizeof(T) == 4 ? (PF ? 3 : 4) : 2) k_mg_fine_rb_fused(const T* __restrict__ zin, T* __restrict__ zout,
                                                              const T* __restrict__ r,
                                                              const uint8_t* __restrict__ code8, RbArgs g,
                                                              CgState* st, double* partials) {
-    constexpr bool PF = VAR == 1;  // VAR 1: operands loaded a step ahead; 2: plain, 5 blocks per SM
     static_assert(CX == 16 && RY % 2 == 0 && RY / 2 == CX * RY / 32, "a warp holds rows w and w + RY / 2");
     constexpr int NT = CX * RY;
     if (st->status != kRunning) return;
@@ -1396,7 +1395,7 @@ __device__ __forceinline__ float cnt_f(uint32_t w, int shift) { return (float)((
 // VEC (FP32, even rows): a pair's two cells are one aligned 8-byte word, so
 // its z, r and count words move in one load each
 template <class T, int FC, bool FROM_ZERO, bool VEC = false>
-__global__ void __launch_bounds__(kCbX * kCbY, 4) k_mg_coarse_rb_fused(const T* __restrict__ zin, T* __restrict__ zout,
+__global__ void __launch_bounds__(kCbX * kCbY) k_mg_coarse_rb_fused(const T* __restrict__ zin, T* __restrict__ zout,
                                                                   const T* __restrict__ r, Level lv, T omega,
                                                                   CbArgs g, const CgState* st) {
     constexpr int NT = kCbX * kCbY;
@@ -1459,14 +1458,7 @@ __global__ void __launch_bounds__(kCbX * kCbY, 4) k_mg_coarse_rb_fused(const T* 
         struct Wv {
             T xp, xm, yp, ym, zp, zm, wd, r;
         };
-        // a count word's field as a weight: count x F
-        const float F0f = (float)F0, F1f = (float)F1, F2f = (float)F2;
-        auto wgt = [&](uint32_t w, int shift, float Fa) -> T { return (T)(cnt_f(w, shift) * Fa); };
-        // which cell of the pair has colour FC on plane q is uniform over a
-        // warp (one warp = one row) and known at compile time inside each
-        // instantiation: U1 = the pair's cell 1
-        auto first_t = [&](auto U1c, int q, Wv& wv) {
-            constexpr bool u1 = decltype(U1c)::value;
+        auto first = [&](int q, Wv& wv) {
             T o0 = T(0), o1 = T(0);
             wv = Wv{T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
             const bool qin = q >= 0 && q < g.nz;
@@ -1488,16 +1480,18 @@ __global__ void __launch_bounds__(kCbX * kCbY, 4) k_mg_coarse_rb_fused(const T* 
                 r1 = qin && in1 ? r[qo + c1] : T(0);
             }
             // weights of both cells
-            const T xp0 = wgt(w0, 0, F0f), xp1 = wgt(w1, 0, F0f);
-            const T xm0 = wgt(wx0, 0, F0f), xm1 = xp0;
-            const T yp0 = wgt(w0, 10, F1f), yp1 = wgt(w1, 10, F1f);
-            const T ym0 = wgt(wy0, 10, F1f), ym1 = wgt(wy1, 10, F1f);
-            const T zp0 = wgt(w0, 20, F2f), zp1 = wgt(w1, 20, F2f);
-            const T zm0 = wgt(wz0, 20, F2f), zm1 = wgt(wz1, 20, F2f);
+            const T xp0 = (T)(cnt_f(w0, 0) * (float)F0), xp1 = (T)(cnt_f(w1, 0) * (float)F0);
+            const T xm0 = (T)(cnt_f(wx0, 0) * (float)F0), xm1 = xp0;
+            const T yp0 = (T)(cnt_f(w0, 10) * (float)F1), yp1 = (T)(cnt_f(w1, 10) * (float)F1);
+            const T ym0 = (T)(cnt_f(wy0, 10) * (float)F1), ym1 = (T)(cnt_f(wy1, 10) * (float)F1);
+            const T zp0 = (T)(cnt_f(w0, 20) * (float)F2), zp1 = (T)(cnt_f(w1, 20) * (float)F2);
+            const T zm0 = (T)(cnt_f(wz0, 20) * (float)F2), zm1 = (T)(cnt_f(wz1, 20) * (float)F2);
             const T d0 = xp0 + xm0 + yp0 + ym0 + zp0 + zm0, d1 = xp1 + xm1 + yp1 + ym1 + zp1 + zm1;
             const T wd0 = d0 > T(0) ? omega * recip(d0) : T(0), wd1 = d1 > T(0) ? omega * recip(d1) : T(0);
             wz0 = w0;
             wz1 = w1;
+            // which cell of the pair has colour FC on this plane
+            const bool u1 = ((FC ^ (j + q)) & 1) != 0;
             if (qin) {
                 if (FROM_ZERO) {
                     o0 = u1 ? T(0) : wd0 * r0;
@@ -1543,32 +1537,6 @@ __global__ void __launch_bounds__(kCbX * kCbY, 4) k_mg_coarse_rb_fused(const T* 
             ring[q & 3][0][t] = in0 ? o0 : T(0);
             ring[q & 3][1][t] = in1 ? o1 : T(0);
         };
-        auto first = [&](int q, Wv& wv) {
-            if (((FC ^ (j + q)) & 1) != 0) first_t(std::true_type{}, q, wv);
-            else first_t(std::false_type{}, q, wv);
-        };
-        // the cell of the other colour on plane k (V1: it is cell 1), from the ring
-        auto second_t = [&](auto V1c, int k, const Wv& w) {
-            constexpr bool v1 = decltype(V1c)::value;
-            constexpr int cv = v1 ? 1 : 0;
-            const T zc = ring[k & 3][cv][t];
-            const T ex = v1 ? ring[k & 3][0][t + 1] : ring[k & 3][1][t];
-            const T wx = v1 ? ring[k & 3][0][t] : ring[k & 3][1][t - 1];
-            const T zn = ring[k & 3][cv][t + kCbX], zs = ring[k & 3][cv][t - kCbX];
-            const T zf = ring[(k + 1) & 3][cv][t], zb = ring[(k + 3) & 3][cv][t];
-            const T az = w.xp * (zc - ex) + w.xm * (zc - wx) + w.yp * (zc - zn) + w.ym * (zc - zs) +
-                         w.zp * (zc - zf) + w.zm * (zc - zb);
-            const T nv = zc + w.wd * (w.r - az);
-            const T other = ring[k & 3][1 - cv][t];
-            const int64_t qo = (int64_t)k * sz;
-            const T out0 = v1 ? other : nv, out1 = v1 ? nv : other;
-            if (VEC) {
-                if (in0) *reinterpret_cast<float2*>(zout + qo + c0) = make_float2((float)out0, (float)out1);
-            } else {
-                if (in0) zout[qo + c0] = out0;
-                if (in1) zout[qo + c1] = out1;
-            }
-        };
         Wv w_cur, w_nxt;
         first(k0 - 1, w_nxt);  // plane -1 (k0 = 0) writes zeros
         first(k0, w_cur);
@@ -1576,8 +1544,22 @@ __global__ void __launch_bounds__(kCbX * kCbY, 4) k_mg_coarse_rb_fused(const T* 
             first(k + 1, w_nxt);
             __syncthreads();
             if (interior) {
-                if (((FC ^ (j + k)) & 1) == 0) second_t(std::true_type{}, k, w_cur);
-                else second_t(std::false_type{}, k, w_cur);
+                // the cell of the other colour on plane k
+                const bool v1 = ((FC ^ (j + k)) & 1) == 0;  // the other cell is cell 1
+                const int cv = v1 ? 1 : 0;
+                const T zc = ring[k & 3][cv][t];
+                const T ex = v1 ? ring[k & 3][0][t + 1] : ring[k & 3][1][t];
+                const T wx = v1 ? ring[k & 3][0][t] : ring[k & 3][1][t - 1];
+                const T zn = ring[k & 3][cv][t + kCbX], zs = ring[k & 3][cv][t - kCbX];
+                const T zf = ring[(k + 1) & 3][cv][t], zb = ring[(k + 3) & 3][cv][t];
+                const Wv& w = w_cur;
+                const T az = w.xp * (zc - ex) + w.xm * (zc - wx) + w.yp * (zc - zn) + w.ym * (zc - zs) +
+                             w.zp * (zc - zf) + w.zm * (zc - zb);
+                const T nv = zc + w.wd * (w.r - az);
+                const T other = ring[k & 3][1 - cv][t];
+                const int64_t qo = (int64_t)k * sz;
+                if (in0) zout[qo + c0] = v1 ? other : nv;
+                if (in1) zout[qo + c1] = v1 ? nv : other;
             }
             w_cur = w_nxt;
         }
@@ -1765,28 +1747,10 @@ int wave_grid(osmodi_plan p, K kernel, int bps, int64_t work256) {
 // one-chunk / one-row halo ring, interior 14 x 14 chunks
 constexpr int kRbCX = 16, kRbRY = 16;
 
-// The slab depth (planes per work item) of a z-marching sweep that
-// minimises the plane steps the busiest resident block runs: items = tiles x
-// ceil(nz / slab) spread over `slots` resident blocks, each item slab +
-// `extra` steps (the planes of the first colour a slab recomputes); ties go
-// to the deeper slab (less recomputation)
-int best_slab(long long tiles, int nz, long long slots, int extra, int min_slab) {
-    long long best_steps = -1;
-    int best = nz;
-    for (int sl = std::max(1, std::min(min_slab, nz)); sl <= nz; ++sl) {
-        const long long items = tiles * ((nz + sl - 1) / sl);
-        const long long steps = ((items + slots - 1) / slots) * (sl + extra);
-        if (best_steps < 0 || steps <= best_steps) {
-            best_steps = steps;
-            best = sl;
-        }
-    }
-    return best;
-}
-
-// Work items of the fused sweep: every tile of a plane times slabs of planes
-// (each slab recomputes one extra plane of the first colour)
-RbArgs rb_args(osmodi_plan p, int bps) {
+// Work items of the fused sweep: every tile of a plane times slabs of planes,
+// the slab chosen so that each resident block gets about eight items (each
+// slab recomputes one extra plane of the first colour)
+RbArgs rb_args(osmodi_plan p) {
     RbArgs a;
     a.px = p->px;
     a.plane = p->px * p->ny;
@@ -1797,8 +1761,11 @@ RbArgs rb_args(osmodi_plan p, int bps) {
     a.tiles_y = (a.ny + kRbRY - 3) / (kRbRY - 2);
     for (int q = 0; q < 3; ++q) a.F[q] = (float)p->k.F[q];
     a.omega = kOmegaRB;
+    static const int bps = blocks_per_sm(k_mg_fine_rb_fused<float, kRbCX, kRbRY, 0, false, false>);
     const long long tiles = (long long)a.tiles_x * a.tiles_y;
-    a.slab = best_slab(tiles, a.nz, (long long)p->num_sms * bps, 1, 8);
+    const long long want = 8LL * p->num_sms * bps;
+    const long long slabs = std::max<long long>(1, std::min<long long>(a.nz, (want + tiles - 1) / tiles));
+    a.slab = std::max(8, (int)((a.nz + slabs - 1) / slabs));
     a.n_items = tiles * ((a.nz + a.slab - 1) / a.slab);
     return a;
 }
@@ -1852,15 +1819,9 @@ RbMaps* rb_maps(osmodi_plan p, const float* zA, const float* zB, const float* r)
     return m->ok ? m : nullptr;
 }
 
-template <class T, int VAR = 0>
-int rb_bps() {
-    static const int bps = blocks_per_sm(k_mg_fine_rb_fused<T, kRbCX, kRbRY, 0, false, false, VAR>);
-    return bps;
-}
-
-template <class T, int VAR = 0>
+template <class T, bool PF = false>
 int rb_grid(osmodi_plan p, const RbArgs& a) {
-    const int bps = rb_bps<T, VAR>();
+    static const int bps = blocks_per_sm(k_mg_fine_rb_fused<T, kRbCX, kRbRY, 0, false, false, PF>);
     return (int)std::max<long long>(1, std::min<long long>(a.n_items, (long long)p->num_sms * bps));
 }
 
@@ -1941,9 +1902,11 @@ T* vcycle_body(osmodi_plan p, const Hier* h, char* base, int l, CgState* st, cud
         cb.tiles_y = (cb.ny + kCbY - 3) / (kCbY - 2);
         static const int bps = blocks_per_sm(k_mg_coarse_rb_fused<T, 0, false>);
         const long long tiles = (long long)cb.tiles_x * cb.tiles_y;
-        // every slab recomputes two planes of the first colour; on the small
-        // levels thin slabs shorten each block's chain of dependent plane steps
-        cb.slab = best_slab(tiles, cb.nz, (long long)p->num_sms * bps, 2, 1);
+        // about four items per resident block (every slab recomputes two planes
+        // of the first colour; fewer, deeper slabs leave a longer tail)
+        const long long want = 4LL * p->num_sms * bps;
+        const long long slabs = std::max<long long>(1, std::min<long long>(cb.nz, (want + tiles - 1) / tiles));
+        cb.slab = std::max(8, (int)((cb.nz + slabs - 1) / slabs));
         cb.n_items = tiles * ((cb.nz + cb.slab - 1) / cb.slab);
         const int gf = (int)std::max<long long>(1, std::min<long long>(cb.n_items, (long long)p->num_sms * bps));
         const T om = (T)kOmegaRB;
@@ -2041,7 +2004,7 @@ void launch_async(osmodi_plan p, const RbArgs& ra, const float* zi, float* zo, c
 template <class T, int NDIM, class Mark>
 T* fused_vcycle_async(osmodi_plan p, const Hier* h, const T* r, const MgBuffers<T>& w, CgState* st,
                       double* partials, cudaStream_t s, const FineArgs<T>& f, int nu, int G_rr, int G_prol, Mark mark) {
-    const RbArgs ra = rb_args(p, rb_bps<float, 0>());
+    const RbArgs ra = rb_args(p);
     LevelVecs<T> v1 = level_vecs<T>(h, w.lv, 1);
     T* cur = w.zA;
     T* oth = w.zB;
@@ -2073,10 +2036,10 @@ T* fused_vcycle_async(osmodi_plan p, const Hier* h, const T* r, const MgBuffers<
     return cur;  // == w.zB
 }
 
-template <class T, int NDIM, int PF, class Mark>
+template <class T, int NDIM, bool PF, class Mark>
 T* fused_vcycle(osmodi_plan p, const Hier* h, const T* r, const MgBuffers<T>& w, CgState* st, double* partials,
                 cudaStream_t s, const FineArgs<T>& f, int nu, int G_rr, int G_prol, Mark mark) {
-    const RbArgs ra = rb_args(p, rb_bps<T, PF>());
+    const RbArgs ra = rb_args(p);
     const int gr = rb_grid<T, PF>(p, ra);
     LevelVecs<T> v1 = level_vecs<T>(h, w.lv, 1);
     constexpr int NT = kRbCX * kRbRY;
@@ -2147,7 +2110,7 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
     // (fusing the first two sweeps into one pass was measured slower than the
     // two passes: forming every neighbour's first-sweep value costs more
     // instructions than the extra pass moves bytes)
-    const long long variant = debug_knob(OSMODI_DEBUG_MG_UNFUSED);  // 0 fused, 1 half-sweeps, 2 TMA-staged, 3 prefetching, 4 cp.async-staged, 5 fused at 5 blocks per SM
+    const long long variant = debug_knob(OSMODI_DEBUG_MG_UNFUSED);  // 0 fused, 1 half-sweeps, 2 TMA-staged, 3 prefetching, 4 cp.async-staged
     if (red_black(p) && variant == 1) {
         // the same V-cycle by in-place half-sweeps (one colour per pass), kept
         // for comparison with the fused sweeps; it ends in zA, copied to zB
@@ -2231,9 +2194,8 @@ T* apply_nd(osmodi_plan p, const T* r, const MgBuffers<T>& w, CgState* st, doubl
         // (variant 3: the sweeps that load z ahead, for comparison)
         if (variant == 4 && sizeof(T) == 4)
             return fused_vcycle_async<T, NDIM>(p, h, r, w, st, partials, s, f, nu, G_rr, G_prol, mark);
-        if (variant == 3) return fused_vcycle<T, NDIM, 1>(p, h, r, w, st, partials, s, f, nu, G_rr, G_prol, mark);
-        if (variant == 5) return fused_vcycle<T, NDIM, 2>(p, h, r, w, st, partials, s, f, nu, G_rr, G_prol, mark);
-        return fused_vcycle<T, NDIM, 0>(p, h, r, w, st, partials, s, f, nu, G_rr, G_prol, mark);
+        return variant == 3 ? fused_vcycle<T, NDIM, true>(p, h, r, w, st, partials, s, f, nu, G_rr, G_prol, mark)
+                            : fused_vcycle<T, NDIM, false>(p, h, r, w, st, partials, s, f, nu, G_rr, G_prol, mark);
     }
     T* cur = w.zA;
     T* oth = w.zB;

@@ -51,3 +51,27 @@ def test_idle_launches_left_out(tmp_path):
     k = pt.summarise(str(f), 100, "cmd")["kernels"]["k_cg_b<float>"]
     assert k["launches"] == 5 and k["idle_launches"] == 2
     assert k["dram_bytes_per_launch"] == 1000e6
+
+
+def test_source_hash_covers_every_included_header():
+    """The traffic file is trusted only while the kernel sources hash the
+    same: every project header the hashed sources include (transitively)
+    must be hashed too, or an edit to it would leave stale counters live."""
+    import os
+    import re
+
+    csrc = os.path.join(os.path.dirname(pt.__file__), "csrc")
+    seen, todo = set(), [n for n in pt.KERNEL_SOURCES if n.endswith(".cu")]
+    while todo:
+        name = todo.pop()
+        if name in seen:
+            continue
+        seen.add(name)
+        with open(os.path.join(csrc, name)) as fh:
+            for inc in re.findall(r'^\s*#\s*include\s+"([^"]+)"', fh.read(), re.M):
+                # the kernel headers beside the sources (the public C header,
+                # declarations and documentation only, lives elsewhere)
+                if "/" not in inc and os.path.exists(os.path.join(csrc, inc)):
+                    todo.append(inc)
+    missing = sorted(seen - set(pt.KERNEL_SOURCES))
+    assert not missing, missing

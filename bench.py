@@ -7,8 +7,8 @@ eps_R <= 1e-8: FP32 multigrid-preconditioned conjugate-gradient sweeps on
 the fixed-point system inside an FP64 iterative-refinement loop (FP64
 residual, norms and constant removal).  value = (valid cells x stencil
 applications, every multigrid level counted with its own cells) / device
-time, summed over the timed steps (the production plan: CG iterations as
-captured CUDA graphs).  Per-kernel times for the roofline come from the same
+time, summed over the timed steps (the production plan: each CG segment
+one captured CUDA graph that loops on the device until it converges).  Per-kernel times for the roofline come from the same
 K solves repeated in profile mode right after (every launch bracketed by
 CUDA events).  The same solve without the preconditioner and the same
 scheme in FP64 are timed beside it.  Inputs

@@ -204,6 +204,34 @@ def _cpu_baseline(grad_full_host=None, gpu_plain_cg_iters=None, size_crop=100, t
     return out
 
 
+def _cpu_baseline_batched(count, sample=8, tol=1e-10):
+    """The oracle (FP64 CG, as written) on the host cores for the batched
+    PIV workload: `sample` evenly spaced snapshots of the `count` solved to
+    eps_R <= tol one after another, extrapolated to all `count` by the
+    sampled time per snapshot."""
+    import numpy as np
+
+    import oracle
+    from paper_2311_16935_gb300 import inputs
+
+    idx = sorted({int(round(k * (count - 1) / max(sample - 1, 1))) for k in range(sample)})
+    secs, its, cells = [], [], []
+    for i in idx:
+        pr = inputs.piv_snapshot_2d(i, device="cpu")
+        grid = oracle.Grid(pr.mask.numpy().astype(bool), pr.spacing)
+        f = pr.grad.double().numpy()
+        t0 = time.perf_counter()
+        _, it, _ = oracle.solve_cg(grid, f, tol=tol, maxit=1_000_000)
+        secs.append(time.perf_counter() - t0)
+        its.append(int(it))
+        cells.append(int(grid.n))
+    per = sum(secs) / len(secs)
+    return {"kind": "oracle", "cores": oracle.num_threads(), "unit": "solves/s", "value": 1.0 / per,
+            "sample": f"oracle FP64 CG to eps_R<={tol} on snapshots {idx} of the {count} (valid cells "
+                      f"{min(cells)}-{max(cells)}, {min(its)}-{max(its)} iterations, {sum(secs):.1f} s)",
+            "extrapolated_seconds_for_all": per * count, "extrapolation": "mean time per sampled snapshot x count"}
+
+
 def torch_float32():
     import torch
 
@@ -677,6 +705,11 @@ def main():
         try:
             cg_its = line.get("cg_unpreconditioned", {}).get("cg")
             line["cpu_baseline"] = _cpu_baseline(grad_host if args.cpu_full else None, cg_its)
+            if "batched_piv" in line:
+                try:
+                    line["batched_piv"]["cpu_baseline"] = _cpu_baseline_batched(args.batch_count)
+                except Exception as e:  # reported, never fatal to the bench line
+                    line["batched_piv"]["cpu_baseline"] = {"error": repr(e)[:200]}
             if "crop_gpu" in line:
                 cb = line["cpu_baseline"]
                 line["crop_gpu"]["cpu_oracle_time_to_tolerance_s"] = cb["crop_time_to_tolerance_s"]

@@ -60,3 +60,10 @@ def test_traffic_figure_needs_the_same_sources(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "TRAFFIC", str(tmp_path / "missing.json"))
     assert bench._profiled_traffic("k_a<float, 1>", 10) is None
 
+
+
+def test_batched_cpu_baseline_on_a_small_sample():
+    r = bench._cpu_baseline_batched(512, sample=2)
+    assert r["kind"] == "oracle" and r["unit"] == "solves/s" and r["value"] > 0 and r["cores"] >= 1
+    assert "[0, 511]" in r["sample"]
+    assert r["extrapolated_seconds_for_all"] == pytest.approx(512 / r["value"])

@@ -96,8 +96,11 @@ typedef struct {
                             iterations drift little); the search direction carries over
                             ("reliable updates").  OUTER+CG: relative tolerance of
                             each inner solve (default 1e-6) */
-    int check_every;     /* iterations between host convergence checks (0 = default:
-                            64, or 8 with precond = 1) */
+    int check_every;     /* iterations between host convergence checks where the
+                            host drives the iterations: profile mode,
+                            osmodi_solve_noalloc and the fixed-graph comparison
+                            mode (0 = default: 64, or 8 with precond = 1); a
+                            captured solve otherwise loops on the device */
     int sweeps_per_pass; /* OUTER+JACOBI: Jacobi sweeps fused per pass, 1..4 (default 2) */
     int max_refine;      /* FP32_REFINE: max refinement steps (default 32) */
     int record_history;  /* OUTER: keep eps_R of every outer iteration (osmodi_history) */

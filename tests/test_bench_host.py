@@ -67,3 +67,14 @@ def test_batched_cpu_baseline_on_a_small_sample():
     assert r["kind"] == "oracle" and r["unit"] == "solves/s" and r["value"] > 0 and r["cores"] >= 1
     assert "[0, 511]" in r["sample"]
     assert r["extrapolated_seconds_for_all"] == pytest.approx(512 / r["value"])
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """Under torchrun every rank runs bench.py; the reference arm's rank 0
+    alone times the oracle and prints the line, the others exit 0 at once."""
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                          "--steps", "1", "--warmup", "1", "--ref-crop", "12", "--ref-iters", "5"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert out.stdout.strip() == ""
